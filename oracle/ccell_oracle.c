@@ -1,0 +1,460 @@
+/*
+ * ccell_oracle.c -- plain, slow, FP64 CPU oracle of the explicit-implicit
+ * heat-conduction time step of Ayriyan et al., "Algorithm and Simulation of
+ * Heat Conduction Process for Design of a Thin Multilayer Technical Device"
+ * (arXiv:1408.5853).
+ *
+ * TEST INFRASTRUCTURE ONLY.  Only tests/, __graft_entry__.smoke() and the
+ * CPU-baseline leg of bench.py may load this library.  The CUDA product path
+ * never links, loads or calls it, and shares no code with it.
+ *
+ * What it computes (Section 3 of the paper):
+ *   rho c (That - T)/tau = Lambda_i[That] + Lambda_j[T] + X          Eq. (scheme_eq)
+ * radial direction r (index i) implicit, axial direction z (index j)
+ * explicit; every line j = 1..M-1 is a tridiagonal system in i solved by the
+ * Thomas algorithm, Eqs. (front_sweep), (ABC), (back_sweep), with the axis and
+ * outer closures Eqs. (first_oder_bc), (alphabeta_ini), (T_ini_for_back_sweep)
+ * and the layer-interface rows Eqs. (cc_first_1)-(cc_first_3).
+ *
+ * Readings of points the paper leaves open (each also listed in the design doc):
+ *   A1 face conductivity lambda_{i+1/2,j} = lambda_m((T_ij + T_i+1,j)/2)
+ *      (face_rule 0); face_rule 1 = mean of the two nodal values.
+ *   A2 boundary conditions per face are flags: default Neumann at r=r_max and
+ *      z=0, Dirichlet T_D at z=z_max (Eq. (boundcond)), symmetry at r=0.
+ *   A3 interface rows: paper Eq. (cc_first_3) with lambda* at the old
+ *      interface temperature (interface_rule 0); interface_rule 1 uses the
+ *      r-weighted face fluxes of the neighbouring rows (conservative).
+ *      Interface nodes carry no heat capacity, no axial term, no source.
+ *   A4 X and the waveform s(t) are evaluated at (T^n, t_n), t_n = t0 + n*tau;
+ *      the rectangular pulse uses the half-open windows of Eq. (period).
+ *   A13 no FMA contraction: build with -ffp-contract=off.
+ *
+ * Array layout: T[j*nr + i], i = 0..nr-1 radial (contiguous), j = 0..nz-1
+ * axial; a line j is one contiguous row of nr values.
+ */
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+#define OR_MAX_LAYERS 8
+
+/* node classes in r */
+#define OR_AXIS 0      /* i = 0, closure That_0 = That_1               */
+#define OR_REGULAR 1   /* interior node inside one layer               */
+#define OR_IFACE 2     /* node on the border between two layers         */
+#define OR_OUTER 3     /* i = N, closure Neumann or Dirichlet           */
+
+typedef struct {
+  /* geometry */
+  int n_layers;
+  double thickness[OR_MAX_LAYERS]; /* innermost (r = 0) first, metres    */
+  int nr, nz;                      /* nodes, including boundary nodes    */
+  double length;                   /* z extent, metres                   */
+  int bc_rmax, bc_z0, bc_zmax;     /* 0 Neumann, 1 Dirichlet             */
+  double t_dirichlet;              /* K                                  */
+  int placement;                   /* 0 vertex nodes, 1 half-cell ghosts */
+  int face_rule, interface_rule;
+  /* materials, per layer */
+  double rho[OR_MAX_LAYERS];
+  int lam_model[OR_MAX_LAYERS];    /* 0 const, 1 power law, 2 polynomial */
+  double lam0[OR_MAX_LAYERS], lam_b[OR_MAX_LAYERS];
+  int cap_model[OR_MAX_LAYERS];    /* 0 const, 1 Debye-saturating, 2 poly */
+  double c0[OR_MAX_LAYERS], theta[OR_MAX_LAYERS];
+  double t_ref[OR_MAX_LAYERS];
+  double lam_scale[OR_MAX_LAYERS], cap_scale[OR_MAX_LAYERS];
+  double lam_poly[OR_MAX_LAYERS][5]; /* b_0..b_4, Eq. (poly_cond)       */
+  double cap_poly[OR_MAX_LAYERS][4]; /* a_0..a_3, Eq. (poly_cap)        */
+  /* heating source, Eqs. (source), (current), (period) */
+  int src_layer;                   /* -1: no source                      */
+  double q0;                       /* W/m^3 amplitude                    */
+  double t_period, t_on, t_start;  /* s                                  */
+  int waveform;                    /* 0 rectangle nu(t), 1 tanh edges    */
+  double edge_w;                   /* s, tanh edge width                 */
+  int g_model;                     /* 0: g = 1, 1: g = g_ref/sqrt(T)     */
+  double g_ref;
+} or_problem;
+
+/* ------------------------------------------------------------------ */
+/* grid: Eq. (uniform_grid), uniform inside each layer                 */
+/* ------------------------------------------------------------------ */
+
+/* Cells per layer: proportional to thickness, largest remainder, at least
+ * 2 cells per layer, ties to the lower layer index. */
+static int cells_per_layer(const or_problem* p, int* n) {
+  int L = p->n_layers, N = p->nr - 1;
+  double total = 0.0, ideal[OR_MAX_LAYERS], rem[OR_MAX_LAYERS];
+  for (int m = 0; m < L; m++) total += p->thickness[m];
+  int sum = 0;
+  for (int m = 0; m < L; m++) {
+    ideal[m] = (double)N * p->thickness[m] / total;
+    n[m] = (int)floor(ideal[m]);
+    rem[m] = ideal[m] - (double)n[m];
+    if (n[m] < 2) n[m] = 2;
+    sum += n[m];
+  }
+  int R = N - sum;
+  int used[OR_MAX_LAYERS] = {0};
+  while (R > 0) {
+    int best = -1;
+    for (int m = 0; m < L; m++)
+      if (!used[m] && (best < 0 || rem[m] > rem[best])) best = m;
+    if (best < 0) { memset(used, 0, sizeof used); continue; }
+    used[best] = 1; n[best]++; R--;
+  }
+  while (R < 0) {
+    int best = -1;
+    for (int m = 0; m < L; m++)
+      if (n[m] > 2 && (best < 0 || n[m] > n[best])) best = m;
+    if (best < 0) return -1;
+    n[best]--; R++;
+  }
+  return 0;
+}
+
+/* r[nr], z[nz], rclass[nr], seg[nr] (layer of segment [r_i, r_{i+1}];
+ * seg[N] = last layer).  Returns 0 or -1 on an invalid problem. */
+int or_grid(const or_problem* p, double* r, double* z, int* rclass, int* seg) {
+  int N = p->nr - 1, M = p->nz - 1;
+  if (p->n_layers < 1 || p->n_layers > OR_MAX_LAYERS || N < 2 || M < 2) return -1;
+  if (p->placement == 0) {
+    int n[OR_MAX_LAYERS];
+    if (cells_per_layer(p, n)) return -1;
+    int i = 0;
+    double start = 0.0;
+    for (int m = 0; m < p->n_layers; m++) {
+      double h = p->thickness[m] / (double)n[m];
+      for (int k = 0; k < n[m]; k++, i++) {
+        r[i] = start + (double)k * h;
+        seg[i] = m;
+        rclass[i] = (k == 0 && m > 0) ? OR_IFACE : OR_REGULAR;
+      }
+      start += p->thickness[m];
+    }
+    r[N] = start;
+    seg[N] = p->n_layers - 1;
+    rclass[0] = OR_AXIS;
+    rclass[N] = OR_OUTER;
+  } else {
+    /* half-cell ghosts: Neumann faces lie on the physical boundary; a
+     * Dirichlet boundary carries a node.  Single layer only. */
+    if (p->n_layers != 1) return -1;
+    double R = p->thickness[0];
+    double off_hi = p->bc_rmax ? 0.0 : 0.5;
+    double h = R / ((double)N - 0.5 - off_hi);
+    for (int i = 0; i <= N; i++) {
+      r[i] = ((double)i - 0.5) * h;
+      seg[i] = 0;
+      rclass[i] = OR_REGULAR;
+    }
+    rclass[0] = OR_AXIS;
+    rclass[N] = OR_OUTER;
+  }
+  if (p->placement == 0) {
+    double eta = p->length / (double)M;
+    for (int j = 0; j <= M; j++) z[j] = (double)j * eta;
+  } else {
+    double lo = p->bc_z0 ? 0.0 : 0.5, hi = p->bc_zmax ? 0.0 : 0.5;
+    double eta = p->length / ((double)M - lo - hi);
+    for (int j = 0; j <= M; j++) z[j] = ((double)j - lo) * eta;
+  }
+  return 0;
+}
+
+/* ------------------------------------------------------------------ */
+/* material functions                                                  */
+/* ------------------------------------------------------------------ */
+
+/* lambda_m(T): power law lambda0 (T/T_ref)^b, or Eq. (poly_cond) */
+static double lam_m(const or_problem* p, int m, double T) {
+  double v;
+  switch (p->lam_model[m]) {
+    case 0: v = p->lam0[m]; break;
+    case 1: v = p->lam0[m] * pow(T / p->t_ref[m], p->lam_b[m]); break;
+    default: {
+      const double* b = p->lam_poly[m];
+      v = b[0] + b[1] * T + b[2] * T * T + b[3] * T * T * T + b[4] * T * T * T * T;
+    }
+  }
+  return p->lam_scale[m] * v;
+}
+
+/* c_m(T): c0 (T/T_ref)^3 / (1 + (T/theta)^3), or Eq. (poly_cap) */
+static double cap_m(const or_problem* p, int m, double T) {
+  double v;
+  switch (p->cap_model[m]) {
+    case 0: v = p->c0[m]; break;
+    case 1: {
+      double x = T / p->t_ref[m], y = T / p->theta[m];
+      v = p->c0[m] * (x * x * x) / (1.0 + y * y * y);
+    } break;
+    default: {
+      const double* a = p->cap_poly[m];
+      v = a[0] + a[1] * T + a[2] * T * T + a[3] * T * T * T;
+    }
+  }
+  return p->cap_scale[m] * v;
+}
+
+/* face conductivity between nodes with temperatures Ta, Tb (reading A1) */
+static double lam_face(const or_problem* p, int m, double Ta, double Tb) {
+  if (p->face_rule == 0) return lam_m(p, m, 0.5 * (Ta + Tb));
+  return 0.5 * (lam_m(p, m, Ta) + lam_m(p, m, Tb));
+}
+
+/* waveform s(t) = nu(t) p(t) of Eqs. (current), (period); p == 1.
+ * waveform 1: tanh-smoothed edges of width edge_w around the nearest pulse. */
+double or_waveform(const or_problem* p, double t) {
+  double u = t - p->t_start;
+  if (p->waveform == 0) {
+    if (u < 0.0) return 0.0;
+    double k = floor(u / p->t_period);
+    double phi = u - k * p->t_period;
+    return (phi < p->t_on) ? 1.0 : 0.0;
+  }
+  double k = floor((u - 0.5 * p->t_on) / p->t_period + 0.5);
+  if (k < 0.0) k = 0.0;
+  double phi = u - k * p->t_period;
+  return 0.5 * (tanh(phi / p->edge_w) - tanh((phi - p->t_on) / p->edge_w));
+}
+
+/* X_m(T, t) of Eq. (source): q0 s(t) g(T) in the heater layer only */
+static double source(const or_problem* p, int m, double T, double s) {
+  if (m != p->src_layer || s == 0.0) return 0.0;
+  double g = (p->g_model == 1) ? p->g_ref / sqrt(T) : 1.0;
+  return p->q0 * s * g;
+}
+
+/* ------------------------------------------------------------------ */
+/* stability bound, Eq. (stability_condition)                          */
+/* ------------------------------------------------------------------ */
+double or_tau_stab(const or_problem* p, double t_lo, double t_hi, int n_samples) {
+  int N = p->nr - 1, M = p->nz - 1;
+  double* r = (double*)malloc(sizeof(double) * (N + 1));
+  double* z = (double*)malloc(sizeof(double) * (M + 1));
+  int* cls = (int*)malloc(sizeof(int) * (N + 1));
+  int* seg = (int*)malloc(sizeof(int) * (N + 1));
+  double out = -1.0;
+  if (or_grid(p, r, z, cls, seg) == 0) {
+    double eta2 = 1e300;
+    for (int j = 1; j <= M; j++) {
+      double e = z[j] - z[j - 1];
+      if (e * e < eta2) eta2 = e * e;
+    }
+    double ratio = 1e300;
+    for (int m = 0; m < p->n_layers; m++)
+      for (int s = 0; s < n_samples; s++) {
+        double T = t_lo + (t_hi - t_lo) * (double)s / (double)(n_samples > 1 ? n_samples - 1 : 1);
+        double q = p->rho[m] * cap_m(p, m, T) / lam_m(p, m, T);
+        if (q < ratio) ratio = q;
+      }
+    out = 0.5 * eta2 * ratio;
+  }
+  free(r); free(z); free(cls); free(seg);
+  return out;
+}
+
+/* Neumaier compensated addition */
+static void kadd(double* s, double* c, double x) {
+  double t = *s + x;
+  if (fabs(*s) >= fabs(x)) *c += (*s - t) + x;
+  else *c += (x - t) + *s;
+  *s = t;
+}
+
+/* ------------------------------------------------------------------ */
+/* n time steps                                                        */
+/* ------------------------------------------------------------------ */
+/*
+ * T       [nz*nr] in/out temperature field (K).
+ * trace   [n_steps*2] or NULL: after step n, (That(r_max, z_0),
+ *         trapezoid-weighted mean over z of That(r_max, z)).
+ * energy  [5] or NULL, accumulated (added to): stored heat dE, injected
+ *         source Q, flux through Dirichlet edges, through interface edges,
+ *         through Neumann/ghost edges.  dE = Q + PhiD + PhiI + PhiN holds for
+ *         the discrete scheme up to rounding.
+ * Returns 0, or -1 on an invalid problem.
+ */
+int or_step_n(const or_problem* p, double* T, long n_steps, double t0, double tau,
+              double* trace, double* energy) {
+  const int N = p->nr - 1, M = p->nz - 1, nr = p->nr;
+  double* r = (double*)malloc(sizeof(double) * (N + 1));
+  double* z = (double*)malloc(sizeof(double) * (M + 1));
+  int* cls = (int*)malloc(sizeof(int) * (N + 1));
+  int* seg = (int*)malloc(sizeof(int) * (N + 1));
+  double* Th = (double*)malloc(sizeof(double) * (size_t)nr * (M + 1));
+  double* part = (double*)malloc(sizeof(double) * 5 * (size_t)(M + 1)); /* per line */
+  if (!r || !z || !cls || !seg || !Th || !part || or_grid(p, r, z, cls, seg)) {
+    free(r); free(z); free(cls); free(seg); free(Th); free(part);
+    return -1;
+  }
+  const double two_pi = 2.0 * 3.14159265358979323846;
+  double esum[5] = {0, 0, 0, 0, 0}, ecmp[5] = {0, 0, 0, 0, 0};
+
+  for (long n = 0; n < n_steps; n++) {
+    const double tn = t0 + (double)n * tau;
+    const double s = or_waveform(p, tn);
+
+#pragma omp parallel
+    {
+      double* alpha = (double*)malloc(sizeof(double) * (N + 1));
+      double* beta = (double*)malloc(sizeof(double) * (N + 1));
+#pragma omp for schedule(static)
+      for (int j = 1; j <= M - 1; j++) {
+        const double* Tj = T + (size_t)j * nr;
+        const double* Ts = T + (size_t)(j - 1) * nr;  /* line j-1 */
+        const double* Tn = T + (size_t)(j + 1) * nr;  /* line j+1 */
+        double* Thj = Th + (size_t)j * nr;
+        const double eta_s = z[j] - z[j - 1], eta_n = z[j + 1] - z[j];
+        const double etabar = 0.5 * (eta_n + eta_s);
+
+        /* forward sweep, Eqs. (front_sweep), (ABC), (cc_first_3) */
+        alpha[0] = 1.0;                     /* Eq. (alphabeta_ini) */
+        beta[0] = 0.0;
+        for (int i = 1; i <= N - 1; i++) {
+          const double h_w = r[i] - r[i - 1], h_e = r[i + 1] - r[i];
+          if (cls[i] == OR_IFACE) {
+            const int mi = seg[i - 1], mo = seg[i];
+            double lm, lp;                  /* lambda*_m, lambda*_m+1 */
+            if (p->interface_rule == 0) {
+              /* Eq. (cc_first_1): lambda*_m (T_i* - T_i*-1)/h_i* =
+               * lambda*_m+1 (T_i*+1 - T_i*)/h_i*+1, lambda* at T_i*,j */
+              lm = lam_m(p, mi, Tj[i]);
+              lp = lam_m(p, mo, Tj[i]);
+            } else {
+              /* same row with the r-weighted face conductivities of the
+               * neighbouring regular rows: flux continuity that conserves */
+              lm = 0.5 * (r[i] + r[i - 1]) * lam_face(p, mi, Tj[i - 1], Tj[i]);
+              lp = 0.5 * (r[i] + r[i + 1]) * lam_face(p, mo, Tj[i], Tj[i + 1]);
+            }
+            /* Eq. (cc_first_3) */
+            const double den = lp * h_w + lm * h_e * (1.0 - alpha[i - 1]);
+            alpha[i] = lp * h_w / den;
+            beta[i] = lm * h_e * beta[i - 1] / den;
+            continue;
+          }
+          const int m = seg[i];
+          const double T0 = Tj[i];
+          const double hbar = 0.5 * (h_e + h_w);
+          const double r_w = 0.5 * (r[i] + r[i - 1]), r_e = 0.5 * (r[i] + r[i + 1]);
+          const double lw = lam_face(p, m, Tj[i - 1], T0);
+          const double le = lam_face(p, m, T0, Tj[i + 1]);
+          const double ls = lam_face(p, m, Ts[i], T0);
+          const double ln = lam_face(p, m, T0, Tn[i]);
+          const double rc = p->rho[m] * cap_m(p, m, T0);
+          /* Eq. (Lambda_j), explicit in T */
+          const double Lj = (ln * (Tn[i] - T0) / eta_n - ls * (T0 - Ts[i]) / eta_s) / etabar;
+          const double X = source(p, m, T0, s);
+          /* Eq. (ABC) */
+          const double A = -r_w * lw / (r[i] * hbar * h_w);
+          const double C = -r_e * le / (r[i] * hbar * h_e);
+          const double B = (r_w * lw / h_w + r_e * le / h_e) / (r[i] * hbar) + rc / tau;
+          const double F = rc / tau * T0 + Lj + X;
+          const double den = B + A * alpha[i - 1];
+          alpha[i] = -C / den;
+          beta[i] = (F - A * beta[i - 1]) / den;
+        }
+        /* Eq. (T_ini_for_back_sweep) or the Dirichlet value */
+        Thj[N] = (p->bc_rmax == 0) ? beta[N - 1] / (1.0 - alpha[N - 1]) : p->t_dirichlet;
+        for (int i = N - 1; i >= 0; i--) Thj[i] = alpha[i] * Thj[i + 1] + beta[i]; /* Eq. (back_sweep) */
+      }
+      free(alpha);
+      free(beta);
+    }
+
+    /* axial boundary rows */
+    for (int i = 0; i <= N; i++) {
+      Th[i] = p->bc_z0 ? p->t_dirichlet : Th[(size_t)nr + i];
+      Th[(size_t)M * nr + i] = p->bc_zmax ? p->t_dirichlet : Th[(size_t)(M - 1) * nr + i];
+    }
+
+    /* energy terms of this step, per line then summed in line order */
+    if (energy) {
+#pragma omp parallel for schedule(static)
+      for (int j = 1; j <= M - 1; j++) {
+        const double* Tj = T + (size_t)j * nr;
+        const double* Ts = T + (size_t)(j - 1) * nr;
+        const double* Tn = T + (size_t)(j + 1) * nr;
+        const double* Hj = Th + (size_t)j * nr;
+        const double eta_s = z[j] - z[j - 1], eta_n = z[j + 1] - z[j];
+        const double etabar = 0.5 * (eta_n + eta_s);
+        double e[5] = {0, 0, 0, 0, 0}, c[5] = {0, 0, 0, 0, 0};
+        for (int i = 1; i <= N - 1; i++) {
+          if (cls[i] != OR_REGULAR) continue;
+          const int m = seg[i];
+          const double h_w = r[i] - r[i - 1], h_e = r[i + 1] - r[i];
+          const double hbar = 0.5 * (h_e + h_w);
+          const double r_w = 0.5 * (r[i] + r[i - 1]), r_e = 0.5 * (r[i] + r[i + 1]);
+          const double V = two_pi * r[i] * hbar * etabar;
+          kadd(&e[0], &c[0], V * p->rho[m] * cap_m(p, m, Tj[i]) * (Hj[i] - Tj[i]));
+          kadd(&e[1], &c[1], tau * V * source(p, m, Tj[i], s));
+          /* radial edges to non-regular neighbours (implicit fluxes) */
+          if (cls[i - 1] != OR_REGULAR) {
+            double f = tau * two_pi * etabar * r_w * lam_face(p, m, Tj[i - 1], Tj[i]) *
+                       (Hj[i - 1] - Hj[i]) / h_w;
+            kadd(cls[i - 1] == OR_IFACE ? &e[3] : &e[4], cls[i - 1] == OR_IFACE ? &c[3] : &c[4], f);
+          }
+          if (cls[i + 1] != OR_REGULAR) {
+            double f = tau * two_pi * etabar * r_e * lam_face(p, m, Tj[i], Tj[i + 1]) *
+                       (Hj[i + 1] - Hj[i]) / h_e;
+            int k = (cls[i + 1] == OR_IFACE) ? 3 : (p->bc_rmax ? 2 : 4);
+            kadd(&e[k], &c[k], f);
+          }
+          /* axial edges to the boundary rows (explicit fluxes) */
+          if (j == 1) {
+            double f = tau * two_pi * r[i] * hbar * lam_face(p, m, Ts[i], Tj[i]) *
+                       (Ts[i] - Tj[i]) / eta_s;
+            int k = p->bc_z0 ? 2 : 4;
+            kadd(&e[k], &c[k], f);
+          }
+          if (j == M - 1) {
+            double f = tau * two_pi * r[i] * hbar * lam_face(p, m, Tj[i], Tn[i]) *
+                       (Tn[i] - Tj[i]) / eta_n;
+            int k = p->bc_zmax ? 2 : 4;
+            kadd(&e[k], &c[k], f);
+          }
+        }
+        for (int k = 0; k < 5; k++) part[5 * (size_t)j + k] = e[k] + c[k];
+      }
+      for (int j = 1; j <= M - 1; j++)
+        for (int k = 0; k < 5; k++) kadd(&esum[k], &ecmp[k], part[5 * (size_t)j + k]);
+    }
+
+    memcpy(T, Th, sizeof(double) * (size_t)nr * (M + 1));
+
+    if (trace) {
+      double wsum = 0.0, acc = 0.0;
+      for (int j = 0; j <= M; j++) {
+        double w = 0.0;
+        if (j > 0) w += 0.5 * (z[j] - z[j - 1]);
+        if (j < M) w += 0.5 * (z[j + 1] - z[j]);
+        wsum += w;
+        acc += w * T[(size_t)j * nr + N];
+      }
+      trace[2 * n] = T[N];
+      trace[2 * n + 1] = acc / wsum;
+    }
+  }
+  if (energy)
+    for (int k = 0; k < 5; k++) energy[k] += esum[k] + ecmp[k];
+  free(r); free(z); free(cls); free(seg); free(Th); free(part);
+  return 0;
+}
+
+int or_num_threads(void) {
+#ifdef _OPENMP
+  return omp_get_max_threads();
+#else
+  return 1;
+#endif
+}
+
+void or_set_threads(int n) {
+#ifdef _OPENMP
+  if (n > 0) omp_set_num_threads(n);
+#else
+  (void)n;
+#endif
+}

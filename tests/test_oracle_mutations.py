@@ -1,0 +1,60 @@
+"""The oracle's pins must catch plausible mistakes.
+
+Each case plants one mistake in a copy of ``oracle/ccell_oracle.c`` (on the
+CPU, in a temporary directory), builds it, and runs the pin suite against that
+build; the suite has to fail.
+"""
+import os
+import shutil
+import subprocess
+import sys
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+SRC = os.path.join(ROOT, "oracle", "ccell_oracle.c")
+
+MUTATIONS = {
+    "wrong face radius in A (r_e for r_w)":
+        ("const double A = -r_w * lw", "const double A = -r_e * lw"),
+    "sign of the south flux in Lambda_j":
+        ("- ls * (T0 - Ts[i]) / eta_s", "+ ls * (T0 - Ts[i]) / eta_s"),
+    "north face conductivity from the south neighbour":
+        ("const double ln = lam_face(p, m, T0, Tn[i]);", "const double ln = lam_face(p, m, T0, Ts[i]);"),
+    "face conductivity at one node instead of the face mean":
+        ("return lam_m(p, m, 0.5 * (Ta + Tb));", "return lam_m(p, m, Ta);"),
+    "heat capacity saturation squared instead of cubed":
+        ("(1.0 + y * y * y)", "(1.0 + y * y)"),
+    "density dropped from rho c":
+        ("const double rc = p->rho[m] * cap_m(p, m, T0);", "const double rc = cap_m(p, m, T0);"),
+    "interface beta with the wrong cell width":
+        ("beta[i] = lm * h_e * beta[i - 1] / den;", "beta[i] = lm * h_w * beta[i - 1] / den;"),
+    "source term dropped from F":
+        ("F = rc / tau * T0 + Lj + X;", "F = rc / tau * T0 + Lj;"),
+    "Neumann closure at r_max dropped":
+        ("beta[N - 1] / (1.0 - alpha[N - 1])", "beta[N - 1]"),
+    "sign of alpha in the forward sweep":
+        ("alpha[i] = -C / den;", "alpha[i] = C / den;"),
+    "stability bound with eta instead of eta^2":
+        ("if (e * e < eta2) eta2 = e * e;", "if (e < eta2) eta2 = e;"),
+    "rectangle pulse closed interval":
+        ("return (phi < p->t_on) ? 1.0 : 0.0;", "return (phi <= p->t_on) ? 1.0 : 0.0;"),
+}
+
+
+@pytest.mark.parametrize("name", sorted(MUTATIONS))
+def test_pins_catch_mutation(name, tmp_path):
+    old, new = MUTATIONS[name]
+    src = open(SRC).read()
+    assert src.count(old) == 1, f"mutation anchor not found once: {old!r}"
+    mut = tmp_path / "mutant.c"
+    mut.write_text(src.replace(old, new))
+    so = tmp_path / "libmutant.so"
+    cc = shutil.which("gcc") or shutil.which("cc")
+    subprocess.run([cc, "-O2", "-std=c11", "-ffp-contract=off", "-fPIC", "-shared", str(mut),
+                    "-o", str(so), "-lm"], check=True, capture_output=True)
+    env = dict(os.environ, CCELL_ORACLE_SO=str(so))
+    res = subprocess.run([sys.executable, "-m", "pytest", "-x", "-q",
+                          os.path.join(ROOT, "tests", "test_oracle_pins.py")],
+                         env=env, capture_output=True, text=True, cwd=ROOT)
+    assert res.returncode != 0, f"pins did not catch: {name}\n{res.stdout[-2000:]}"
