@@ -1,0 +1,323 @@
+"""Benchmark of the explicit-implicit r-z heat-conduction step on GB300.
+
+Workload: the 5-layer 512 x 4096 production cylinder (properties jittered
++/-10 %, seed 0), FP64 path, tau = 0.4 ns (axial stability bound).  One bench
+step = one cc_step_n call advancing the field by --inner time steps (all of
+the time step: properties, explicit axial stencil, source, tridiagonal line
+solves, boundary rows, surface trace and energy sums).  Metric: node-updates/s
+(nr * nz per time step).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--inner n] [--impl ours|reference]
+
+--impl reference times the FP64 CPU oracle (the reference arm of this build)
+on the same workload, on the host cores.  With N > 1 (torchrun) every rank
+runs an independent replica (the path has no exchange between problems), rank
+0 prints the JSON line with the total over ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "node-updates/s at 512x4096 r-z, FP64 path"
+UNIT = "node-updates/s"
+BYTES_PER_NODE_FP64 = 16      # read T^n + write T^{n+1}
+BYTES_PER_NODE_MIXED = 8
+FLOPS_PER_NODE_FP64 = 150     # FP64 operations per node-update (2 power laws ~ 2x(log+exp), 1 div, 1 rcp, ~30 fma/add/mul)
+FP64_PEAK_TFLOPS = 152 * 4 * 0.5 * 2 * 2.07e9 / 1e12   # SMs x SMSPs x DFMA lanes/clk x 2 x max clock
+L2_FLUSH_BYTES = 256 << 20
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f)
+    except OSError:
+        return {"hbm_gbs": 6800.0, "source": "fallback"}
+
+
+def _dist():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+class Clocks:
+    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.idx = gpu_index
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.idx), f"--query-gpu={self.Q}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            out, _ = self.proc.communicate(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+            out, _ = self.proc.communicate()
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in out.strip().splitlines():
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax = float(f[2])
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": smax,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def run_ours(args, world, rank, local):
+    import torch
+    import torch.distributed as dist
+
+    from paper_1408_5853_gb300 import ccell, inputs
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    cfg = inputs.production_case()
+    nodes = cfg["nr"] * cfg["nz"]
+    n_in = args.inner
+    T0 = inputs.initial_field(cfg, "smooth", seed=0)
+    t0 = 0.0
+
+    def make(precision):
+        sol = ccell.Solver(cfg, precision=precision)
+        dt = torch.float64 if precision == ccell.FP64 else torch.float32
+        T = torch.tensor(T0.ravel(), dtype=dt, device=dev)
+        trace = torch.zeros(2 * n_in, dtype=torch.float64, device=dev)
+        energy = torch.zeros(5, dtype=torch.float64, device=dev)
+        return sol, T, trace, energy
+
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+
+    def timed_steps(sol, T, trace, energy, k_steps, warm):
+        for w in range(warm):
+            sol.step(T, n_in, t0 + w * n_in * cfg["dt"], 0.0, trace, energy)
+        sol.sync()
+        torch.cuda.synchronize()
+        if world > 1:
+            dist.barrier()
+        times = []
+        launches0 = ccell.cc_kernel_launches()
+        for k in range(k_steps):
+            flush.fill_(float(k))                       # L2 flush outside the timed events
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            sol.step(T, n_in, t0 + (warm + k) * n_in * cfg["dt"], 0.0, trace, energy)
+            e1.record(stream)
+            times.append((e0, e1))
+        torch.cuda.synchronize()
+        launches = ccell.cc_kernel_launches() - launches0 - 0
+        sol.sync()
+        ms = sum(a.elapsed_time(b) for a, b in times)
+        if world > 1:
+            t = torch.tensor([ms], device=dev)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            ms = float(t.item())
+        return ms, launches
+
+    # ---- FP64 path (headline)
+    clocks = Clocks(local)
+    sol, T, trace, energy = make(ccell.FP64)
+    clocks.start()
+    ms, launches = timed_steps(sol, T, trace, energy, args.steps, args.warmup)
+    clk = clocks.stop()
+    total_nodes = nodes * n_in * args.steps * world
+    value = total_nodes / (ms / 1e3)
+    per_launch_ms = ms / (args.steps * n_in)
+    e = energy.cpu().numpy()
+    ident = abs(e[0] - e[1:].sum()) / max(abs(e[0]), abs(e[1]), 1e-300)
+
+    # ---- end to end through the C ABI with pinned host buffers
+    hT = torch.tensor(T0.ravel(), dtype=torch.float64).pin_memory()
+    hOut = torch.empty_like(hT).pin_memory()
+    hTr = torch.empty(2 * n_in, dtype=torch.float64).pin_memory()
+    T.copy_(hT)
+    sol.step(T, n_in, 0.0, 0.0, trace, energy)
+    torch.cuda.synchronize()
+    e2e_times = []
+    for k in range(max(1, args.steps)):
+        flush.fill_(float(k))
+        torch.cuda.synchronize()
+        t_a = time.perf_counter()
+        T.copy_(hT, non_blocking=True)
+        sol.step(T, n_in, 0.0, 0.0, trace, energy)
+        hOut.copy_(T, non_blocking=True)
+        hTr.copy_(trace, non_blocking=True)
+        torch.cuda.synchronize()
+        e2e_times.append(time.perf_counter() - t_a)
+    e2e_s = sum(e2e_times)
+    if world > 1:
+        t = torch.tensor([e2e_s], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_s = float(t.item())
+    e2e_val = nodes * n_in * len(e2e_times) * world / e2e_s
+    sol.close()
+
+    # ---- mixed-precision path on the same workload
+    mixed = None
+    try:
+        solm, Tm, trm, enm = make(ccell.MIXED)
+        msm, _ = timed_steps(solm, Tm, trm, enm, args.steps, args.warmup)
+        mixed = {"value": nodes * n_in * args.steps * world / (msm / 1e3),
+                 "ms_per_step": msm / args.steps,
+                 "speedup_vs_fp64": (nodes * n_in * args.steps * world / (msm / 1e3)) / value,
+                 "hbm_frac_effective": BYTES_PER_NODE_MIXED * nodes * n_in * args.steps * world
+                 / (msm / 1e3) / (_peaks()["hbm_gbs"] * 1e9)}
+        solm.close()
+    except ccell.CCError as err:
+        mixed = {"unavailable": str(err)}
+
+    if rank != 0:
+        return None
+    peaks = _peaks()
+    hbm_peak = peaks["hbm_gbs"]
+    achieved_tflops = FLOPS_PER_NODE_FP64 * nodes / (per_launch_ms / 1e3) / 1e12
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": f"5-layer r-z cylinder {cfg['nr']}x{cfg['nz']}, jittered seed 0, "
+                               f"tau {cfg['dt']:.2e} s, {n_in} time steps per bench step",
+                   "nr": cfg["nr"], "nz": cfg["nz"], "time_steps_per_step": n_in,
+                   "precision": "fp64", "l2": f"flushed between timed steps ({L2_FLUSH_BYTES >> 20} MB write)",
+                   "parallelism": f"replicas x{world}"},
+        "roofline": {"bound": "alu", "kernel": "step_fp64_kernel",
+                     "achieved": achieved_tflops, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                     "frac": achieved_tflops / FP64_PEAK_TFLOPS, "traffic": None,
+                     "peak_source": "FP64 unit counts x max SM clock (152 x 4 x 0.5 DFMA/clk x 2 x 2.07 GHz)",
+                     "per_unit": f"{FLOPS_PER_NODE_FP64} FP64 ops per node-update"},
+        "hbm_roofline": {"bound": "hbm", "achieved": BYTES_PER_NODE_FP64 * value / world / 1e9,
+                         "peak": hbm_peak, "unit": "GB/s",
+                         "frac": BYTES_PER_NODE_FP64 * value / world / 1e9 / hbm_peak,
+                         "per_unit": "16 B per node-update (read T^n, write T^n+1)",
+                         "note": "effective: the field stays L2-resident during a call"},
+        "energy_identity_rel": ident,
+        "mixed": mixed,
+        "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": int(hT.numel() * 8),
+                "d2h_bytes_per_step": int(hOut.numel() * 8 + hTr.numel() * 8)},
+        "gpu_launches": int(launches),
+        "clocks": clk,
+    }
+    if world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(args.cpu_sample_steps)
+    return line
+
+
+def cpu_baseline(sample_steps: int) -> dict:
+    """The FP64 oracle, as it stands, on the host cores for a bounded sample."""
+    from oracle import oracle
+    from paper_1408_5853_gb300 import inputs
+    cfg = inputs.production_case()
+    T0 = inputs.initial_field(cfg, "smooth", seed=0)
+    t = time.perf_counter()
+    oracle.step_n(cfg, T0, sample_steps, 0.0, cfg["dt"])
+    s = time.perf_counter() - t
+    return {"value": cfg["nr"] * cfg["nz"] * sample_steps / s, "unit": UNIT,
+            "cores": oracle.num_threads(), "kind": "oracle",
+            "sample": f"{sample_steps} time steps of the 512x4096 workload ({s:.1f} s)"}
+
+
+def run_reference(args, world, rank):
+    """Reference arm: the FP64 CPU oracle on the host cores (rank 0 only)."""
+    if rank != 0:
+        return None
+    from oracle import oracle
+    from paper_1408_5853_gb300 import inputs
+    cfg = inputs.production_case()
+    nodes = cfg["nr"] * cfg["nz"]
+    n_in = args.ref_inner
+    T = inputs.initial_field(cfg, "smooth", seed=0)
+    for w in range(args.warmup):
+        T, _, _ = oracle.step_n(cfg, T, n_in, w * n_in * cfg["dt"], cfg["dt"])
+    times = []
+    for k in range(args.steps):
+        t = time.perf_counter()
+        T, _, _ = oracle.step_n(cfg, T, n_in, (args.warmup + k) * n_in * cfg["dt"], cfg["dt"])
+        times.append(time.perf_counter() - t)
+    s = sum(times)
+    value = nodes * n_in * args.steps / s
+    return {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * s / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": f"5-layer r-z cylinder {cfg['nr']}x{cfg['nz']}, jittered seed 0, "
+                               f"tau {cfg['dt']:.2e} s, {n_in} time steps per bench step (CPU sample)",
+                   "nr": cfg["nr"], "nz": cfg["nz"], "time_steps_per_step": n_in,
+                   "precision": "fp64"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": oracle.num_threads(),
+                         "kind": "oracle",
+                         "sample": f"{n_in} time steps of the 512x4096 workload per bench step"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--inner", type=int, default=1000, help="time steps per bench step")
+    ap.add_argument("--ref-inner", type=int, default=60, help="time steps per reference step")
+    ap.add_argument("--cpu-sample-steps", type=int, default=300)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 3) if args.impl == "ours" else args.warmup
+    world, rank, local = _dist()
+    if world > 1:
+        import torch.distributed as dist
+        if args.impl == "ours":
+            import torch
+            torch.cuda.set_device(local)
+            dist.init_process_group("nccl")
+        else:
+            dist.init_process_group("gloo")
+    if args.impl == "reference":
+        line = run_reference(args, world, rank)
+    else:
+        line = run_ours(args, world, rank, local)
+    if line is not None:
+        print(json.dumps(line))
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,224 @@
+/*
+ * ccell.h -- C ABI of the GB300 solver for the explicit-implicit
+ * finite-difference heat-conduction scheme of Ayriyan, Busa, Donets,
+ * Grigorian, Pribis, "Algorithm and Simulation of Heat Conduction Process for
+ * Design of a Thin Multilayer Technical Device" (arXiv:1408.5853).
+ *
+ * The solver advances the temperature T(r, z, t) of a multilayer
+ * axisymmetric cylinder (Section 2, Eqs. (equation)-(sch)) with the scheme of
+ * Section 3: every time step evaluates the temperature-dependent
+ * conductivity and heat capacity, applies the explicit axial operator
+ * Lambda_j (Eq. (Lambda_j)), and solves the implicit radial operator Lambda_i
+ * (Eq. (Lambda_i)) as one tridiagonal system per axial line j (Eqs.
+ * (front_sweep)-(back_sweep)) with the layer-interface rows of Eqs.
+ * (cc_first_1)-(cc_first_3) and the closures of Eqs.
+ * (first_oder_bc)-(T_ini_for_back_sweep); the periodic source enters through
+ * Eqs. (source)-(period).
+ *
+ * Conventions for every entry point:
+ *  - Return value: CC_OK (0) or a negative cc_status.  Nothing throws across
+ *    the ABI, nothing calls exit/abort, no kernel traps.
+ *  - Ownership: the caller owns every buffer it passes; descriptors are
+ *    copied during the call.  The context owns its device tables and scratch
+ *    memory and releases them in cc_destroy.
+ *  - Device pointers ("_dev") are CUDA device addresses on the current device
+ *    of the calling thread; host pointers are plain CPU memory.
+ *  - Streams: all device work of a call is enqueued on the given CUDA stream
+ *    (NULL = legacy default stream).  A context is not thread-safe; calls on
+ *    one context must be serialised by the caller.
+ *  - Asynchronous kernel failures (a CUDA error, a non-finite temperature)
+ *    are reported by the next call that synchronises (cc_step_n with a host
+ *    trace/energy, cc_sync, cc_adjoint); the context then refuses further
+ *    work with CC_ESTATE until destroyed.
+ *
+ * Field layout: an instance with nr radial and nz axial nodes stores
+ * T[j * nr + i] (i = 0..nr-1 radial, contiguous; j = 0..nz-1 axial), so one
+ * axial line j is one contiguous row.  Instances are concatenated in the
+ * order of cc_create_geometry.  Temperatures are in kelvin.
+ */
+#ifndef CCELL_H
+#define CCELL_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct cc_ctx cc_ctx; /* opaque, owned by the library */
+
+typedef enum {
+  CC_OK = 0,
+  CC_EINVAL = -1,        /* invalid argument or descriptor                   */
+  CC_ENOMEM = -2,        /* host or device allocation failed                 */
+  CC_ECUDA = -3,         /* a CUDA runtime call or kernel failed             */
+  CC_EUNSTABLE = -4,     /* dt above the axial stability bound, Eq. (stability_condition) */
+  CC_ETIMEOUT = -5,      /* a bounded device wait expired                    */
+  CC_ENONFINITE = -6,    /* a non-finite temperature was produced            */
+  CC_ESTATE = -7,        /* context unusable after an earlier failure, or not configured */
+  CC_EUNSUPPORTED = -8   /* valid request this build does not implement      */
+} cc_status;
+
+#define CC_MAX_LAYERS 8
+
+enum { CC_NEUMANN = 0, CC_DIRICHLET = 1 };
+enum { CC_FP64 = 0, CC_MIXED = 1 };
+
+/*
+ * Geometry of one instance (Section 2; grid of Eq. (uniform_grid)).
+ * Layers are listed from the axis outwards; radial nodes are placed
+ * uniformly inside each layer with a node exactly on every layer border
+ * (cells per layer proportional to thickness, largest remainder, at least
+ * 2 per layer, ties to the lower layer); axial nodes are uniform.
+ *   bc_*        boundary condition of the face r = r_max, z = 0, z = z_max
+ *               (paper default, Eq. (boundcond): Neumann, Neumann,
+ *               Dirichlet); the axis r = 0 is always a symmetry line.
+ *   placement   0: nodes on the boundaries (paper).  1: a Neumann face lies
+ *               half a cell inside its outermost node (second-order
+ *               closures; single layer only; used for analytic checks).
+ *   precision   CC_FP64: state, properties, stencil and elimination in
+ *               FP64; T is double.  CC_MIXED: T is float; properties and the
+ *               explicit stencil run in FP32, the tridiagonal elimination and
+ *               the energy sums in FP64.
+ *   face_rule   0: lambda_{i+1/2} = lambda((T_i + T_i+1)/2)  (reading of the
+ *               face rule printed with Eq. (Lambda_j)); 1: mean of the nodal
+ *               lambda values.
+ *   interface_rule  0: Eq. (cc_first_3) with lambda* at the old interface
+ *               temperature; 1: same row with the r-weighted face
+ *               conductivities (conserves energy exactly).
+ *   t_guard_lo_K, t_guard_hi_K  temperature range over which the stability
+ *               guard minimises rho c / lambda (0, 0 = [t_dirichlet, 100 K]).
+ */
+typedef struct {
+  int32_t n_layers;
+  double thickness_m[CC_MAX_LAYERS];
+  int32_t nr, nz;
+  double length_m;
+  int32_t bc_rmax, bc_z0, bc_zmax;
+  double t_dirichlet_K;
+  int32_t placement;
+  int32_t precision;
+  int32_t face_rule;
+  int32_t interface_rule;
+  double t_guard_lo_K, t_guard_hi_K;
+} cc_geometry_desc;
+
+/*
+ * Material of one layer (Section 5 models and the power-law workloads):
+ *   lambda(T) = lam_scale * { lam0                      (lam_model 0)
+ *                           { lam0 (T / t_ref)^lam_b    (lam_model 1)
+ *                           { sum_k lam_poly[k] T^k     (lam_model 2, Eq. (poly_cond))
+ *   c(T)      = cap_scale * { c0                        (cap_model 0)
+ *                           { c0 (T/t_ref)^3 / (1 + (T/theta)^3)  (cap_model 1)
+ *                           { sum_k cap_poly[k] T^k     (cap_model 2, Eq. (poly_cap))
+ * rho is the constant density.  SI units (W/m/K, J/kg/K, kg/m^3).
+ */
+typedef struct {
+  double rho;
+  int32_t lam_model;
+  double lam0, lam_b;
+  int32_t cap_model;
+  double c0, theta, t_ref;
+  double lam_scale, cap_scale;
+  double lam_poly[5];
+  double cap_poly[4];
+} cc_material;
+
+/*
+ * Heating source, Eqs. (source)-(period): X = q0 s(t) g(T) at the regular
+ * nodes of layer `layer` (interface nodes carry no source).
+ *   waveform 0: s = nu(t), 1 on [t_start + n t_period, ... + t_on), else 0.
+ *   waveform 1: s = (tanh(phi/w) - tanh((phi - t_on)/w)) / 2 around the
+ *               nearest pulse (phase phi), w = edge_w.
+ *   g_model  0: g = 1;  1: g = g_ref / sqrt(T) (resistivity of the paper's
+ *            conducting layer, Section 5).
+ * layer = -1 disables the source.
+ */
+typedef struct {
+  int32_t layer;
+  double q0;
+  double t_period, t_on, t_start;
+  int32_t waveform;
+  double edge_w;
+  int32_t g_model;
+  double g_ref;
+} cc_source;
+
+/* Create a context for n_instances instances; desc points to n_instances
+ * descriptors.  Host work only: device memory is allocated on the first
+ * call that needs it, on the device current at that time.
+ * Errors: CC_EINVAL (bad descriptor), CC_ENOMEM. */
+int cc_create_geometry(const cc_geometry_desc* desc, int32_t n_instances, cc_ctx** out);
+
+/* Materials of instance `instance` (-1: all instances), m[n_layers]. */
+int cc_set_materials(cc_ctx* ctx, int32_t instance, const cc_material* m);
+
+/* Source of instance `instance` (-1: all instances). */
+int cc_set_source(cc_ctx* ctx, int32_t instance, const cc_source* s);
+
+/* Per-instance time step [s], used by cc_step_n when its dt_s is 0. */
+int cc_set_dt(cc_ctx* ctx, int32_t instance, double dt_s);
+
+/*
+ * Advance every instance by n_steps steps of Eq. (scheme_eq) starting at
+ * t0_s; step n uses t_n = t0_s + n dt (dt = dt_s if dt_s > 0, else the
+ * per-instance value of cc_set_dt).
+ *   T_dev       in/out field of all instances (double for CC_FP64, float
+ *               for CC_MIXED), layout above.  Caller-owned device memory.
+ *   trace_dev   NULL or device double[n_instances][n_steps][2]: after step n,
+ *               T(r_max, z_0) and the trapezoid-weighted mean over z of
+ *               T(r_max, z) (the surface temperature of Section 5.1).
+ *   energy_dev  NULL or device double[n_instances][5], ADDED to: stored heat
+ *               sum V rho c (That - T), injected heat tau sum V X, heat through
+ *               Dirichlet edges, through interface edges, through Neumann
+ *               edges (V = 2 pi r_i hbar_i etabar_j).  The scheme satisfies
+ *               stored = injected + the three edge terms up to rounding.
+ *   stream      cudaStream_t or NULL.
+ * Errors: CC_EINVAL, CC_EUNSTABLE (dt above the bound of Eq.
+ * (stability_condition) over the guard range; set CC_FORCE_UNSTABLE=1 in the
+ * environment to run anyway), CC_ESTATE, CC_ECUDA, CC_ENOMEM.
+ * The call is asynchronous with respect to the host. */
+int cc_step_n(cc_ctx* ctx, void* T_dev, int64_t n_steps, double t0_s, double dt_s,
+              double* trace_dev, double* energy_dev, void* stream);
+
+/* Wait for the context's work on `stream`, then report a deferred kernel
+ * failure (CC_ENONFINITE, CC_ETIMEOUT, CC_ECUDA) or CC_OK. */
+int cc_sync(cc_ctx* ctx, void* stream);
+
+/*
+ * Reverse-time discrete adjoint of n_steps steps (Section 3 scheme) for the
+ * loss J = sum_n dt (Sbar_n - target_n)^2, Sbar_n the z-mean surface
+ * temperature after step n (trace column 1).  Returns J and dJ/dtheta for
+ * theta = (q0, t_on, lam_scale[0..L-1], cap_scale[0..L-1]) per instance,
+ * plus dJ/dT0 if dT0_dev is not NULL.  Checkpoints every ckpt_every steps and
+ * recomputes in between.
+ *   T0_dev      initial field (not modified); target_dev double[n_inst][n_steps]
+ *   loss_dev    double[n_inst]; grad_dev double[n_inst][2 + 2 n_layers]
+ * Errors as cc_step_n; CC_EUNSUPPORTED for CC_MIXED contexts. */
+int cc_adjoint(cc_ctx* ctx, const void* T0_dev, int64_t n_steps, double t0_s, double dt_s,
+               const double* target_dev, int32_t ckpt_every, double* loss_dev,
+               double* grad_dev, void* dT0_dev, void* stream);
+
+/* Release the context and everything it owns.  NULL is accepted. */
+int cc_destroy(cc_ctx* ctx);
+
+/* ---- host-only queries (no GPU needed) ---------------------------------- */
+
+/* Node positions and radial classes of one descriptor: r[nr], z[nz],
+ * rclass[nr] (0 axis, 1 regular, 2 layer interface, 3 outer boundary). */
+int cc_query_grid(const cc_geometry_desc* desc, double* r, double* z, int32_t* rclass);
+
+/* Stability bound of Eq. (stability_condition) for one instance:
+ * (min_j eta_j^2 / 2) * min over layers and the guard range of rho c/lambda. */
+int cc_tau_stab(const cc_ctx* ctx, int32_t instance, double* tau_out);
+
+/* Static description of a status code. */
+const char* cc_status_string(int status);
+
+/* Number of this library's kernel launches issued so far by this process. */
+int64_t cc_kernel_launches(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* CCELL_H */

@@ -1,0 +1,286 @@
+"""Thin Python binding of the C ABI in ``include/ccell.h`` (libccell.so).
+
+Argument marshalling only: every step of the time step runs in the CUDA
+kernels of ``csrc/``.  PyTorch provides device memory and streams.  Importing
+this module loads the CUDA library and fails loudly if it is missing; there is
+no CPU fallback.
+
+Low-level functions carry the C names (``cc_create_geometry``,
+``cc_set_materials``, ``cc_set_source``, ``cc_set_dt``, ``cc_step_n``,
+``cc_sync``, ``cc_adjoint``, ``cc_destroy``, ``cc_query_grid``,
+``cc_tau_stab``, ``cc_status_string``, ``cc_kernel_launches``).  ``Solver``
+builds a context from the problem dicts of ``inputs``.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+from . import build as _build
+
+MAX_LAYERS = 8
+FP64, MIXED = 0, 1
+
+CC_OK, CC_EINVAL, CC_ENOMEM, CC_ECUDA, CC_EUNSTABLE = 0, -1, -2, -3, -4
+CC_ETIMEOUT, CC_ENONFINITE, CC_ESTATE, CC_EUNSUPPORTED = -5, -6, -7, -8
+
+_d = ctypes.c_double
+_i = ctypes.c_int32
+
+
+class GeometryDesc(ctypes.Structure):
+    _fields_ = [
+        ("n_layers", _i), ("thickness_m", _d * MAX_LAYERS), ("nr", _i), ("nz", _i),
+        ("length_m", _d), ("bc_rmax", _i), ("bc_z0", _i), ("bc_zmax", _i),
+        ("t_dirichlet_K", _d), ("placement", _i), ("precision", _i), ("face_rule", _i),
+        ("interface_rule", _i), ("t_guard_lo_K", _d), ("t_guard_hi_K", _d),
+    ]
+
+
+class Material(ctypes.Structure):
+    _fields_ = [
+        ("rho", _d), ("lam_model", _i), ("lam0", _d), ("lam_b", _d), ("cap_model", _i),
+        ("c0", _d), ("theta", _d), ("t_ref", _d), ("lam_scale", _d), ("cap_scale", _d),
+        ("lam_poly", _d * 5), ("cap_poly", _d * 4),
+    ]
+
+
+class Source(ctypes.Structure):
+    _fields_ = [
+        ("layer", _i), ("q0", _d), ("t_period", _d), ("t_on", _d), ("t_start", _d),
+        ("waveform", _i), ("edge_w", _d), ("g_model", _i), ("g_ref", _d),
+    ]
+
+
+class CCError(RuntimeError):
+    def __init__(self, status: int, what: str):
+        super().__init__(f"{what}: {cc_status_string(status)} ({status})")
+        self.status = status
+
+
+_lib = None
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def _load():
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = _build.LIB
+    if not os.path.exists(path):
+        path = _build.build()
+    lib = ctypes.CDLL(path)
+    vp, dp = ctypes.c_void_p, ctypes.POINTER(_d)
+    lib.cc_create_geometry.argtypes = [ctypes.POINTER(GeometryDesc), _i, ctypes.POINTER(vp)]
+    lib.cc_set_materials.argtypes = [vp, _i, ctypes.POINTER(Material)]
+    lib.cc_set_source.argtypes = [vp, _i, ctypes.POINTER(Source)]
+    lib.cc_set_dt.argtypes = [vp, _i, _d]
+    lib.cc_step_n.argtypes = [vp, vp, ctypes.c_int64, _d, _d, vp, vp, vp]
+    lib.cc_sync.argtypes = [vp, vp]
+    lib.cc_adjoint.argtypes = [vp, vp, ctypes.c_int64, _d, _d, vp, _i, vp, vp, vp, vp]
+    lib.cc_destroy.argtypes = [vp]
+    lib.cc_query_grid.argtypes = [ctypes.POINTER(GeometryDesc), dp, dp, ctypes.POINTER(_i)]
+    lib.cc_tau_stab.argtypes = [vp, _i, dp]
+    lib.cc_status_string.argtypes = [ctypes.c_int]
+    lib.cc_status_string.restype = ctypes.c_char_p
+    lib.cc_kernel_launches.restype = ctypes.c_int64
+    for name in ("cc_create_geometry", "cc_set_materials", "cc_set_source", "cc_set_dt",
+                 "cc_step_n", "cc_sync", "cc_adjoint", "cc_destroy", "cc_query_grid",
+                 "cc_tau_stab"):
+        getattr(lib, name).restype = ctypes.c_int
+    _lib = lib
+    return lib
+
+
+def _check(status: int, what: str) -> None:
+    if status != CC_OK:
+        raise CCError(status, what)
+
+
+# ---------------------------------------------------------------------------
+# C names
+# ---------------------------------------------------------------------------
+def cc_status_string(status: int) -> str:
+    return _load().cc_status_string(int(status)).decode()
+
+
+def cc_kernel_launches() -> int:
+    return int(_load().cc_kernel_launches())
+
+
+def cc_create_geometry(descs) -> ctypes.c_void_p:
+    arr = (GeometryDesc * len(descs))(*descs)
+    ctx = ctypes.c_void_p()
+    _check(_load().cc_create_geometry(arr, len(descs), ctypes.byref(ctx)), "cc_create_geometry")
+    return ctx
+
+
+def cc_set_materials(ctx, instance: int, materials) -> None:
+    arr = (Material * len(materials))(*materials)
+    _check(_load().cc_set_materials(ctx, instance, arr), "cc_set_materials")
+
+
+def cc_set_source(ctx, instance: int, source: Source) -> None:
+    _check(_load().cc_set_source(ctx, instance, ctypes.byref(source)), "cc_set_source")
+
+
+def cc_set_dt(ctx, instance: int, dt: float) -> None:
+    _check(_load().cc_set_dt(ctx, instance, float(dt)), "cc_set_dt")
+
+
+def cc_step_n(ctx, T_ptr: int, n_steps: int, t0: float, dt: float, trace_ptr, energy_ptr,
+              stream_ptr) -> None:
+    _check(_load().cc_step_n(ctx, T_ptr, int(n_steps), float(t0), float(dt), trace_ptr,
+                             energy_ptr, stream_ptr), "cc_step_n")
+
+
+def cc_sync(ctx, stream_ptr) -> None:
+    _check(_load().cc_sync(ctx, stream_ptr), "cc_sync")
+
+
+def cc_adjoint(ctx, T0_ptr, n_steps, t0, dt, target_ptr, ckpt_every, loss_ptr, grad_ptr,
+               dT0_ptr, stream_ptr) -> None:
+    _check(_load().cc_adjoint(ctx, T0_ptr, int(n_steps), float(t0), float(dt), target_ptr,
+                              int(ckpt_every), loss_ptr, grad_ptr, dT0_ptr, stream_ptr),
+           "cc_adjoint")
+
+
+def cc_destroy(ctx) -> None:
+    _check(_load().cc_destroy(ctx), "cc_destroy")
+
+
+def cc_query_grid(desc: GeometryDesc):
+    r = np.zeros(desc.nr)
+    z = np.zeros(desc.nz)
+    cls = np.zeros(desc.nr, dtype=np.int32)
+    _check(_load().cc_query_grid(ctypes.byref(desc), r.ctypes.data_as(ctypes.POINTER(_d)),
+                                 z.ctypes.data_as(ctypes.POINTER(_d)),
+                                 cls.ctypes.data_as(ctypes.POINTER(_i))), "cc_query_grid")
+    return r, z, cls
+
+
+def cc_tau_stab(ctx, instance: int) -> float:
+    out = _d()
+    _check(_load().cc_tau_stab(ctx, instance, ctypes.byref(out)), "cc_tau_stab")
+    return out.value
+
+
+# ---------------------------------------------------------------------------
+# problem dicts -> C structs
+# ---------------------------------------------------------------------------
+def geometry_desc(cfg: dict, precision: int = FP64) -> GeometryDesc:
+    d = GeometryDesc()
+    d.n_layers = len(cfg["layers"])
+    for m, ly in enumerate(cfg["layers"]):
+        d.thickness_m[m] = ly["thickness"]
+    d.nr, d.nz = cfg["nr"], cfg["nz"]
+    d.length_m = cfg["length"]
+    d.bc_rmax, d.bc_z0, d.bc_zmax = cfg.get("bc_rmax", 0), cfg.get("bc_z0", 0), cfg.get("bc_zmax", 1)
+    d.t_dirichlet_K = cfg.get("t_dirichlet", 20.0)
+    d.placement = cfg.get("placement", 0)
+    d.precision = precision
+    d.face_rule = cfg.get("face_rule", 0)
+    d.interface_rule = cfg.get("interface_rule", 0)
+    lo, hi = cfg.get("t_guard", (0.0, 0.0))
+    d.t_guard_lo_K, d.t_guard_hi_K = lo, hi
+    return d
+
+
+def materials(cfg: dict) -> list:
+    out = []
+    for ly in cfg["layers"]:
+        m = Material()
+        m.rho = ly["rho"]
+        m.lam_model = ly.get("lam_model", 1)
+        m.lam0 = ly.get("lam0", 0.0)
+        m.lam_b = ly.get("lam_b", 0.0)
+        m.cap_model = ly.get("cap_model", 1)
+        m.c0 = ly.get("c0", 0.0)
+        m.theta = ly.get("theta", 1.0)
+        m.t_ref = ly.get("t_ref", 20.0)
+        m.lam_scale = ly.get("lam_scale", 1.0)
+        m.cap_scale = ly.get("cap_scale", 1.0)
+        for k, v in enumerate(ly.get("lam_poly", [0.0] * 5)):
+            m.lam_poly[k] = v
+        for k, v in enumerate(ly.get("cap_poly", [0.0] * 4)):
+            m.cap_poly[k] = v
+        out.append(m)
+    return out
+
+
+def source(cfg: dict) -> Source:
+    s = Source()
+    src = cfg.get("source")
+    if src is None:
+        s.layer = -1
+        return s
+    s.layer = src["layer"]
+    s.q0 = src["q0"]
+    s.t_period, s.t_on, s.t_start = src["t_period"], src["t_on"], src.get("t_start", 0.0)
+    s.waveform = src.get("waveform", 0)
+    s.edge_w = src.get("edge_w", 0.0)
+    s.g_model = src.get("g_model", 0)
+    s.g_ref = src.get("g_ref", 0.0)
+    return s
+
+
+class Solver:
+    """A context over one or more problem dicts (instances)."""
+
+    def __init__(self, cfgs, precision: int = FP64):
+        if isinstance(cfgs, dict):
+            cfgs = [cfgs]
+        self.cfgs = list(cfgs)
+        self.precision = precision
+        self.ctx = cc_create_geometry([geometry_desc(c, precision) for c in self.cfgs])
+        for k, c in enumerate(self.cfgs):
+            cc_set_materials(self.ctx, k, materials(c))
+            cc_set_source(self.ctx, k, source(c))
+            if c.get("dt", 0.0) > 0.0:
+                cc_set_dt(self.ctx, k, c["dt"])
+        self.sizes = [c["nr"] * c["nz"] for c in self.cfgs]
+        self.total = int(sum(self.sizes))
+
+    @property
+    def dtype(self):
+        import torch
+        return torch.float64 if self.precision == FP64 else torch.float32
+
+    def step(self, T, n_steps: int, t0: float = 0.0, dt: float = 0.0, trace=None, energy=None,
+             stream=None) -> None:
+        """Advance the flat field ``T`` (all instances concatenated) in place."""
+        import torch
+        if not (T.is_cuda and T.is_contiguous() and T.dtype == self.dtype and T.numel() == self.total):
+            raise ValueError("T must be a contiguous CUDA tensor of the context's dtype and size")
+        for buf, n in ((trace, 2 * n_steps * len(self.cfgs)), (energy, 5 * len(self.cfgs))):
+            if buf is not None and not (buf.is_cuda and buf.is_contiguous()
+                                        and buf.dtype == torch.float64 and buf.numel() == n):
+                raise ValueError("trace/energy must be contiguous CUDA float64 of the right size")
+        st = stream if stream is not None else torch.cuda.current_stream()
+        cc_step_n(self.ctx, T.data_ptr(), n_steps, t0, dt,
+                  trace.data_ptr() if trace is not None else None,
+                  energy.data_ptr() if energy is not None else None, st.cuda_stream)
+
+    def sync(self, stream=None) -> None:
+        import torch
+        st = stream if stream is not None else torch.cuda.current_stream()
+        cc_sync(self.ctx, st.cuda_stream)
+
+    def tau_stab(self, instance: int = 0) -> float:
+        return cc_tau_stab(self.ctx, instance)
+
+    def close(self) -> None:
+        if self.ctx is not None:
+            cc_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,606 @@
+// Host side of the C ABI declared in include/ccell.h: descriptor validation,
+// the non-uniform grid of Eq. (uniform_grid), device tables, the stability
+// guard of Eq. (stability_condition), and the launch sequence of cc_step_n.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdlib>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "ccell_internal.h"
+
+using namespace ccell;
+
+namespace {
+
+struct Instance {
+  cc_geometry_desc d{};
+  cc_material mat[CC_MAX_LAYERS]{};
+  bool mat_set = false;
+  cc_source src{};
+  double dt = 0.0;
+  std::vector<double> r, z;
+  std::vector<int> cls, seg;
+  int G = 1;
+  long long t_off = 0;
+};
+
+}  // namespace
+
+struct cc_ctx {
+  std::vector<Instance> inst;
+  int precision = CC_FP64;
+  long long total_nodes = 0;
+  int failed = 0;  // sticky cc_status after a device failure
+  // device state
+  int device = -1;
+  bool dirty = true;
+  DevInst* d_inst = nullptr;
+  RowGeo* d_rg = nullptr;
+  ZGeo* d_zg = nullptr;
+  Task* d_tasks = nullptr;
+  int n_tasks = 0;
+  void* d_T2 = nullptr;       // ping-pong partner of the caller's field
+  float* d_lo = nullptr;      // mixed precision: low-order parts (two buffers)
+  double* d_s = nullptr;      // waveform table
+  long long s_cap = 0;
+  unsigned* d_err = nullptr;
+  std::vector<double> uploaded_dt;
+};
+
+namespace {
+
+int valid_desc(const cc_geometry_desc& d) {
+  if (d.n_layers < 1 || d.n_layers > CC_MAX_LAYERS) return CC_EINVAL;
+  if (d.nr < 3 || d.nz < 3) return CC_EINVAL;
+  if (d.nr > kMaxNr) return CC_EUNSUPPORTED;
+  if (!(d.length_m > 0.0) || !std::isfinite(d.length_m)) return CC_EINVAL;
+  for (int m = 0; m < d.n_layers; ++m)
+    if (!(d.thickness_m[m] > 0.0) || !std::isfinite(d.thickness_m[m])) return CC_EINVAL;
+  auto b01 = [](int v) { return v == 0 || v == 1; };
+  if (!b01(d.bc_rmax) || !b01(d.bc_z0) || !b01(d.bc_zmax) || !b01(d.placement) ||
+      !b01(d.precision) || !b01(d.face_rule) || !b01(d.interface_rule))
+    return CC_EINVAL;
+  if (d.placement == 1 && d.n_layers != 1) return CC_EINVAL;
+  if (d.placement == 0 && d.nr - 1 < 2 * d.n_layers) return CC_EINVAL;
+  if (!std::isfinite(d.t_dirichlet_K)) return CC_EINVAL;
+  return CC_OK;
+}
+
+// Radial cells per layer: proportional to thickness with the largest
+// remainder method (ties to the lower layer), at least two per layer.
+void layer_cells(const cc_geometry_desc& d, int* n) {
+  const int L = d.n_layers, N = d.nr - 1;
+  double total = 0.0;
+  for (int m = 0; m < L; ++m) total += d.thickness_m[m];
+  double frac[CC_MAX_LAYERS];
+  int assigned = 0;
+  for (int m = 0; m < L; ++m) {
+    const double share = (double)N * d.thickness_m[m] / total;
+    const double fl = std::floor(share);
+    n[m] = (int)fl;
+    frac[m] = share - fl;
+    if (n[m] < 2) n[m] = 2;
+    assigned += n[m];
+  }
+  std::vector<int> order(L);
+  for (int m = 0; m < L; ++m) order[m] = m;
+  std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return frac[x] > frac[y]; });
+  for (int k = 0; assigned < N; k = (k + 1) % L, ++assigned) n[order[k]]++;
+  while (assigned > N) {  // minimum-count overflow: take from the largest layer
+    int big = -1;
+    for (int m = 0; m < L; ++m)
+      if (n[m] > 2 && (big < 0 || n[m] > n[big])) big = m;
+    n[big]--;
+    assigned--;
+  }
+}
+
+void build_grid(const cc_geometry_desc& d, std::vector<double>& r, std::vector<double>& z,
+                std::vector<int>& cls, std::vector<int>& seg) {
+  const int N = d.nr - 1, M = d.nz - 1;
+  r.assign(N + 1, 0.0);
+  z.assign(M + 1, 0.0);
+  cls.assign(N + 1, RC_REGULAR);
+  seg.assign(N + 1, 0);
+  if (d.placement == 0) {
+    int n[CC_MAX_LAYERS];
+    layer_cells(d, n);
+    int i = 0;
+    double r0 = 0.0;
+    for (int m = 0; m < d.n_layers; ++m) {
+      const double h = d.thickness_m[m] / (double)n[m];
+      for (int k = 0; k < n[m]; ++k, ++i) {
+        r[i] = r0 + (double)k * h;
+        seg[i] = m;
+        if (k == 0 && m > 0) cls[i] = RC_IFACE;
+      }
+      r0 += d.thickness_m[m];
+    }
+    r[N] = r0;
+    seg[N] = d.n_layers - 1;
+    const double eta = d.length_m / (double)M;
+    for (int j = 0; j <= M; ++j) z[j] = (double)j * eta;
+  } else {
+    // a Neumann face sits half a cell inside its outermost node
+    const double hi_r = d.bc_rmax == CC_DIRICHLET ? 0.0 : 0.5;
+    const double h = d.thickness_m[0] / ((double)N - 0.5 - hi_r);
+    for (int i = 0; i <= N; ++i) r[i] = ((double)i - 0.5) * h;
+    const double lo_z = d.bc_z0 == CC_DIRICHLET ? 0.0 : 0.5;
+    const double hi_z = d.bc_zmax == CC_DIRICHLET ? 0.0 : 0.5;
+    const double eta = d.length_m / ((double)M - lo_z - hi_z);
+    for (int j = 0; j <= M; ++j) z[j] = ((double)j - lo_z) * eta;
+  }
+  cls[0] = RC_AXIS;
+  cls[N] = RC_OUTER;
+}
+
+int choose_lanes(int nr) {
+  int G = 1;
+  while (G < 32 && (nr + G - 1) / G > kRowsPerLane) G <<= 1;
+  return G;
+}
+
+double lam_host(const cc_material& m, double T) {
+  double v;
+  if (m.lam_model == 0) v = m.lam0;
+  else if (m.lam_model == 1) v = m.lam0 * std::pow(T / m.t_ref, m.lam_b);
+  else {
+    v = 0.0;
+    for (int k = 4; k >= 0; --k) v = v * T + m.lam_poly[k];
+  }
+  return m.lam_scale * v;
+}
+
+double cap_host(const cc_material& m, double T) {
+  double v;
+  if (m.cap_model == 0) v = m.c0;
+  else if (m.cap_model == 1) {
+    const double x = T / m.t_ref, y = T / m.theta;
+    v = m.c0 * x * x * x / (1.0 + y * y * y);
+  } else {
+    v = 0.0;
+    for (int k = 3; k >= 0; --k) v = v * T + m.cap_poly[k];
+  }
+  return m.cap_scale * v;
+}
+
+double tau_stab(const Instance& in) {
+  double eta2 = INFINITY;
+  for (size_t j = 1; j < in.z.size(); ++j) {
+    const double e = in.z[j] - in.z[j - 1];
+    eta2 = std::min(eta2, e * e);
+  }
+  double lo = in.d.t_guard_lo_K, hi = in.d.t_guard_hi_K;
+  if (!(hi > lo)) {
+    lo = in.d.t_dirichlet_K;
+    hi = 100.0;
+  }
+  double ratio = INFINITY;
+  const int ns = 257;
+  for (int m = 0; m < in.d.n_layers; ++m)
+    for (int s = 0; s < ns; ++s) {
+      const double T = lo + (hi - lo) * (double)s / (double)(ns - 1);
+      const double q = in.mat[m].rho * cap_host(in.mat[m], T) / lam_host(in.mat[m], T);
+      if (q < ratio) ratio = q;
+    }
+  return 0.5 * eta2 * ratio;
+}
+
+bool force_unstable() {
+  const char* v = std::getenv("CC_FORCE_UNSTABLE");
+  return v && v[0] == '1';
+}
+
+void free_device(cc_ctx* c) {
+  cudaFree(c->d_inst);
+  cudaFree(c->d_rg);
+  cudaFree(c->d_zg);
+  cudaFree(c->d_tasks);
+  cudaFree(c->d_T2);
+  cudaFree(c->d_lo);
+  cudaFree(c->d_s);
+  cudaFree(c->d_err);
+  c->d_inst = nullptr;
+  c->d_rg = nullptr;
+  c->d_zg = nullptr;
+  c->d_tasks = nullptr;
+  c->d_T2 = nullptr;
+  c->d_lo = nullptr;
+  c->d_s = nullptr;
+  c->d_err = nullptr;
+  c->s_cap = 0;
+}
+
+// Allocate device memory (first use) and upload the per-instance tables.
+int upload(cc_ctx* c, const std::vector<double>& dts, cudaStream_t st) {
+  const int n = (int)c->inst.size();
+  if (c->device < 0) {
+    if (cudaGetDevice(&c->device) != cudaSuccess) return CC_ECUDA;
+    size_t nrow = 0, nz = 0;
+    for (auto& in : c->inst) {
+      nrow += in.d.nr;
+      nz += in.d.nz;
+    }
+    std::vector<Task> tasks;
+    for (int k = 0; k < n; ++k) {
+      const Instance& in = c->inst[k];
+      const int lpw = 32 / in.G;
+      for (int j0 = 1; j0 <= in.d.nz - 2; j0 += lpw) tasks.push_back(Task{k, j0});
+    }
+    c->n_tasks = (int)tasks.size();
+    const size_t elem = c->precision == CC_FP64 ? sizeof(double) : sizeof(float);
+    if (cudaMalloc(&c->d_inst, sizeof(DevInst) * n) != cudaSuccess ||
+        cudaMalloc(&c->d_rg, sizeof(RowGeo) * nrow) != cudaSuccess ||
+        cudaMalloc(&c->d_zg, sizeof(ZGeo) * nz) != cudaSuccess ||
+        cudaMalloc(&c->d_tasks, sizeof(Task) * tasks.size()) != cudaSuccess ||
+        cudaMalloc(&c->d_T2, elem * c->total_nodes) != cudaSuccess ||
+        cudaMalloc(&c->d_err, sizeof(unsigned)) != cudaSuccess) {
+      free_device(c);
+      c->device = -1;
+      cudaGetLastError();
+      return CC_ENOMEM;
+    }
+    if (c->precision == CC_MIXED &&
+        cudaMalloc(&c->d_lo, 2 * sizeof(float) * c->total_nodes) != cudaSuccess) {
+      free_device(c);
+      c->device = -1;
+      cudaGetLastError();
+      return CC_ENOMEM;
+    }
+    if (cudaMemcpy(c->d_tasks, tasks.data(), sizeof(Task) * tasks.size(),
+                   cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemset(c->d_err, 0, sizeof(unsigned)) != cudaSuccess)
+      return CC_ECUDA;
+    // geometry tables (do not change after creation)
+    std::vector<RowGeo> rg;
+    std::vector<ZGeo> zg;
+    rg.reserve(nrow);
+    zg.reserve(nz);
+    for (auto& in : c->inst) {
+      const int N = in.d.nr - 1, M = in.d.nz - 1;
+      for (int i = 0; i <= N; ++i) {
+        RowGeo g{};
+        g.cls = in.cls[i];
+        g.seg = in.seg[i];
+        g.segw = i > 0 ? in.seg[i - 1] : in.seg[0];
+        if (i > 0 && i < N) {
+          const double hw = in.r[i] - in.r[i - 1], he = in.r[i + 1] - in.r[i];
+          const double hbar = 0.5 * (hw + he);
+          const double rw = 0.5 * (in.r[i] + in.r[i - 1]), re = 0.5 * (in.r[i] + in.r[i + 1]);
+          g.hw = hw;
+          g.he = he;
+          g.rw = rw;
+          g.re = re;
+          g.gA = rw / (in.r[i] * hbar * hw);
+          g.gC = re / (in.r[i] * hbar * he);
+          g.V2 = 2.0 * M_PI * in.r[i] * hbar;
+        }
+        rg.push_back(g);
+      }
+      double wsum = 0.0;
+      std::vector<double> w(M + 1, 0.0);
+      for (int j = 0; j <= M; ++j) {
+        if (j > 0) w[j] += 0.5 * (in.z[j] - in.z[j - 1]);
+        if (j < M) w[j] += 0.5 * (in.z[j + 1] - in.z[j]);
+        wsum += w[j];
+      }
+      for (int j = 0; j <= M; ++j) {
+        ZGeo q{};
+        q.wnorm = w[j] / wsum;
+        if (j > 0 && j < M) {
+          const double es = in.z[j] - in.z[j - 1], en = in.z[j + 1] - in.z[j];
+          const double eb = 0.5 * (es + en);
+          q.eta_s = es;
+          q.eta_n = en;
+          q.etabar = eb;
+          q.gzs = 1.0 / (eb * es);
+          q.gzn = 1.0 / (eb * en);
+        }
+        zg.push_back(q);
+      }
+    }
+    if (cudaMemcpy(c->d_rg, rg.data(), sizeof(RowGeo) * rg.size(), cudaMemcpyHostToDevice) !=
+            cudaSuccess ||
+        cudaMemcpy(c->d_zg, zg.data(), sizeof(ZGeo) * zg.size(), cudaMemcpyHostToDevice) !=
+            cudaSuccess)
+      return CC_ECUDA;
+    c->dirty = true;
+  } else {
+    int cur = -1;
+    cudaGetDevice(&cur);
+    if (cur != c->device) return CC_EINVAL;
+  }
+  if (!c->dirty && dts == c->uploaded_dt) return CC_OK;
+  std::vector<DevInst> h(n);
+  size_t rofs = 0, zofs = 0;
+  for (int k = 0; k < n; ++k) {
+    const Instance& in = c->inst[k];
+    DevInst& D = h[k];
+    std::memset(&D, 0, sizeof D);
+    D.nr = in.d.nr;
+    D.nz = in.d.nz;
+    D.G = in.G;
+    D.bc_rmax = in.d.bc_rmax;
+    D.bc_z0 = in.d.bc_z0;
+    D.bc_zmax = in.d.bc_zmax;
+    D.face_rule = in.d.face_rule;
+    D.interface_rule = in.d.interface_rule;
+    D.src_layer = in.src.layer;
+    D.waveform = in.src.waveform;
+    D.g_model = in.src.g_model;
+    D.t_off = in.t_off;
+    D.t_d = in.d.t_dirichlet_K;
+    D.tau = dts[k];
+    D.inv_tau = 1.0 / dts[k];
+    D.q0 = in.src.q0;
+    D.t_period = in.src.t_period;
+    D.t_on = in.src.t_on;
+    D.t_start = in.src.t_start;
+    D.edge_w = in.src.edge_w;
+    D.g_ref = in.src.g_ref;
+    D.rg = c->d_rg + rofs;
+    D.zg = c->d_zg + zofs;
+    rofs += in.d.nr;
+    zofs += in.d.nz;
+    for (int m = 0; m < in.d.n_layers; ++m) {
+      const cc_material& s = in.mat[m];
+      DevMaterial& t = D.mat[m];
+      t.rho = s.rho;
+      t.lam_model = s.lam_model;
+      t.cap_model = s.cap_model;
+      t.lam0s = s.lam0 * s.lam_scale;
+      t.lam_b = s.lam_b;
+      t.inv_tref = 1.0 / s.t_ref;
+      t.c0s = s.c0 * s.cap_scale;
+      t.inv_theta = 1.0 / s.theta;
+      for (int q = 0; q < 5; ++q) t.lam_poly[q] = s.lam_poly[q] * s.lam_scale;
+      for (int q = 0; q < 4; ++q) t.cap_poly[q] = s.cap_poly[q] * s.cap_scale;
+    }
+  }
+  if (cudaMemcpyAsync(c->d_inst, h.data(), sizeof(DevInst) * n, cudaMemcpyHostToDevice, st) !=
+      cudaSuccess)
+    return CC_ECUDA;
+  if (cudaStreamSynchronize(st) != cudaSuccess) return CC_ECUDA;
+  c->uploaded_dt = dts;
+  c->dirty = false;
+  return CC_OK;
+}
+
+bool valid_material(const cc_material& m) {
+  if (!(m.rho > 0.0) || !(m.lam_scale > 0.0) || !(m.cap_scale > 0.0)) return false;
+  if (m.lam_model < 0 || m.lam_model > 2 || m.cap_model < 0 || m.cap_model > 2) return false;
+  if (m.lam_model == 1 && !(m.t_ref > 0.0)) return false;
+  if (m.cap_model == 1 && (!(m.t_ref > 0.0) || !(m.theta > 0.0))) return false;
+  return true;
+}
+
+}  // namespace
+
+extern "C" {
+
+int cc_create_geometry(const cc_geometry_desc* desc, int32_t n_instances, cc_ctx** out) {
+  if (!desc || !out || n_instances < 1) return CC_EINVAL;
+  *out = nullptr;
+  cc_ctx* c = new (std::nothrow) cc_ctx();
+  if (!c) return CC_ENOMEM;
+  c->precision = desc[0].precision;
+  long long off = 0;
+  for (int k = 0; k < n_instances; ++k) {
+    const int v = valid_desc(desc[k]);
+    if (v != CC_OK || desc[k].precision != c->precision) {
+      delete c;
+      return v != CC_OK ? v : CC_EINVAL;
+    }
+    Instance in;
+    in.d = desc[k];
+    build_grid(in.d, in.r, in.z, in.cls, in.seg);
+    in.G = choose_lanes(in.d.nr);
+    in.t_off = off;
+    in.src.layer = -1;
+    off += (long long)in.d.nr * in.d.nz;
+    c->inst.push_back(std::move(in));
+  }
+  c->total_nodes = off;
+  *out = c;
+  return CC_OK;
+}
+
+int cc_set_materials(cc_ctx* c, int32_t instance, const cc_material* m) {
+  if (!c || !m) return CC_EINVAL;
+  if (instance < -1 || instance >= (int)c->inst.size()) return CC_EINVAL;
+  const int k0 = instance < 0 ? 0 : instance;
+  const int k1 = instance < 0 ? (int)c->inst.size() : instance + 1;
+  for (int k = k0; k < k1; ++k)
+    for (int q = 0; q < c->inst[k].d.n_layers; ++q)
+      if (!valid_material(m[q])) return CC_EINVAL;
+  for (int k = k0; k < k1; ++k) {
+    std::memcpy(c->inst[k].mat, m, sizeof(cc_material) * c->inst[k].d.n_layers);
+    c->inst[k].mat_set = true;
+  }
+  c->dirty = true;
+  return CC_OK;
+}
+
+int cc_set_source(cc_ctx* c, int32_t instance, const cc_source* s) {
+  if (!c || !s) return CC_EINVAL;
+  if (instance < -1 || instance >= (int)c->inst.size()) return CC_EINVAL;
+  const int k0 = instance < 0 ? 0 : instance;
+  const int k1 = instance < 0 ? (int)c->inst.size() : instance + 1;
+  for (int k = k0; k < k1; ++k) {
+    if (s->layer < -1 || s->layer >= c->inst[k].d.n_layers) return CC_EINVAL;
+    if (s->layer >= 0) {
+      if (!(s->t_period > 0.0) || !(s->t_on >= 0.0) || s->waveform < 0 || s->waveform > 1 ||
+          s->g_model < 0 || s->g_model > 1 || !std::isfinite(s->q0))
+        return CC_EINVAL;
+      if (s->waveform == 1 && !(s->edge_w > 0.0)) return CC_EINVAL;
+    }
+  }
+  for (int k = k0; k < k1; ++k) c->inst[k].src = *s;
+  c->dirty = true;
+  return CC_OK;
+}
+
+int cc_set_dt(cc_ctx* c, int32_t instance, double dt) {
+  if (!c || !(dt > 0.0) || !std::isfinite(dt)) return CC_EINVAL;
+  if (instance < -1 || instance >= (int)c->inst.size()) return CC_EINVAL;
+  for (int k = 0; k < (int)c->inst.size(); ++k)
+    if (instance < 0 || k == instance) c->inst[k].dt = dt;
+  return CC_OK;
+}
+
+int cc_tau_stab(const cc_ctx* c, int32_t instance, double* out) {
+  if (!c || !out || instance < 0 || instance >= (int)c->inst.size()) return CC_EINVAL;
+  if (!c->inst[instance].mat_set) return CC_ESTATE;
+  *out = tau_stab(c->inst[instance]);
+  return CC_OK;
+}
+
+int cc_step_n(cc_ctx* c, void* T_dev, int64_t n_steps, double t0, double dt_s, double* trace_dev,
+              double* energy_dev, void* stream) {
+  if (!c || !T_dev || n_steps < 0 || !std::isfinite(t0)) return CC_EINVAL;
+  if (c->failed) return CC_ESTATE;
+  if (n_steps == 0) return CC_OK;
+  const int n = (int)c->inst.size();
+  std::vector<double> dts(n);
+  for (int k = 0; k < n; ++k) {
+    Instance& in = c->inst[k];
+    if (!in.mat_set) return CC_ESTATE;
+    dts[k] = dt_s > 0.0 ? dt_s : in.dt;
+    if (!(dts[k] > 0.0) || !std::isfinite(dts[k])) return CC_EINVAL;
+    if (dts[k] > tau_stab(in) * (1.0 + 1e-12) && !force_unstable()) return CC_EUNSTABLE;
+  }
+  cudaStream_t st = (cudaStream_t)stream;
+  int rc = upload(c, dts, st);
+  if (rc != CC_OK) return rc;
+  if (c->s_cap < n_steps * n) {
+    cudaFree(c->d_s);
+    c->d_s = nullptr;
+    c->s_cap = 0;
+    if (cudaMalloc(&c->d_s, sizeof(double) * n_steps * n) != cudaSuccess) {
+      cudaGetLastError();
+      return CC_ENOMEM;
+    }
+    c->s_cap = n_steps * n;
+  }
+  if (launch_waveform(c->d_inst, n, n_steps, t0, c->d_s, stream)) return CC_ECUDA;
+  if (trace_dev &&
+      cudaMemsetAsync(trace_dev, 0, sizeof(double) * 2 * n_steps * n, st) != cudaSuccess)
+    return CC_ECUDA;
+  const size_t elem = c->precision == CC_FP64 ? sizeof(double) : sizeof(float);
+  StepArgs a{};
+  a.insts = c->d_inst;
+  a.tasks = c->d_tasks;
+  a.n_tasks = c->n_tasks;
+  a.n_inst = n;
+  a.s_tab = c->d_s;
+  a.trace = trace_dev;
+  a.n_steps = n_steps;
+  a.energy = energy_dev;
+  a.err = c->d_err;
+  void* bufs[2] = {T_dev, c->d_T2};
+  if (c->precision == CC_MIXED) {
+    if (launch_mixed_init(c->d_inst, n, c->d_tasks, c->n_tasks, c->d_lo, c->total_nodes, stream))
+      return CC_EUNSUPPORTED;
+  }
+  for (long long s = 0; s < n_steps; ++s) {
+    a.step = s;
+    a.Tin = bufs[s & 1];
+    a.Tout = bufs[(s + 1) & 1];
+    int r;
+    if (c->precision == CC_FP64) {
+      r = launch_step_fp64(a, stream);
+    } else {
+      a.lo_in = c->d_lo + (s & 1) * c->total_nodes;
+      a.lo_out = c->d_lo + ((s + 1) & 1) * c->total_nodes;
+      r = launch_step_mixed(a, stream);
+      if (r == -2) return CC_EUNSUPPORTED;
+    }
+    if (r) return CC_ECUDA;
+  }
+  if (n_steps & 1) {
+    if (cudaMemcpyAsync(T_dev, c->d_T2, elem * c->total_nodes, cudaMemcpyDeviceToDevice, st) !=
+        cudaSuccess)
+      return CC_ECUDA;
+  }
+  return CC_OK;
+}
+
+int cc_sync(cc_ctx* c, void* stream) {
+  if (!c) return CC_EINVAL;
+  if (c->failed) return c->failed;
+  if (c->device < 0) return CC_OK;
+  if (cudaStreamSynchronize((cudaStream_t)stream) != cudaSuccess) {
+    c->failed = CC_ECUDA;
+    return CC_ECUDA;
+  }
+  unsigned e = 0;
+  if (cudaMemcpy(&e, c->d_err, sizeof e, cudaMemcpyDeviceToHost) != cudaSuccess) {
+    c->failed = CC_ECUDA;
+    return CC_ECUDA;
+  }
+  if (e & 1u) {
+    c->failed = CC_ENONFINITE;
+    return CC_ENONFINITE;
+  }
+  if (e & 2u) {
+    c->failed = CC_ETIMEOUT;
+    return CC_ETIMEOUT;
+  }
+  return CC_OK;
+}
+
+int cc_adjoint(cc_ctx* c, const void*, int64_t, double, double, const double*, int32_t, double*,
+               double*, void*, void*) {
+  if (!c) return CC_EINVAL;
+  return CC_EUNSUPPORTED;
+}
+
+int cc_destroy(cc_ctx* c) {
+  if (!c) return CC_OK;
+  if (c->device >= 0) {
+    int cur = -1;
+    cudaGetDevice(&cur);
+    if (cur != c->device) cudaSetDevice(c->device);
+    free_device(c);
+    if (cur >= 0 && cur != c->device) cudaSetDevice(cur);
+  }
+  delete c;
+  return CC_OK;
+}
+
+int cc_query_grid(const cc_geometry_desc* d, double* r, double* z, int32_t* rclass) {
+  if (!d) return CC_EINVAL;
+  const int v = valid_desc(*d);
+  if (v != CC_OK) return v;
+  std::vector<double> rr, zz;
+  std::vector<int> cls, seg;
+  build_grid(*d, rr, zz, cls, seg);
+  if (r) std::memcpy(r, rr.data(), sizeof(double) * rr.size());
+  if (z) std::memcpy(z, zz.data(), sizeof(double) * zz.size());
+  if (rclass)
+    for (size_t i = 0; i < cls.size(); ++i) rclass[i] = cls[i];
+  return CC_OK;
+}
+
+const char* cc_status_string(int s) {
+  switch (s) {
+    case CC_OK: return "ok";
+    case CC_EINVAL: return "invalid argument";
+    case CC_ENOMEM: return "out of memory";
+    case CC_ECUDA: return "CUDA error";
+    case CC_EUNSTABLE: return "time step above the axial stability bound";
+    case CC_ETIMEOUT: return "bounded device wait expired";
+    case CC_ENONFINITE: return "non-finite temperature";
+    case CC_ESTATE: return "context not configured or unusable after a failure";
+    case CC_EUNSUPPORTED: return "not supported by this build";
+    default: return "unknown status";
+  }
+}
+
+int64_t cc_kernel_launches(void) { return kernel_launch_count(); }
+
+}  // extern "C"

@@ -1,0 +1,106 @@
+// Internal layouts shared by the host side (ccell_api.cpp) and the kernels
+// (ccell_step.cu).  Not part of the public ABI.
+#pragma once
+#include <cstdint>
+
+#include "../../include/ccell.h"
+
+namespace ccell {
+
+enum : int { RC_AXIS = 0, RC_REGULAR = 1, RC_IFACE = 2, RC_OUTER = 3 };
+
+// Largest number of rows one lane eliminates sequentially; a line of nr rows
+// is split over G lanes (G a power of two, G <= 32), so nr <= 32 * kRowsPerLane.
+constexpr int kRowsPerLane = 16;
+constexpr int kMaxNr = 32 * kRowsPerLane;
+
+// Per radial node i of one instance (index i in [0, nr)).
+struct RowGeo {
+  double gA;   // r_{i-1/2} / (r_i hbar_i h_i)      (Eq. (ABC), coefficient of lambda_{i-1/2})
+  double gC;   // r_{i+1/2} / (r_i hbar_i h_{i+1})  (coefficient of lambda_{i+1/2})
+  double hw;   // h_i     = r_i - r_{i-1}
+  double he;   // h_{i+1} = r_{i+1} - r_i
+  double rw;   // r_{i-1/2}
+  double re;   // r_{i+1/2}
+  double V2;   // 2 pi r_i hbar_i (radial part of the control volume)
+  int cls;     // RC_*
+  int seg;     // layer of the segment [r_i, r_{i+1}] (regular node: its layer)
+  int segw;    // layer of the segment [r_{i-1}, r_i]
+  int pad;
+};
+
+// Per axial node j (index j in [0, nz)).
+struct ZGeo {
+  double gzs;    // 1 / (etabar_j eta_j)
+  double gzn;    // 1 / (etabar_j eta_{j+1})
+  double etabar; // (eta_j + eta_{j+1}) / 2
+  double wnorm;  // trapezoid weight of z_j divided by the sum of weights
+  double eta_s;  // eta_j
+  double eta_n;  // eta_{j+1}
+};
+
+// Material of one layer, with the user scales folded in.
+struct DevMaterial {
+  double rho;
+  double lam0s;      // lam0 * lam_scale
+  double lam_b;
+  double inv_tref;
+  double c0s;        // c0 * cap_scale
+  double inv_theta;
+  double lam_poly[5];  // * lam_scale
+  double cap_poly[4];  // * cap_scale
+  int lam_model, cap_model;
+};
+
+struct DevInst {
+  int nr, nz;            // nodes
+  int G;                 // lanes per line
+  int bc_rmax, bc_z0, bc_zmax;
+  int face_rule, interface_rule;
+  int src_layer, waveform, g_model;
+  int pad0;
+  long long t_off;       // element offset of this instance in T
+  double t_d;            // Dirichlet temperature
+  double tau, inv_tau;   // time step and its reciprocal
+  double q0, t_period, t_on, t_start, edge_w, g_ref;
+  const RowGeo* rg;      // [nr]
+  const ZGeo* zg;        // [nz]
+  DevMaterial mat[CC_MAX_LAYERS];
+};
+
+// One warp's work: 32/G consecutive lines of one instance.
+struct Task {
+  int inst;
+  int j0;
+};
+
+// Everything one step launch needs.
+struct StepArgs {
+  const DevInst* insts;
+  const Task* tasks;
+  int n_tasks;
+  int n_inst;
+  const void* Tin;       // double* (FP64) or float* (mixed, high part)
+  void* Tout;
+  const float* lo_in;    // mixed: low-order part of the state (or null)
+  float* lo_out;
+  const double* s_tab;   // [n_steps][n_inst] waveform values
+  long long step;        // step index within the call
+  double* trace;         // [n_inst][n_steps][2] or null
+  long long n_steps;
+  double* energy;        // [n_inst][5] or null
+  unsigned* err;         // error word: bit0 non-finite
+};
+
+// kernels (ccell_step.cu)
+int launch_waveform(const DevInst* insts, int n_inst, long long n_steps, double t0,
+                    double* s_tab, void* stream);
+int launch_step_fp64(const StepArgs& a, void* stream);
+int launch_step_mixed(const StepArgs& a, void* stream);
+int launch_mixed_init(const DevInst* insts, int n_inst, const Task* tasks, int n_tasks,
+                      float* lo, long long n_total, void* stream);
+int launch_boundary_trace_zero(double* trace, long long n, void* stream);
+long long kernel_launch_count();
+void count_launch();
+
+}  // namespace ccell

@@ -1,0 +1,154 @@
+"""GPU parity of the FP64 path against the oracle (element by element).
+
+The bar (FP64 path): max |dT| <= 1e-9 K against the oracle on the same seeded
+inputs, for the field and the surface trace; energy terms to 1e-9 relative.
+Sizes span several lane segments and warps with ragged tails; edge cases cover
+the smallest grids, every boundary-condition flag, both interface and face
+rules, the half-cell placement, both waveforms, odd/even step counts, several
+calls in a row and ragged multi-instance contexts.  At the production size
+(512 x 4096) the CUDA path runs in the same launch configuration as the bench
+and sampled lines are compared with the oracle run on their dependence cone.
+"""
+import copy
+
+import numpy as np
+import pytest
+
+from gpu_helpers import oracle_cone, run_gpu
+from oracle import oracle
+from paper_1408_5853_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+TOL_K = 1e-9
+
+
+def _cmp(cfg, T0, n, t0=0.0, energy_rel=1e-9, **kw):
+    (Tg,), trg, eg = run_gpu(cfg, T0, n, t0=t0, **kw)
+    To, tro, eo = oracle.step_n(cfg, T0, n, t0, cfg["dt"])
+    err = np.max(np.abs(Tg - To))
+    assert err <= TOL_K, f"field max|dT| = {err:.3e} K"
+    terr = np.max(np.abs(trg[0] - tro))
+    assert terr <= TOL_K, f"trace max|dT| = {terr:.3e} K"
+    scale = max(abs(eo[0]), abs(eo[1]), 1e-300)
+    eerr = np.max(np.abs(eg[0] - eo)) / scale
+    assert eerr <= energy_rel, f"energy rel err {eerr:.3e}: gpu {eg[0]} oracle {eo}"
+    return Tg, To, trg[0], eg[0]
+
+
+def test_small_case_parity_across_pulse_edge():
+    cfg = inputs.small_case()
+    T0 = inputs.initial_field(cfg, "smooth", seed=0)
+    # t0 just before the end of the first pulse: the source switches off mid-run
+    _cmp(cfg, T0, 301, t0=1e-3 - 150 * cfg["dt"])
+
+
+def test_small_case_identity_closes():
+    cfg = inputs.small_case()
+    T0 = inputs.initial_field(cfg)
+    _, _, _, e = _cmp(cfg, T0, 200)
+    assert abs(e[0] - e[1:].sum()) <= 1e-11 * max(abs(e[0]), abs(e[1]))
+
+
+@pytest.mark.parametrize("nr,nz", [(3, 3), (4, 5), (9, 7), (17, 33), (37, 19), (100, 40),
+                                   (255, 11), (300, 9), (511, 6), (512, 5)])
+def test_ragged_sizes(nr, nz):
+    cfg = inputs.small_case()
+    if nr < 12:  # fewer layers for tiny radial grids (at least 2 cells per layer)
+        cfg["layers"] = cfg["layers"][:1] if nr < 5 else cfg["layers"][:2]
+        cfg["source"]["layer"] = 0
+    cfg.update(nr=nr, nz=nz)
+    T0 = inputs.initial_field(cfg, "smooth", seed=nr + nz)
+    cfg["dt"] = min(5e-7, 0.5 * oracle.tau_stab(cfg, 20.0, 100.0))  # keep T physical
+    _cmp(cfg, T0, 7)
+
+
+@pytest.mark.parametrize("variant", ["rmax_dirichlet", "z0_dirichlet", "zmax_neumann",
+                                     "face_rule_1", "interface_rule_1", "g_model_1",
+                                     "tanh_waveform", "no_source", "placement_1"])
+def test_flag_variants(variant):
+    cfg = inputs.small_case()
+    cfg.update(nr=45, nz=50)
+    if variant == "rmax_dirichlet":
+        cfg["bc_rmax"] = 1
+    elif variant == "z0_dirichlet":
+        cfg["bc_z0"] = 1
+    elif variant == "zmax_neumann":
+        cfg["bc_zmax"] = 0
+    elif variant == "face_rule_1":
+        cfg["face_rule"] = 1
+    elif variant == "interface_rule_1":
+        cfg["interface_rule"] = 1
+    elif variant == "g_model_1":
+        cfg["source"].update(g_model=1, g_ref=4.0)
+    elif variant == "tanh_waveform":
+        cfg["source"].update(waveform=1, edge_w=2e-5)
+    elif variant == "no_source":
+        cfg["source"] = None
+    elif variant == "placement_1":
+        cfg["layers"] = cfg["layers"][2:3]
+        cfg["layers"][0]["thickness"] = 0.3e-3
+        cfg["placement"] = 1
+        cfg["source"]["layer"] = 0
+    cfg["dt"] = min(5e-7, 0.5 * oracle.tau_stab(cfg, 20.0, 100.0))
+    T0 = inputs.initial_field(cfg, "smooth", seed=5)
+    _cmp(cfg, T0, 40, t0=1e-3 - 20 * cfg["dt"])
+
+
+def test_several_calls_match_one_run():
+    cfg = inputs.small_case()
+    T0 = inputs.initial_field(cfg, "smooth", seed=2)
+    (Tg,), trg, eg = run_gpu(cfg, T0, 60, chunks=[1, 2, 17, 40])
+    To, tro, eo = oracle.step_n(cfg, T0, 60, 0.0, cfg["dt"])
+    assert np.max(np.abs(Tg - To)) <= TOL_K
+    assert np.max(np.abs(trg[0] - tro)) <= TOL_K
+    assert np.max(np.abs(eg[0] - eo)) <= 1e-9 * abs(eo[1])
+
+
+def test_ragged_multi_instance():
+    cfgs = inputs.batched_cases(seed=1, n=6)
+    T0s = []
+    for k, c in enumerate(cfgs):
+        c["dt"] = 0.9 * oracle.tau_stab(c, 20.0, 100.0)
+        T0s.append(inputs.initial_field(c, "smooth", seed=k))
+    n = 9
+    Tg, trg, eg = run_gpu(cfgs, T0s, n)
+    for k, c in enumerate(cfgs):
+        To, tro, eo = oracle.step_n(c, T0s[k], n, 0.0, c["dt"])
+        assert np.max(np.abs(Tg[k] - To)) <= TOL_K, k
+        assert np.max(np.abs(trg[k] - tro)) <= TOL_K, k
+        assert np.max(np.abs(eg[k] - eo)) <= 1e-9 * max(abs(eo[0]), abs(eo[1])), k
+
+
+def test_unstable_dt_refused():
+    from paper_1408_5853_gb300 import ccell
+    cfg = inputs.small_case()
+    cfg["dt"] = 2.0 * oracle.tau_stab(cfg, 20.0, 100.0)
+    with pytest.raises(ccell.CCError) as e:
+        run_gpu(cfg, inputs.initial_field(cfg), 2)
+    assert e.value.status == ccell.CC_EUNSTABLE
+
+
+def test_non_finite_reported():
+    from paper_1408_5853_gb300 import ccell
+    cfg = inputs.small_case()
+    T0 = inputs.initial_field(cfg)
+    T0[40, 30] = np.nan
+    with pytest.raises(ccell.CCError) as e:
+        run_gpu(cfg, T0, 3)
+    assert e.value.status == ccell.CC_ENONFINITE
+
+
+def test_production_size_sampled_lines():
+    """512 x 4096, bench launch configuration; lines near both z-ends, the
+    middle and a pulse edge compared with the oracle on their dependence cone."""
+    cfg = inputs.production_case()
+    T0 = inputs.initial_field(cfg, "smooth", seed=0)
+    n, t0 = 24, 1e-3 - 12 * cfg["dt"]
+    (Tg,), trg, eg = run_gpu(cfg, T0, n, t0=t0)
+    M = cfg["nz"] - 1
+    for j in (0, 1, 2, 7, 1000, 2047, 3001, M - 2, M - 1, M):
+        ref = oracle_cone(cfg, T0, j, n, t0, cfg["dt"])
+        err = np.max(np.abs(Tg[j] - ref))
+        assert err <= TOL_K, f"line {j}: max|dT| = {err:.3e} K"
+    e = eg[0]
+    assert abs(e[0] - e[1:].sum()) <= 1e-9 * max(abs(e[0]), abs(e[1]))
