@@ -202,6 +202,46 @@ int cc_adjoint(cc_ctx* ctx, const void* T0_dev, int64_t n_steps, double t0_s, do
 /* Release the context and everything it owns.  NULL is accepted. */
 int cc_destroy(cc_ctx* ctx);
 
+/* ---- no-allocation variant --------------------------------------------- */
+
+/* Limits of cc_step_n_noalloc (they size its static device scratch array). */
+#define CC_NOALLOC_MAX_NR 512
+#define CC_NOALLOC_MAX_NZ 16384
+#define CC_NOALLOC_MAX_NODES (1 << 20)   /* nr * nz */
+#define CC_NOALLOC_MAX_STEPS 65536       /* n_steps per call */
+
+/*
+ * cc_step_n for one FP64 instance, for callers that cannot allocate device
+ * memory.  The paper has no counterpart to this entry point; it exists
+ * because some callers cannot call cudaMalloc (an embedding framework whose
+ * allocator owns the device memory, loops that forbid allocation after
+ * start-up), while cc_step_n allocates its context tables and scratch on
+ * first use.  This call allocates nothing, on the device or the host: its
+ * scratch (tables, work list, waveform table, error word, and the ping-pong
+ * partner of T_dev) lives in a file-scope static device array of about
+ * 9.5 MiB that every GPU loading the library holds until the process exits.
+ *   desc        geometry (precision must be CC_FP64); materials[n_layers];
+ *               source (layer -1 for none).  Same meaning as cc_create_geometry,
+ *               cc_set_materials and cc_set_source.
+ *   T_dev       caller-owned device double[nz][nr], advanced in place.
+ *   trace_dev, energy_dev  as in cc_step_n (one instance), or NULL.
+ *   dt_s        time step, > 0.
+ * Limits: nr <= CC_NOALLOC_MAX_NR, nz <= CC_NOALLOC_MAX_NZ,
+ * nr * nz <= CC_NOALLOC_MAX_NODES, n_steps <= CC_NOALLOC_MAX_STEPS; larger
+ * requests return CC_EINVAL before any device work.
+ * The first call on a device looks up the device address of the static array
+ * (cudaGetSymbolAddress, with that device current); make that first call
+ * before any stream capture.  All calls share the array and it keeps the
+ * last call's contents: calls whose work overlaps on the GPU (different
+ * streams or host threads) race and must be serialised by the caller.
+ * The call waits for its own work on `stream` before returning, so that it can
+ * report CC_ENONFINITE.  Errors: CC_EINVAL, CC_EUNSTABLE, CC_ECUDA,
+ * CC_ENONFINITE.
+ */
+int cc_step_n_noalloc(const cc_geometry_desc* desc, const cc_material* materials,
+                      const cc_source* source, double* T_dev, int64_t n_steps, double t0_s,
+                      double dt_s, double* trace_dev, double* energy_dev, void* stream);
+
 /* ---- host-only queries (no GPU needed) ---------------------------------- */
 
 /* Node positions and radial classes of one descriptor: r[nr], z[nz],

@@ -7,7 +7,7 @@ no CPU fallback.
 
 Low-level functions carry the C names (``cc_create_geometry``,
 ``cc_set_materials``, ``cc_set_source``, ``cc_set_dt``, ``cc_step_n``,
-``cc_sync``, ``cc_adjoint``, ``cc_destroy``, ``cc_query_grid``,
+``cc_sync``, ``cc_adjoint``, ``cc_destroy``, ``cc_step_n_noalloc``, ``cc_query_grid``,
 ``cc_tau_stab``, ``cc_status_string``, ``cc_kernel_launches``).  ``Solver``
 builds a context from the problem dicts of ``inputs``.
 """
@@ -89,6 +89,10 @@ def _load():
     lib.cc_status_string.argtypes = [ctypes.c_int]
     lib.cc_status_string.restype = ctypes.c_char_p
     lib.cc_kernel_launches.restype = ctypes.c_int64
+    lib.cc_step_n_noalloc.argtypes = [ctypes.POINTER(GeometryDesc), ctypes.POINTER(Material),
+                                      ctypes.POINTER(Source), vp, ctypes.c_int64, _d, _d, vp,
+                                      vp, vp]
+    lib.cc_step_n_noalloc.restype = ctypes.c_int
     for name in ("cc_create_geometry", "cc_set_materials", "cc_set_source", "cc_set_dt",
                  "cc_step_n", "cc_sync", "cc_adjoint", "cc_destroy", "cc_query_grid",
                  "cc_tau_stab"):
@@ -148,6 +152,16 @@ def cc_adjoint(ctx, T0_ptr, n_steps, t0, dt, target_ptr, ckpt_every, loss_ptr, g
     _check(_load().cc_adjoint(ctx, T0_ptr, int(n_steps), float(t0), float(dt), target_ptr,
                               int(ckpt_every), loss_ptr, grad_ptr, dT0_ptr, stream_ptr),
            "cc_adjoint")
+
+
+def cc_step_n_noalloc(desc: GeometryDesc, materials_list, source_struct: Source, T_ptr: int,
+                      n_steps: int, t0: float, dt: float, trace_ptr, energy_ptr,
+                      stream_ptr) -> None:
+    """One FP64 instance, no device allocation (scratch in a static device array)."""
+    arr = (Material * len(materials_list))(*materials_list)
+    _check(_load().cc_step_n_noalloc(ctypes.byref(desc), arr, ctypes.byref(source_struct), T_ptr,
+                                     int(n_steps), float(t0), float(dt), trace_ptr, energy_ptr,
+                                     stream_ptr), "cc_step_n_noalloc")
 
 
 def cc_destroy(ctx) -> None:
