@@ -46,6 +46,7 @@ struct cc_ctx {
   void* d_T2 = nullptr;       // ping-pong partner of the caller's field
   float* d_lo = nullptr;      // mixed precision: low-order parts (two buffers)
   double* d_s = nullptr;      // waveform table
+  double* d_ptab = nullptr;   // power-law tables [instance][layer][kPowTabLen]
   long long s_cap = 0;
   unsigned* d_err = nullptr;
   std::vector<double> uploaded_dt;
@@ -203,6 +204,7 @@ void free_device(cc_ctx* c) {
   cudaFree(c->d_T2);
   cudaFree(c->d_lo);
   cudaFree(c->d_s);
+  cudaFree(c->d_ptab);
   cudaFree(c->d_err);
   c->d_inst = nullptr;
   c->d_rg = nullptr;
@@ -211,6 +213,7 @@ void free_device(cc_ctx* c) {
   c->d_T2 = nullptr;
   c->d_lo = nullptr;
   c->d_s = nullptr;
+  c->d_ptab = nullptr;
   c->d_err = nullptr;
   c->s_cap = 0;
 }
@@ -238,6 +241,7 @@ int upload(cc_ctx* c, const std::vector<double>& dts, cudaStream_t st) {
         cudaMalloc(&c->d_zg, sizeof(ZGeo) * nz) != cudaSuccess ||
         cudaMalloc(&c->d_tasks, sizeof(Task) * tasks.size()) != cudaSuccess ||
         cudaMalloc(&c->d_T2, elem * c->total_nodes) != cudaSuccess ||
+        cudaMalloc(&c->d_ptab, sizeof(double) * kPowTabLen * CC_MAX_LAYERS * n) != cudaSuccess ||
         cudaMalloc(&c->d_err, sizeof(unsigned)) != cudaSuccess) {
       free_device(c);
       c->device = -1;
@@ -316,6 +320,7 @@ int upload(cc_ctx* c, const std::vector<double>& dts, cudaStream_t st) {
   }
   if (!c->dirty && dts == c->uploaded_dt) return CC_OK;
   std::vector<DevInst> h(n);
+  std::vector<double> ptab((size_t)kPowTabLen * CC_MAX_LAYERS * n, 0.0);
   size_t rofs = 0, zofs = 0;
   for (int k = 0; k < n; ++k) {
     const Instance& in = c->inst[k];
@@ -359,9 +364,19 @@ int upload(cc_ctx* c, const std::vector<double>& dts, cudaStream_t st) {
       t.inv_theta = 1.0 / s.theta;
       for (int q = 0; q < 5; ++q) t.lam_poly[q] = s.lam_poly[q] * s.lam_scale;
       for (int q = 0; q < 4; ++q) t.cap_poly[q] = s.cap_poly[q] * s.cap_scale;
+      t.ptab = nullptr;
+      if (s.lam_model == 1) {
+        const size_t ofs = ((size_t)k * CC_MAX_LAYERS + m) * kPowTabLen;
+        const double lam0s = s.lam0 * s.lam_scale;
+        if (build_pow_table(s.lam_b, lam0s * std::pow(2.0 * s.t_ref, -s.lam_b),
+                            lam0s * std::pow(s.t_ref, -s.lam_b), ptab.data() + ofs))
+          t.ptab = c->d_ptab + ofs;
+      }
     }
   }
-  if (cudaMemcpyAsync(c->d_inst, h.data(), sizeof(DevInst) * n, cudaMemcpyHostToDevice, st) !=
+  if (cudaMemcpyAsync(c->d_ptab, ptab.data(), sizeof(double) * ptab.size(),
+                      cudaMemcpyHostToDevice, st) != cudaSuccess ||
+      cudaMemcpyAsync(c->d_inst, h.data(), sizeof(DevInst) * n, cudaMemcpyHostToDevice, st) !=
       cudaSuccess)
     return CC_ECUDA;
   if (cudaStreamSynchronize(st) != cudaSuccess) return CC_ECUDA;

@@ -39,6 +39,17 @@ struct ZGeo {
   double eta_n;  // eta_{j+1}
 };
 
+// Power-law tables: x^b = 2^(e b) * p_q(m - c_q) for x = m 2^e, m in [1, 2),
+// with 2^kPowBits mantissa intervals q of centre c_q and degree-kPowDeg
+// polynomials p_q; binary exponents e in [kPowEmin, kPowEmin + kPowNE).
+constexpr int kPowBits = 7;
+constexpr int kPowQ = 1 << kPowBits;
+constexpr int kPowDeg = 5;
+constexpr int kPowEmin = -2;
+constexpr int kPowNE = 16;
+// per layer: [face scale kPowNE][node scale kPowNE][kPowQ][kPowDeg + 1]
+constexpr int kPowTabLen = 2 * kPowNE + kPowQ * (kPowDeg + 1);
+
 // Material of one layer, with the user scales folded in.
 struct DevMaterial {
   double rho;
@@ -49,6 +60,7 @@ struct DevMaterial {
   double inv_theta;
   double lam_poly[5];  // * lam_scale
   double cap_poly[4];  // * cap_scale
+  const double* ptab;  // power-law table (kPowTabLen doubles) or null: use pow()
   int lam_model, cap_model;
 };
 
@@ -101,6 +113,9 @@ int launch_mixed_init(const DevInst* insts, int n_inst, const Task* tasks, int n
                       float* lo, long long n_total, void* stream);
 int launch_boundary_trace_zero(double* trace, long long n, void* stream);
 long long kernel_launch_count();
+// Host: fill one power-law table for exponent b and scales; returns false if
+// the polynomial fit misses the accuracy bound (the kernel then calls pow).
+bool build_pow_table(double b, double face_scale, double node_scale, double* tab);
 void count_launch();
 
 }  // namespace ccell

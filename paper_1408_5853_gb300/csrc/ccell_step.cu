@@ -36,8 +36,42 @@ constexpr unsigned kFull = 0xffffffffu;
 // ---------------------------------------------------------------------------
 // material functions (FP64)
 // ---------------------------------------------------------------------------
+// 1/d to about 1 ulp: hardware approximation of the reciprocal of the high
+// word, then one cubic Newton step (e = 1 - d r, r (1 + e + e^2)).
+__device__ __forceinline__ double frcp(double d) {
+  double r;
+  asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(r) : "d"(d));
+  const double e = fma(-d, r, 1.0);
+  return fma(fma(e, e, e), r, r);
+}
+
+// Power law lam0 (x / t_ref)^b from the material's table: y = m 2^e with
+// m in [1, 2); the scale row e holds lam0 (k t_ref)^-b 2^(e b) (k = 2 for a
+// face, where y = T_a + T_b, k = 1 for a node, where y = T), and m^b is a
+// degree-5 polynomial in m - c_q on mantissa interval q.  Arguments outside
+// the table (or non-finite, or <= 0) take the exact pow path.
+__device__ __forceinline__ double lam_pow(const DevMaterial& M, double y, bool face) {
+  const long long bits = __double_as_longlong(y);
+  const int e = (int)(bits >> 52) - 1023 - kPowEmin;
+  if (M.ptab != nullptr && (unsigned)e < (unsigned)kPowNE) {
+    const unsigned q = (unsigned)(bits >> (52 - kPowBits)) & (kPowQ - 1);
+    const double m = __longlong_as_double((bits & 0x000FFFFFFFFFFFFFLL) | 0x3FF0000000000000LL);
+    const double c = __longlong_as_double(0x3FF0000000000000LL | ((long long)q << (52 - kPowBits)) |
+                                          (1LL << (51 - kPowBits)));
+    const double* P = M.ptab + 2 * kPowNE + q * (kPowDeg + 1);
+    const double u = m - c;
+    double r = fma(__ldg(P + 5), u, __ldg(P + 4));
+    r = fma(r, u, __ldg(P + 3));
+    r = fma(r, u, __ldg(P + 2));
+    r = fma(r, u, __ldg(P + 1));
+    r = fma(r, u, __ldg(P + 0));
+    return r * __ldg(M.ptab + (face ? 0 : kPowNE) + e);
+  }
+  return M.lam0s * pow((face ? 0.5 * y : y) * M.inv_tref, M.lam_b);
+}
+
 __device__ __forceinline__ double lam_eval(const DevMaterial& M, double T) {
-  if (M.lam_model == 1) return M.lam0s * pow(T * M.inv_tref, M.lam_b);
+  if (M.lam_model == 1) return lam_pow(M, T, false);
   if (M.lam_model == 0) return M.lam0s;
   const double* b = M.lam_poly;
   return fma(fma(fma(fma(b[4], T, b[3]), T, b[2]), T, b[1]), T, b[0]);
@@ -45,14 +79,17 @@ __device__ __forceinline__ double lam_eval(const DevMaterial& M, double T) {
 
 __device__ __forceinline__ double lam_face(const DevMaterial& M, int rule, double Ta,
                                            double Tb) {
-  if (rule == 0) return lam_eval(M, 0.5 * (Ta + Tb));
+  if (rule == 0) {
+    if (M.lam_model == 1) return lam_pow(M, Ta + Tb, true);
+    return lam_eval(M, 0.5 * (Ta + Tb));
+  }
   return 0.5 * (lam_eval(M, Ta) + lam_eval(M, Tb));
 }
 
 __device__ __forceinline__ double cap_eval(const DevMaterial& M, double T) {
   if (M.cap_model == 1) {
     const double x = T * M.inv_tref, y = T * M.inv_theta;
-    return M.c0s * (x * x * x) / fma(y * y, y, 1.0);
+    return M.c0s * (x * x * x) * frcp(fma(y * y, y, 1.0));
   }
   if (M.cap_model == 0) return M.c0s;
   const double* a = M.cap_poly;
@@ -222,7 +259,7 @@ __global__ void __launch_bounds__(128) step_fp64_kernel(const StepArgs a) {
       mm[k] = m;
       if (k < cnt - 1) {
         const double den = (k == 0) ? rb : fma(-ra, pc, rb);
-        const double r = 1.0 / den;
+        const double r = frcp(den);
         const double c1 = rc * r;
         const double a1 = (k == 0) ? ra * r : -ra * pa * r;
         const double d1 = (k == 0) ? rd * r : fma(-ra, pd, rd) * r;
@@ -252,7 +289,7 @@ __global__ void __launch_bounds__(128) step_fp64_kernel(const StepArgs a) {
   double ct = -ce * C2n;
   double dt = fma(-ae, pd, de) - ce * D2n;
   for (int d = 1; d < G; d <<= 1) {  // parallel cyclic reduction
-    const double ib = 1.0 / bt;
+    const double ib = frcp(bt);
     const double am = __shfl_up_sync(kFull, at, d, G);
     const double cm = __shfl_up_sync(kFull, ct, d, G);
     const double dm = __shfl_up_sync(kFull, dt, d, G);
@@ -270,7 +307,7 @@ __global__ void __launch_bounds__(128) step_fp64_kernel(const StepArgs a) {
     bt = nb;
     dt = nd;
   }
-  const double xs = dt / bt;  // this lane's separator (last row)
+  const double xs = dt * frcp(bt);  // this lane's separator (last row)
 
   // ---- 3. back substitution inside the segment
   const double L = __shfl_up_sync(kFull, xs, 1, G);
