@@ -198,6 +198,8 @@ def run_ours(args, world, rank, local):
                  "hbm_frac_effective": BYTES_PER_NODE_MIXED * nodes * n_in * args.steps * world
                  / (msm / 1e3) / (_peaks()["hbm_gbs"] * 1e9)}
         solm.close()
+        if args.acc_steps > 0:
+            mixed.update(mixed_accuracy(cfg, T0, args.acc_steps, dev))
     except ccell.CCError as err:
         mixed = {"unavailable": str(err)}
 
@@ -235,6 +237,35 @@ def run_ours(args, world, rank, local):
     if world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(args.cpu_sample_steps)
     return line
+
+
+def mixed_accuracy(cfg, T0, n, dev) -> dict:
+    """Mixed path against the FP64 path (itself parity-checked against the
+    oracle to 1e-9 K) from the same FP32-rounded field, n steps from t = 0
+    (heater on): max |dT| over the field, surface-trace peak error, and the
+    energy-identity residuals of both."""
+    import numpy as np
+    import torch
+
+    from paper_1408_5853_gb300 import ccell
+    T0 = np.asarray(T0, dtype=np.float32).astype(np.float64).ravel()
+    out = {}
+    for prec, dt in ((ccell.FP64, torch.float64), (ccell.MIXED, torch.float32)):
+        sol = ccell.Solver(cfg, precision=prec)
+        T = torch.tensor(T0, dtype=dt, device=dev)
+        tr = torch.zeros(2 * n, dtype=torch.float64, device=dev)
+        en = torch.zeros(5, dtype=torch.float64, device=dev)
+        sol.step(T, n, 0.0, 0.0, tr, en)
+        sol.sync()
+        out[prec] = (T.double(), tr.view(n, 2), en.cpu().numpy())
+        sol.close()
+    (Td, trd, ed), (Tm, trm, em) = out[ccell.FP64], out[ccell.MIXED]
+    ident = lambda e: float(abs(e[0] - e[1:].sum()) / max(abs(e[0]), abs(e[1])))
+    return {"acc_steps": n,
+            "max_dT_vs_fp64_K": float((Tm - Td).abs().max().item()),
+            "surface_peak_err_K": float(abs(trm[:, 1].max().item() - trd[:, 1].max().item())),
+            "surface_trace_max_err_K": float((trm - trd).abs().max().item()),
+            "energy_identity_rel": ident(em), "energy_identity_rel_fp64": ident(ed)}
 
 
 def cpu_baseline(sample_steps: int) -> dict:
@@ -295,6 +326,8 @@ def main():
     ap.add_argument("--ref-inner", type=int, default=60, help="time steps per reference step")
     ap.add_argument("--cpu-sample-steps", type=int, default=300)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--acc-steps", type=int, default=20000,
+                    help="steps of the mixed-vs-FP64 accuracy check (0: skip)")
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3) if args.impl == "ours" else args.warmup

@@ -283,6 +283,13 @@ int upload(cc_ctx* c, const std::vector<double>& dts, cudaStream_t st) {
           g.gC = re / (in.r[i] * hbar * he);
           g.V2 = 2.0 * M_PI * in.r[i] * hbar;
         }
+        g.gA_f = (float)g.gA;
+        g.gC_f = (float)g.gC;
+        g.hw_f = (float)g.hw;
+        g.he_f = (float)g.he;
+        g.rw_f = (float)g.rw;
+        g.re_f = (float)g.re;
+        g.V2_f = (float)g.V2;
         rg.push_back(g);
       }
       double wsum = 0.0;
@@ -304,6 +311,9 @@ int upload(cc_ctx* c, const std::vector<double>& dts, cudaStream_t st) {
           q.gzs = 1.0 / (eb * es);
           q.gzn = 1.0 / (eb * en);
         }
+        q.gzs_f = (float)q.gzs;
+        q.gzn_f = (float)q.gzn;
+        q.etabar_f = (float)q.etabar;
         zg.push_back(q);
       }
     }
@@ -347,6 +357,12 @@ int upload(cc_ctx* c, const std::vector<double>& dts, cudaStream_t st) {
     D.t_start = in.src.t_start;
     D.edge_w = in.src.edge_w;
     D.g_ref = in.src.g_ref;
+    D.tau_f = (float)D.tau;
+    D.inv_tau_f = (float)D.inv_tau;
+    D.q0_f = (float)D.q0;
+    D.g_ref_f = (float)D.g_ref;
+    D.td_hi = (float)D.t_d;
+    D.td_lo = (float)(D.t_d - (double)D.td_hi);
     D.rg = c->d_rg + rofs;
     D.zg = c->d_zg + zofs;
     rofs += in.d.nr;
@@ -364,6 +380,14 @@ int upload(cc_ctx* c, const std::vector<double>& dts, cudaStream_t st) {
       t.inv_theta = 1.0 / s.theta;
       for (int q = 0; q < 5; ++q) t.lam_poly[q] = s.lam_poly[q] * s.lam_scale;
       for (int q = 0; q < 4; ++q) t.cap_poly[q] = s.cap_poly[q] * s.cap_scale;
+      t.rho_f = (float)t.rho;
+      t.lam0s_f = (float)t.lam0s;
+      t.lam_b_f = (float)t.lam_b;
+      t.inv_tref_f = (float)t.inv_tref;
+      t.c0s_f = (float)t.c0s;
+      t.inv_theta_f = (float)t.inv_theta;
+      for (int q = 0; q < 5; ++q) t.lam_poly_f[q] = (float)t.lam_poly[q];
+      for (int q = 0; q < 4; ++q) t.cap_poly_f[q] = (float)t.cap_poly[q];
       t.ptab = nullptr;
       if (s.lam_model == 1) {
         const size_t ofs = ((size_t)k * CC_MAX_LAYERS + m) * kPowTabLen;
@@ -519,7 +543,7 @@ int cc_step_n(cc_ctx* c, void* T_dev, int64_t n_steps, double t0, double dt_s, d
   void* bufs[2] = {T_dev, c->d_T2};
   if (c->precision == CC_MIXED) {
     if (launch_mixed_init(c->d_inst, n, c->d_tasks, c->n_tasks, c->d_lo, c->total_nodes, stream))
-      return CC_EUNSUPPORTED;
+      return CC_ECUDA;
   }
   for (long long s = 0; s < n_steps; ++s) {
     a.step = s;
@@ -532,7 +556,6 @@ int cc_step_n(cc_ctx* c, void* T_dev, int64_t n_steps, double t0, double dt_s, d
       a.lo_in = c->d_lo + (s & 1) * c->total_nodes;
       a.lo_out = c->d_lo + ((s + 1) & 1) * c->total_nodes;
       r = launch_step_mixed(a, stream);
-      if (r == -2) return CC_EUNSUPPORTED;
     }
     if (r) return CC_ECUDA;
   }

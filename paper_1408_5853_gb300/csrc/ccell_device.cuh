@@ -1,0 +1,119 @@
+// Device helpers shared by the FP64 and mixed-precision step kernels.
+#pragma once
+#include <cuda_runtime.h>
+
+#include "ccell_internal.h"
+
+namespace ccell {
+
+constexpr unsigned kFull = 0xffffffffu;
+
+// ---------------------------------------------------------------------------
+// material functions (FP64)
+// ---------------------------------------------------------------------------
+// 1/d to about 1 ulp: hardware approximation of the reciprocal of the high
+// word, then one cubic Newton step (e = 1 - d r, r (1 + e + e^2)).
+__device__ __forceinline__ double frcp(double d) {
+  double r;
+  asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(r) : "d"(d));
+  const double e = fma(-d, r, 1.0);
+  return fma(fma(e, e, e), r, r);
+}
+
+// Power law lam0 (x / t_ref)^b from the material's table: y = m 2^e with
+// m in [1, 2); the scale row e holds lam0 (k t_ref)^-b 2^(e b) (k = 2 for a
+// face, where y = T_a + T_b, k = 1 for a node, where y = T), and m^b is a
+// degree-5 polynomial in m - c_q on mantissa interval q.  Arguments outside
+// the table (or non-finite, or <= 0) take the exact pow path.
+__device__ __forceinline__ double lam_pow(const DevMaterial& M, double y, bool face) {
+  const long long bits = __double_as_longlong(y);
+  const int e = (int)(bits >> 52) - 1023 - kPowEmin;
+  if (M.ptab != nullptr && (unsigned)e < (unsigned)kPowNE) {
+    const unsigned q = (unsigned)(bits >> (52 - kPowBits)) & (kPowQ - 1);
+    const double m = __longlong_as_double((bits & 0x000FFFFFFFFFFFFFLL) | 0x3FF0000000000000LL);
+    const double c = __longlong_as_double(0x3FF0000000000000LL | ((long long)q << (52 - kPowBits)) |
+                                          (1LL << (51 - kPowBits)));
+    const double* P = M.ptab + 2 * kPowNE + q * (kPowDeg + 1);
+    const double u = m - c;
+    double r = fma(__ldg(P + 5), u, __ldg(P + 4));
+    r = fma(r, u, __ldg(P + 3));
+    r = fma(r, u, __ldg(P + 2));
+    r = fma(r, u, __ldg(P + 1));
+    r = fma(r, u, __ldg(P + 0));
+    return r * __ldg(M.ptab + (face ? 0 : kPowNE) + e);
+  }
+  return M.lam0s * pow((face ? 0.5 * y : y) * M.inv_tref, M.lam_b);
+}
+
+__device__ __forceinline__ double lam_eval(const DevMaterial& M, double T) {
+  if (M.lam_model == 1) return lam_pow(M, T, false);
+  if (M.lam_model == 0) return M.lam0s;
+  const double* b = M.lam_poly;
+  return fma(fma(fma(fma(b[4], T, b[3]), T, b[2]), T, b[1]), T, b[0]);
+}
+
+__device__ __forceinline__ double lam_face(const DevMaterial& M, int rule, double Ta,
+                                           double Tb) {
+  if (rule == 0) {
+    if (M.lam_model == 1) return lam_pow(M, Ta + Tb, true);
+    return lam_eval(M, 0.5 * (Ta + Tb));
+  }
+  return 0.5 * (lam_eval(M, Ta) + lam_eval(M, Tb));
+}
+
+__device__ __forceinline__ double cap_eval(const DevMaterial& M, double T) {
+  if (M.cap_model == 1) {
+    const double x = T * M.inv_tref, y = T * M.inv_theta;
+    return M.c0s * (x * x * x) * frcp(fma(y * y, y, 1.0));
+  }
+  if (M.cap_model == 0) return M.c0s;
+  const double* a = M.cap_poly;
+  return fma(fma(fma(a[3], T, a[2]), T, a[1]), T, a[0]);
+}
+
+__device__ __forceinline__ bool not_finite(double x) {
+  const unsigned hi = (unsigned)(__double_as_longlong(x) >> 32);
+  return (hi & 0x7ff00000u) == 0x7ff00000u;
+}
+
+// Phase 2 of a line solve.  Lane l of a group of G lanes holds the separator
+// row of its segment (row e_l: a x_{e-1} + b x_e + c x_{e+1} = d) plus, from
+// its downward elimination, the normalised last interior row
+// (x_{e-1} + pc x_e + pa x_{e_{l-1}} = pd) and the expression of its first
+// interior row in the two neighbouring separators (Dacc + P x_e - Aacc x_{e_{l-1}}).
+// Substituting the neighbours' rows gives a tridiagonal system in the G
+// separators, solved by parallel cyclic reduction over warp shuffles.
+// Returns x at this lane's separator.
+__device__ __forceinline__ double solve_separators(double ae, double be, double ce, double de,
+                                                   double pa, double pc, double pd, double Dacc,
+                                                   double Aacc, double P, int G, int l) {
+  const double D2n = __shfl_down_sync(kFull, Dacc, 1, G);
+  const double A2n = __shfl_down_sync(kFull, Aacc, 1, G);
+  const double C2n = -__shfl_down_sync(kFull, P, 1, G);
+  double at = -ae * pa;
+  double bt = fma(-ae, pc, be) - ce * A2n;
+  double ct = -ce * C2n;
+  double dt = fma(-ae, pd, de) - ce * D2n;
+  for (int d = 1; d < G; d <<= 1) {
+    const double ib = frcp(bt);
+    const double am = __shfl_up_sync(kFull, at, d, G);
+    const double cm = __shfl_up_sync(kFull, ct, d, G);
+    const double dm = __shfl_up_sync(kFull, dt, d, G);
+    const double ibm = __shfl_up_sync(kFull, ib, d, G);
+    const double apv = __shfl_down_sync(kFull, at, d, G);
+    const double cpv = __shfl_down_sync(kFull, ct, d, G);
+    const double dpv = __shfl_down_sync(kFull, dt, d, G);
+    const double ibp = __shfl_down_sync(kFull, ib, d, G);
+    const double al = (l >= d) ? -at * ibm : 0.0;
+    const double ga = (l + d < G) ? -ct * ibp : 0.0;
+    const double nb = fma(ga, apv, fma(al, cm, bt));
+    const double nd = fma(ga, dpv, fma(al, dm, dt));
+    at = al * am;
+    ct = ga * cpv;
+    bt = nb;
+    dt = nd;
+  }
+  return dt * frcp(bt);
+}
+
+}  // namespace ccell

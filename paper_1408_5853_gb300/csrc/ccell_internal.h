@@ -23,6 +23,7 @@ struct RowGeo {
   double rw;   // r_{i-1/2}
   double re;   // r_{i+1/2}
   double V2;   // 2 pi r_i hbar_i (radial part of the control volume)
+  float gA_f, gC_f, hw_f, he_f, rw_f, re_f, V2_f;  // FP32 copies (mixed precision)
   int cls;     // RC_*
   int seg;     // layer of the segment [r_i, r_{i+1}] (regular node: its layer)
   int segw;    // layer of the segment [r_{i-1}, r_i]
@@ -37,6 +38,7 @@ struct ZGeo {
   double wnorm;  // trapezoid weight of z_j divided by the sum of weights
   double eta_s;  // eta_j
   double eta_n;  // eta_{j+1}
+  float gzs_f, gzn_f, etabar_f, pad_f;  // FP32 copies (mixed precision)
 };
 
 // Power-law tables: x^b = 2^(e b) * p_q(m - c_q) for x = m 2^e, m in [1, 2),
@@ -61,6 +63,9 @@ struct DevMaterial {
   double lam_poly[5];  // * lam_scale
   double cap_poly[4];  // * cap_scale
   const double* ptab;  // power-law table (kPowTabLen doubles) or null: use pow()
+  // FP32 copies (mixed precision)
+  float rho_f, lam0s_f, lam_b_f, inv_tref_f, c0s_f, inv_theta_f;
+  float lam_poly_f[5], cap_poly_f[4];
   int lam_model, cap_model;
 };
 
@@ -75,6 +80,8 @@ struct DevInst {
   double t_d;            // Dirichlet temperature
   double tau, inv_tau;   // time step and its reciprocal
   double q0, t_period, t_on, t_start, edge_w, g_ref;
+  float tau_f, inv_tau_f, q0_f, g_ref_f;  // FP32 copies (mixed precision)
+  float td_hi, td_lo;    // Dirichlet temperature as an FP32 pair
   const RowGeo* rg;      // [nr]
   const ZGeo* zg;        // [nz]
   DevMaterial mat[CC_MAX_LAYERS];

@@ -23,83 +23,13 @@
 #include <atomic>
 #include <cmath>
 
-#include "ccell_internal.h"
+#include "ccell_device.cuh"
 
 namespace ccell {
 
 static std::atomic<long long> g_launches{0};
 void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
 long long kernel_launch_count() { return g_launches.load(std::memory_order_relaxed); }
-
-constexpr unsigned kFull = 0xffffffffu;
-
-// ---------------------------------------------------------------------------
-// material functions (FP64)
-// ---------------------------------------------------------------------------
-// 1/d to about 1 ulp: hardware approximation of the reciprocal of the high
-// word, then one cubic Newton step (e = 1 - d r, r (1 + e + e^2)).
-__device__ __forceinline__ double frcp(double d) {
-  double r;
-  asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(r) : "d"(d));
-  const double e = fma(-d, r, 1.0);
-  return fma(fma(e, e, e), r, r);
-}
-
-// Power law lam0 (x / t_ref)^b from the material's table: y = m 2^e with
-// m in [1, 2); the scale row e holds lam0 (k t_ref)^-b 2^(e b) (k = 2 for a
-// face, where y = T_a + T_b, k = 1 for a node, where y = T), and m^b is a
-// degree-5 polynomial in m - c_q on mantissa interval q.  Arguments outside
-// the table (or non-finite, or <= 0) take the exact pow path.
-__device__ __forceinline__ double lam_pow(const DevMaterial& M, double y, bool face) {
-  const long long bits = __double_as_longlong(y);
-  const int e = (int)(bits >> 52) - 1023 - kPowEmin;
-  if (M.ptab != nullptr && (unsigned)e < (unsigned)kPowNE) {
-    const unsigned q = (unsigned)(bits >> (52 - kPowBits)) & (kPowQ - 1);
-    const double m = __longlong_as_double((bits & 0x000FFFFFFFFFFFFFLL) | 0x3FF0000000000000LL);
-    const double c = __longlong_as_double(0x3FF0000000000000LL | ((long long)q << (52 - kPowBits)) |
-                                          (1LL << (51 - kPowBits)));
-    const double* P = M.ptab + 2 * kPowNE + q * (kPowDeg + 1);
-    const double u = m - c;
-    double r = fma(__ldg(P + 5), u, __ldg(P + 4));
-    r = fma(r, u, __ldg(P + 3));
-    r = fma(r, u, __ldg(P + 2));
-    r = fma(r, u, __ldg(P + 1));
-    r = fma(r, u, __ldg(P + 0));
-    return r * __ldg(M.ptab + (face ? 0 : kPowNE) + e);
-  }
-  return M.lam0s * pow((face ? 0.5 * y : y) * M.inv_tref, M.lam_b);
-}
-
-__device__ __forceinline__ double lam_eval(const DevMaterial& M, double T) {
-  if (M.lam_model == 1) return lam_pow(M, T, false);
-  if (M.lam_model == 0) return M.lam0s;
-  const double* b = M.lam_poly;
-  return fma(fma(fma(fma(b[4], T, b[3]), T, b[2]), T, b[1]), T, b[0]);
-}
-
-__device__ __forceinline__ double lam_face(const DevMaterial& M, int rule, double Ta,
-                                           double Tb) {
-  if (rule == 0) {
-    if (M.lam_model == 1) return lam_pow(M, Ta + Tb, true);
-    return lam_eval(M, 0.5 * (Ta + Tb));
-  }
-  return 0.5 * (lam_eval(M, Ta) + lam_eval(M, Tb));
-}
-
-__device__ __forceinline__ double cap_eval(const DevMaterial& M, double T) {
-  if (M.cap_model == 1) {
-    const double x = T * M.inv_tref, y = T * M.inv_theta;
-    return M.c0s * (x * x * x) * frcp(fma(y * y, y, 1.0));
-  }
-  if (M.cap_model == 0) return M.c0s;
-  const double* a = M.cap_poly;
-  return fma(fma(fma(a[3], T, a[2]), T, a[1]), T, a[0]);
-}
-
-__device__ __forceinline__ bool not_finite(double x) {
-  const unsigned hi = (unsigned)(__double_as_longlong(x) >> 32);
-  return (hi & 0x7ff00000u) == 0x7ff00000u;
-}
 
 // ---------------------------------------------------------------------------
 // waveform table: s[n][k] = s(t_n) of instance k, t_n = t0 + n tau_k
@@ -149,12 +79,9 @@ int launch_waveform(const DevInst* insts, int n_inst, long long n_steps, double 
 // ---------------------------------------------------------------------------
 // FP64 step
 // ---------------------------------------------------------------------------
+// One warp task: 32/G consecutive lines of one instance.
 template <bool ENERGY, bool TRACE>
-__global__ void __launch_bounds__(128) step_fp64_kernel(const StepArgs a) {
-  const int wid = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
-  if (wid >= a.n_tasks) return;  // uniform per warp
-  const int lane = threadIdx.x & 31;
-  const Task tk = a.tasks[wid];
+__device__ __forceinline__ void step_fp64_task(const StepArgs& a, const Task tk, const int lane) {
   const DevInst& I = a.insts[tk.inst];
   const int G = I.G;
   const int lg = __ffs(G) - 1;
@@ -280,34 +207,8 @@ __global__ void __launch_bounds__(128) step_fp64_kernel(const StepArgs a) {
     }
   }
 
-  // ---- 2. separator system: row e_l couples the separators of lanes l-1, l, l+1
-  const double D2n = __shfl_down_sync(kFull, Dacc, 1, G);
-  const double A2n = __shfl_down_sync(kFull, Aacc, 1, G);
-  const double C2n = -__shfl_down_sync(kFull, P, 1, G);
-  double at = -ae * pa;
-  double bt = fma(-ae, pc, be) - ce * A2n;
-  double ct = -ce * C2n;
-  double dt = fma(-ae, pd, de) - ce * D2n;
-  for (int d = 1; d < G; d <<= 1) {  // parallel cyclic reduction
-    const double ib = frcp(bt);
-    const double am = __shfl_up_sync(kFull, at, d, G);
-    const double cm = __shfl_up_sync(kFull, ct, d, G);
-    const double dm = __shfl_up_sync(kFull, dt, d, G);
-    const double ibm = __shfl_up_sync(kFull, ib, d, G);
-    const double apv = __shfl_down_sync(kFull, at, d, G);
-    const double cpv = __shfl_down_sync(kFull, ct, d, G);
-    const double dpv = __shfl_down_sync(kFull, dt, d, G);
-    const double ibp = __shfl_down_sync(kFull, ib, d, G);
-    const double al = (l >= d) ? -at * ibm : 0.0;
-    const double ga = (l + d < G) ? -ct * ibp : 0.0;
-    const double nb = fma(ga, apv, fma(al, cm, bt));
-    const double nd = fma(ga, dpv, fma(al, dm, dt));
-    at = al * am;
-    ct = ga * cpv;
-    bt = nb;
-    dt = nd;
-  }
-  const double xs = dt * frcp(bt);  // this lane's separator (last row)
+  // ---- 2. separator system (one row per lane), cyclic reduction
+  const double xs = solve_separators(ae, be, ce, de, pa, pc, pd, Dacc, Aacc, P, G, l);
 
   // ---- 3. back substitution inside the segment
   const double L = __shfl_up_sync(kFull, xs, 1, G);
@@ -412,22 +313,42 @@ __global__ void __launch_bounds__(128) step_fp64_kernel(const StepArgs a) {
   }
 }
 
-int launch_step_fp64(const StepArgs& a, void* stream) {
-  const int threads = 128;
-  const int blocks = (a.n_tasks * 32 + threads - 1) / threads;
-  cudaStream_t st = (cudaStream_t)stream;
-  const bool E = a.energy != nullptr, T = a.trace != nullptr;
-  if (E && T) step_fp64_kernel<true, true><<<blocks, threads, 0, st>>>(a);
-  else if (E) step_fp64_kernel<true, false><<<blocks, threads, 0, st>>>(a);
-  else if (T) step_fp64_kernel<false, true><<<blocks, threads, 0, st>>>(a);
-  else step_fp64_kernel<false, false><<<blocks, threads, 0, st>>>(a);
-  count_launch();
-  return cudaGetLastError() == cudaSuccess ? 0 : -1;
+// Persistent grid: as many blocks as can be resident, each warp looping over
+// tasks with a grid stride, so that no partial last wave leaves SMs idle.
+template <bool ENERGY, bool TRACE>
+__global__ void __launch_bounds__(128) step_fp64_kernel(const StepArgs a) {
+  const int lane = threadIdx.x & 31;
+  const int n_warps = (int)((gridDim.x * blockDim.x) >> 5);
+  for (int w = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5); w < a.n_tasks; w += n_warps)
+    step_fp64_task<ENERGY, TRACE>(a, a.tasks[w], lane);
 }
 
-int launch_step_mixed(const StepArgs&, void*) { return -2; }
-int launch_mixed_init(const DevInst*, int, const Task*, int, float*, long long, void*) {
-  return -2;
+template <bool ENERGY, bool TRACE>
+static int launch_fp64_variant(const StepArgs& a, cudaStream_t st) {
+  constexpr int threads = 128;
+  static int resident = 0;  // blocks per SM x SMs, per variant (one device per process)
+  if (resident == 0) {
+    int dev = 0, sms = 0, per_sm = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, step_fp64_kernel<ENERGY, TRACE>,
+                                                  threads, 0);
+    resident = sms * (per_sm > 0 ? per_sm : 1);
+  }
+  const int need = (a.n_tasks * 32 + threads - 1) / threads;
+  step_fp64_kernel<ENERGY, TRACE><<<need < resident ? need : resident, threads, 0, st>>>(a);
+  return 0;
+}
+
+int launch_step_fp64(const StepArgs& a, void* stream) {
+  cudaStream_t st = (cudaStream_t)stream;
+  const bool E = a.energy != nullptr, T = a.trace != nullptr;
+  if (E && T) launch_fp64_variant<true, true>(a, st);
+  else if (E) launch_fp64_variant<true, false>(a, st);
+  else if (T) launch_fp64_variant<false, true>(a, st);
+  else launch_fp64_variant<false, false>(a, st);
+  count_launch();
+  return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }
 
 }  // namespace ccell
