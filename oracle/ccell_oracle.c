@@ -458,3 +458,311 @@ void or_set_threads(int n) {
   (void)n;
 #endif
 }
+
+/* ------------------------------------------------------------------ */
+/* discrete adjoint of or_step_n                                       */
+/* ------------------------------------------------------------------ */
+/*
+ * One step maps T^n to That = T^{n+1}: for every line j = 1..M-1 the rows
+ * a_i That_{i-1} + b_i That_i + c_i That_{i+1} = f_i (regular rows: Eq. (ABC);
+ * interface rows: Eq. (cc_first_1) written as (-lm h_{i*+1}, lm h_{i*+1} +
+ * lp h_{i*}, -lp h_{i*} | 0); closures of Eq. (first_oder_bc)), then the axial
+ * boundary rows.  The coefficients depend on T^n through lambda, c and X, and
+ * on the parameters theta = (q0, t_on, lam_scale[m], cap_scale[m]).
+ *
+ * Given mu = dJ/dThat, the adjoint of a line solve is xi = M^{-T} mu, and
+ * dJ/dT^n, dJ/dtheta follow from the residual r_i = f_i - (a_i y_{i-1} +
+ * b_i y_i + c_i y_{i+1}) with y = That held fixed: dJ/dv = sum_i xi_i dr_i/dv.
+ */
+
+/* d lambda_m / dT */
+static double dlam_m(const or_problem* p, int m, double T) {
+  double v;
+  switch (p->lam_model[m]) {
+    case 0: v = 0.0; break;
+    case 1: v = p->lam0[m] * p->lam_b[m] * pow(T / p->t_ref[m], p->lam_b[m] - 1.0) / p->t_ref[m]; break;
+    default: {
+      const double* b = p->lam_poly[m];
+      v = b[1] + 2.0 * b[2] * T + 3.0 * b[3] * T * T + 4.0 * b[4] * T * T * T;
+    }
+  }
+  return p->lam_scale[m] * v;
+}
+
+/* d c_m / dT */
+static double dcap_m(const or_problem* p, int m, double T) {
+  double v;
+  switch (p->cap_model[m]) {
+    case 0: v = 0.0; break;
+    case 1: {
+      double x = T / p->t_ref[m], y = T / p->theta[m], d = 1.0 + y * y * y;
+      /* c0 x^3 / (1 + y^3): derivative 3 c0 x^2 / t_ref / (1+y^3) - c0 x^3 3 y^2 / theta / (1+y^3)^2 */
+      v = p->c0[m] * (3.0 * x * x / p->t_ref[m] / d - x * x * x * 3.0 * y * y / p->theta[m] / (d * d));
+    } break;
+    default: {
+      const double* a = p->cap_poly[m];
+      v = a[1] + 2.0 * a[2] * T + 3.0 * a[3] * T * T;
+    }
+  }
+  return p->cap_scale[m] * v;
+}
+
+/* face conductivity and its derivatives with respect to the two temperatures */
+static void lam_face_d(const or_problem* p, int m, double Ta, double Tb, double* l, double* da,
+                       double* db) {
+  if (p->face_rule == 0) {
+    double Tm = 0.5 * (Ta + Tb);
+    *l = lam_m(p, m, Tm);
+    *da = *db = 0.5 * dlam_m(p, m, Tm);
+  } else {
+    *l = 0.5 * (lam_m(p, m, Ta) + lam_m(p, m, Tb));
+    *da = 0.5 * dlam_m(p, m, Ta);
+    *db = 0.5 * dlam_m(p, m, Tb);
+  }
+}
+
+/* d s / d t_on of the waveform at time t */
+static double dwave_dton(const or_problem* p, double t) {
+  if (p->waveform == 0) return 0.0;
+  double u = t - p->t_start;
+  double k = floor((u - 0.5 * p->t_on) / p->t_period + 0.5);
+  if (k < 0.0) k = 0.0;
+  double phi = u - k * p->t_period;
+  double th = tanh((phi - p->t_on) / p->edge_w);
+  return 0.5 * (1.0 - th * th) / p->edge_w;
+}
+
+/* g(T) of the source and its derivative */
+static double src_g(const or_problem* p, double T) {
+  return (p->g_model == 1) ? p->g_ref / sqrt(T) : 1.0;
+}
+static double src_dg(const or_problem* p, double T) {
+  return (p->g_model == 1) ? -0.5 * p->g_ref / (T * sqrt(T)) : 0.0;
+}
+
+/*
+ * Vector-Jacobian product of one step.  x: T^n, y: T^{n+1} (as produced by
+ * or_step_n from x), mu: dJ/dT^{n+1} (modified: the axial boundary rows are
+ * folded into lines 1 and M-1).  Adds dJ/dT^n to xbar and dJ/dtheta to gbar
+ * (2 + 2 n_layers: q0, t_on, lam_scale[], cap_scale[]).
+ */
+int or_step_vjp(const or_problem* p, const double* x, const double* y, double* mu, double tn,
+                double tau, double* xbar, double* gbar) {
+  const int N = p->nr - 1, M = p->nz - 1, nr = p->nr, L = p->n_layers;
+  double* r = (double*)malloc(sizeof(double) * (N + 1));
+  double* z = (double*)malloc(sizeof(double) * (M + 1));
+  int* cls = (int*)malloc(sizeof(int) * (N + 1));
+  int* seg = (int*)malloc(sizeof(int) * (N + 1));
+  double* a = (double*)malloc(sizeof(double) * (N + 1));
+  double* b = (double*)malloc(sizeof(double) * (N + 1));
+  double* c = (double*)malloc(sizeof(double) * (N + 1));
+  double* xi = (double*)malloc(sizeof(double) * (N + 1));
+  double* cw = (double*)malloc(sizeof(double) * (N + 1));
+  double* dw = (double*)malloc(sizeof(double) * (N + 1));
+  if (!r || !z || !cls || !seg || !a || !b || !c || !xi || !cw || !dw || or_grid(p, r, z, cls, seg)) {
+    free(r); free(z); free(cls); free(seg); free(a); free(b); free(c); free(xi); free(cw); free(dw);
+    return -1;
+  }
+  const double s = or_waveform(p, tn);
+  const double ds_dton = (p->src_layer >= 0) ? dwave_dton(p, tn) : 0.0;
+  /* axial boundary rows: That_0 = That_1 (Neumann) or T_D; That_M likewise */
+  for (int i = 0; i <= N; i++) {
+    if (!p->bc_z0) mu[(size_t)nr + i] += mu[i];
+    mu[i] = 0.0;
+    if (!p->bc_zmax) mu[(size_t)(M - 1) * nr + i] += mu[(size_t)M * nr + i];
+    mu[(size_t)M * nr + i] = 0.0;
+  }
+  for (int j = 1; j <= M - 1; j++) {
+    const double* Tj = x + (size_t)j * nr;
+    const double* Ts = x + (size_t)(j - 1) * nr;
+    const double* Tn = x + (size_t)(j + 1) * nr;
+    const double* yj = y + (size_t)j * nr;
+    const double* mj = mu + (size_t)j * nr;
+    double* xb = xbar + (size_t)j * nr;
+    double* xbs = xbar + (size_t)(j - 1) * nr;
+    double* xbn = xbar + (size_t)(j + 1) * nr;
+    const double eta_s = z[j] - z[j - 1], eta_n = z[j + 1] - z[j];
+    const double etabar = 0.5 * (eta_n + eta_s);
+    /* rows of the line system */
+    for (int i = 0; i <= N; i++) {
+      if (i == 0) { a[i] = 0.0; b[i] = 1.0; c[i] = -1.0; continue; }
+      if (i == N) {
+        if (p->bc_rmax) { a[i] = 0.0; b[i] = 1.0; c[i] = 0.0; }
+        else { a[i] = -1.0; b[i] = 1.0; c[i] = 0.0; }
+        continue;
+      }
+      const double h_w = r[i] - r[i - 1], h_e = r[i + 1] - r[i];
+      if (cls[i] == OR_IFACE) {
+        double lm, lp;
+        if (p->interface_rule == 0) {
+          lm = lam_m(p, seg[i - 1], Tj[i]);
+          lp = lam_m(p, seg[i], Tj[i]);
+        } else {
+          lm = 0.5 * (r[i] + r[i - 1]) * lam_face(p, seg[i - 1], Tj[i - 1], Tj[i]);
+          lp = 0.5 * (r[i] + r[i + 1]) * lam_face(p, seg[i], Tj[i], Tj[i + 1]);
+        }
+        a[i] = -lm * h_e; b[i] = lm * h_e + lp * h_w; c[i] = -lp * h_w;
+        continue;
+      }
+      const int m = seg[i];
+      const double hbar = 0.5 * (h_e + h_w);
+      const double r_w = 0.5 * (r[i] + r[i - 1]), r_e = 0.5 * (r[i] + r[i + 1]);
+      const double lw = lam_face(p, m, Tj[i - 1], Tj[i]);
+      const double le = lam_face(p, m, Tj[i], Tj[i + 1]);
+      const double rc = p->rho[m] * cap_m(p, m, Tj[i]);
+      a[i] = -r_w * lw / (r[i] * hbar * h_w);
+      c[i] = -r_e * le / (r[i] * hbar * h_e);
+      b[i] = (r_w * lw / h_w + r_e * le / h_e) / (r[i] * hbar) + rc / tau;
+    }
+    /* xi = M^{-T} mu_j: Thomas on the transposed rows (c_{i-1}, b_i, a_{i+1}) */
+    cw[0] = a[1] / b[0];
+    dw[0] = mj[0] / b[0];
+    for (int i = 1; i <= N; i++) {
+      const double sub = c[i - 1], sup = (i < N) ? a[i + 1] : 0.0;
+      const double den = b[i] - sub * cw[i - 1];
+      cw[i] = sup / den;
+      dw[i] = (mj[i] - sub * dw[i - 1]) / den;
+    }
+    xi[N] = dw[N];
+    for (int i = N - 1; i >= 0; i--) xi[i] = dw[i] - cw[i] * xi[i + 1];
+    /* partial derivatives of the residuals */
+    for (int i = 1; i <= N - 1; i++) {
+      const double h_w = r[i] - r[i - 1], h_e = r[i + 1] - r[i];
+      const double X = xi[i];
+      if (X == 0.0) continue;
+      if (cls[i] == OR_IFACE) {
+        const int mi = seg[i - 1], mo = seg[i];
+        const double gw = yj[i - 1] - yj[i], ge = yj[i + 1] - yj[i];
+        if (p->interface_rule == 0) {
+          /* r = lm h_e (y_{i-1} - y_i) + lp h_w (y_{i+1} - y_i) */
+          xb[i] += X * (dlam_m(p, mi, Tj[i]) * h_e * gw + dlam_m(p, mo, Tj[i]) * h_w * ge);
+          gbar[2 + mi] += X * lam_m(p, mi, Tj[i]) * h_e * gw / p->lam_scale[mi];
+          gbar[2 + mo] += X * lam_m(p, mo, Tj[i]) * h_w * ge / p->lam_scale[mo];
+        } else {
+          const double rw = 0.5 * (r[i] + r[i - 1]), re = 0.5 * (r[i] + r[i + 1]);
+          double l1, d1a, d1b, l2, d2a, d2b;
+          lam_face_d(p, mi, Tj[i - 1], Tj[i], &l1, &d1a, &d1b);
+          lam_face_d(p, mo, Tj[i], Tj[i + 1], &l2, &d2a, &d2b);
+          xb[i - 1] += X * rw * d1a * h_e * gw;
+          xb[i] += X * (rw * d1b * h_e * gw + re * d2a * h_w * ge);
+          xb[i + 1] += X * re * d2b * h_w * ge;
+          gbar[2 + mi] += X * rw * l1 * h_e * gw / p->lam_scale[mi];
+          gbar[2 + mo] += X * re * l2 * h_w * ge / p->lam_scale[mo];
+        }
+        continue;
+      }
+      const int m = seg[i];
+      const double hbar = 0.5 * (h_e + h_w);
+      const double r_w = 0.5 * (r[i] + r[i - 1]), r_e = 0.5 * (r[i] + r[i + 1]);
+      const double gA = r_w / (r[i] * hbar * h_w), gC = r_e / (r[i] * hbar * h_e);
+      const double T0 = Tj[i];
+      double lw, lw_a, lw_b, le, le_a, le_b, ls, ls_a, ls_b, ln, ln_a, ln_b;
+      lam_face_d(p, m, Tj[i - 1], T0, &lw, &lw_a, &lw_b);
+      lam_face_d(p, m, T0, Tj[i + 1], &le, &le_a, &le_b);
+      lam_face_d(p, m, Ts[i], T0, &ls, &ls_a, &ls_b);
+      lam_face_d(p, m, T0, Tn[i], &ln, &ln_a, &ln_b);
+      const double rc = p->rho[m] * cap_m(p, m, T0);
+      const double drc = p->rho[m] * dcap_m(p, m, T0);
+      const double gw = yj[i - 1] - yj[i], ge = yj[i + 1] - yj[i];
+      const double dN = Tn[i] - T0, dS = T0 - Ts[i];
+      /* r = rc/tau (T0 - y_i) + (ln dN/eta_n - ls dS/eta_s)/etabar + X
+       *     + gA lw (y_{i-1} - y_i) + gC le (y_{i+1} - y_i) */
+      double d0 = drc / tau * (T0 - yj[i]) + rc / tau;
+      d0 += (ln_a * dN - ln) / eta_n / etabar - (ls_b * dS + ls) / eta_s / etabar;
+      d0 += gA * lw_b * gw + gC * le_a * ge;
+      if (m == p->src_layer) d0 += p->q0 * s * src_dg(p, T0);
+      xb[i] += X * d0;
+      xb[i - 1] += X * gA * lw_a * gw;
+      xb[i + 1] += X * gC * le_b * ge;
+      xbn[i] += X * (ln_b * dN + ln) / eta_n / etabar;
+      xbs[i] += X * (-ls_a * dS + ls) / eta_s / etabar;
+      /* parameters */
+      const double lam_part = (ln * dN / eta_n - ls * dS / eta_s) / etabar + gA * lw * gw + gC * le * ge;
+      gbar[2 + m] += X * lam_part / p->lam_scale[m];
+      gbar[2 + L + m] += X * rc / tau * (T0 - yj[i]) / p->cap_scale[m];
+      if (m == p->src_layer) {
+        gbar[0] += X * s * src_g(p, T0);
+        gbar[1] += X * p->q0 * ds_dton * src_g(p, T0);
+      }
+    }
+  }
+  free(r); free(z); free(cls); free(seg); free(a); free(b); free(c); free(xi); free(cw); free(dw);
+  return 0;
+}
+
+/*
+ * Loss J = sum_n tau (Sbar_n - target_n)^2 over the n_steps steps from T0 at
+ * t0 (Sbar_n: the z-mean surface temperature after step n, trace column 1 of
+ * or_step_n), its gradient with respect to theta (grad[2 + 2 n_layers]) and,
+ * if dT0 is not NULL, with respect to T0.  States are checkpointed every
+ * ckpt steps and recomputed segment by segment in the reverse sweep.
+ */
+int or_adjoint(const or_problem* p, const double* T0, long n_steps, double t0, double tau,
+               const double* target, int ckpt, double* loss, double* grad, double* dT0) {
+  const int N = p->nr - 1, M = p->nz - 1, nr = p->nr, L = p->n_layers;
+  const size_t nodes = (size_t)nr * (M + 1);
+  if (ckpt < 1) ckpt = 1;
+  const long n_ck = (n_steps + ckpt - 1) / ckpt;
+  double* ck = (double*)malloc(sizeof(double) * nodes * (size_t)(n_ck > 0 ? n_ck : 1));
+  double* seg_states = (double*)malloc(sizeof(double) * nodes * (size_t)(ckpt + 1));
+  double* trace = (double*)malloc(sizeof(double) * 2 * (size_t)(n_steps > 0 ? n_steps : 1));
+  double* lam = (double*)calloc(nodes, sizeof(double));
+  double* lam2 = (double*)calloc(nodes, sizeof(double));
+  double* w = (double*)malloc(sizeof(double) * (M + 1));
+  double* r = (double*)malloc(sizeof(double) * (N + 1));
+  double* z = (double*)malloc(sizeof(double) * (M + 1));
+  int* cls = (int*)malloc(sizeof(int) * (N + 1));
+  int* seg = (int*)malloc(sizeof(int) * (N + 1));
+  int rc = -1;
+  if (!ck || !seg_states || !trace || !lam || !lam2 || !w || !r || !z || !cls || !seg ||
+      or_grid(p, r, z, cls, seg))
+    goto done;
+  {
+    double wsum = 0.0;
+    for (int j = 0; j <= M; j++) {
+      w[j] = 0.0;
+      if (j > 0) w[j] += 0.5 * (z[j] - z[j - 1]);
+      if (j < M) w[j] += 0.5 * (z[j + 1] - z[j]);
+      wsum += w[j];
+    }
+    for (int j = 0; j <= M; j++) w[j] /= wsum;
+  }
+  /* forward sweep with checkpoints */
+  memcpy(seg_states, T0, sizeof(double) * nodes);
+  *loss = 0.0;
+  for (long n = 0; n < n_steps; n++) {
+    if (n % ckpt == 0) memcpy(ck + nodes * (size_t)(n / ckpt), seg_states, sizeof(double) * nodes);
+    if (or_step_n(p, seg_states, 1, t0 + (double)n * tau, tau, trace + 2 * n, NULL)) goto done;
+    const double e = trace[2 * n + 1] - target[n];
+    *loss += tau * e * e;
+  }
+  for (int k = 0; k < 2 + 2 * L; k++) grad[k] = 0.0;
+  /* reverse sweep */
+  for (long k = n_ck - 1; k >= 0; k--) {
+    const long n_lo = k * ckpt, n_hi = (n_lo + ckpt < n_steps) ? n_lo + ckpt : n_steps;
+    memcpy(seg_states, ck + nodes * (size_t)k, sizeof(double) * nodes);
+    for (long n = n_lo; n < n_hi; n++) {
+      memcpy(seg_states + nodes * (size_t)(n - n_lo + 1), seg_states + nodes * (size_t)(n - n_lo),
+             sizeof(double) * nodes);
+      if (or_step_n(p, seg_states + nodes * (size_t)(n - n_lo + 1), 1, t0 + (double)n * tau, tau,
+                    NULL, NULL))
+        goto done;
+    }
+    for (long n = n_hi - 1; n >= n_lo; n--) {
+      /* dJ/dT^{n+1} from the loss term of step n */
+      const double e = trace[2 * n + 1] - target[n];
+      for (int j = 0; j <= M; j++) lam[(size_t)j * nr + N] += 2.0 * tau * e * w[j];
+      memset(lam2, 0, sizeof(double) * nodes);
+      if (or_step_vjp(p, seg_states + nodes * (size_t)(n - n_lo), seg_states + nodes * (size_t)(n - n_lo + 1),
+                      lam, t0 + (double)n * tau, tau, lam2, grad))
+        goto done;
+      double* t = lam; lam = lam2; lam2 = t;
+    }
+  }
+  if (dT0) memcpy(dT0, lam, sizeof(double) * nodes);
+  rc = 0;
+done:
+  free(ck); free(seg_states); free(trace); free(lam); free(lam2); free(w); free(r); free(z);
+  free(cls); free(seg);
+  return rc;
+}

@@ -95,6 +95,11 @@ def _load():
         lib.or_tau_stab.restype = ctypes.c_double
         lib.or_waveform.argtypes = [P, ctypes.c_double]
         lib.or_waveform.restype = ctypes.c_double
+        lib.or_step_vjp.argtypes = [P, dp, dp, dp, ctypes.c_double, ctypes.c_double, dp, dp]
+        lib.or_step_vjp.restype = ctypes.c_int
+        lib.or_adjoint.argtypes = [P, dp, ctypes.c_long, ctypes.c_double, ctypes.c_double, dp,
+                                   ctypes.c_int, dp, dp, dp]
+        lib.or_adjoint.restype = ctypes.c_int
         lib.or_num_threads.restype = ctypes.c_int
         lib.or_set_threads.argtypes = [ctypes.c_int]
         _lib = lib
@@ -183,6 +188,46 @@ def step_n(cfg: dict, T: np.ndarray, n_steps: int, t0: float, dt: float,
     if rc != 0:
         raise ValueError("oracle rejected the problem")
     return T, trace, energy
+
+
+def n_params(cfg: dict) -> int:
+    """Parameters of the adjoint: q0, t_on, lam_scale[L], cap_scale[L]."""
+    return 2 + 2 * len(cfg["layers"])
+
+
+def step_vjp(cfg: dict, x: np.ndarray, y: np.ndarray, mu: np.ndarray, tn: float, dt: float):
+    """Adjoint of one step from x (T^n) to y (T^{n+1}) for mu = dJ/dT^{n+1}.
+    Returns (dJ/dT^n, dJ/dtheta)."""
+    lib = _load()
+    p = problem(cfg)
+    x = np.ascontiguousarray(x, dtype=np.float64)
+    y = np.ascontiguousarray(y, dtype=np.float64)
+    mu = np.ascontiguousarray(mu, dtype=np.float64).copy()
+    xbar = np.zeros_like(x)
+    gbar = np.zeros(n_params(cfg))
+    if lib.or_step_vjp(ctypes.byref(p), _dp(x), _dp(y), _dp(mu), float(tn), float(dt),
+                       _dp(xbar), _dp(gbar)) != 0:
+        raise ValueError("oracle rejected the problem")
+    return xbar, gbar
+
+
+def adjoint(cfg: dict, T0: np.ndarray, n_steps: int, t0: float, dt: float, target: np.ndarray,
+            ckpt: int = 256):
+    """Loss J = sum_n dt (Sbar_n - target_n)^2 and its gradient with respect to
+    theta = (q0, t_on, lam_scale[], cap_scale[]) and to T0."""
+    lib = _load()
+    p = problem(cfg)
+    T0 = np.ascontiguousarray(T0, dtype=np.float64)
+    target = np.ascontiguousarray(target, dtype=np.float64)
+    if target.shape != (n_steps,):
+        raise ValueError("target must have n_steps entries")
+    loss = np.zeros(1)
+    grad = np.zeros(n_params(cfg))
+    dT0 = np.zeros_like(T0)
+    if lib.or_adjoint(ctypes.byref(p), _dp(T0), int(n_steps), float(t0), float(dt), _dp(target),
+                      int(ckpt), _dp(loss), _dp(grad), _dp(dT0)) != 0:
+        raise ValueError("oracle rejected the problem")
+    return float(loss[0]), grad, dT0
 
 
 def tau_stab(cfg: dict, t_lo: float, t_hi: float, n_samples: int = 257) -> float:

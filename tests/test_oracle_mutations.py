@@ -26,7 +26,8 @@ MUTATIONS = {
     "heat capacity saturation squared instead of cubed":
         ("(1.0 + y * y * y)", "(1.0 + y * y)"),
     "density dropped from rho c":
-        ("const double rc = p->rho[m] * cap_m(p, m, T0);", "const double rc = cap_m(p, m, T0);"),
+        ("const double rc = p->rho[m] * cap_m(p, m, T0);\n          /* Eq. (Lambda_j)",
+         "const double rc = cap_m(p, m, T0);\n          /* Eq. (Lambda_j)"),
     "interface beta with the wrong cell width":
         ("beta[i] = lm * h_e * beta[i - 1] / den;", "beta[i] = lm * h_w * beta[i - 1] / den;"),
     "source term dropped from F":
@@ -39,6 +40,21 @@ MUTATIONS = {
         ("if (e * e < eta2) eta2 = e * e;", "if (e < eta2) eta2 = e;"),
     "rectangle pulse closed interval":
         ("return (phi < p->t_on) ? 1.0 : 0.0;", "return (phi <= p->t_on) ? 1.0 : 0.0;"),
+    # discrete adjoint
+    "adjoint: lambda term of the north flux derivative dropped":
+        ("d0 += (ln_a * dN - ln) / eta_n / etabar", "d0 += (ln_a * dN) / eta_n / etabar"),
+    "adjoint: south-neighbour derivative with the wrong sign":
+        ("xbs[i] += X * (-ls_a * dS + ls) / eta_s / etabar;", "xbs[i] += X * (ls_a * dS + ls) / eta_s / etabar;"),
+    "adjoint: heat-capacity derivative without the saturation term":
+        ("v = p->c0[m] * (3.0 * x * x / p->t_ref[m] / d - x * x * x * 3.0 * y * y / p->theta[m] / (d * d));",
+         "v = p->c0[m] * (3.0 * x * x / p->t_ref[m] / d);"),
+    "adjoint: untransposed line solve":
+        ("const double sub = c[i - 1], sup = (i < N) ? a[i + 1] : 0.0;",
+         "const double sub = a[i], sup = (i < N) ? c[i] : 0.0;"),
+    "adjoint: pulse-duration derivative with the wrong sign":
+        ("return 0.5 * (1.0 - th * th) / p->edge_w;", "return -0.5 * (1.0 - th * th) / p->edge_w;"),
+    "adjoint: Neumann row z=0 not folded into line 1":
+        ("if (!p->bc_z0) mu[(size_t)nr + i] += mu[i];", "(void)0;"),
 }
 
 
@@ -55,6 +71,7 @@ def test_pins_catch_mutation(name, tmp_path):
                     "-o", str(so), "-lm"], check=True, capture_output=True)
     env = dict(os.environ, CCELL_ORACLE_SO=str(so))
     res = subprocess.run([sys.executable, "-m", "pytest", "-x", "-q",
-                          os.path.join(ROOT, "tests", "test_oracle_pins.py")],
+                          os.path.join(ROOT, "tests", "test_oracle_pins.py"),
+                          os.path.join(ROOT, "tests", "test_oracle_adjoint.py")],
                          env=env, capture_output=True, text=True, cwd=ROOT)
     assert res.returncode != 0, f"pins did not catch: {name}\n{res.stdout[-2000:]}"
