@@ -193,11 +193,26 @@ int cc_sync(cc_ctx* ctx, void* stream);
  * plus dJ/dT0 if dT0_dev is not NULL.  Checkpoints every ckpt_every steps and
  * recomputes in between.
  *   T0_dev      initial field (not modified); target_dev double[n_inst][n_steps]
- *   loss_dev    double[n_inst]; grad_dev double[n_inst][2 + 2 n_layers]
+ *   loss_dev    double[n_inst]; grad_dev: for each instance in order, 2 + 2 n_layers
+ *               doubles (q0, t_on, lam_scale[0..L-1], cap_scale[0..L-1])
+ *   dT0_dev     NULL or double field like T0: dJ/dT0
+ * Each step of the reverse sweep rebuilds the rows of the forward step at the
+ * recomputed state, solves the transposed line systems, and gathers the
+ * derivatives through lambda(T), c(T), X and the interface rows.  The
+ * t_on derivative is nonzero only for the smoothed waveform (waveform 1).
  * Errors as cc_step_n; CC_EUNSUPPORTED for CC_MIXED contexts. */
 int cc_adjoint(cc_ctx* ctx, const void* T0_dev, int64_t n_steps, double t0_s, double dt_s,
                const double* target_dev, int32_t ckpt_every, double* loss_dev,
                double* grad_dev, void* dT0_dev, void* stream);
+
+/* Same reverse sweep as cc_adjoint for a loss that is any function of the
+ * surface traces: seed_dev is device double[n_inst][n_steps] holding
+ * dJ/dSbar_n (Sbar_n = trace column 1 after step n).  Fills grad_dev
+ * (layout of cc_adjoint) and, if not NULL, dT0_dev.  Used by the autograd
+ * binding.  Errors as cc_adjoint. */
+int cc_adjoint_vjp(cc_ctx* ctx, const void* T0_dev, int64_t n_steps, double t0_s, double dt_s,
+                   const double* seed_dev, int32_t ckpt_every, double* grad_dev, void* dT0_dev,
+                   void* stream);
 
 /* Release the context and everything it owns.  NULL is accepted. */
 int cc_destroy(cc_ctx* ctx);

@@ -93,6 +93,8 @@ def _load():
                                       ctypes.POINTER(Source), vp, ctypes.c_int64, _d, _d, vp,
                                       vp, vp]
     lib.cc_step_n_noalloc.restype = ctypes.c_int
+    lib.cc_adjoint_vjp.argtypes = [vp, vp, ctypes.c_int64, _d, _d, vp, _i, vp, vp, vp]
+    lib.cc_adjoint_vjp.restype = ctypes.c_int
     for name in ("cc_create_geometry", "cc_set_materials", "cc_set_source", "cc_set_dt",
                  "cc_step_n", "cc_sync", "cc_adjoint", "cc_destroy", "cc_query_grid",
                  "cc_tau_stab"):
@@ -152,6 +154,13 @@ def cc_adjoint(ctx, T0_ptr, n_steps, t0, dt, target_ptr, ckpt_every, loss_ptr, g
     _check(_load().cc_adjoint(ctx, T0_ptr, int(n_steps), float(t0), float(dt), target_ptr,
                               int(ckpt_every), loss_ptr, grad_ptr, dT0_ptr, stream_ptr),
            "cc_adjoint")
+
+
+def cc_adjoint_vjp(ctx, T0_ptr, n_steps, t0, dt, seed_ptr, ckpt_every, grad_ptr, dT0_ptr,
+                   stream_ptr) -> None:
+    _check(_load().cc_adjoint_vjp(ctx, T0_ptr, int(n_steps), float(t0), float(dt), seed_ptr,
+                                  int(ckpt_every), grad_ptr, dT0_ptr, stream_ptr),
+           "cc_adjoint_vjp")
 
 
 def cc_step_n_noalloc(desc: GeometryDesc, materials_list, source_struct: Source, T_ptr: int,
@@ -280,6 +289,45 @@ class Solver:
                   trace.data_ptr() if trace is not None else None,
                   energy.data_ptr() if energy is not None else None, st.cuda_stream)
 
+    # ---- parameters of the adjoint: (q0, t_on, lam_scale[L], cap_scale[L]) per instance
+    def n_params(self, instance: int = 0) -> int:
+        return 2 + 2 * len(self.cfgs[instance]["layers"])
+
+    def get_params(self, instance: int = 0) -> list:
+        c = self.cfgs[instance]
+        src = c.get("source") or {"q0": 0.0, "t_on": 0.0}
+        return ([src["q0"], src["t_on"]] + [ly.get("lam_scale", 1.0) for ly in c["layers"]]
+                + [ly.get("cap_scale", 1.0) for ly in c["layers"]])
+
+    def set_params(self, instance: int, theta) -> None:
+        """Apply theta = (q0, t_on, lam_scale[], cap_scale[]) to one instance."""
+        c = self.cfgs[instance]
+        L = len(c["layers"])
+        theta = [float(v) for v in theta]
+        if c.get("source") is not None:
+            c["source"] = dict(c["source"], q0=theta[0], t_on=theta[1])
+            cc_set_source(self.ctx, instance, source(c))
+        for m in range(L):
+            c["layers"][m] = dict(c["layers"][m], lam_scale=theta[2 + m], cap_scale=theta[2 + L + m])
+        cc_set_materials(self.ctx, instance, materials(c))
+
+    def adjoint(self, T0, n_steps: int, t0: float, dt: float, target, ckpt_every: int = 256,
+                want_dT0: bool = False, stream=None):
+        """Loss sum_n dt (Sbar_n - target_n)^2 per instance, its gradient
+        (per instance: q0, t_on, lam_scale[], cap_scale[]) and optionally dJ/dT0."""
+        import torch
+        dev = T0.device
+        st = stream if stream is not None else torch.cuda.current_stream()
+        loss = torch.zeros(len(self.cfgs), dtype=torch.float64, device=dev)
+        grad = torch.zeros(sum(self.n_params(k) for k in range(len(self.cfgs))),
+                           dtype=torch.float64, device=dev)
+        dT0 = torch.zeros_like(T0) if want_dT0 else None
+        target = target.contiguous().to(device=dev, dtype=torch.float64)
+        cc_adjoint(self.ctx, T0.data_ptr(), n_steps, t0, dt, target.data_ptr(), ckpt_every,
+                   loss.data_ptr(), grad.data_ptr(), dT0.data_ptr() if want_dT0 else None,
+                   st.cuda_stream)
+        return loss, grad, dT0
+
     def sync(self, stream=None) -> None:
         import torch
         st = stream if stream is not None else torch.cuda.current_stream()
@@ -298,3 +346,49 @@ class Solver:
             self.close()
         except Exception:
             pass
+
+
+def _autograd_fn():
+    import torch
+
+    class SurfaceTrace(torch.autograd.Function):
+        """theta [n_inst, 2 + 2L] and T0 -> z-mean surface temperature after each
+        step, [n_inst, n_steps].  Backward runs the reverse-time adjoint sweep on
+        the GPU (checkpoint every ``ckpt`` steps, recompute in between)."""
+
+        @staticmethod
+        def forward(ctx, theta, T0, solver, n_steps, t0, dt, ckpt):
+            for k in range(len(solver.cfgs)):
+                solver.set_params(k, theta[k].tolist())
+            T = T0.detach().clone()
+            trace = torch.zeros(len(solver.cfgs) * n_steps * 2, dtype=torch.float64,
+                                device=T0.device)
+            solver.step(T, n_steps, t0, dt, trace, None)
+            ctx.solver, ctx.n, ctx.t0, ctx.dt, ctx.ckpt = solver, n_steps, t0, dt, ckpt
+            ctx.save_for_backward(theta, T0)
+            return trace.view(len(solver.cfgs), n_steps, 2)[:, :, 1].clone()
+
+        @staticmethod
+        def backward(ctx, g):
+            theta, T0 = ctx.saved_tensors
+            sol = ctx.solver
+            for k in range(len(sol.cfgs)):
+                sol.set_params(k, theta[k].tolist())
+            seed = g.detach().to(dtype=torch.float64).contiguous()
+            grad = torch.zeros(theta.numel(), dtype=torch.float64, device=T0.device)
+            dT0 = torch.zeros_like(T0)
+            cc_adjoint_vjp(sol.ctx, T0.data_ptr(), ctx.n, ctx.t0, ctx.dt, seed.data_ptr(), ctx.ckpt,
+                           grad.data_ptr(), dT0.data_ptr(), torch.cuda.current_stream().cuda_stream)
+            sol.sync()
+            return (grad.view(theta.shape).to(device=theta.device, dtype=theta.dtype), dT0,
+                    None, None, None, None, None)
+
+    return SurfaceTrace
+
+
+def surface_trace(theta, T0, solver: "Solver", n_steps: int, t0: float = 0.0, dt: float = 0.0,
+                  ckpt: int = 256):
+    """Differentiable surface trace: see ``SurfaceTrace``.  theta has one row of
+    (q0, t_on, lam_scale[], cap_scale[]) per instance (all instances must have
+    the same number of layers); T0 is the flat FP64 field of all instances."""
+    return _autograd_fn().apply(theta, T0, solver, n_steps, t0, dt, ckpt)

@@ -50,6 +50,9 @@ struct cc_ctx {
   long long s_cap = 0;
   unsigned* d_err = nullptr;
   std::vector<double> uploaded_dt;
+  // adjoint scratch, grown on demand
+  double* d_adj = nullptr;
+  size_t adj_cap = 0;
 };
 
 namespace {
@@ -206,6 +209,9 @@ void free_device(cc_ctx* c) {
   cudaFree(c->d_s);
   cudaFree(c->d_ptab);
   cudaFree(c->d_err);
+  cudaFree(c->d_adj);
+  c->d_adj = nullptr;
+  c->adj_cap = 0;
   c->d_inst = nullptr;
   c->d_rg = nullptr;
   c->d_zg = nullptr;
@@ -374,6 +380,8 @@ int upload(cc_ctx* c, const std::vector<double>& dts, cudaStream_t st) {
       t.lam_model = s.lam_model;
       t.cap_model = s.cap_model;
       t.lam0s = s.lam0 * s.lam_scale;
+      t.inv_lam_scale = 1.0 / s.lam_scale;
+      t.inv_cap_scale = 1.0 / s.cap_scale;
       t.lam_b = s.lam_b;
       t.inv_tref = 1.0 / s.t_ref;
       t.c0s = s.c0 * s.cap_scale;
@@ -591,10 +599,170 @@ int cc_sync(cc_ctx* c, void* stream) {
   return CC_OK;
 }
 
-int cc_adjoint(cc_ctx* c, const void*, int64_t, double, double, const double*, int32_t, double*,
-               double*, void*, void*) {
-  if (!c) return CC_EINVAL;
-  return CC_EUNSUPPORTED;
+}  // extern "C"
+
+namespace {
+
+// Reverse sweep shared by cc_adjoint and cc_adjoint_vjp.  If target is not
+// null the seeds are 2 tau (Sbar_n - target_n) and the loss is written; else
+// seed_in holds dJ/dSbar_n for every instance and step.
+int adjoint_impl(cc_ctx* c, const void* T0_dev, int64_t n_steps, double t0, double dt_s,
+                 const double* target, const double* seed_in, int32_t ckpt, double* loss_dev,
+                 double* grad_dev, void* dT0_dev, void* stream) {
+  if (!c || !T0_dev || !grad_dev || n_steps < 1 || !std::isfinite(t0)) return CC_EINVAL;
+  if (c->failed) return CC_ESTATE;
+  if (c->precision != CC_FP64) return CC_EUNSUPPORTED;
+  const int n = (int)c->inst.size();
+  std::vector<double> dts(n);
+  for (int k = 0; k < n; ++k) {
+    Instance& in = c->inst[k];
+    if (!in.mat_set) return CC_ESTATE;
+    dts[k] = dt_s > 0.0 ? dt_s : in.dt;
+    if (!(dts[k] > 0.0)) return CC_EINVAL;
+    if (dts[k] > tau_stab(in) * (1.0 + 1e-12) && !force_unstable()) return CC_EUNSTABLE;
+  }
+  cudaStream_t st = (cudaStream_t)stream;
+  int rc = upload(c, dts, st);
+  if (rc != CC_OK) return rc;
+  const long long K = ckpt > 0 ? ckpt : 256;
+  const long long n_ck = (n_steps + K - 1) / K;
+  const size_t nodes = (size_t)c->total_nodes;
+  long long max_nodes = 0;
+  std::vector<long long> goff(n);
+  std::vector<int> nl(n);
+  long long gsum = 0;
+  for (int k = 0; k < n; ++k) {
+    max_nodes = std::max(max_nodes, (long long)c->inst[k].d.nr * c->inst[k].d.nz);
+    goff[k] = gsum;
+    nl[k] = c->inst[k].d.n_layers;
+    gsum += 2 + 2 * nl[k];
+  }
+  // scratch layout (doubles): checkpoints, segment states, lam x2, xi, sa, sb, sc,
+  // trace, seed, s, ds, grad offsets and layer counts
+  const size_t need = nodes * (size_t)(n_ck + K + 1 + 6) + (size_t)n * n_steps * 5 + 2 * (size_t)n + 8;
+  if (c->adj_cap < need) {
+    cudaFree(c->d_adj);
+    c->d_adj = nullptr;
+    c->adj_cap = 0;
+    if (cudaMalloc(&c->d_adj, sizeof(double) * need) != cudaSuccess) {
+      cudaGetLastError();
+      return CC_ENOMEM;
+    }
+    c->adj_cap = need;
+  }
+  double* p = c->d_adj;
+  double* ck = p; p += nodes * n_ck;
+  double* segs = p; p += nodes * (K + 1);
+  double* lamA = p; p += nodes;
+  double* lamB = p; p += nodes;
+  double* xi = p; p += nodes;
+  double* sa = p; p += nodes;
+  double* sb = p; p += nodes;
+  double* sc = p; p += nodes;
+  double* trace = p; p += (size_t)n * n_steps * 2;
+  double* seed = p; p += (size_t)n * n_steps;
+  double* s_tab = p; p += (size_t)n * n_steps;
+  double* ds_tab = p; p += (size_t)n * n_steps;
+  long long* d_goff = reinterpret_cast<long long*>(p); p += n;
+  int* d_nl = reinterpret_cast<int*>(p);
+  if (cudaMemcpyAsync(d_goff, goff.data(), sizeof(long long) * n, cudaMemcpyHostToDevice, st) ||
+      cudaMemcpyAsync(d_nl, nl.data(), sizeof(int) * n, cudaMemcpyHostToDevice, st) ||
+      cudaMemsetAsync(trace, 0, sizeof(double) * 2 * n * n_steps, st) ||
+      cudaMemsetAsync(lamA, 0, sizeof(double) * nodes, st) ||
+      cudaMemsetAsync(grad_dev, 0, sizeof(double) * gsum, st) ||
+      cudaMemcpyAsync(segs, T0_dev, sizeof(double) * nodes, cudaMemcpyDeviceToDevice, st))
+    return CC_ECUDA;
+  if (launch_waveform(c->d_inst, n, n_steps, t0, s_tab, stream, ds_tab)) return CC_ECUDA;
+  StepArgs a{};
+  a.insts = c->d_inst;
+  a.tasks = c->d_tasks;
+  a.n_tasks = c->n_tasks;
+  a.n_inst = n;
+  a.s_tab = s_tab;
+  a.n_steps = n_steps;
+  a.err = c->d_err;
+  // forward sweep with checkpoints (slots 0 and 1 of the segment buffer)
+  for (long long s = 0; s < n_steps; ++s) {
+    double* cur = segs + nodes * (s & 1);
+    if (s % K == 0 &&
+        cudaMemcpyAsync(ck + nodes * (s / K), cur, sizeof(double) * nodes, cudaMemcpyDeviceToDevice,
+                        st))
+      return CC_ECUDA;
+    a.step = s;
+    a.Tin = cur;
+    a.Tout = segs + nodes * ((s + 1) & 1);
+    a.trace = trace;
+    if (launch_step_fp64(a, stream)) return CC_ECUDA;
+  }
+  if (target) {
+    if (launch_adj_seed(c->d_inst, n, trace, target, n_steps, seed, loss_dev, stream))
+      return CC_ECUDA;
+  } else if (cudaMemcpyAsync(seed, seed_in, sizeof(double) * n * n_steps, cudaMemcpyDeviceToDevice,
+                             st)) {
+    return CC_ECUDA;
+  }
+  // reverse sweep, one checkpoint segment at a time
+  AdjArgs b{};
+  b.insts = c->d_inst;
+  b.tasks = c->d_tasks;
+  b.n_tasks = c->n_tasks;
+  b.n_inst = n;
+  b.sa = sa;
+  b.sb = sb;
+  b.sc = sc;
+  b.xi = xi;
+  b.seed = seed;
+  b.s_tab = s_tab;
+  b.ds_tab = ds_tab;
+  b.n_steps = n_steps;
+  b.grad_off = d_goff;
+  b.grad = grad_dev;
+  b.n_layers = d_nl;
+  a.trace = nullptr;
+  for (long long k = n_ck - 1; k >= 0; --k) {
+    const long long lo = k * K, hi = std::min(lo + K, (long long)n_steps);
+    if (cudaMemcpyAsync(segs, ck + nodes * k, sizeof(double) * nodes, cudaMemcpyDeviceToDevice, st))
+      return CC_ECUDA;
+    for (long long s = lo; s < hi; ++s) {
+      a.step = s;
+      a.Tin = segs + nodes * (s - lo);
+      a.Tout = segs + nodes * (s - lo + 1);
+      if (launch_step_fp64(a, stream)) return CC_ECUDA;
+    }
+    for (long long s = hi - 1; s >= lo; --s) {
+      b.step = s;
+      b.x = segs + nodes * (s - lo);
+      b.y = segs + nodes * (s - lo + 1);
+      b.lam = lamA;
+      b.lam_out = lamB;
+      if (launch_adj_line(b, stream) || launch_adj_gather(b, max_nodes, stream)) return CC_ECUDA;
+      std::swap(lamA, lamB);
+    }
+  }
+  if (dT0_dev &&
+      cudaMemcpyAsync(dT0_dev, lamA, sizeof(double) * nodes, cudaMemcpyDeviceToDevice, st))
+    return CC_ECUDA;
+  return CC_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int cc_adjoint(cc_ctx* c, const void* T0_dev, int64_t n_steps, double t0, double dt_s,
+               const double* target_dev, int32_t ckpt_every, double* loss_dev, double* grad_dev,
+               void* dT0_dev, void* stream) {
+  if (!target_dev || !loss_dev) return CC_EINVAL;
+  return adjoint_impl(c, T0_dev, n_steps, t0, dt_s, target_dev, nullptr, ckpt_every, loss_dev,
+                      grad_dev, dT0_dev, stream);
+}
+
+int cc_adjoint_vjp(cc_ctx* c, const void* T0_dev, int64_t n_steps, double t0, double dt_s,
+                   const double* seed_dev, int32_t ckpt_every, double* grad_dev, void* dT0_dev,
+                   void* stream) {
+  if (!seed_dev) return CC_EINVAL;
+  return adjoint_impl(c, T0_dev, n_steps, t0, dt_s, nullptr, seed_dev, ckpt_every, nullptr,
+                      grad_dev, dT0_dev, stream);
 }
 
 int cc_destroy(cc_ctx* c) {

@@ -63,6 +63,7 @@ struct DevMaterial {
   double lam_poly[5];  // * lam_scale
   double cap_poly[4];  // * cap_scale
   const double* ptab;  // power-law table (kPowTabLen doubles) or null: use pow()
+  double inv_lam_scale, inv_cap_scale;  // adjoint: d/d scale = value / scale
   // FP32 copies (mixed precision)
   float rho_f, lam0s_f, lam_b_f, inv_tref_f, c0s_f, inv_theta_f;
   float lam_poly_f[5], cap_poly_f[4];
@@ -111,9 +112,38 @@ struct StepArgs {
   unsigned* err;         // error word: bit0 non-finite
 };
 
+// Reverse sweep of the adjoint (ccell_adjoint.cu).
+struct AdjArgs {
+  const DevInst* insts;
+  const Task* tasks;
+  int n_tasks;
+  int n_inst;
+  const double* x;       // T^n, all instances
+  const double* y;       // T^{n+1}
+  const double* lam;     // dJ/dT^{n+1} (without the seed of step n)
+  double* lam_out;       // dJ/dT^n
+  double* sa;            // row coefficients of the step, [node]
+  double* sb;
+  double* sc;
+  double* xi;            // M^{-T} mu, [node]
+  const double* seed;    // [n_inst][n_steps]: dJ/dSbar_n
+  const double* s_tab;   // [n_steps][n_inst] waveform
+  const double* ds_tab;  // [n_steps][n_inst] d waveform / d t_on
+  long long step;
+  long long n_steps;
+  const long long* grad_off;  // per instance offset into grad
+  double* grad;          // [sum_k (2 + 2 L_k)]
+  const int* n_layers;   // per instance
+};
+
 // kernels (ccell_step.cu)
 int launch_waveform(const DevInst* insts, int n_inst, long long n_steps, double t0,
-                    double* s_tab, void* stream);
+                    double* s_tab, void* stream, double* ds_tab = nullptr);
+// adjoint (ccell_adjoint.cu)
+int launch_adj_line(const AdjArgs& a, void* stream);
+int launch_adj_gather(const AdjArgs& a, long long max_nodes, void* stream);
+int launch_adj_seed(const DevInst* insts, int n_inst, const double* trace, const double* target,
+                    long long n_steps, double* seed, double* loss, void* stream);
 int launch_step_fp64(const StepArgs& a, void* stream);
 int launch_step_mixed(const StepArgs& a, void* stream);
 int launch_mixed_init(const DevInst* insts, int n_inst, const Task* tasks, int n_tasks,

@@ -38,7 +38,8 @@ long long kernel_launch_count() { return g_launches.load(std::memory_order_relax
 // IEEE evaluation.
 // ---------------------------------------------------------------------------
 __global__ void waveform_kernel(const DevInst* __restrict__ insts, int n_inst,
-                                long long n_steps, double t0, double* __restrict__ s_tab) {
+                                long long n_steps, double t0, double* __restrict__ s_tab,
+                                double* __restrict__ ds_tab) {
   const long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (idx >= n_steps * n_inst) return;
   const long long n = idx / n_inst;
@@ -46,7 +47,7 @@ __global__ void waveform_kernel(const DevInst* __restrict__ insts, int n_inst,
   const DevInst& I = insts[k];
   const double tn = __dadd_rn(t0, __dmul_rn((double)n, I.tau));
   const double u = __dsub_rn(tn, I.t_start);
-  double s = 0.0;
+  double s = 0.0, ds = 0.0;
   if (I.src_layer >= 0) {
     if (I.waveform == 0) {
       if (u >= 0.0) {
@@ -58,20 +59,23 @@ __global__ void waveform_kernel(const DevInst* __restrict__ insts, int n_inst,
       double kk = floor(__dadd_rn(__ddiv_rn(__dsub_rn(u, __dmul_rn(0.5, I.t_on)), I.t_period), 0.5));
       if (kk < 0.0) kk = 0.0;
       const double phi = __dsub_rn(u, __dmul_rn(kk, I.t_period));
-      s = 0.5 * (tanh(phi / I.edge_w) - tanh((phi - I.t_on) / I.edge_w));
+      const double th = tanh((phi - I.t_on) / I.edge_w);
+      s = 0.5 * (tanh(phi / I.edge_w) - th);
+      ds = 0.5 * (1.0 - th * th) / I.edge_w;  // d s / d t_on
     }
   }
   s_tab[idx] = s;
+  if (ds_tab) ds_tab[idx] = ds;
 }
 
 int launch_waveform(const DevInst* insts, int n_inst, long long n_steps, double t0,
-                    double* s_tab, void* stream) {
+                    double* s_tab, void* stream, double* ds_tab) {
   const long long n = n_steps * n_inst;
   if (n <= 0) return 0;
   const int threads = 256;
   const long long blocks = (n + threads - 1) / threads;
   waveform_kernel<<<(unsigned)blocks, threads, 0, (cudaStream_t)stream>>>(insts, n_inst, n_steps,
-                                                                          t0, s_tab);
+                                                                          t0, s_tab, ds_tab);
   count_launch();
   return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }
