@@ -181,6 +181,28 @@ int cc_set_dt(cc_ctx* ctx, int32_t instance, double dt_s);
 int cc_step_n(cc_ctx* ctx, void* T_dev, int64_t n_steps, double t0_s, double dt_s,
               double* trace_dev, double* energy_dev, void* stream);
 
+/* Launch shape of cc_step_n (the numerics do not depend on it):
+ *   mode 0: one kernel launch per time step; mode 1: all steps of a call in
+ *   one cooperative (co-resident) launch with a grid barrier between steps
+ *   (bounded wait: a barrier that does not complete within ~seconds ends the
+ *   kernel and cc_sync reports CC_ETIMEOUT; if the grid cannot be
+ *   co-resident the call falls back to mode 0).
+ *   threads: 64, 128 or 256 per block.
+ *   rows_per_lane: 2..16, target rows per lane of the line solve; a line of
+ *   nr rows is split over the smallest power-of-two number of lanes G <= 32
+ *   that meets it (at least 2 rows per lane, at most 16).
+ * After a first call has sized the context's buffers, cc_step_n performs no
+ * allocation and no host synchronisation, so a call can be captured in a
+ * CUDA graph (its t0 is then part of the graph). */
+int cc_set_launch(cc_ctx* ctx, int32_t mode, int32_t threads, int32_t rows_per_lane);
+int cc_get_launch(const cc_ctx* ctx, int32_t* mode, int32_t* threads, int32_t* rows_per_lane);
+
+/* Autotuner: times n_trial steps of every launch shape (mode x threads x the
+ * row policies that change G for some instance) on the caller's field T_dev,
+ * keeps the fastest (cc_get_launch), restores T_dev, and returns its time per
+ * step in best_ms (may be NULL).  Synchronous. */
+int cc_autotune(cc_ctx* ctx, void* T_dev, int32_t n_trial, float* best_ms, void* stream);
+
 /* Wait for the context's work on `stream`, then report a deferred kernel
  * failure (CC_ENONFINITE, CC_ETIMEOUT, CC_ECUDA) or CC_OK. */
 int cc_sync(cc_ctx* ctx, void* stream);

@@ -10,10 +10,12 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libccell.so")
-SOURCES = ["ccell_step.cu", "ccell_step_mixed.cu", "ccell_adjoint.cu", "ccell_api.cpp",
-           "ccell_noalloc.cu", "ccell_powtab.cpp"]
+SOURCES = ["ccell_step.cu", "ccell_step_persist.cu", "ccell_step_mixed.cu",
+           "ccell_step_mixed_persist.cu", "ccell_adjoint.cu", "ccell_api.cpp", "ccell_noalloc.cu",
+           "ccell_powtab.cpp"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-HEADERS = ["ccell_internal.h", "ccell_device.cuh", os.path.join("..", "..", "include", "ccell.h")]
+HEADERS = ["ccell_internal.h", "ccell_device.cuh", "ccell_fp64_task.cuh", "ccell_mixed_task.cuh",
+           os.path.join("..", "..", "include", "ccell.h")]
 
 
 def _nvcc() -> str:

@@ -7,7 +7,8 @@ no CPU fallback.
 
 Low-level functions carry the C names (``cc_create_geometry``,
 ``cc_set_materials``, ``cc_set_source``, ``cc_set_dt``, ``cc_step_n``,
-``cc_sync``, ``cc_adjoint``, ``cc_destroy``, ``cc_step_n_noalloc``, ``cc_query_grid``,
+``cc_sync``, ``cc_adjoint``, ``cc_adjoint_vjp``, ``cc_set_launch``, ``cc_get_launch``,
+``cc_autotune``, ``cc_destroy``, ``cc_step_n_noalloc``, ``cc_query_grid``,
 ``cc_tau_stab``, ``cc_status_string``, ``cc_kernel_launches``).  ``Solver``
 builds a context from the problem dicts of ``inputs``.
 """
@@ -93,6 +94,12 @@ def _load():
                                       ctypes.POINTER(Source), vp, ctypes.c_int64, _d, _d, vp,
                                       vp, vp]
     lib.cc_step_n_noalloc.restype = ctypes.c_int
+    lib.cc_set_launch.argtypes = [vp, _i, _i, _i]
+    lib.cc_set_launch.restype = ctypes.c_int
+    lib.cc_get_launch.argtypes = [vp, ctypes.POINTER(_i), ctypes.POINTER(_i), ctypes.POINTER(_i)]
+    lib.cc_get_launch.restype = ctypes.c_int
+    lib.cc_autotune.argtypes = [vp, vp, _i, ctypes.POINTER(ctypes.c_float), vp]
+    lib.cc_autotune.restype = ctypes.c_int
     lib.cc_adjoint_vjp.argtypes = [vp, vp, ctypes.c_int64, _d, _d, vp, _i, vp, vp, vp]
     lib.cc_adjoint_vjp.restype = ctypes.c_int
     for name in ("cc_create_geometry", "cc_set_materials", "cc_set_source", "cc_set_dt",
@@ -154,6 +161,25 @@ def cc_adjoint(ctx, T0_ptr, n_steps, t0, dt, target_ptr, ckpt_every, loss_ptr, g
     _check(_load().cc_adjoint(ctx, T0_ptr, int(n_steps), float(t0), float(dt), target_ptr,
                               int(ckpt_every), loss_ptr, grad_ptr, dT0_ptr, stream_ptr),
            "cc_adjoint")
+
+
+def cc_set_launch(ctx, mode: int, threads: int, rows_per_lane: int) -> None:
+    _check(_load().cc_set_launch(ctx, int(mode), int(threads), int(rows_per_lane)),
+           "cc_set_launch")
+
+
+def cc_get_launch(ctx) -> tuple:
+    m, t, r = _i(), _i(), _i()
+    _check(_load().cc_get_launch(ctx, ctypes.byref(m), ctypes.byref(t), ctypes.byref(r)),
+           "cc_get_launch")
+    return m.value, t.value, r.value
+
+
+def cc_autotune(ctx, T_ptr: int, n_trial: int, stream_ptr) -> float:
+    best = ctypes.c_float()
+    _check(_load().cc_autotune(ctx, T_ptr, int(n_trial), ctypes.byref(best), stream_ptr),
+           "cc_autotune")
+    return best.value
 
 
 def cc_adjoint_vjp(ctx, T0_ptr, n_steps, t0, dt, seed_ptr, ckpt_every, grad_ptr, dT0_ptr,
@@ -288,6 +314,18 @@ class Solver:
         cc_step_n(self.ctx, T.data_ptr(), n_steps, t0, dt,
                   trace.data_ptr() if trace is not None else None,
                   energy.data_ptr() if energy is not None else None, st.cuda_stream)
+
+    def set_launch(self, mode: int, threads: int = 128, rows_per_lane: int = 16) -> None:
+        cc_set_launch(self.ctx, mode, threads, rows_per_lane)
+
+    def get_launch(self) -> tuple:
+        return cc_get_launch(self.ctx)
+
+    def autotune(self, T, n_trial: int = 3, stream=None) -> float:
+        """Pick the fastest launch shape on field T (restored); returns ms per step."""
+        import torch
+        st = stream if stream is not None else torch.cuda.current_stream()
+        return cc_autotune(self.ctx, T.data_ptr(), n_trial, st.cuda_stream)
 
     # ---- parameters of the adjoint: (q0, t_on, lam_scale[L], cap_scale[L]) per instance
     def n_params(self, instance: int = 0) -> int:

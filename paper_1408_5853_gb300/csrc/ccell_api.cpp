@@ -53,6 +53,12 @@ struct cc_ctx {
   // adjoint scratch, grown on demand
   double* d_adj = nullptr;
   size_t adj_cap = 0;
+  // launch shape: 0 one launch per step, 1 one persistent cooperative launch;
+  // threads per block; target rows per lane (sets the lanes per line G)
+  int mode = 0, threads = 128, rows = kRowsPerLane;
+  bool tasks_dirty = true;
+  size_t tasks_cap = 0;
+  void* d_tune = nullptr;  // autotuner copy of the caller's field
 };
 
 namespace {
@@ -142,9 +148,12 @@ void build_grid(const cc_geometry_desc& d, std::vector<double>& r, std::vector<d
   cls[N] = RC_OUTER;
 }
 
-int choose_lanes(int nr) {
+// Lanes per line: the smallest power of two giving at most `rows` rows per
+// lane (rows <= kRowsPerLane), keeping at least two rows per lane.
+int choose_lanes(int nr, int rows = kRowsPerLane) {
   int G = 1;
-  while (G < 32 && (nr + G - 1) / G > kRowsPerLane) G <<= 1;
+  while (G < 32 && (nr + G - 1) / G > rows && nr >= 4 * G) G <<= 1;
+  while ((nr + G - 1) / G > kRowsPerLane) G <<= 1;
   return G;
 }
 
@@ -212,6 +221,9 @@ void free_device(cc_ctx* c) {
   cudaFree(c->d_adj);
   c->d_adj = nullptr;
   c->adj_cap = 0;
+  cudaFree(c->d_tune);
+  c->d_tune = nullptr;
+  c->tasks_cap = 0;
   c->d_inst = nullptr;
   c->d_rg = nullptr;
   c->d_zg = nullptr;
@@ -234,21 +246,13 @@ int upload(cc_ctx* c, const std::vector<double>& dts, cudaStream_t st) {
       nrow += in.d.nr;
       nz += in.d.nz;
     }
-    std::vector<Task> tasks;
-    for (int k = 0; k < n; ++k) {
-      const Instance& in = c->inst[k];
-      const int lpw = 32 / in.G;
-      for (int j0 = 1; j0 <= in.d.nz - 2; j0 += lpw) tasks.push_back(Task{k, j0});
-    }
-    c->n_tasks = (int)tasks.size();
     const size_t elem = c->precision == CC_FP64 ? sizeof(double) : sizeof(float);
     if (cudaMalloc(&c->d_inst, sizeof(DevInst) * n) != cudaSuccess ||
         cudaMalloc(&c->d_rg, sizeof(RowGeo) * nrow) != cudaSuccess ||
         cudaMalloc(&c->d_zg, sizeof(ZGeo) * nz) != cudaSuccess ||
-        cudaMalloc(&c->d_tasks, sizeof(Task) * tasks.size()) != cudaSuccess ||
         cudaMalloc(&c->d_T2, elem * c->total_nodes) != cudaSuccess ||
         cudaMalloc(&c->d_ptab, sizeof(double) * kPowTabLen * CC_MAX_LAYERS * n) != cudaSuccess ||
-        cudaMalloc(&c->d_err, sizeof(unsigned)) != cudaSuccess) {
+        cudaMalloc(&c->d_err, 4 * sizeof(unsigned)) != cudaSuccess) {
       free_device(c);
       c->device = -1;
       cudaGetLastError();
@@ -261,10 +265,7 @@ int upload(cc_ctx* c, const std::vector<double>& dts, cudaStream_t st) {
       cudaGetLastError();
       return CC_ENOMEM;
     }
-    if (cudaMemcpy(c->d_tasks, tasks.data(), sizeof(Task) * tasks.size(),
-                   cudaMemcpyHostToDevice) != cudaSuccess ||
-        cudaMemset(c->d_err, 0, sizeof(unsigned)) != cudaSuccess)
-      return CC_ECUDA;
+    if (cudaMemset(c->d_err, 0, 4 * sizeof(unsigned)) != cudaSuccess) return CC_ECUDA;
     // geometry tables (do not change after creation)
     std::vector<RowGeo> rg;
     std::vector<ZGeo> zg;
@@ -333,6 +334,31 @@ int upload(cc_ctx* c, const std::vector<double>& dts, cudaStream_t st) {
     int cur = -1;
     cudaGetDevice(&cur);
     if (cur != c->device) return CC_EINVAL;
+  }
+  if (c->tasks_dirty) {
+    std::vector<Task> tasks;
+    for (int k = 0; k < n; ++k) {
+      Instance& in = c->inst[k];
+      in.G = choose_lanes(in.d.nr, c->rows);
+      const int lpw = 32 / in.G;
+      for (int j0 = 1; j0 <= in.d.nz - 2; j0 += lpw) tasks.push_back(Task{k, j0});
+    }
+    if (tasks.size() > c->tasks_cap) {
+      cudaFree(c->d_tasks);
+      c->d_tasks = nullptr;
+      c->tasks_cap = 0;
+      if (cudaMalloc(&c->d_tasks, sizeof(Task) * tasks.size()) != cudaSuccess) {
+        cudaGetLastError();
+        return CC_ENOMEM;
+      }
+      c->tasks_cap = tasks.size();
+    }
+    if (cudaMemcpy(c->d_tasks, tasks.data(), sizeof(Task) * tasks.size(),
+                   cudaMemcpyHostToDevice) != cudaSuccess)
+      return CC_ECUDA;
+    c->n_tasks = (int)tasks.size();
+    c->tasks_dirty = false;
+    c->dirty = true;
   }
   if (!c->dirty && dts == c->uploaded_dt) return CC_OK;
   std::vector<DevInst> h(n);
@@ -411,7 +437,6 @@ int upload(cc_ctx* c, const std::vector<double>& dts, cudaStream_t st) {
       cudaMemcpyAsync(c->d_inst, h.data(), sizeof(DevInst) * n, cudaMemcpyHostToDevice, st) !=
       cudaSuccess)
     return CC_ECUDA;
-  if (cudaStreamSynchronize(st) != cudaSuccess) return CC_ECUDA;
   c->uploaded_dt = dts;
   c->dirty = false;
   return CC_OK;
@@ -548,12 +573,36 @@ int cc_step_n(cc_ctx* c, void* T_dev, int64_t n_steps, double t0, double dt_s, d
   a.n_steps = n_steps;
   a.energy = energy_dev;
   a.err = c->d_err;
+  a.threads = c->threads;
+  a.bar = c->d_err + 1;
+  a.bar_extra = 0;
+  a.spin_limit = 1LL << 24;
+  if (const char* v = std::getenv("CC_TEST_BARRIER_TIMEOUT")) {
+    if (v[0] == '1') {  // test hook: a barrier that can never complete, short wait
+      a.bar_extra = 1;
+      a.spin_limit = 1LL << 12;
+    }
+  }
   void* bufs[2] = {T_dev, c->d_T2};
   if (c->precision == CC_MIXED) {
     if (launch_mixed_init(c->d_inst, n, c->d_tasks, c->n_tasks, c->d_lo, c->total_nodes, stream))
       return CC_ECUDA;
   }
-  for (long long s = 0; s < n_steps; ++s) {
+  bool done = false;
+  if (c->mode == 1) {
+    // all steps in one cooperative launch with a bounded grid barrier per step
+    if (cudaMemsetAsync(a.bar, 0, sizeof(unsigned), st) != cudaSuccess) return CC_ECUDA;
+    a.step = 0;
+    a.Tin = T_dev;
+    a.Tout = c->d_T2;
+    a.lo_in = c->d_lo;
+    a.lo_out = c->d_lo + c->total_nodes;
+    const int r = c->precision == CC_FP64 ? launch_steps_fp64_persistent(a, n_steps, stream)
+                                          : launch_steps_mixed_persistent(a, n_steps, stream);
+    if (r == 0) done = true;
+    else if (r != -3) return CC_ECUDA;  // -3: grid cannot be co-resident, use per-step launches
+  }
+  for (long long s = 0; !done && s < n_steps; ++s) {
     a.step = s;
     a.Tin = bufs[s & 1];
     a.Tout = bufs[(s + 1) & 1];
@@ -573,6 +622,84 @@ int cc_step_n(cc_ctx* c, void* T_dev, int64_t n_steps, double t0, double dt_s, d
       return CC_ECUDA;
   }
   return CC_OK;
+}
+
+int cc_set_launch(cc_ctx* c, int32_t mode, int32_t threads, int32_t rows_per_lane) {
+  if (!c || (mode != 0 && mode != 1) || (threads != 64 && threads != 128 && threads != 256) ||
+      rows_per_lane < 2 || rows_per_lane > kRowsPerLane)
+    return CC_EINVAL;
+  if (rows_per_lane != c->rows) c->tasks_dirty = true;
+  c->mode = mode;
+  c->threads = threads;
+  c->rows = rows_per_lane;
+  return CC_OK;
+}
+
+int cc_get_launch(const cc_ctx* c, int32_t* mode, int32_t* threads, int32_t* rows_per_lane) {
+  if (!c) return CC_EINVAL;
+  if (mode) *mode = c->mode;
+  if (threads) *threads = c->threads;
+  if (rows_per_lane) *rows_per_lane = c->rows;
+  return CC_OK;
+}
+
+int cc_autotune(cc_ctx* c, void* T_dev, int32_t n_trial, float* best_ms, void* stream) {
+  if (!c || !T_dev || n_trial < 1) return CC_EINVAL;
+  if (c->failed) return CC_ESTATE;
+  cudaStream_t st = (cudaStream_t)stream;
+  const size_t elem = c->precision == CC_FP64 ? sizeof(double) : sizeof(float);
+  const size_t bytes = elem * (size_t)c->total_nodes;
+  if (!c->d_tune) {
+    if (cudaMalloc(&c->d_tune, bytes) != cudaSuccess) {
+      cudaGetLastError();
+      return CC_ENOMEM;
+    }
+  }
+  if (cudaMemcpyAsync(c->d_tune, T_dev, bytes, cudaMemcpyDeviceToDevice, st) != cudaSuccess)
+    return CC_ECUDA;
+  // candidate lane policies: only those that change G for some instance
+  std::vector<int> rows_opts = {kRowsPerLane};
+  for (int r : {8, 4}) {
+    bool differs = false;
+    for (auto& in : c->inst) differs |= choose_lanes(in.d.nr, r) != choose_lanes(in.d.nr, kRowsPerLane);
+    if (differs) rows_opts.push_back(r);
+  }
+  cudaEvent_t e0, e1;
+  if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) return CC_ECUDA;
+  float best = 1e30f;
+  int bm = c->mode, bt = c->threads, br = c->rows;
+  int rc = CC_OK;
+  for (int mode : {0, 1})
+    for (int threads : {64, 128, 256})
+      for (int rows : rows_opts) {
+        cc_set_launch(c, mode, threads, rows);
+        rc = cc_step_n(c, T_dev, 1, 0.0, 0.0, nullptr, nullptr, stream);  // warm and upload
+        if (rc != CC_OK) break;
+        cudaEventRecord(e0, st);
+        rc = cc_step_n(c, T_dev, n_trial, 0.0, 0.0, nullptr, nullptr, stream);
+        cudaEventRecord(e1, st);
+        if (rc != CC_OK || cudaEventSynchronize(e1) != cudaSuccess) {
+          rc = rc != CC_OK ? rc : CC_ECUDA;
+          break;
+        }
+        float ms = 0.0f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        ms /= (float)n_trial;
+        if (ms < best) {
+          best = ms;
+          bm = mode;
+          bt = threads;
+          br = rows;
+        }
+        cudaMemcpyAsync(T_dev, c->d_tune, bytes, cudaMemcpyDeviceToDevice, st);
+      }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  cc_set_launch(c, bm, bt, br);
+  cudaMemcpyAsync(T_dev, c->d_tune, bytes, cudaMemcpyDeviceToDevice, st);
+  if (cudaStreamSynchronize(st) != cudaSuccess) return CC_ECUDA;
+  if (best_ms) *best_ms = best;
+  return rc == CC_OK ? cc_sync(c, stream) : rc;
 }
 
 int cc_sync(cc_ctx* c, void* stream) {
@@ -681,6 +808,7 @@ int adjoint_impl(cc_ctx* c, const void* T0_dev, int64_t n_steps, double t0, doub
   a.s_tab = s_tab;
   a.n_steps = n_steps;
   a.err = c->d_err;
+  a.threads = c->threads;
   // forward sweep with checkpoints (slots 0 and 1 of the segment buffer)
   for (long long s = 0; s < n_steps; ++s) {
     double* cur = segs + nodes * (s & 1);

@@ -116,4 +116,42 @@ __device__ __forceinline__ double solve_separators(double ae, double be, double 
   return dt * frcp(bt);
 }
 
+// Grid-wide barrier of a cooperative (co-resident) launch with a bounded wait.
+// bar[0] counts arrivals, bar[1] is the generation.  Every thread fences its
+// writes before thread 0 arrives; the last arrival resets the count and bumps
+// the generation; the others poll the generation at most spin_limit times,
+// then record a timeout (bit 1 of the error word) and report failure, so a
+// failed barrier ends the kernel instead of hanging the GPU.
+__device__ __forceinline__ bool grid_barrier(unsigned* bar, unsigned extra, long long spin_limit,
+                                             unsigned* err) {
+  __shared__ int ok_s;
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    volatile unsigned* vgen = bar + 1;
+    const unsigned gen = *vgen;
+    int ok = 1;
+    const unsigned arrived = atomicAdd(bar, 1u);
+    if (arrived == gridDim.x + extra - 1) {
+      atomicExch(bar, 0u);
+      __threadfence();
+      atomicAdd(bar + 1, 1u);
+    } else {
+      long long spins = 0;
+      while (*vgen == gen) {
+        if (++spins > spin_limit) {
+          atomicOr(err, 2u);
+          ok = 0;
+          break;
+        }
+        __nanosleep(64);
+      }
+    }
+    __threadfence();
+    ok_s = ok;
+  }
+  __syncthreads();
+  return ok_s != 0;
+}
+
 }  // namespace ccell

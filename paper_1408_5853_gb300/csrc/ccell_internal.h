@@ -109,7 +109,13 @@ struct StepArgs {
   double* trace;         // [n_inst][n_steps][2] or null
   long long n_steps;
   double* energy;        // [n_inst][5] or null
-  unsigned* err;         // error word: bit0 non-finite
+  unsigned* err;         // error word: bit0 non-finite, bit1 barrier timeout
+  // launch shape
+  int threads;           // threads per block (64, 128 or 256)
+  // persistent launches: grid barrier state [count, generation], bounded wait
+  unsigned* bar;
+  unsigned bar_extra;    // extra arrivals expected (nonzero only to test the timeout)
+  long long spin_limit;  // polls before a barrier wait gives up
 };
 
 // Reverse sweep of the adjoint (ccell_adjoint.cu).
@@ -146,6 +152,10 @@ int launch_adj_seed(const DevInst* insts, int n_inst, const double* trace, const
                     long long n_steps, double* seed, double* loss, void* stream);
 int launch_step_fp64(const StepArgs& a, void* stream);
 int launch_step_mixed(const StepArgs& a, void* stream);
+// n steps in one cooperative launch; buffers alternate Tin -> Tout -> Tin ...
+// (and lo_in/lo_out for mixed).  Returns -3 if the grid cannot be co-resident.
+int launch_steps_fp64_persistent(const StepArgs& a, long long n, void* stream);
+int launch_steps_mixed_persistent(const StepArgs& a, long long n, void* stream);
 int launch_mixed_init(const DevInst* insts, int n_inst, const Task* tasks, int n_tasks,
                       float* lo, long long n_total, void* stream);
 int launch_boundary_trace_zero(double* trace, long long n, void* stream);

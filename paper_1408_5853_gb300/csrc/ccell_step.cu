@@ -23,7 +23,7 @@
 #include <atomic>
 #include <cmath>
 
-#include "ccell_device.cuh"
+#include "ccell_fp64_task.cuh"
 
 namespace ccell {
 
@@ -80,247 +80,10 @@ int launch_waveform(const DevInst* insts, int n_inst, long long n_steps, double 
   return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }
 
-// ---------------------------------------------------------------------------
-// FP64 step
-// ---------------------------------------------------------------------------
-// One warp task: 32/G consecutive lines of one instance.
+// Grid-stride over warp tasks; the grid is sized to the resident capacity so
+// that no partial last wave leaves SMs idle.
 template <bool ENERGY, bool TRACE>
-__device__ __forceinline__ void step_fp64_task(const StepArgs& a, const Task tk, const int lane) {
-  const DevInst& I = a.insts[tk.inst];
-  const int G = I.G;
-  const int lg = __ffs(G) - 1;
-  const int grp = lane >> lg, l = lane & (G - 1);
-  const int nr = I.nr, N = nr - 1, M = I.nz - 1;
-  const int j_req = tk.j0 + grp;
-  const bool active = j_req <= M - 1;
-  const int j = active ? j_req : M - 1;  // idle lane groups recompute a valid line
-  const int i_lo = (l * nr) >> lg;
-  const int i_hi = ((l + 1) * nr) >> lg;
-  const int cnt = i_hi - i_lo;  // 2 .. kRowsPerLane
-
-  const double* Tin = static_cast<const double*>(a.Tin) + I.t_off;
-  double* Tout = static_cast<double*>(a.Tout) + I.t_off;
-  const double* Tj = Tin + (long long)j * nr;
-  const double* Ts = Tj - nr;
-  const double* Tn = Tj + nr;
-  const ZGeo zg = I.zg[j];
-  const double s = a.s_tab[a.step * a.n_inst + tk.inst];
-  const double tau = I.tau, inv_tau = I.inv_tau;
-  const int frule = I.face_rule;
-
-  double cp[kRowsPerLane], ap[kRowsPerLane], dp[kRowsPerLane], mm[kRowsPerLane];
-  double pc = 0.0, pa = 0.0, pd = 0.0;   // c', a', d' of the previous interior row
-  double Dacc = 0.0, Aacc = 0.0, P = 1.0; // first interior row = Dacc + P x_next - Aacc L
-  double ae = 0.0, be = 1.0, ce = 0.0, de = 0.0;  // separator row
-  double le_prev = 0.0;
-  bool have_le = false;
-  double eQ = 0.0, eD = 0.0, eN = 0.0;
-
-  double Tm1 = (i_lo > 0) ? Tj[i_lo - 1] : 0.0;
-  double T0 = Tj[i_lo];
-
-  // ---- 1. assemble rows and eliminate the segment downwards
-#pragma unroll
-  for (int k = 0; k < kRowsPerLane; ++k) {
-    if (k < cnt) {
-      const int i = i_lo + k;
-      const RowGeo g = I.rg[i];
-      const double Tp1 = (i < N) ? Tj[i + 1] : 0.0;
-      double ra, rb, rc, rd, m = 0.0;
-      if (g.cls == RC_REGULAR) {
-        const DevMaterial& Mt = I.mat[g.seg];
-        const double tS = Ts[i], tN = Tn[i];
-        const double lw = have_le ? le_prev : lam_face(Mt, frule, Tm1, T0);
-        const double le = lam_face(Mt, frule, T0, Tp1);
-        const double ls = lam_face(Mt, frule, tS, T0);
-        const double ln = lam_face(Mt, frule, T0, tN);
-        const double rhoc = Mt.rho * cap_eval(Mt, T0);
-        // Eq. (Lambda_j), explicit in T
-        const double Lj = ln * (tN - T0) * zg.gzn - ls * (T0 - tS) * zg.gzs;
-        double X = 0.0;  // Eq. (source)
-        if (g.seg == I.src_layer && s != 0.0) {
-          X = I.q0 * s;
-          if (I.g_model == 1) X *= I.g_ref / sqrt(T0);
-        }
-        // Eq. (ABC)
-        const double A = -g.gA * lw, C = -g.gC * le;
-        const double rct = rhoc * inv_tau;
-        ra = A;
-        rc = C;
-        rb = rct - A - C;
-        rd = fma(rct, T0, Lj + X);
-        le_prev = le;
-        have_le = true;
-        if (ENERGY) {
-          const double V = g.V2 * zg.etabar;
-          m = V * rhoc;
-          eQ = fma(tau * V, X, eQ);
-          if (j == 1) {
-            const double f = tau * g.V2 * ls * (tS - T0) / zg.eta_s;
-            if (I.bc_z0 == CC_DIRICHLET) eD += f; else eN += f;
-          }
-          if (j == M - 1) {
-            const double f = tau * g.V2 * ln * (tN - T0) / zg.eta_n;
-            if (I.bc_zmax == CC_DIRICHLET) eD += f; else eN += f;
-          }
-        }
-      } else if (g.cls == RC_IFACE) {
-        // Eq. (cc_first_1)/(cc_first_3) as the row (a, b, c | 0)
-        double lm, lp;
-        if (I.interface_rule == 0) {
-          lm = lam_eval(I.mat[g.segw], T0);
-          lp = lam_eval(I.mat[g.seg], T0);
-        } else {
-          lm = g.rw * lam_face(I.mat[g.segw], frule, Tm1, T0);
-          lp = g.re * lam_face(I.mat[g.seg], frule, T0, Tp1);
-        }
-        ra = -lm * g.he;
-        rc = -lp * g.hw;
-        rb = fma(lm, g.he, lp * g.hw);
-        rd = 0.0;
-        have_le = false;
-      } else if (g.cls == RC_AXIS) {  // That_0 = That_1
-        ra = 0.0; rb = 1.0; rc = -1.0; rd = 0.0;
-        have_le = false;
-      } else {  // r = r_max
-        if (I.bc_rmax == CC_DIRICHLET) { ra = 0.0; rb = 1.0; rc = 0.0; rd = I.t_d; }
-        else { ra = -1.0; rb = 1.0; rc = 0.0; rd = 0.0; }
-        have_le = false;
-      }
-      mm[k] = m;
-      if (k < cnt - 1) {
-        const double den = (k == 0) ? rb : fma(-ra, pc, rb);
-        const double r = frcp(den);
-        const double c1 = rc * r;
-        const double a1 = (k == 0) ? ra * r : -ra * pa * r;
-        const double d1 = (k == 0) ? rd * r : fma(-ra, pd, rd) * r;
-        cp[k] = c1;
-        ap[k] = a1;
-        dp[k] = d1;
-        Dacc = fma(P, d1, Dacc);
-        Aacc = fma(P, a1, Aacc);
-        P = -P * c1;
-        pc = c1;
-        pa = a1;
-        pd = d1;
-      } else {
-        ae = ra; be = rb; ce = rc; de = rd;
-      }
-      Tm1 = T0;
-      T0 = Tp1;
-    }
-  }
-
-  // ---- 2. separator system (one row per lane), cyclic reduction
-  const double xs = solve_separators(ae, be, ce, de, pa, pc, pd, Dacc, Aacc, P, G, l);
-
-  // ---- 3. back substitution inside the segment
-  const double L = __shfl_up_sync(kFull, xs, 1, G);
-  {
-    double xn = xs;
-#pragma unroll
-    for (int k = kRowsPerLane - 2; k >= 0; --k) {
-      if (k <= cnt - 2) {
-        const double x = fma(-cp[k], xn, fma(-ap[k], L, dp[k]));
-        dp[k] = x;
-        xn = x;
-      }
-    }
-#pragma unroll
-    for (int k = 0; k < kRowsPerLane; ++k)
-      if (k == cnt - 1) dp[k] = xs;  // dp[k] = x_k for every row of the segment
-  }
-  const double xfirst = dp[0];
-  const double xnext = __shfl_down_sync(kFull, xfirst, 1, G);  // first row of lane l+1
-
-  // ---- 4. stores, boundary rows, energy and trace epilogue
-  double eE = 0.0, eI = 0.0;
-  bool bad = false;
-  if (active) {
-    double* Oj = Tout + (long long)j * nr;
-    const bool row0 = (j == 1), rowM = (j == M - 1);
-    double* O0 = Tout;
-    double* OM = Tout + (long long)M * nr;
-#pragma unroll
-    for (int k = 0; k < kRowsPerLane; ++k) {
-      if (k < cnt) {
-        const int i = i_lo + k;
-        const double x = dp[k];
-        bad |= not_finite(x);
-        Oj[i] = x;
-        if (row0) O0[i] = (I.bc_z0 == CC_DIRICHLET) ? I.t_d : x;
-        if (rowM) OM[i] = (I.bc_zmax == CC_DIRICHLET) ? I.t_d : x;
-        if (ENERGY) {
-          eE = fma(mm[k], x - Tj[i], eE);
-          const int cls = I.rg[i].cls;
-          if (cls == RC_IFACE || cls == RC_OUTER) {
-            const double xw = (k == 0) ? L : dp[k > 0 ? k - 1 : 0];
-            const double Tw = Tj[i - 1], Ti = Tj[i];
-            const RowGeo gw = I.rg[i - 1];
-            const double ke = tau * gw.V2 * zg.etabar * gw.gC *
-                              lam_face(I.mat[gw.seg], frule, Tw, Ti);
-            const double fw = ke * (x - xw);  // into node i-1 (regular)
-            if (cls == RC_OUTER) {
-              if (I.bc_rmax == CC_DIRICHLET) eD += fw; else eN += fw;
-            } else {
-              const double xe = (k == cnt - 1) ? xnext : dp[k < kRowsPerLane - 1 ? k + 1 : k];  // x_{i+1}
-              const RowGeo ge = I.rg[i + 1];
-              const double kw = tau * ge.V2 * zg.etabar * ge.gA *
-                                lam_face(I.mat[ge.seg], frule, Ti, Tj[i + 1]);
-              eI += fw + kw * (x - xe);  // into node i+1 (regular)
-            }
-          }
-        }
-      }
-    }
-  }
-  if (bad) atomicOr(a.err, 1u);
-
-  if (ENERGY || TRACE) {
-    double tr = 0.0;
-    if (TRACE && active && l == G - 1) {  // this lane owns That(r_max, z_j)
-      tr = zg.wnorm * xs;
-      double* trs = a.trace + ((long long)tk.inst * a.n_steps + a.step) * 2;
-      if (j == 1) {
-        const double x0 = (I.bc_z0 == CC_DIRICHLET) ? I.t_d : xs;
-        tr = fma(I.zg[0].wnorm, x0, tr);
-        trs[0] = x0;
-      }
-      if (j == M - 1) {
-        const double xM = (I.bc_zmax == CC_DIRICHLET) ? I.t_d : xs;
-        tr = fma(I.zg[M].wnorm, xM, tr);
-      }
-    }
-    if (!active) { eE = eQ = eD = eI = eN = 0.0; }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-      if (ENERGY) {
-        eE += __shfl_xor_sync(kFull, eE, o);
-        eQ += __shfl_xor_sync(kFull, eQ, o);
-        eD += __shfl_xor_sync(kFull, eD, o);
-        eI += __shfl_xor_sync(kFull, eI, o);
-        eN += __shfl_xor_sync(kFull, eN, o);
-      }
-      if (TRACE) tr += __shfl_xor_sync(kFull, tr, o);
-    }
-    if (lane == 0) {
-      if (ENERGY) {
-        double* e = a.energy + (long long)tk.inst * 5;
-        atomicAdd(e + 0, eE);
-        atomicAdd(e + 1, eQ);
-        atomicAdd(e + 2, eD);
-        atomicAdd(e + 3, eI);
-        atomicAdd(e + 4, eN);
-      }
-      if (TRACE) atomicAdd(a.trace + ((long long)tk.inst * a.n_steps + a.step) * 2 + 1, tr);
-    }
-  }
-}
-
-// Persistent grid: as many blocks as can be resident, each warp looping over
-// tasks with a grid stride, so that no partial last wave leaves SMs idle.
-template <bool ENERGY, bool TRACE>
-__global__ void __launch_bounds__(128) step_fp64_kernel(const StepArgs a) {
+__global__ void __launch_bounds__(256) step_fp64_kernel(const StepArgs a) {
   const int lane = threadIdx.x & 31;
   const int n_warps = (int)((gridDim.x * blockDim.x) >> 5);
   for (int w = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5); w < a.n_tasks; w += n_warps)
@@ -328,20 +91,12 @@ __global__ void __launch_bounds__(128) step_fp64_kernel(const StepArgs a) {
 }
 
 template <bool ENERGY, bool TRACE>
-static int launch_fp64_variant(const StepArgs& a, cudaStream_t st) {
-  constexpr int threads = 128;
-  static int resident = 0;  // blocks per SM x SMs, per variant (one device per process)
-  if (resident == 0) {
-    int dev = 0, sms = 0, per_sm = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, step_fp64_kernel<ENERGY, TRACE>,
-                                                  threads, 0);
-    resident = sms * (per_sm > 0 ? per_sm : 1);
-  }
-  const int need = (a.n_tasks * 32 + threads - 1) / threads;
-  step_fp64_kernel<ENERGY, TRACE><<<need < resident ? need : resident, threads, 0, st>>>(a);
-  return 0;
+static void launch_fp64_variant(const StepArgs& a, cudaStream_t st) {
+  static int resident[3] = {0, 0, 0};
+  const int t = a.threads > 0 ? a.threads : 128, si = shape_index(t);
+  if (resident[si] == 0) resident[si] = resident_blocks(step_fp64_kernel<ENERGY, TRACE>, t);
+  const int need = (a.n_tasks * 32 + t - 1) / t;
+  step_fp64_kernel<ENERGY, TRACE><<<need < resident[si] ? need : resident[si], t, 0, st>>>(a);
 }
 
 int launch_step_fp64(const StepArgs& a, void* stream) {

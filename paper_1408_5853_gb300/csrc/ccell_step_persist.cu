@@ -1,0 +1,57 @@
+// FP64 time step, all steps of a call in one cooperative launch (see
+// ccell_step.cu for the scheme and ccell_fp64_task.cuh for one warp task).
+#include <cuda_runtime.h>
+
+#include "ccell_fp64_task.cuh"
+
+namespace ccell {
+
+// All n steps in one cooperative launch, a bounded grid barrier between steps.
+template <bool ENERGY, bool TRACE>
+__global__ void __launch_bounds__(256) steps_fp64_persistent_kernel(const StepArgs a,
+                                                                     long long n) {
+  const int lane = threadIdx.x & 31;
+  const int n_warps = (int)((gridDim.x * blockDim.x) >> 5);
+  StepArgs s = a;
+  for (long long q = 0; q < n; ++q) {
+    s.step = a.step + q;
+    s.Tin = (q & 1) ? a.Tout : a.Tin;
+    s.Tout = (q & 1) ? const_cast<void*>(a.Tin) : a.Tout;
+    for (int w = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5); w < a.n_tasks; w += n_warps)
+      step_fp64_task<ENERGY, TRACE>(s, a.tasks[w], lane);
+    if (!grid_barrier(a.bar, a.bar_extra, a.spin_limit, a.err)) return;
+  }
+}
+
+template <bool ENERGY, bool TRACE>
+static int launch_fp64_persistent_variant(const StepArgs& a, long long n, cudaStream_t st) {
+  static int resident[3] = {0, 0, 0};
+  const int t = a.threads > 0 ? a.threads : 128, si = shape_index(t);
+  auto kern = steps_fp64_persistent_kernel<ENERGY, TRACE>;
+  if (resident[si] == 0) resident[si] = resident_blocks(kern, t);
+  const int need = (a.n_tasks * 32 + t - 1) / t;
+  const int blocks = need < resident[si] ? need : resident[si];
+  StepArgs copy = a;
+  void* args[] = {&copy, &n};
+  const cudaError_t e = cudaLaunchCooperativeKernel((const void*)kern, blocks, t, args, 0, st);
+  if (e == cudaErrorCooperativeLaunchTooLarge) {
+    cudaGetLastError();
+    return -3;
+  }
+  return e == cudaSuccess ? 0 : -1;
+}
+
+int launch_steps_fp64_persistent(const StepArgs& a, long long n, void* stream) {
+  cudaStream_t st = (cudaStream_t)stream;
+  const bool E = a.energy != nullptr, T = a.trace != nullptr;
+  int r;
+  if (E && T) r = launch_fp64_persistent_variant<true, true>(a, n, st);
+  else if (E) r = launch_fp64_persistent_variant<true, false>(a, n, st);
+  else if (T) r = launch_fp64_persistent_variant<false, true>(a, n, st);
+  else r = launch_fp64_persistent_variant<false, false>(a, n, st);
+  count_launch();
+  if (r) return r;
+  return cudaGetLastError() == cudaSuccess ? 0 : -1;
+}
+
+}  // namespace ccell

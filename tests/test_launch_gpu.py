@@ -1,0 +1,139 @@
+"""Launch shapes of the time step on the GPU: one launch per step or all steps
+in one cooperative launch with a bounded grid barrier, block sizes and lane
+policies, the autotuner, the barrier timeout report, and CUDA-graph capture.
+Results must not depend on the launch shape beyond rounding (FP64 bar:
+1e-9 K against the oracle; mixed: 1e-3 K)."""
+import os
+
+import numpy as np
+import pytest
+
+from oracle import oracle
+from paper_1408_5853_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+
+def _run(cfgs, T0s, n, precision, shape, t0=0.0):
+    import torch
+    from paper_1408_5853_gb300 import ccell
+    sol = ccell.Solver(cfgs, precision=precision)
+    if shape is not None:
+        sol.set_launch(*shape)
+    dt = torch.float64 if precision == 0 else torch.float32
+    T = torch.tensor(np.concatenate([t.ravel() for t in T0s]), dtype=dt, device="cuda")
+    tr = torch.zeros(len(cfgs) * n * 2, dtype=torch.float64, device="cuda")
+    en = torch.zeros(len(cfgs) * 5, dtype=torch.float64, device="cuda")
+    sol.step(T, n, t0, 0.0, tr, en)
+    sol.sync()
+    out = T.double().cpu().numpy()
+    sol.close()
+    return out, tr.view(len(cfgs), n, 2).cpu().numpy(), en.view(len(cfgs), 5).cpu().numpy()
+
+
+SHAPES = [(1, 128, 16), (1, 256, 8), (1, 64, 4), (0, 64, 4), (0, 256, 8)]
+
+
+@pytest.mark.parametrize("shape", SHAPES)
+@pytest.mark.parametrize("precision", [0, 1])
+def test_launch_shapes_parity(shape, precision):
+    cfgs = inputs.batched_cases(seed=1, n=5)
+    T0s = []
+    for k, c in enumerate(cfgs):
+        c["dt"] = 0.9 * oracle.tau_stab(c, 20.0, 100.0)
+        T0 = inputs.initial_field(c, "smooth", seed=k)
+        if precision == 1:
+            T0 = T0.astype(np.float32).astype(np.float64)
+        T0s.append(T0)
+    n = 13
+    out, tr, en = _run(cfgs, T0s, n, precision, shape)
+    tol = 1e-9 if precision == 0 else 1e-3
+    ofs = 0
+    for k, c in enumerate(cfgs):
+        To, tro, eo = oracle.step_n(c, T0s[k], n, 0.0, c["dt"])
+        nn = c["nr"] * c["nz"]
+        assert np.max(np.abs(out[ofs:ofs + nn].reshape(To.shape) - To)) <= tol, k
+        assert np.max(np.abs(tr[k] - tro)) <= tol, k
+        ofs += nn
+
+
+def test_persistent_small_case_matches_oracle():
+    cfg = inputs.small_case()
+    T0 = inputs.initial_field(cfg, "smooth", seed=3)
+    n = 400
+    t0 = 1e-3 - 200 * cfg["dt"]
+    out, tr, en = _run([cfg], [T0], n, 0, (1, 128, 16), t0=t0)
+    To, tro, eo = oracle.step_n(cfg, T0, n, t0, cfg["dt"])
+    assert np.max(np.abs(out.reshape(To.shape) - To)) <= 1e-9
+    assert np.max(np.abs(tr[0] - tro)) <= 1e-9
+    assert np.max(np.abs(en[0] - eo)) <= 1e-9 * abs(eo[1])
+
+
+def test_barrier_timeout_is_reported():
+    """A barrier that can never complete (test hook: one arrival too many
+    expected, short wait) must end the kernel and surface as CC_ETIMEOUT."""
+    from paper_1408_5853_gb300 import ccell
+    cfg = inputs.small_case()
+    T0 = inputs.initial_field(cfg)
+    os.environ["CC_TEST_BARRIER_TIMEOUT"] = "1"
+    try:
+        with pytest.raises(ccell.CCError) as e:
+            _run([cfg], [T0], 5, 0, (1, 128, 16))
+        assert e.value.status == ccell.CC_ETIMEOUT
+    finally:
+        del os.environ["CC_TEST_BARRIER_TIMEOUT"]
+    # the GPU context stays usable afterwards
+    out, _, _ = _run([cfg], [T0], 3, 0, (1, 128, 16))
+    To, _, _ = oracle.step_n(cfg, T0, 3, 0.0, cfg["dt"])
+    assert np.max(np.abs(out.reshape(To.shape) - To)) <= 1e-9
+
+
+def test_autotune_keeps_field_and_picks_a_valid_shape():
+    import torch
+    from paper_1408_5853_gb300 import ccell
+    cfgs = inputs.batched_cases(seed=1, n=8)
+    for c in cfgs:
+        c["dt"] = 0.9 * oracle.tau_stab(c, 20.0, 100.0)
+    sol = ccell.Solver(cfgs, precision=ccell.MIXED)
+    T0 = np.concatenate([inputs.initial_field(c, "smooth", seed=k).ravel()
+                         for k, c in enumerate(cfgs)])
+    T = torch.tensor(T0, dtype=torch.float32, device="cuda")
+    keep = T.clone()
+    ms = sol.autotune(T, n_trial=2)
+    assert ms > 0.0
+    mode, threads, rows = sol.get_launch()
+    assert mode in (0, 1) and threads in (64, 128, 256) and 2 <= rows <= 16
+    assert torch.equal(T, keep)
+    sol.close()
+
+
+@pytest.mark.parametrize("mode", [0, 1])
+def test_cuda_graph_replay_equals_direct_call(mode):
+    import torch
+    from paper_1408_5853_gb300 import ccell
+    cfg = inputs.small_case()
+    T0 = inputs.initial_field(cfg, "smooth", seed=8)
+    n = 25
+    sol = ccell.Solver(cfg)
+    sol.set_launch(mode, 128, 16)
+    Ta = torch.tensor(T0.ravel(), dtype=torch.float64, device="cuda")
+    tra = torch.zeros(2 * n, dtype=torch.float64, device="cuda")
+    ena = torch.zeros(5, dtype=torch.float64, device="cuda")
+    sol.step(Ta.clone(), n, 0.0, 0.0, tra, ena)   # warm-up: sizes the context's buffers
+    torch.cuda.synchronize()
+    Tb, trb, enb = Ta.clone(), torch.zeros_like(tra), torch.zeros_like(ena)
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g):
+        sol.step(Tb, n, 0.0, 0.0, trb, enb)
+    Tb.copy_(Ta)
+    enb.zero_()
+    g.replay()
+    torch.cuda.synchronize()
+    Tc, trc, enc = Ta.clone(), torch.zeros_like(tra), torch.zeros_like(ena)
+    sol.step(Tc, n, 0.0, 0.0, trc, enc)
+    sol.sync()
+    assert torch.equal(Tb, Tc)
+    # the z-mean of the trace is summed with FP64 atomics: equal up to summation order
+    assert torch.allclose(trb, trc, rtol=1e-13, atol=0.0)
+    assert torch.allclose(enb, enc, rtol=1e-12, atol=0.0)
+    sol.close()
