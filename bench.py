@@ -24,6 +24,8 @@ import subprocess
 import sys
 import time
 
+import numpy as np
+
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
@@ -189,7 +191,10 @@ def run_ours(args, world, rank, local):
 
     # ---- mixed-precision path on the same workload
     mixed = None
-    try:
+    if "mixed" not in args.parts:
+        mixed = {"skipped": True}
+    else:
+      try:
         solm, Tm, trm, enm = make(ccell.MIXED)
         msm, _ = timed_steps(solm, Tm, trm, enm, args.steps, args.warmup)
         mixed = {"value": nodes * n_in * args.steps * world / (msm / 1e3),
@@ -200,8 +205,10 @@ def run_ours(args, world, rank, local):
         solm.close()
         if args.acc_steps > 0:
             mixed.update(mixed_accuracy(cfg, T0, args.acc_steps, dev))
-    except ccell.CCError as err:
+      except ccell.CCError as err:
         mixed = {"unavailable": str(err)}
+    batched = run_batched(args, dev) if "batched" in args.parts else {"skipped": True}
+    adjoint = run_adjoint(args, dev) if "adjoint" in args.parts else {"skipped": True}
 
     if rank != 0:
         return None
@@ -229,6 +236,8 @@ def run_ours(args, world, rank, local):
                          "note": "effective: the field stays L2-resident during a call"},
         "energy_identity_rel": ident,
         "mixed": mixed,
+        "batched": batched,
+        "adjoint": adjoint,
         "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": int(hT.numel() * 8),
                 "d2h_bytes_per_step": int(hOut.numel() * 8 + hTr.numel() * 8)},
         "gpu_launches": int(launches),
@@ -237,6 +246,88 @@ def run_ours(args, world, rank, local):
     if world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(args.cpu_sample_steps)
     return line
+
+
+def run_batched(args, dev) -> dict:
+    """Design sweep: 256 ragged 5-layer instances (seed 1) in one context,
+    mixed precision, per-instance dt = 0.9 x the axial stability bound, the
+    launch shape chosen by the autotuner, each call captured in a CUDA graph
+    and replayed."""
+    import torch
+
+    from paper_1408_5853_gb300 import ccell, inputs
+    cfgs = inputs.batched_cases(seed=1, n=args.batch_instances)
+    sol = ccell.Solver(cfgs, precision=ccell.MIXED)
+    for k in range(len(cfgs)):
+        ccell.cc_set_dt(sol.ctx, k, 0.9 * sol.tau_stab(k))
+    total = sol.total
+    T0 = np.concatenate([inputs.initial_field(c, "uniform").ravel() for c in cfgs])
+    T = torch.tensor(T0, dtype=torch.float32, device=dev)
+    tune_ms = sol.autotune(T, n_trial=2)
+    n_in = args.batch_inner
+    trace = torch.zeros(len(cfgs) * n_in * 2, dtype=torch.float64, device=dev)
+    energy = torch.zeros(len(cfgs) * 5, dtype=torch.float64, device=dev)
+    sol.step(T, n_in, 0.0, 0.0, trace, energy)      # warm-up sizes the buffers
+    torch.cuda.synchronize()
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph):
+        sol.step(T, n_in, 0.0, 0.0, trace, energy)
+    for _ in range(args.warmup):
+        graph.replay()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(args.steps):
+        graph.replay()
+    e1.record()
+    torch.cuda.synchronize()
+    sol.sync()
+    ms = e0.elapsed_time(e1)
+    mode, threads, rows = sol.get_launch()
+    sol.close()
+    return {"instances": len(cfgs), "nodes": int(total), "time_steps_per_replay": n_in,
+            "precision": "mixed", "value": total * n_in * args.steps / (ms / 1e3),
+            "unit": "node-updates/s", "ms_per_replay": ms / args.steps,
+            "launch": {"mode": "persistent" if mode == 1 else "per-step", "threads": threads,
+                       "rows_per_lane": rows, "autotune_ms_per_step": tune_ms},
+            "graph": "each replay is one captured cc_step_n call"}
+
+
+def run_adjoint(args, dev) -> dict:
+    """Gradient of the surface-waveform loss on the 5-layer 256 x 1024 case
+    (tanh pulse edges, 28/42 K target), checkpoint every 256 steps; then a
+    batch of 64 such gradients in one context."""
+    import torch
+
+    from paper_1408_5853_gb300 import ccell, inputs
+    out = {}
+    for label, n_inst, n in (("single", 1, args.adj_steps), ("batch64", 64, args.adj_batch_steps)):
+        cfg = inputs.adjoint_case()
+        cfgs = [cfg] * n_inst
+        sol = ccell.Solver(cfgs)
+        T0 = torch.tensor(np.tile(inputs.initial_field(cfg, "uniform").ravel(), n_inst),
+                          dtype=torch.float64, device=dev)
+        t = cfg["dt"] * np.arange(1, n + 1)
+        tgt = torch.tensor(np.tile(inputs.target_waveform(cfg, t), n_inst), dtype=torch.float64,
+                           device=dev)
+        n_w = min(n, 256)                                     # warm-up on the first steps
+        sol.adjoint(T0, n_w, 0.0, 0.0, tgt.view(n_inst, n)[:, :n_w].contiguous().view(-1),
+                    ckpt_every=256)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        loss, grad, _ = sol.adjoint(T0, n, 0.0, 0.0, tgt, ckpt_every=256)
+        e1.record()
+        torch.cuda.synchronize()
+        sol.sync()
+        ms = e0.elapsed_time(e1)
+        nodes = cfg["nr"] * cfg["nz"] * n_inst
+        out[label] = {"instances": n_inst, "grid": f"{cfg['nr']}x{cfg['nz']}", "steps": n,
+                      "ms_per_gradient": ms / n_inst, "ms_total": ms,
+                      "forward_equivalent_node_updates_per_s": nodes * n / (ms / 1e3),
+                      "loss": float(loss[0].item()), "grad_norm": float(grad.norm().item())}
+        sol.close()
+    return out
 
 
 def mixed_accuracy(cfg, T0, n, dev) -> dict:
@@ -326,10 +417,17 @@ def main():
     ap.add_argument("--ref-inner", type=int, default=60, help="time steps per reference step")
     ap.add_argument("--cpu-sample-steps", type=int, default=300)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--parts", default="fp64,mixed,batched,adjoint",
+                    help="comma list of extra parts to run besides the FP64 headline")
+    ap.add_argument("--batch-instances", type=int, default=256)
+    ap.add_argument("--batch-inner", type=int, default=20, help="time steps per batched replay")
+    ap.add_argument("--adj-steps", type=int, default=4096)
+    ap.add_argument("--adj-batch-steps", type=int, default=512)
     ap.add_argument("--acc-steps", type=int, default=20000,
                     help="steps of the mixed-vs-FP64 accuracy check (0: skip)")
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     args = ap.parse_args()
+    args.parts = set(args.parts.split(","))
     args.warmup = max(args.warmup, 3) if args.impl == "ours" else args.warmup
     world, rank, local = _dist()
     if world > 1:
