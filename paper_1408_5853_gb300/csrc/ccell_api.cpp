@@ -43,6 +43,10 @@ struct cc_ctx {
   ZGeo* d_zg = nullptr;
   Task* d_tasks = nullptr;
   int n_tasks = 0;
+  TileTask* d_tiles = nullptr;
+  int n_tiles = 0;
+  size_t tiles_cap = 0;
+  int smem_bytes = 0;
   void* d_T2 = nullptr;       // ping-pong partner of the caller's field
   float* d_lo = nullptr;      // mixed precision: low-order parts (two buffers)
   double* d_s = nullptr;      // waveform table
@@ -213,6 +217,9 @@ void free_device(cc_ctx* c) {
   cudaFree(c->d_rg);
   cudaFree(c->d_zg);
   cudaFree(c->d_tasks);
+  cudaFree(c->d_tiles);
+  c->d_tiles = nullptr;
+  c->tiles_cap = 0;
   cudaFree(c->d_T2);
   cudaFree(c->d_lo);
   cudaFree(c->d_s);
@@ -357,6 +364,34 @@ int upload(cc_ctx* c, const std::vector<double>& dts, cudaStream_t st) {
                    cudaMemcpyHostToDevice) != cudaSuccess)
       return CC_ECUDA;
     c->n_tasks = (int)tasks.size();
+    // FP64 CTA tiles: (threads / 32) warps x 32/G lines
+    std::vector<TileTask> tiles;
+    int smem = 0;
+    for (int k = 0; k < n; ++k) {
+      const Instance& in = c->inst[k];
+      const int lpc = (c->threads / 32) * (32 / in.G);
+      for (int j0 = 1; j0 <= in.d.nz - 2; j0 += lpc) {
+        const int nl = std::min(lpc, in.d.nz - 1 - j0);
+        tiles.push_back(TileTask{k, j0, nl, 0});
+      }
+      smem = std::max(smem, (2 * std::min(lpc, in.d.nz - 2) + 3) * smem_row_stride(in.d.nr) *
+                                (int)sizeof(double));
+    }
+    if (tiles.size() > c->tiles_cap) {
+      cudaFree(c->d_tiles);
+      c->d_tiles = nullptr;
+      c->tiles_cap = 0;
+      if (cudaMalloc(&c->d_tiles, sizeof(TileTask) * tiles.size()) != cudaSuccess) {
+        cudaGetLastError();
+        return CC_ENOMEM;
+      }
+      c->tiles_cap = tiles.size();
+    }
+    if (cudaMemcpy(c->d_tiles, tiles.data(), sizeof(TileTask) * tiles.size(),
+                   cudaMemcpyHostToDevice) != cudaSuccess)
+      return CC_ECUDA;
+    c->n_tiles = (int)tiles.size();
+    c->smem_bytes = smem;
     c->tasks_dirty = false;
     c->dirty = true;
   }
@@ -414,6 +449,11 @@ int upload(cc_ctx* c, const std::vector<double>& dts, cudaStream_t st) {
       t.inv_theta = 1.0 / s.theta;
       for (int q = 0; q < 5; ++q) t.lam_poly[q] = s.lam_poly[q] * s.lam_scale;
       for (int q = 0; q < 4; ++q) t.cap_poly[q] = s.cap_poly[q] * s.cap_scale;
+      const double rho_tau = s.rho * D.inv_tau;
+      t.rho_tau = rho_tau;  // cap_poly already carries cap_scale
+      t.inv_theta3 = 1.0 / (s.theta * s.theta * s.theta);
+      t.rct_k = s.cap_model == 1 ? rho_tau * t.c0s / (s.t_ref * s.t_ref * s.t_ref)
+                                 : rho_tau * t.c0s;
       t.rho_f = (float)t.rho;
       t.lam0s_f = (float)t.lam0s;
       t.lam_b_f = (float)t.lam_b;
@@ -567,6 +607,9 @@ int cc_step_n(cc_ctx* c, void* T_dev, int64_t n_steps, double t0, double dt_s, d
   a.insts = c->d_inst;
   a.tasks = c->d_tasks;
   a.n_tasks = c->n_tasks;
+  a.tiles = c->d_tiles;
+  a.n_tiles = c->n_tiles;
+  a.smem_bytes = c->smem_bytes;
   a.n_inst = n;
   a.s_tab = c->d_s;
   a.trace = trace_dev;
@@ -628,7 +671,7 @@ int cc_set_launch(cc_ctx* c, int32_t mode, int32_t threads, int32_t rows_per_lan
   if (!c || (mode != 0 && mode != 1) || (threads != 64 && threads != 128 && threads != 256) ||
       rows_per_lane < 2 || rows_per_lane > kRowsPerLane)
     return CC_EINVAL;
-  if (rows_per_lane != c->rows) c->tasks_dirty = true;
+  if (rows_per_lane != c->rows || threads != c->threads) c->tasks_dirty = true;
   c->mode = mode;
   c->threads = threads;
   c->rows = rows_per_lane;
@@ -804,6 +847,9 @@ int adjoint_impl(cc_ctx* c, const void* T0_dev, int64_t n_steps, double t0, doub
   a.insts = c->d_inst;
   a.tasks = c->d_tasks;
   a.n_tasks = c->n_tasks;
+  a.tiles = c->d_tiles;
+  a.n_tiles = c->n_tiles;
+  a.smem_bytes = c->smem_bytes;
   a.n_inst = n;
   a.s_tab = s_tab;
   a.n_steps = n_steps;

@@ -1,66 +1,123 @@
-// FP64 time-step task shared by the per-step and the persistent kernels.
+// FP64 time step of one CTA tile, shared by the per-step and the persistent
+// kernels.
+//
+// A tile is nl consecutive axial lines j0 .. j0+nl-1 of one instance; each
+// warp of the CTA owns 32/G of them and each line is split over G lanes (lane
+// l holds rows [l nr/G, (l+1) nr/G)).  Per time step:
+//   0. the CTA stages the field rows j0-1 .. j0+nl (contiguous in global
+//      memory) into shared memory, padded so lanes 16 rows apart do not share
+//      a bank, and evaluates every axial face conductivity lambda_{i,j+1/2}
+//      of the tile once (a face is shared by the two lines it separates);
+//   1. every lane assembles its rows of the tridiagonal system of Eq. (ABC)
+//      (regular nodes), the interface rows of Eq. (cc_first_1) and the
+//      closures of Eq. (first_oder_bc) -- radial face conductivities are
+//      evaluated along the segment, heat capacities in registers
+//      (Eqs. (Lambda_i), (Lambda_j), (source)) -- and eliminates the segment's
+//      interior rows downwards (the forward sweep of Eq. (front_sweep)
+//      restricted to the segment, keeping the coupling to the previous
+//      segment's last row);
+//   2. the G separator rows are solved by cyclic reduction with shuffles;
+//   3. back substitution (Eq. (back_sweep)) inside each segment;
+//   4. stores, axial boundary rows, surface trace and energy terms.
+// For G = 1 the line solve is the Thomas algorithm of the paper with
+// alpha_0 = 1, beta_0 = 0 and That_N = beta_{N-1}/(1 - alpha_{N-1}).
 #pragma once
 #include "ccell_device.cuh"
 
 namespace ccell {
 
-// ---------------------------------------------------------------------------
-// FP64 step
-// ---------------------------------------------------------------------------
-// One warp task: 32/G consecutive lines of one instance.
+// rho c(T) / tau from the folded material constants
+__device__ __forceinline__ double rct_eval(const DevMaterial& M, double T) {
+  if (M.cap_model == 1) {
+    const double T3 = T * T * T;
+    return M.rct_k * T3 * frcp(fma(M.inv_theta3, T3, 1.0));
+  }
+  if (M.cap_model == 0) return M.rct_k;
+  const double* a = M.cap_poly;
+  return M.rho_tau * fma(fma(fma(a[3], T, a[2]), T, a[1]), T, a[0]);
+}
+
 template <bool ENERGY, bool TRACE>
-__device__ __forceinline__ void step_fp64_task(const StepArgs& a, const Task tk, const int lane) {
+__device__ __forceinline__ void step_fp64_tile(const StepArgs& a, const TileTask tk,
+                                               double* __restrict__ sm) {
   const DevInst& I = a.insts[tk.inst];
+  const int nr = I.nr, N = nr - 1, M = I.nz - 1;
   const int G = I.G;
   const int lg = __ffs(G) - 1;
+  const int lpw = 32 >> lg;
+  const int j0 = tk.j0, nl = tk.nl;
+  const int nrp = smem_row_stride(nr);
+  const int frule = I.face_rule;
+  double* sT = sm;                            // rows j0-1 .. j0+nl
+  double* sF = sm + (size_t)(nl + 2) * nrp;   // faces (j0-1+r, j0+r), r = 0..nl
+  const double* Tin = static_cast<const double*>(a.Tin) + I.t_off;
+  double* Tout = static_cast<double*>(a.Tout) + I.t_off;
+
+  // ---- 0. stage the rows, then the axial face conductivities
+  {
+    const double* src = Tin + (long long)(j0 - 1) * nr;
+    for (int r = 0; r < nl + 2; ++r)
+      for (int i = threadIdx.x; i < nr; i += blockDim.x)
+        sT[r * nrp + smem_col(i)] = __ldcg(src + (long long)r * nr + i);
+  }
+  __syncthreads();
+  for (int r = 0; r <= nl; ++r)
+    for (int i = threadIdx.x; i < nr; i += blockDim.x) {
+      const RowGeo& g = I.rg[i];
+      if (g.cls == RC_REGULAR) {
+        const int c = smem_col(i);
+        sF[r * nrp + c] = lam_face(I.mat[g.seg], frule, sT[r * nrp + c], sT[(r + 1) * nrp + c]);
+      }
+    }
+  __syncthreads();
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int grp = lane >> lg, l = lane & (G - 1);
-  const int nr = I.nr, N = nr - 1, M = I.nz - 1;
-  const int j_req = tk.j0 + grp;
-  const bool active = j_req <= M - 1;
-  const int j = active ? j_req : M - 1;  // idle lane groups recompute a valid line
+  const int q_req = warp * lpw + grp;
+  const bool active = q_req < nl;
+  const int q = active ? q_req : nl - 1;  // idle lane groups recompute a valid line
+  const int j = j0 + q;
   const int i_lo = (l * nr) >> lg;
   const int i_hi = ((l + 1) * nr) >> lg;
   const int cnt = i_hi - i_lo;  // 2 .. kRowsPerLane
-
-  const double* Tin = static_cast<const double*>(a.Tin) + I.t_off;
-  double* Tout = static_cast<double*>(a.Tout) + I.t_off;
-  const double* Tj = Tin + (long long)j * nr;
-  const double* Ts = Tj - nr;
-  const double* Tn = Tj + nr;
+  const double* Tj = sT + (q + 1) * nrp;
+  const double* Ts = Tj - nrp;
+  const double* Tn = Tj + nrp;
+  const double* Fs = sF + q * nrp;   // face (j-1, j)
+  const double* Fn = Fs + nrp;       // face (j, j+1)
   const ZGeo zg = I.zg[j];
   const double s = a.s_tab[a.step * a.n_inst + tk.inst];
-  const double tau = I.tau, inv_tau = I.inv_tau;
-  const int frule = I.face_rule;
+  const double etau = zg.etabar * I.tau;  // V tau = V2 etabar tau
 
   double cp[kRowsPerLane], ap[kRowsPerLane], dp[kRowsPerLane], mm[kRowsPerLane];
-  double pc = 0.0, pa = 0.0, pd = 0.0;   // c', a', d' of the previous interior row
+  double pc = 0.0, pa = 0.0, pd = 0.0;    // c', a', d' of the previous interior row
   double Dacc = 0.0, Aacc = 0.0, P = 1.0; // first interior row = Dacc + P x_next - Aacc L
   double ae = 0.0, be = 1.0, ce = 0.0, de = 0.0;  // separator row
   double le_prev = 0.0;
   bool have_le = false;
   double eQ = 0.0, eD = 0.0, eN = 0.0;
 
-  double Tm1 = (i_lo > 0) ? __ldcg(Tj + (i_lo - 1)) : 0.0;
-  double T0 = __ldcg(Tj + (i_lo));
+  double Tm1 = (i_lo > 0) ? Tj[smem_col(i_lo - 1)] : 0.0;
+  double T0 = Tj[smem_col(i_lo)];
 
   // ---- 1. assemble rows and eliminate the segment downwards
 #pragma unroll
   for (int k = 0; k < kRowsPerLane; ++k) {
     if (k < cnt) {
       const int i = i_lo + k;
+      const int c = smem_col(i);
       const RowGeo g = I.rg[i];
-      const double Tp1 = (i < N) ? __ldcg(Tj + (i + 1)) : 0.0;
+      const double Tp1 = (i < N) ? Tj[smem_col(i + 1)] : 0.0;
       double ra, rb, rc, rd, m = 0.0;
       if (g.cls == RC_REGULAR) {
         const DevMaterial& Mt = I.mat[g.seg];
-        const double tS = __ldcg(Ts + (i)), tN = __ldcg(Tn + (i));
+        const double tS = Ts[c], tN = Tn[c];
         const double lw = have_le ? le_prev : lam_face(Mt, frule, Tm1, T0);
         const double le = lam_face(Mt, frule, T0, Tp1);
-        const double ls = lam_face(Mt, frule, tS, T0);
-        const double ln = lam_face(Mt, frule, T0, tN);
-        const double rhoc = Mt.rho * cap_eval(Mt, T0);
+        const double ls = Fs[c], ln = Fn[c];
+        const double rct = rct_eval(Mt, T0);  // rho c / tau
         // Eq. (Lambda_j), explicit in T
-        const double Lj = ln * (tN - T0) * zg.gzn - ls * (T0 - tS) * zg.gzs;
+        const double Lj = fma(ln * zg.gzn, tN - T0, -ls * zg.gzs * (T0 - tS));
         double X = 0.0;  // Eq. (source)
         if (g.seg == I.src_layer && s != 0.0) {
           X = I.q0 * s;
@@ -68,7 +125,6 @@ __device__ __forceinline__ void step_fp64_task(const StepArgs& a, const Task tk,
         }
         // Eq. (ABC)
         const double A = -g.gA * lw, C = -g.gC * le;
-        const double rct = rhoc * inv_tau;
         ra = A;
         rc = C;
         rb = rct - A - C;
@@ -76,31 +132,31 @@ __device__ __forceinline__ void step_fp64_task(const StepArgs& a, const Task tk,
         le_prev = le;
         have_le = true;
         if (ENERGY) {
-          const double V = g.V2 * zg.etabar;
-          m = V * rhoc;
-          eQ = fma(tau * V, X, eQ);
+          const double Vt = g.V2 * etau;  // tau V
+          m = Vt * rct;                   // V rho c
+          if (X != 0.0) eQ = fma(Vt, X, eQ);
           if (j == 1) {
-            const double f = tau * g.V2 * ls * (tS - T0) / zg.eta_s;
+            const double f = I.tau * g.V2 * ls * (tS - T0) / zg.eta_s;
             if (I.bc_z0 == CC_DIRICHLET) eD += f; else eN += f;
           }
           if (j == M - 1) {
-            const double f = tau * g.V2 * ln * (tN - T0) / zg.eta_n;
+            const double f = I.tau * g.V2 * ln * (tN - T0) / zg.eta_n;
             if (I.bc_zmax == CC_DIRICHLET) eD += f; else eN += f;
           }
         }
       } else if (g.cls == RC_IFACE) {
         // Eq. (cc_first_1)/(cc_first_3) as the row (a, b, c | 0)
-        double lm, lp;
+        double lmv, lpv;
         if (I.interface_rule == 0) {
-          lm = lam_eval(I.mat[g.segw], T0);
-          lp = lam_eval(I.mat[g.seg], T0);
+          lmv = lam_eval(I.mat[g.segw], T0);
+          lpv = lam_eval(I.mat[g.seg], T0);
         } else {
-          lm = g.rw * lam_face(I.mat[g.segw], frule, Tm1, T0);
-          lp = g.re * lam_face(I.mat[g.seg], frule, T0, Tp1);
+          lmv = g.rw * lam_face(I.mat[g.segw], frule, Tm1, T0);
+          lpv = g.re * lam_face(I.mat[g.seg], frule, T0, Tp1);
         }
-        ra = -lm * g.he;
-        rc = -lp * g.hw;
-        rb = fma(lm, g.he, lp * g.hw);
+        ra = -lmv * g.he;
+        rc = -lpv * g.hw;
+        rb = fma(lmv, g.he, lpv * g.hw);
         rd = 0.0;
         have_le = false;
       } else if (g.cls == RC_AXIS) {  // That_0 = That_1
@@ -154,8 +210,7 @@ __device__ __forceinline__ void step_fp64_task(const StepArgs& a, const Task tk,
     for (int k = 0; k < kRowsPerLane; ++k)
       if (k == cnt - 1) dp[k] = xs;  // dp[k] = x_k for every row of the segment
   }
-  const double xfirst = dp[0];
-  const double xnext = __shfl_down_sync(kFull, xfirst, 1, G);  // first row of lane l+1
+  const double xnext = __shfl_down_sync(kFull, dp[0], 1, G);  // first row of lane l+1
 
   // ---- 4. stores, boundary rows, energy and trace epilogue
   double eE = 0.0, eI = 0.0;
@@ -175,23 +230,25 @@ __device__ __forceinline__ void step_fp64_task(const StepArgs& a, const Task tk,
         if (row0) O0[i] = (I.bc_z0 == CC_DIRICHLET) ? I.t_d : x;
         if (rowM) OM[i] = (I.bc_zmax == CC_DIRICHLET) ? I.t_d : x;
         if (ENERGY) {
-          eE = fma(mm[k], x - __ldcg(Tj + (i)), eE);
+          const double Ti = Tj[smem_col(i)];
+          eE = fma(mm[k], x - Ti, eE);
           const int cls = I.rg[i].cls;
           if (cls == RC_IFACE || cls == RC_OUTER) {
+            // heat through the edges to the regular neighbours, at That
             const double xw = (k == 0) ? L : dp[k > 0 ? k - 1 : 0];
-            const double Tw = __ldcg(Tj + (i - 1)), Ti = __ldcg(Tj + (i));
+            const double Tw = Tj[smem_col(i - 1)];
             const RowGeo gw = I.rg[i - 1];
-            const double ke = tau * gw.V2 * zg.etabar * gw.gC *
+            const double kw = I.tau * gw.V2 * zg.etabar * gw.gC *
                               lam_face(I.mat[gw.seg], frule, Tw, Ti);
-            const double fw = ke * (x - xw);  // into node i-1 (regular)
+            const double fw = kw * (x - xw);  // into node i-1
             if (cls == RC_OUTER) {
               if (I.bc_rmax == CC_DIRICHLET) eD += fw; else eN += fw;
             } else {
-              const double xe = (k == cnt - 1) ? xnext : dp[k < kRowsPerLane - 1 ? k + 1 : k];  // x_{i+1}
+              const double xe = (k == cnt - 1) ? xnext : dp[k < kRowsPerLane - 1 ? k + 1 : k];
               const RowGeo ge = I.rg[i + 1];
-              const double kw = tau * ge.V2 * zg.etabar * ge.gA *
-                                lam_face(I.mat[ge.seg], frule, Ti, __ldcg(Tj + (i + 1)));
-              eI += fw + kw * (x - xe);  // into node i+1 (regular)
+              const double ke = I.tau * ge.V2 * zg.etabar * ge.gA *
+                                lam_face(I.mat[ge.seg], frule, Ti, Tj[smem_col(i + 1)]);
+              eI += fw + ke * (x - xe);  // and into node i+1
             }
           }
         }
@@ -239,15 +296,16 @@ __device__ __forceinline__ void step_fp64_task(const StepArgs& a, const Task tk,
       if (TRACE) atomicAdd(a.trace + ((long long)tk.inst * a.n_steps + a.step) * 2 + 1, tr);
     }
   }
+  __syncthreads();  // the next tile reuses the shared memory
 }
 
-// Resident blocks per SM x SMs for a kernel and block size.
+// Resident blocks per SM x SMs for a kernel, block size and shared memory.
 template <class K>
-static int resident_blocks(K kernel, int threads) {
+static int resident_blocks(K kernel, int threads, int smem = 0) {
   int dev = 0, sms = 0, per_sm = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, threads, 0);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, threads, smem);
   return sms * (per_sm > 0 ? per_sm : 1);
 }
 

@@ -63,6 +63,9 @@ struct DevMaterial {
   double lam_poly[5];  // * lam_scale
   double cap_poly[4];  // * cap_scale
   const double* ptab;  // power-law table (kPowTabLen doubles) or null: use pow()
+  // rho c(T) / tau = rct_k T^3 / (1 + inv_theta3 T^3) (cap_model 1), rct_k
+  // (cap_model 0), rho_tau * poly(T) (cap_model 2)
+  double rct_k, inv_theta3, rho_tau;
   double inv_lam_scale, inv_cap_scale;  // adjoint: d/d scale = value / scale
   // FP32 copies (mixed precision)
   float rho_f, lam0s_f, lam_b_f, inv_tref_f, c0s_f, inv_theta_f;
@@ -94,11 +97,34 @@ struct Task {
   int j0;
 };
 
+// One CTA's work in the FP64 step: nl consecutive lines starting at j0
+// (nl <= warps per CTA x 32/G).
+struct TileTask {
+  int inst;
+  int j0;
+  int nl;
+  int pad;
+};
+
+#ifdef __CUDACC__
+#define CC_HOST_DEVICE __host__ __device__
+#else
+#define CC_HOST_DEVICE
+#endif
+
+// Shared-memory stride of one staged row of nr doubles: one pad double after
+// every 16, so lanes reading rows 16 apart hit different banks.
+CC_HOST_DEVICE inline int smem_row_stride(int nr) { return nr + (nr >> 4) + 1; }
+CC_HOST_DEVICE inline int smem_col(int i) { return i + (i >> 4); }
+
 // Everything one step launch needs.
 struct StepArgs {
   const DevInst* insts;
   const Task* tasks;
   int n_tasks;
+  const TileTask* tiles; // FP64 step: CTA tiles
+  int n_tiles;
+  int smem_bytes;        // dynamic shared memory of the FP64 tile kernel
   int n_inst;
   const void* Tin;       // double* (FP64) or float* (mixed, high part)
   void* Tout;

@@ -24,6 +24,7 @@
 // of every call; the rest is rewritten before it is read.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cmath>
 #include <cstdlib>
 #include <cstring>
@@ -41,7 +42,8 @@ constexpr size_t kOffErr = align256(kOffInst + sizeof(DevInst));
 constexpr size_t kOffRg = align256(kOffErr + sizeof(unsigned));
 constexpr size_t kOffZg = align256(kOffRg + sizeof(RowGeo) * CC_NOALLOC_MAX_NR);
 constexpr size_t kOffTask = align256(kOffZg + sizeof(ZGeo) * CC_NOALLOC_MAX_NZ);
-constexpr size_t kOffS = align256(kOffTask + sizeof(Task) * CC_NOALLOC_MAX_NZ);
+constexpr size_t kOffTile = align256(kOffTask + sizeof(Task) * CC_NOALLOC_MAX_NZ);
+constexpr size_t kOffS = align256(kOffTile + sizeof(TileTask) * CC_NOALLOC_MAX_NZ);
 constexpr size_t kOffT2 = align256(kOffS + sizeof(double) * CC_NOALLOC_MAX_STEPS);
 constexpr size_t kScratchBytes = align256(kOffT2 + sizeof(double) * CC_NOALLOC_MAX_NODES);
 
@@ -56,6 +58,7 @@ DevInst h_inst;
 RowGeo h_rg[CC_NOALLOC_MAX_NR];
 ZGeo h_zg[CC_NOALLOC_MAX_NZ];
 Task h_task[CC_NOALLOC_MAX_NZ];
+TileTask h_tile[CC_NOALLOC_MAX_NZ];
 double h_r[CC_NOALLOC_MAX_NR], h_z[CC_NOALLOC_MAX_NZ];
 int h_cls[CC_NOALLOC_MAX_NR], h_seg[CC_NOALLOC_MAX_NR];
 
@@ -273,6 +276,10 @@ extern "C" int cc_step_n_noalloc(const cc_geometry_desc* desc, const cc_material
   while (G < 32 && (d.nr + G - 1) / G > kRowsPerLane) G <<= 1;
   int n_tasks = 0;
   for (int j0 = 1; j0 <= M - 1; j0 += 32 / G) h_task[n_tasks++] = Task{0, j0};
+  const int lpc = 4 * (32 / G);  // CTA tiles of the FP64 step: 4 warps, 128 threads
+  int n_tiles = 0;
+  for (int j0 = 1; j0 <= M - 1; j0 += lpc) h_tile[n_tiles++] = TileTask{0, j0, std::min(lpc, M - j0), 0};
+  const int smem = (2 * std::min(lpc, M - 1) + 3) * smem_row_stride(d.nr) * (int)sizeof(double);
 
   std::memset(&h_inst, 0, sizeof h_inst);
   h_inst.nr = d.nr;
@@ -310,6 +317,10 @@ extern "C" int cc_step_n_noalloc(const cc_geometry_desc* desc, const cc_material
     t.inv_theta = 1.0 / s.theta;
     for (int q = 0; q < 5; ++q) t.lam_poly[q] = s.lam_poly[q] * s.lam_scale;
     for (int q = 0; q < 4; ++q) t.cap_poly[q] = s.cap_poly[q] * s.cap_scale;
+    const double rho_tau = s.rho / dt_s;
+    t.rho_tau = rho_tau;
+    t.inv_theta3 = 1.0 / (s.theta * s.theta * s.theta);
+    t.rct_k = s.cap_model == 1 ? rho_tau * t.c0s / (s.t_ref * s.t_ref * s.t_ref) : rho_tau * t.c0s;
   }
 
   cudaStream_t st = static_cast<cudaStream_t>(stream);
@@ -318,6 +329,8 @@ extern "C" int cc_step_n_noalloc(const cc_geometry_desc* desc, const cc_material
       cudaMemcpyAsync(base + kOffRg, h_rg, sizeof(RowGeo) * d.nr, cudaMemcpyHostToDevice, st) ||
       cudaMemcpyAsync(base + kOffZg, h_zg, sizeof(ZGeo) * d.nz, cudaMemcpyHostToDevice, st) ||
       cudaMemcpyAsync(base + kOffTask, h_task, sizeof(Task) * n_tasks, cudaMemcpyHostToDevice,
+                      st) ||
+      cudaMemcpyAsync(base + kOffTile, h_tile, sizeof(TileTask) * n_tiles, cudaMemcpyHostToDevice,
                       st) ||
       cudaMemsetAsync(base + kOffErr, 0, sizeof(unsigned), st))
     return CC_ECUDA;
@@ -332,6 +345,10 @@ extern "C" int cc_step_n_noalloc(const cc_geometry_desc* desc, const cc_material
   a.insts = dinst;
   a.tasks = reinterpret_cast<const Task*>(base + kOffTask);
   a.n_tasks = n_tasks;
+  a.tiles = reinterpret_cast<const TileTask*>(base + kOffTile);
+  a.n_tiles = n_tiles;
+  a.smem_bytes = smem;
+  a.threads = 128;
   a.n_inst = 1;
   a.s_tab = s_tab;
   a.trace = trace_dev;

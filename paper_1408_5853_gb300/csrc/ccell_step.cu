@@ -80,23 +80,34 @@ int launch_waveform(const DevInst* insts, int n_inst, long long n_steps, double 
   return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }
 
-// Grid-stride over warp tasks; the grid is sized to the resident capacity so
-// that no partial last wave leaves SMs idle.
+// Grid-stride over CTA tiles; the grid is sized to the resident capacity.
 template <bool ENERGY, bool TRACE>
 __global__ void __launch_bounds__(256) step_fp64_kernel(const StepArgs a) {
-  const int lane = threadIdx.x & 31;
-  const int n_warps = (int)((gridDim.x * blockDim.x) >> 5);
-  for (int w = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5); w < a.n_tasks; w += n_warps)
-    step_fp64_task<ENERGY, TRACE>(a, a.tasks[w], lane);
+  extern __shared__ double sm[];
+  for (int t = blockIdx.x; t < a.n_tiles; t += gridDim.x)
+    step_fp64_tile<ENERGY, TRACE>(a, a.tiles[t], sm);
 }
+
+// Largest dynamic shared memory any tile needs (rows + faces of the biggest
+// tile); kernels are opted in up to this size once.
+constexpr int kTileSmemMax = 160 * 1024;
 
 template <bool ENERGY, bool TRACE>
 static void launch_fp64_variant(const StepArgs& a, cudaStream_t st) {
-  static int resident[3] = {0, 0, 0};
+  static int resident[3] = {0, 0, 0}, resident_smem[3] = {-1, -1, -1};
+  static bool opted = false;
+  if (!opted) {
+    cudaFuncSetAttribute(step_fp64_kernel<ENERGY, TRACE>,
+                         cudaFuncAttributeMaxDynamicSharedMemorySize, kTileSmemMax);
+    opted = true;
+  }
   const int t = a.threads > 0 ? a.threads : 128, si = shape_index(t);
-  if (resident[si] == 0) resident[si] = resident_blocks(step_fp64_kernel<ENERGY, TRACE>, t);
-  const int need = (a.n_tasks * 32 + t - 1) / t;
-  step_fp64_kernel<ENERGY, TRACE><<<need < resident[si] ? need : resident[si], t, 0, st>>>(a);
+  if (resident_smem[si] != a.smem_bytes) {
+    resident[si] = resident_blocks(step_fp64_kernel<ENERGY, TRACE>, t, a.smem_bytes);
+    resident_smem[si] = a.smem_bytes;
+  }
+  const int blocks = a.n_tiles < resident[si] ? a.n_tiles : resident[si];
+  step_fp64_kernel<ENERGY, TRACE><<<blocks, t, a.smem_bytes, st>>>(a);
 }
 
 int launch_step_fp64(const StepArgs& a, void* stream) {

@@ -10,30 +10,39 @@ namespace ccell {
 template <bool ENERGY, bool TRACE>
 __global__ void __launch_bounds__(256) steps_fp64_persistent_kernel(const StepArgs a,
                                                                      long long n) {
-  const int lane = threadIdx.x & 31;
-  const int n_warps = (int)((gridDim.x * blockDim.x) >> 5);
+  extern __shared__ double sm[];
   StepArgs s = a;
   for (long long q = 0; q < n; ++q) {
     s.step = a.step + q;
     s.Tin = (q & 1) ? a.Tout : a.Tin;
     s.Tout = (q & 1) ? const_cast<void*>(a.Tin) : a.Tout;
-    for (int w = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5); w < a.n_tasks; w += n_warps)
-      step_fp64_task<ENERGY, TRACE>(s, a.tasks[w], lane);
+    for (int t = blockIdx.x; t < a.n_tiles; t += gridDim.x)
+      step_fp64_tile<ENERGY, TRACE>(s, a.tiles[t], sm);
     if (!grid_barrier(a.bar, a.bar_extra, a.spin_limit, a.err)) return;
   }
 }
 
+constexpr int kTileSmemMaxP = 160 * 1024;
+
 template <bool ENERGY, bool TRACE>
 static int launch_fp64_persistent_variant(const StepArgs& a, long long n, cudaStream_t st) {
-  static int resident[3] = {0, 0, 0};
-  const int t = a.threads > 0 ? a.threads : 128, si = shape_index(t);
+  static int resident[3] = {0, 0, 0}, resident_smem[3] = {-1, -1, -1};
+  static bool opted = false;
   auto kern = steps_fp64_persistent_kernel<ENERGY, TRACE>;
-  if (resident[si] == 0) resident[si] = resident_blocks(kern, t);
-  const int need = (a.n_tasks * 32 + t - 1) / t;
-  const int blocks = need < resident[si] ? need : resident[si];
+  if (!opted) {
+    cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, kTileSmemMaxP);
+    opted = true;
+  }
+  const int t = a.threads > 0 ? a.threads : 128, si = shape_index(t);
+  if (resident_smem[si] != a.smem_bytes) {
+    resident[si] = resident_blocks(kern, t, a.smem_bytes);
+    resident_smem[si] = a.smem_bytes;
+  }
+  const int blocks = a.n_tiles < resident[si] ? a.n_tiles : resident[si];
   StepArgs copy = a;
   void* args[] = {&copy, &n};
-  const cudaError_t e = cudaLaunchCooperativeKernel((const void*)kern, blocks, t, args, 0, st);
+  const cudaError_t e =
+      cudaLaunchCooperativeKernel((const void*)kern, blocks, t, args, a.smem_bytes, st);
   if (e == cudaErrorCooperativeLaunchTooLarge) {
     cudaGetLastError();
     return -3;
