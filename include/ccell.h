@@ -130,6 +130,12 @@ typedef struct {
  *   waveform 0: s = nu(t), 1 on [t_start + n t_period, ... + t_on), else 0.
  *   waveform 1: s = (tanh(phi/w) - tanh((phi - t_on)/w)) / 2 around the
  *               nearest pulse (phase phi), w = edge_w.
+ *   waveform 2: s = nu(t) p^2(t), the transient turn-on of Section 3.1,
+ *               Eq. (transient_function) with the exponent read as negative:
+ *               p^2 = 1 - exp(-phi / (7 tau*)) for phase phi < tau, else 1,
+ *               with tau = edge_w and tau* = tau / 100.  The paper advances
+ *               the first tau of each period with steps tau* (a schedule of
+ *               cc_step_n calls).
  *   g_model  0: g = 1;  1: g = g_ref / sqrt(T) (resistivity of the paper's
  *            conducting layer, Section 5).
  * layer = -1 disables the source.

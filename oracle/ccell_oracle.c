@@ -205,9 +205,21 @@ static double lam_face(const or_problem* p, int m, double Ta, double Tb) {
 }
 
 /* waveform s(t) = nu(t) p(t) of Eqs. (current), (period); p == 1.
- * waveform 1: tanh-smoothed edges of width edge_w around the nearest pulse. */
+ * waveform 1: tanh-smoothed edges of width edge_w around the nearest pulse.
+ * waveform 2: nu(t) p^2(t), the transient turn-on of Eq. (transient_function)
+ *   with the sign of the exponent read as negative (A5): p^2 = 1 -
+ *   exp(-(t - n t_prd) / (7 tau*)) for t in [n t_prd, n t_prd + tau), else 1;
+ *   tau = edge_w and tau* = tau / 100 (Section 3.1). */
 double or_waveform(const or_problem* p, double t) {
   double u = t - p->t_start;
+  if (p->waveform == 2) {
+    if (u < 0.0) return 0.0;
+    double k = floor(u / p->t_period);
+    double phi = u - k * p->t_period;
+    if (!(phi < p->t_on)) return 0.0;
+    if (phi < p->edge_w) return 1.0 - exp(-phi / (7.0 * (p->edge_w / 100.0)));
+    return 1.0;
+  }
   if (p->waveform == 0) {
     if (u < 0.0) return 0.0;
     double k = floor(u / p->t_period);

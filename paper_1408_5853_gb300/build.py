@@ -41,6 +41,7 @@ def build(force: bool = False, verbose: bool = False) -> str:
     nvcc = _nvcc()
     common = ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC,-ffp-contract=off",
                      "-I", os.path.join(HERE, "..", "include")]
+    common += os.environ.get("CCELL_NVCC_EXTRA", "").split()
 
     def compile_one(src: str) -> str:
         obj = os.path.join(BUILD, src + ".o")

@@ -545,10 +545,10 @@ int cc_set_source(cc_ctx* c, int32_t instance, const cc_source* s) {
   for (int k = k0; k < k1; ++k) {
     if (s->layer < -1 || s->layer >= c->inst[k].d.n_layers) return CC_EINVAL;
     if (s->layer >= 0) {
-      if (!(s->t_period > 0.0) || !(s->t_on >= 0.0) || s->waveform < 0 || s->waveform > 1 ||
+      if (!(s->t_period > 0.0) || !(s->t_on >= 0.0) || s->waveform < 0 || s->waveform > 2 ||
           s->g_model < 0 || s->g_model > 1 || !std::isfinite(s->q0))
         return CC_EINVAL;
-      if (s->waveform == 1 && !(s->edge_w > 0.0)) return CC_EINVAL;
+      if (s->waveform >= 1 && !(s->edge_w > 0.0)) return CC_EINVAL;
     }
   }
   for (int k = k0; k < k1; ++k) c->inst[k].src = *s;

@@ -24,6 +24,14 @@
 #pragma once
 #include "ccell_device.cuh"
 
+// Launch bounds of the FP64 step kernels (register budget per thread).
+#ifndef CC_FP64_MAX_THREADS
+#define CC_FP64_MAX_THREADS 256
+#endif
+#ifndef CC_FP64_MIN_BLOCKS
+#define CC_FP64_MIN_BLOCKS 1
+#endif
+
 namespace ccell {
 
 // rho c(T) / tau from the folded material constants

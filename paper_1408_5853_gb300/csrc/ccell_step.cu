@@ -49,7 +49,14 @@ __global__ void waveform_kernel(const DevInst* __restrict__ insts, int n_inst,
   const double u = __dsub_rn(tn, I.t_start);
   double s = 0.0, ds = 0.0;
   if (I.src_layer >= 0) {
-    if (I.waveform == 0) {
+    if (I.waveform == 2) {  // nu(t) p^2(t), transient turn-on of Section 3.1
+      if (u >= 0.0) {
+        const double kk = floor(__ddiv_rn(u, I.t_period));
+        const double phi = __dsub_rn(u, __dmul_rn(kk, I.t_period));
+        if (phi < I.t_on)
+          s = (phi < I.edge_w) ? 1.0 - exp(-phi / (7.0 * (I.edge_w / 100.0))) : 1.0;
+      }
+    } else if (I.waveform == 0) {
       if (u >= 0.0) {
         const double kk = floor(__ddiv_rn(u, I.t_period));
         const double phi = __dsub_rn(u, __dmul_rn(kk, I.t_period));
@@ -82,7 +89,7 @@ int launch_waveform(const DevInst* insts, int n_inst, long long n_steps, double 
 
 // Grid-stride over CTA tiles; the grid is sized to the resident capacity.
 template <bool ENERGY, bool TRACE>
-__global__ void __launch_bounds__(256) step_fp64_kernel(const StepArgs a) {
+__global__ void __launch_bounds__(CC_FP64_MAX_THREADS, CC_FP64_MIN_BLOCKS) step_fp64_kernel(const StepArgs a) {
   extern __shared__ double sm[];
   for (int t = blockIdx.x; t < a.n_tiles; t += gridDim.x)
     step_fp64_tile<ENERGY, TRACE>(a, a.tiles[t], sm);

@@ -8,7 +8,7 @@ namespace ccell {
 
 // All n steps in one cooperative launch, a bounded grid barrier between steps.
 template <bool ENERGY, bool TRACE>
-__global__ void __launch_bounds__(256) steps_fp64_persistent_kernel(const StepArgs a,
+__global__ void __launch_bounds__(CC_FP64_MAX_THREADS, CC_FP64_MIN_BLOCKS) steps_fp64_persistent_kernel(const StepArgs a,
                                                                      long long n) {
   extern __shared__ double sm[];
   StepArgs s = a;

@@ -139,6 +139,42 @@ def adjoint_case(nr: int = 256, nz: int = 1024, dt: float = 6.25e-9) -> dict:
     return cfg
 
 
+_GOLDEN = os.path.join(os.path.dirname(_HERE), "tests", "golden", "paper_material_fits.json")
+
+
+def paper_case(nr: int = 256, nz: int = 201) -> dict:
+    """The paper's cryogenic cell (Section 5) on a rectangular r-z domain:
+    copper core 1.2 mm, insulator 0.05 mm, graphite heater 0.05 mm, outer
+    insulator 1 um; length 5 cm; polynomial fits of c_V and lambda (Tables
+    a_coefs, b_coefs), converted from cgs to SI; Joule source
+    chi(T) I(t)^2 / S_2^2 with chi = 1.8 / sqrt(T) Ohm cm, I0 = 363 mA and the
+    transient turn-on (waveform 2); 1 ms pulse every 25 ms; T0 = 4.2 K.
+    The non-rectangular outline of the paper's figure is not reproduced."""
+    with open(_GOLDEN) as f:
+        fit = json.load(f)
+    r_cm = fit["radii_cm"]
+    thick_cm = [r_cm["r0"], r_cm["r1"] - r_cm["r0"], r_cm["r2"] - r_cm["r1"],
+                r_cm["rmax"] - r_cm["r2"]]
+    layers = []
+    for m in range(4):
+        layers.append(dict(thickness=thick_cm[m] * 1e-2, rho=fit["rho_g_cm3"][m] * 1e3,
+                           lam_model=2, lam_poly=[100.0 * b for b in fit["lam_b0_b1_b2_b3_b4"][m]],
+                           cap_model=2, cap_poly=[1e3 * a for a in fit["cap_a0_a1_a2_a3"][m]],
+                           t_ref=1.0, theta=1.0, lam_scale=1.0, cap_scale=1.0))
+    run = fit["run"]
+    s2 = math.pi * ((r_cm["r2"] * 1e-2) ** 2 - (r_cm["r1"] * 1e-2) ** 2)  # heater cross-section, m^2
+    chi0 = fit["chi_ohm_cm_sqrtK"] * 1e-2                                     # Ohm m sqrt(K)
+    q0 = chi0 * run["I0_A"] ** 2 / s2 ** 2          # X = q0 s(t) / sqrt(T), W/m^3
+    cfg = dict(layers=layers, nr=nr, nz=nz, length=fit["z_cm"]["zmax"] * 1e-2,
+               bc_rmax=0, bc_z0=0, bc_zmax=1, t_dirichlet=run["T0_K"], placement=0,
+               face_rule=0, interface_rule=0,
+               source=dict(layer=2, q0=q0, t_period=run["t_prd_s"], t_on=run["t_src_s"],
+                           t_start=0.0, waveform=2, edge_w=run["tau_s"], g_model=1, g_ref=1.0),
+               dt=run["tau_s"], t_guard=(run["T0_K"], 60.0))
+    cfg["name"] = f"paper cryogenic cell {nr}x{nz} (polynomial materials, transient source)"
+    return cfg
+
+
 def target_waveform(cfg: dict, t: np.ndarray) -> np.ndarray:
     """Surface-temperature target: 42 K while the nominal pulse window is open,
     28 K while it is closed."""

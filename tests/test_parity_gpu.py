@@ -152,3 +152,27 @@ def test_production_size_sampled_lines():
         assert err <= TOL_K, f"line {j}: max|dT| = {err:.3e} K"
     e = eg[0]
     assert abs(e[0] - e[1:].sum()) <= 1e-9 * max(abs(e[0]), abs(e[1]))
+
+
+def test_paper_case_transient_schedule():
+    """The paper's cryogenic cell (polynomial fits of Section 5, resistive
+    source chi(T) I^2/S^2, transient turn-on of Section 3.1 with tau* = tau/100
+    sub-steps) over the first pulse, run as the schedule of cc_step_n calls."""
+    import torch
+    from paper_1408_5853_gb300 import ccell, schedule
+    cfg = inputs.paper_case(nr=64, nz=41)
+    cfg["t_guard"] = (4.2, 20.0)   # the graphite c_V fit is positive below ~22 K
+    chunks = schedule.transient_schedule(cfg["source"]["t_period"], cfg["dt"], 1.2e-3)
+    sol = ccell.Solver(cfg)
+    T = torch.full((cfg["nz"] * cfg["nr"],), 4.2, dtype=torch.float64, device="cuda")
+    To = np.full((cfg["nz"], cfg["nr"]), 4.2)
+    for t0, dt, n in chunks:
+        tr = torch.zeros(2 * n, dtype=torch.float64, device="cuda")
+        sol.step(T, n, t0, dt, tr, None)
+        To, tro, _ = oracle.step_n(cfg, To, n, t0, dt, want_energy=False)
+        assert np.max(np.abs(tr.view(n, 2).cpu().numpy() - tro)) <= TOL_K
+    sol.sync()
+    err = np.max(np.abs(T.cpu().numpy().reshape(To.shape) - To))
+    sol.close()
+    assert err <= TOL_K, err
+    assert 10.0 < To.max() < 22.0
