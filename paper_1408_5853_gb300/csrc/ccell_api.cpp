@@ -343,12 +343,20 @@ int upload(cc_ctx* c, const std::vector<double>& dts, cudaStream_t st) {
     if (cur != c->device) return CC_EINVAL;
   }
   if (c->tasks_dirty) {
+    // Lanes per line from the rows-per-lane policy; when the lines of all
+    // instances give fewer than kMinWarpTasks warp tasks, use more lanes per
+    // line (fewer rows per lane) so that every SM sub-partition has work.
+    constexpr int kMinWarpTasks = 2048;
     std::vector<Task> tasks;
-    for (int k = 0; k < n; ++k) {
-      Instance& in = c->inst[k];
-      in.G = choose_lanes(in.d.nr, c->rows);
-      const int lpw = 32 / in.G;
-      for (int j0 = 1; j0 <= in.d.nz - 2; j0 += lpw) tasks.push_back(Task{k, j0});
+    for (int rows = c->rows;; rows /= 2) {
+      tasks.clear();
+      for (int k = 0; k < n; ++k) {
+        Instance& in = c->inst[k];
+        in.G = choose_lanes(in.d.nr, rows);
+        const int lpw = 32 / in.G;
+        for (int j0 = 1; j0 <= in.d.nz - 2; j0 += lpw) tasks.push_back(Task{k, j0});
+      }
+      if ((int)tasks.size() >= kMinWarpTasks || rows <= 4) break;
     }
     if (tasks.size() > c->tasks_cap) {
       cudaFree(c->d_tasks);
