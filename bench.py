@@ -34,6 +34,11 @@ UNIT = "node-updates/s"
 BYTES_PER_NODE_FP64 = 16      # read T^n + write T^{n+1}
 BYTES_PER_NODE_MIXED = 8
 FLOPS_PER_NODE_FP64 = 150     # FP64 operations per node-update (2 power laws ~ 2x(log+exp), 1 div, 1 rcp, ~30 fma/add/mul)
+
+# DRAM bytes (read + write) of one step_fp64_kernel launch on the 512x4096 workload, from the
+# ncu capture summarised in profiles/step_fp64_kernel_512x4096.md (cache flushed before the
+# launch).  Valid only for the kernel as captured there: reset to None when the kernel changes.
+STEP_FP64_TRAFFIC_512x4096 = 17.478144e6 + 3.84e3
 FP64_PEAK_TFLOPS = 152 * 4 * 0.5 * 2 * 2.07e9 / 1e12   # SMs x SMSPs x DFMA lanes/clk x 2 x max clock
 L2_FLUSH_BYTES = 256 << 20
 
@@ -227,7 +232,11 @@ def run_ours(args, world, rank, local):
                    "parallelism": f"replicas x{world}"},
         "roofline": {"bound": "alu", "kernel": "step_fp64_kernel",
                      "achieved": achieved_tflops, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                     "frac": achieved_tflops / FP64_PEAK_TFLOPS, "traffic": None,
+                     "frac": achieved_tflops / FP64_PEAK_TFLOPS,
+                     "traffic": (STEP_FP64_TRAFFIC_512x4096
+                                 if (cfg["nr"], cfg["nz"]) == (512, 4096) else None),
+                     "traffic_note": "ncu dram__bytes_read.sum + dram__bytes_write.sum per launch, "
+                                     "cold L2 (the output rows stay in L2)",
                      "peak_source": "FP64 unit counts x max SM clock (152 x 4 x 0.5 DFMA/clk x 2 x 2.07 GHz)",
                      "per_unit": f"{FLOPS_PER_NODE_FP64} FP64 ops per node-update"},
         "hbm_roofline": {"bound": "hbm", "achieved": BYTES_PER_NODE_FP64 * value / world / 1e9,
