@@ -121,6 +121,8 @@ def run_ours(args, world, rank, local):
 
     def make(precision):
         sol = ccell.Solver(cfg, precision=precision)
+        if args.launch:
+            sol.set_launch(*[int(v) for v in args.launch.split(",")])
         dt = torch.float64 if precision == ccell.FP64 else torch.float32
         T = torch.tensor(T0.ravel(), dtype=dt, device=dev)
         trace = torch.zeros(2 * n_in, dtype=torch.float64, device=dev)
@@ -162,6 +164,7 @@ def run_ours(args, world, rank, local):
     clocks.start()
     ms, launches = timed_steps(sol, T, trace, energy, args.steps, args.warmup)
     clk = clocks.stop()
+    launch_shape = sol.get_launch()
     total_nodes = nodes * n_in * args.steps * world
     value = total_nodes / (ms / 1e3)
     per_launch_ms = ms / (args.steps * n_in)
@@ -229,7 +232,8 @@ def run_ours(args, world, rank, local):
                                f"tau {cfg['dt']:.2e} s, {n_in} time steps per bench step",
                    "nr": cfg["nr"], "nz": cfg["nz"], "time_steps_per_step": n_in,
                    "precision": "fp64", "l2": f"flushed between timed steps ({L2_FLUSH_BYTES >> 20} MB write)",
-                   "parallelism": f"replicas x{world}"},
+                   "parallelism": f"replicas x{world}",
+                   "launch": dict(zip(("mode", "threads", "rows_per_lane"), launch_shape))},
         "roofline": {"bound": "alu", "kernel": "step_fp64_kernel",
                      "achieved": achieved_tflops, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
                      "frac": achieved_tflops / FP64_PEAK_TFLOPS,
@@ -487,6 +491,8 @@ def main():
                          "(negative above ~22 K) the heater stays below 20 K up to ~0.1 ms")
     ap.add_argument("--acc-steps", type=int, default=20000,
                     help="steps of the mixed-vs-FP64 accuracy check (0: skip)")
+    ap.add_argument("--launch", default="",
+                    help="mode,threads,rows_per_lane of the 512x4096 runs (default: the library's)")
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     args = ap.parse_args()
     args.parts = set(args.parts.split(","))

@@ -382,8 +382,7 @@ int upload(cc_ctx* c, const std::vector<double>& dts, cudaStream_t st) {
         const int nl = std::min(lpc, in.d.nz - 1 - j0);
         tiles.push_back(TileTask{k, j0, nl, 0});
       }
-      smem = std::max(smem, (2 * std::min(lpc, in.d.nz - 2) + 3) * smem_row_stride(in.d.nr) *
-                                (int)sizeof(double));
+      smem = std::max(smem, fp64_tile_smem_bytes(std::min(lpc, in.d.nz - 2), in.d.nr));
     }
     if (tiles.size() > c->tiles_cap) {
       cudaFree(c->d_tiles);
@@ -438,6 +437,10 @@ int upload(cc_ctx* c, const std::vector<double>& dts, cudaStream_t st) {
     D.g_ref_f = (float)D.g_ref;
     D.td_hi = (float)D.t_d;
     D.td_lo = (float)(D.t_d - (double)D.td_hi);
+    D.n_if = 0;
+    for (int i = 0; i < in.d.nr; ++i)
+      if ((in.cls[i] == RC_IFACE || in.cls[i] == RC_OUTER) && D.n_if < CC_MAX_LAYERS)
+        D.if_i[D.n_if++] = i;
     D.rg = c->d_rg + rofs;
     D.zg = c->d_zg + zofs;
     rofs += in.d.nr;

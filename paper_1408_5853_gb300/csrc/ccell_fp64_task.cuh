@@ -34,6 +34,47 @@
 
 namespace ccell {
 
+// Energy and trace partial sums of one thread, carried over the tiles of a
+// launch and flushed (warp sums, one atomic per warp and term) when the
+// instance changes, at the end of a step and at the end of the launch.
+struct EAcc {
+  double e[5];  // dE, Q, Phi_D, Phi_I, Phi_N
+  double tr;    // trapezoid-weighted z-sum of That(r_max, z)
+  int inst;     // instance the sums belong to (-1: none yet)
+};
+
+__device__ __forceinline__ void eacc_init(EAcc& c) {
+#pragma unroll
+  for (int k = 0; k < 5; ++k) c.e[k] = 0.0;
+  c.tr = 0.0;
+  c.inst = -1;
+}
+
+// Called by every thread of the block (c.inst is block-uniform).
+template <bool ENERGY, bool TRACE>
+__device__ __forceinline__ void eacc_flush(const StepArgs& a, EAcc& c) {
+  if (!(ENERGY || TRACE) || c.inst < 0) return;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    if (ENERGY) {
+#pragma unroll
+      for (int k = 0; k < 5; ++k) c.e[k] += __shfl_xor_sync(kFull, c.e[k], o);
+    }
+    if (TRACE) c.tr += __shfl_xor_sync(kFull, c.tr, o);
+  }
+  if ((threadIdx.x & 31) == 0) {
+    if (ENERGY) {
+      double* e = a.energy + (long long)c.inst * 5;
+#pragma unroll
+      for (int k = 0; k < 5; ++k) atomicAdd(e + k, c.e[k]);
+    }
+    if (TRACE) atomicAdd(a.trace + ((long long)c.inst * a.n_steps + a.step) * 2 + 1, c.tr);
+  }
+#pragma unroll
+  for (int k = 0; k < 5; ++k) c.e[k] = 0.0;
+  c.tr = 0.0;
+}
+
 // rho c(T) / tau from the folded material constants
 __device__ __forceinline__ double rct_eval(const DevMaterial& M, double T) {
   if (M.cap_model == 1) {
@@ -47,7 +88,11 @@ __device__ __forceinline__ double rct_eval(const DevMaterial& M, double T) {
 
 template <bool ENERGY, bool TRACE>
 __device__ __forceinline__ void step_fp64_tile(const StepArgs& a, const TileTask tk,
-                                               double* __restrict__ sm) {
+                                               double* __restrict__ sm, EAcc& acc) {
+  if (tk.inst != acc.inst) {  // block-uniform
+    eacc_flush<ENERGY, TRACE>(a, acc);
+    acc.inst = tk.inst;
+  }
   const DevInst& I = a.insts[tk.inst];
   const int nr = I.nr, N = nr - 1, M = I.nz - 1;
   const int G = I.G;
@@ -58,6 +103,7 @@ __device__ __forceinline__ void step_fp64_tile(const StepArgs& a, const TileTask
   const int frule = I.face_rule;
   double* sT = sm;                            // rows j0-1 .. j0+nl
   double* sF = sm + (size_t)(nl + 2) * nrp;   // faces (j0-1+r, j0+r), r = 0..nl
+  double* sX = sF + (size_t)(nl + 1) * nrp;   // That of lines j0 .. j0+nl-1 (energy pass)
   const double* Tin = static_cast<const double*>(a.Tin) + I.t_off;
   double* Tout = static_cast<double*>(a.Tout) + I.t_off;
 
@@ -97,7 +143,8 @@ __device__ __forceinline__ void step_fp64_tile(const StepArgs& a, const TileTask
   const double s = a.s_tab[a.step * a.n_inst + tk.inst];
   const double etau = zg.etabar * I.tau;  // V tau = V2 etabar tau
 
-  double cp[kRowsPerLane], ap[kRowsPerLane], dp[kRowsPerLane], mm[kRowsPerLane];
+  double cp[kRowsPerLane], ap[kRowsPerLane], dp[kRowsPerLane];
+  double* Xq = sX + q * nrp;  // heat capacity V rho c of row i until phase 4, then That
   double pc = 0.0, pa = 0.0, pd = 0.0;    // c', a', d' of the previous interior row
   double Dacc = 0.0, Aacc = 0.0, P = 1.0; // first interior row = Dacc + P x_next - Aacc L
   double ae = 0.0, be = 1.0, ce = 0.0, de = 0.0;  // separator row
@@ -175,7 +222,7 @@ __device__ __forceinline__ void step_fp64_tile(const StepArgs& a, const TileTask
         else { ra = -1.0; rb = 1.0; rc = 0.0; rd = 0.0; }
         have_le = false;
       }
-      mm[k] = m;
+      if (ENERGY && active) Xq[c] = m;
       if (k < cnt - 1) {
         const double den = (k == 0) ? rb : fma(-ra, pc, rb);
         const double r = frcp(den);
@@ -215,13 +262,12 @@ __device__ __forceinline__ void step_fp64_tile(const StepArgs& a, const TileTask
       }
     }
 #pragma unroll
-    for (int k = 0; k < kRowsPerLane; ++k)
-      if (k == cnt - 1) dp[k] = xs;  // dp[k] = x_k for every row of the segment
+    for (int k = 0; k < kRowsPerLane; ++k)  // dp[k] = x_k for every row of the segment
+      dp[k] = (k == cnt - 1) ? xs : dp[k];  // (a select: an indexed store would demote dp to local memory)
   }
-  const double xnext = __shfl_down_sync(kFull, dp[0], 1, G);  // first row of lane l+1
 
   // ---- 4. stores, boundary rows, energy and trace epilogue
-  double eE = 0.0, eI = 0.0;
+  double eE = 0.0;
   bool bad = false;
   if (active) {
     double* Oj = Tout + (long long)j * nr;
@@ -238,70 +284,59 @@ __device__ __forceinline__ void step_fp64_tile(const StepArgs& a, const TileTask
         if (row0) O0[i] = (I.bc_z0 == CC_DIRICHLET) ? I.t_d : x;
         if (rowM) OM[i] = (I.bc_zmax == CC_DIRICHLET) ? I.t_d : x;
         if (ENERGY) {
-          const double Ti = Tj[smem_col(i)];
-          eE = fma(mm[k], x - Ti, eE);
-          const int cls = I.rg[i].cls;
-          if (cls == RC_IFACE || cls == RC_OUTER) {
-            // heat through the edges to the regular neighbours, at That
-            const double xw = (k == 0) ? L : dp[k > 0 ? k - 1 : 0];
-            const double Tw = Tj[smem_col(i - 1)];
-            const RowGeo gw = I.rg[i - 1];
-            const double kw = I.tau * gw.V2 * zg.etabar * gw.gC *
-                              lam_face(I.mat[gw.seg], frule, Tw, Ti);
-            const double fw = kw * (x - xw);  // into node i-1
-            if (cls == RC_OUTER) {
-              if (I.bc_rmax == CC_DIRICHLET) eD += fw; else eN += fw;
-            } else {
-              const double xe = (k == cnt - 1) ? xnext : dp[k < kRowsPerLane - 1 ? k + 1 : k];
-              const RowGeo ge = I.rg[i + 1];
-              const double ke = I.tau * ge.V2 * zg.etabar * ge.gA *
-                                lam_face(I.mat[ge.seg], frule, Ti, Tj[smem_col(i + 1)]);
-              eI += fw + ke * (x - xe);  // and into node i+1
-            }
-          }
+          const int c = smem_col(i);
+          eE = fma(Xq[c], x - Tj[c], eE);
+          Xq[c] = x;
         }
       }
     }
   }
   if (bad) atomicOr(a.err, 1u);
 
-  if (ENERGY || TRACE) {
-    double tr = 0.0;
-    if (TRACE && active && l == G - 1) {  // this lane owns That(r_max, z_j)
-      tr = zg.wnorm * xs;
-      double* trs = a.trace + ((long long)tk.inst * a.n_steps + a.step) * 2;
-      if (j == 1) {
-        const double x0 = (I.bc_z0 == CC_DIRICHLET) ? I.t_d : xs;
-        tr = fma(I.zg[0].wnorm, x0, tr);
-        trs[0] = x0;
-      }
-      if (j == M - 1) {
-        const double xM = (I.bc_zmax == CC_DIRICHLET) ? I.t_d : xs;
-        tr = fma(I.zg[M].wnorm, xM, tr);
-      }
+  if (TRACE && active && l == G - 1) {  // this lane owns That(r_max, z_j)
+    double tr = zg.wnorm * xs;
+    double* trs = a.trace + ((long long)tk.inst * a.n_steps + a.step) * 2;
+    if (j == 1) {
+      const double x0 = (I.bc_z0 == CC_DIRICHLET) ? I.t_d : xs;
+      tr = fma(I.zg[0].wnorm, x0, tr);
+      trs[0] = x0;
     }
-    if (!active) { eE = eQ = eD = eI = eN = 0.0; }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-      if (ENERGY) {
-        eE += __shfl_xor_sync(kFull, eE, o);
-        eQ += __shfl_xor_sync(kFull, eQ, o);
-        eD += __shfl_xor_sync(kFull, eD, o);
-        eI += __shfl_xor_sync(kFull, eI, o);
-        eN += __shfl_xor_sync(kFull, eN, o);
-      }
-      if (TRACE) tr += __shfl_xor_sync(kFull, tr, o);
+    if (j == M - 1) {
+      const double xM = (I.bc_zmax == CC_DIRICHLET) ? I.t_d : xs;
+      tr = fma(I.zg[M].wnorm, xM, tr);
     }
-    if (lane == 0) {
-      if (ENERGY) {
-        double* e = a.energy + (long long)tk.inst * 5;
-        atomicAdd(e + 0, eE);
-        atomicAdd(e + 1, eQ);
-        atomicAdd(e + 2, eD);
-        atomicAdd(e + 3, eI);
-        atomicAdd(e + 4, eN);
+    acc.tr += tr;
+  }
+  if (ENERGY && active) {
+    acc.e[0] += eE;
+    acc.e[1] += eQ;
+    acc.e[2] += eD;
+    acc.e[4] += eN;
+  }
+  if (ENERGY && I.n_if > 0) {
+    // heat through the radial edges between each interface (or r_max) node
+    // and its regular neighbours, at That, with the faces' conductivities at
+    // T^n (Eq. (Lambda_i)); one thread per (line, interface) of the tile
+    __syncthreads();  // sX complete
+    for (int it = threadIdx.x; it < nl * I.n_if; it += blockDim.x) {
+      const int qq = it / I.n_if;
+      const int i = I.if_i[it - qq * I.n_if];
+      const double* Tr = sT + (qq + 1) * nrp;
+      const double* Xr = sX + qq * nrp;
+      const double Ti = Tr[smem_col(i)], x = Xr[smem_col(i)];
+      const double etab = I.zg[j0 + qq].etabar;
+      const RowGeo gw = I.rg[i - 1];
+      const double kw = I.tau * gw.V2 * etab * gw.gC *
+                        lam_face(I.mat[gw.seg], frule, Tr[smem_col(i - 1)], Ti);
+      const double fw = kw * (x - Xr[smem_col(i - 1)]);  // into node i-1
+      if (I.rg[i].cls == RC_OUTER) {
+        if (I.bc_rmax == CC_DIRICHLET) acc.e[2] += fw; else acc.e[4] += fw;
+      } else {
+        const RowGeo ge = I.rg[i + 1];
+        const double ke = I.tau * ge.V2 * etab * ge.gA *
+                          lam_face(I.mat[ge.seg], frule, Ti, Tr[smem_col(i + 1)]);
+        acc.e[3] += fw + ke * (x - Xr[smem_col(i + 1)]);  // and into node i+1
       }
-      if (TRACE) atomicAdd(a.trace + ((long long)tk.inst * a.n_steps + a.step) * 2 + 1, tr);
     }
   }
   __syncthreads();  // the next tile reuses the shared memory

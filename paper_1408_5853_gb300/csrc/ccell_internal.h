@@ -80,6 +80,8 @@ struct DevInst {
   int face_rule, interface_rule;
   int src_layer, waveform, g_model;
   int pad0;
+  int n_if;              // interface and r_max nodes (classes RC_IFACE, RC_OUTER) ...
+  int if_i[CC_MAX_LAYERS];  // ... their radial indices, ascending
   long long t_off;       // element offset of this instance in T
   double t_d;            // Dirichlet temperature
   double tau, inv_tau;   // time step and its reciprocal
@@ -116,6 +118,20 @@ struct TileTask {
 // every 16, so lanes reading rows 16 apart hit different banks.
 CC_HOST_DEVICE inline int smem_row_stride(int nr) { return nr + (nr >> 4) + 1; }
 CC_HOST_DEVICE inline int smem_col(int i) { return i + (i >> 4); }
+
+// Dynamic shared memory of one FP64 CTA tile of nl lines: the staged field
+// rows j0-1 .. j0+nl, the axial faces between them, and the new values of
+// the nl lines (read back by the interface energy pass).
+CC_HOST_DEVICE inline int fp64_tile_smem_bytes(int nl, int nr) {
+  return (3 * nl + 3) * smem_row_stride(nr) * (int)sizeof(double);
+}
+
+// Interface and r_max nodes of one instance, from the row classes.
+inline void fill_iface_list(const RowGeo* rg, int nr, DevInst& D) {
+  D.n_if = 0;
+  for (int i = 0; i < nr && D.n_if < CC_MAX_LAYERS; ++i)
+    if (rg[i].cls == RC_IFACE || rg[i].cls == RC_OUTER) D.if_i[D.n_if++] = i;
+}
 
 // Everything one step launch needs.
 struct StepArgs {

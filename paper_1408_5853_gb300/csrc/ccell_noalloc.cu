@@ -279,7 +279,7 @@ extern "C" int cc_step_n_noalloc(const cc_geometry_desc* desc, const cc_material
   const int lpc = 4 * (32 / G);  // CTA tiles of the FP64 step: 4 warps, 128 threads
   int n_tiles = 0;
   for (int j0 = 1; j0 <= M - 1; j0 += lpc) h_tile[n_tiles++] = TileTask{0, j0, std::min(lpc, M - j0), 0};
-  const int smem = (2 * std::min(lpc, M - 1) + 3) * smem_row_stride(d.nr) * (int)sizeof(double);
+  const int smem = fp64_tile_smem_bytes(std::min(lpc, M - 1), d.nr);
 
   std::memset(&h_inst, 0, sizeof h_inst);
   h_inst.nr = d.nr;
@@ -302,6 +302,7 @@ extern "C" int cc_step_n_noalloc(const cc_geometry_desc* desc, const cc_material
   h_inst.t_start = source->t_start;
   h_inst.edge_w = source->edge_w;
   h_inst.g_ref = source->g_ref;
+  fill_iface_list(h_rg, d.nr, h_inst);
   h_inst.rg = reinterpret_cast<const RowGeo*>(base + kOffRg);
   h_inst.zg = reinterpret_cast<const ZGeo*>(base + kOffZg);
   for (int m = 0; m < d.n_layers; ++m) {

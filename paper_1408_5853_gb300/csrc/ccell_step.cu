@@ -91,8 +91,11 @@ int launch_waveform(const DevInst* insts, int n_inst, long long n_steps, double 
 template <bool ENERGY, bool TRACE>
 __global__ void __launch_bounds__(CC_FP64_MAX_THREADS, CC_FP64_MIN_BLOCKS) step_fp64_kernel(const StepArgs a) {
   extern __shared__ double sm[];
+  EAcc acc;
+  eacc_init(acc);
   for (int t = blockIdx.x; t < a.n_tiles; t += gridDim.x)
-    step_fp64_tile<ENERGY, TRACE>(a, a.tiles[t], sm);
+    step_fp64_tile<ENERGY, TRACE>(a, a.tiles[t], sm, acc);
+  eacc_flush<ENERGY, TRACE>(a, acc);
 }
 
 // Largest dynamic shared memory any tile needs (rows + faces of the biggest

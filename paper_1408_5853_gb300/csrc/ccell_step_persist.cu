@@ -16,8 +16,11 @@ __global__ void __launch_bounds__(CC_FP64_MAX_THREADS, CC_FP64_MIN_BLOCKS) steps
     s.step = a.step + q;
     s.Tin = (q & 1) ? a.Tout : a.Tin;
     s.Tout = (q & 1) ? const_cast<void*>(a.Tin) : a.Tout;
+    EAcc acc;
+    eacc_init(acc);
     for (int t = blockIdx.x; t < a.n_tiles; t += gridDim.x)
-      step_fp64_tile<ENERGY, TRACE>(s, a.tiles[t], sm);
+      step_fp64_tile<ENERGY, TRACE>(s, a.tiles[t], sm, acc);
+    eacc_flush<ENERGY, TRACE>(s, acc);
     if (!grid_barrier(a.bar, a.bar_extra, a.spin_limit, a.err)) return;
   }
 }
