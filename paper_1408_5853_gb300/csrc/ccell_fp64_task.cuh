@@ -6,16 +6,17 @@
 // l holds rows [l nr/G, (l+1) nr/G)).  Per time step:
 //   0. the CTA stages the field rows j0-1 .. j0+nl (contiguous in global
 //      memory) into shared memory, padded so lanes 16 rows apart do not share
-//      a bank, and evaluates every axial face conductivity lambda_{i,j+1/2}
-//      of the tile once (a face is shared by the two lines it separates);
+//      a bank, and evaluates, with all threads over the columns, every
+//      conductivity and heat capacity the tile needs: the axial faces
+//      lambda_{i,j+1/2} (a face is shared by the two lines it separates and
+//      is evaluated once), the radial faces lambda_{i+1/2,j} and
+//      rho c(T_ij) / tau (Eqs. (Lambda_i), (Lambda_j));
 //   1. every lane assembles its rows of the tridiagonal system of Eq. (ABC)
 //      (regular nodes), the interface rows of Eq. (cc_first_1) and the
-//      closures of Eq. (first_oder_bc) -- radial face conductivities are
-//      evaluated along the segment, heat capacities in registers
-//      (Eqs. (Lambda_i), (Lambda_j), (source)) -- and eliminates the segment's
-//      interior rows downwards (the forward sweep of Eq. (front_sweep)
-//      restricted to the segment, keeping the coupling to the previous
-//      segment's last row);
+//      closures of Eq. (first_oder_bc) from those values and the source of
+//      Eq. (source), and eliminates the segment's interior rows downwards
+//      (the forward sweep of Eq. (front_sweep) restricted to the segment,
+//      keeping the coupling to the previous segment's last row);
 //   2. the G separator rows are solved by cyclic reduction with shuffles;
 //   3. back substitution (Eq. (back_sweep)) inside each segment;
 //   4. stores, axial boundary rows, surface trace and energy terms.
@@ -53,7 +54,8 @@ __device__ __forceinline__ void eacc_init(EAcc& c) {
 // Called by every thread of the block (c.inst is block-uniform).
 template <bool ENERGY, bool TRACE>
 __device__ __forceinline__ void eacc_flush(const StepArgs& a, EAcc& c) {
-  if (!(ENERGY || TRACE) || c.inst < 0) return;
+  if constexpr (!(ENERGY || TRACE)) return;
+  if (c.inst < 0) return;
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) {
     if (ENERGY) {
@@ -86,9 +88,32 @@ __device__ __forceinline__ double rct_eval(const DevMaterial& M, double T) {
   return M.rho_tau * fma(fma(fma(a[3], T, a[2]), T, a[1]), T, a[0]);
 }
 
-template <bool ENERGY, bool TRACE>
+// Copy the field rows j0-1 .. j0+nl of a tile into a staging buffer with
+// asynchronous 8-byte copies (one commit group).  Only for per-step launches:
+// the copies read through L1, which is coherent with earlier launches but not
+// with other blocks of the same launch.
+__device__ __forceinline__ void stage_rows_async(const StepArgs& a, const TileTask tk,
+                                                 double* sT) {
+  const DevInst& I = a.insts[tk.inst];
+  const int nr = I.nr, nrp = smem_row_stride(nr);
+  const double* src = static_cast<const double*>(a.Tin) + I.t_off + (long long)(tk.j0 - 1) * nr;
+  for (int r = 0; r < tk.nl + 2; ++r)
+    for (int i = threadIdx.x; i < nr; i += blockDim.x) {
+      const unsigned dst = (unsigned)__cvta_generic_to_shared(sT + r * nrp + smem_col(i));
+      asm volatile("cp.async.ca.shared.global [%0], [%1], 8;"
+                   :: "r"(dst), "l"(src + (long long)r * nr + i) : "memory");
+    }
+  asm volatile("cp.async.commit_group;" ::: "memory");
+}
+
+// One tile.  PREFETCH: the tile's rows were staged by stage_rows_async into
+// sT, and the rows of next (if next.nl > 0) are staged into sTn meanwhile;
+// otherwise the rows are loaded here (L2 loads, coherent within a launch).
+template <bool ENERGY, bool TRACE, bool PREFETCH>
 __device__ __forceinline__ void step_fp64_tile(const StepArgs& a, const TileTask tk,
-                                               double* __restrict__ sm, EAcc& acc) {
+                                               double* __restrict__ sT, double* __restrict__ sTn,
+                                               const TileTask next, double* __restrict__ sW,
+                                               EAcc& acc) {
   if (tk.inst != acc.inst) {  // block-uniform
     eacc_flush<ENERGY, TRACE>(a, acc);
     acc.inst = tk.inst;
@@ -101,28 +126,56 @@ __device__ __forceinline__ void step_fp64_tile(const StepArgs& a, const TileTask
   const int j0 = tk.j0, nl = tk.nl;
   const int nrp = smem_row_stride(nr);
   const int frule = I.face_rule;
-  double* sT = sm;                            // rows j0-1 .. j0+nl
-  double* sF = sm + (size_t)(nl + 2) * nrp;   // faces (j0-1+r, j0+r), r = 0..nl
-  double* sX = sF + (size_t)(nl + 1) * nrp;   // That of lines j0 .. j0+nl-1 (energy pass)
-  const double* Tin = static_cast<const double*>(a.Tin) + I.t_off;
+  const int n_if = I.n_if;
+  double* sF = sW;                      // axial face fluxes lambda (T_{j+1} - T_j), r = 0..nl
+  double* sR = sF + (size_t)(nl + 1) * nrp;  // radial faces (i, i+1) of lines j0 .. j0+nl-1
+  double* sX = sR + (size_t)nl * nrp;        // rho c / tau, then V2 rho c, then That
+  double* sI = sX + (size_t)nl * nrp;        // interface rows: lambda_w(T), lambda_e(T)
   double* Tout = static_cast<double*>(a.Tout) + I.t_off;
 
-  // ---- 0. stage the rows, then the axial face conductivities
-  {
-    const double* src = Tin + (long long)(j0 - 1) * nr;
+  // ---- 0. stage the rows (sT rows 0 .. nl+1 = lines j0-1 .. j0+nl)
+  if constexpr (PREFETCH) {
+    asm volatile("cp.async.wait_all;" ::: "memory");
+    __syncthreads();
+    if (next.nl > 0) stage_rows_async(a, next, sTn);
+  } else {
+    const double* src = static_cast<const double*>(a.Tin) + I.t_off + (long long)(j0 - 1) * nr;
     for (int r = 0; r < nl + 2; ++r)
       for (int i = threadIdx.x; i < nr; i += blockDim.x)
         sT[r * nrp + smem_col(i)] = __ldcg(src + (long long)r * nr + i);
+    __syncthreads();
   }
-  __syncthreads();
-  for (int r = 0; r <= nl; ++r)
-    for (int i = threadIdx.x; i < nr; i += blockDim.x) {
-      const RowGeo& g = I.rg[i];
-      if (g.cls == RC_REGULAR) {
-        const int c = smem_col(i);
-        sF[r * nrp + c] = lam_face(I.mat[g.seg], frule, sT[r * nrp + c], sT[(r + 1) * nrp + c]);
+  // Then every conductivity and heat capacity of the tile, with all threads
+  // over the columns (independent items): the axial faces (each shared by two
+  // lines, evaluated once) as fluxes, the radial faces (segment [r_i, r_{i+1}]
+  // lies in layer rg[i].seg), rho c(T)/tau at the nodes, and the nodal
+  // conductivities of the interface rows.
+  for (int i = threadIdx.x; i < nr; i += blockDim.x) {
+    const DevMaterial& Mt = I.mat[I.rg[i].seg];
+    const int c = smem_col(i), c1 = smem_col(i < N ? i + 1 : i);
+    double Tlo = sT[c];
+#pragma unroll 2
+    for (int r = 0; r <= nl; ++r) {
+      const double Thi = sT[(r + 1) * nrp + c];
+      sF[r * nrp + c] = lam_face(Mt, frule, Tlo, Thi) * (Thi - Tlo);
+      if (r < nl) {
+        sR[r * nrp + c] = (i < N) ? lam_face(Mt, frule, Thi, sT[(r + 1) * nrp + c1]) : 0.0;
+        sX[r * nrp + c] = rct_eval(Mt, Thi);
+      }
+      Tlo = Thi;
+    }
+  }
+  if (I.interface_rule == 0) {
+    for (int it = threadIdx.x; it < nl * n_if; it += blockDim.x) {
+      const int q = it / n_if;
+      const RowGeo& g = I.rg[I.if_i[it - q * n_if]];
+      if (g.cls == RC_IFACE) {
+        const double T = sT[(q + 1) * nrp + smem_col(I.if_i[it - q * n_if])];
+        sI[2 * it] = lam_eval(I.mat[g.segw], T);
+        sI[2 * it + 1] = lam_eval(I.mat[g.seg], T);
       }
     }
+  }
   __syncthreads();
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -135,8 +188,6 @@ __device__ __forceinline__ void step_fp64_tile(const StepArgs& a, const TileTask
   const int i_hi = ((l + 1) * nr) >> lg;
   const int cnt = i_hi - i_lo;  // 2 .. kRowsPerLane
   const double* Tj = sT + (q + 1) * nrp;
-  const double* Ts = Tj - nrp;
-  const double* Tn = Tj + nrp;
   const double* Fs = sF + q * nrp;   // face (j-1, j)
   const double* Fn = Fs + nrp;       // face (j, j+1)
   const ZGeo zg = I.zg[j];
@@ -144,16 +195,13 @@ __device__ __forceinline__ void step_fp64_tile(const StepArgs& a, const TileTask
   const double etau = zg.etabar * I.tau;  // V tau = V2 etabar tau
 
   double cp[kRowsPerLane], ap[kRowsPerLane], dp[kRowsPerLane];
-  double* Xq = sX + q * nrp;  // heat capacity V rho c of row i until phase 4, then That
+  const double* Rq = sR + q * nrp;  // radial faces of line j
+  double* Xq = sX + q * nrp;        // rho c / tau; V2 rho c from phase 1; That from phase 4
   double pc = 0.0, pa = 0.0, pd = 0.0;    // c', a', d' of the previous interior row
   double Dacc = 0.0, Aacc = 0.0, P = 1.0; // first interior row = Dacc + P x_next - Aacc L
   double ae = 0.0, be = 1.0, ce = 0.0, de = 0.0;  // separator row
-  double le_prev = 0.0;
-  bool have_le = false;
-  double eQ = 0.0, eD = 0.0, eN = 0.0;
-
-  double Tm1 = (i_lo > 0) ? Tj[smem_col(i_lo - 1)] : 0.0;
-  double T0 = Tj[smem_col(i_lo)];
+  double eQ = 0.0, eD = 0.0, eN = 0.0;    // source: sum V2 X (times etabar tau at the end)
+  double lw = (i_lo > 0) ? Rq[smem_col(i_lo - 1)] : 0.0;  // face (i-1, i)
 
   // ---- 1. assemble rows and eliminate the segment downwards
 #pragma unroll
@@ -162,17 +210,14 @@ __device__ __forceinline__ void step_fp64_tile(const StepArgs& a, const TileTask
       const int i = i_lo + k;
       const int c = smem_col(i);
       const RowGeo g = I.rg[i];
-      const double Tp1 = (i < N) ? Tj[smem_col(i + 1)] : 0.0;
+      const double T0 = Tj[c];
+      const double le = Rq[c];  // face (i, i+1)
       double ra, rb, rc, rd, m = 0.0;
       if (g.cls == RC_REGULAR) {
-        const DevMaterial& Mt = I.mat[g.seg];
-        const double tS = Ts[c], tN = Tn[c];
-        const double lw = have_le ? le_prev : lam_face(Mt, frule, Tm1, T0);
-        const double le = lam_face(Mt, frule, T0, Tp1);
-        const double ls = Fs[c], ln = Fn[c];
-        const double rct = rct_eval(Mt, T0);  // rho c / tau
-        // Eq. (Lambda_j), explicit in T
-        const double Lj = fma(ln * zg.gzn, tN - T0, -ls * zg.gzs * (T0 - tS));
+        const double fs = Fs[c], fn = Fn[c];  // lambda (T - T_S), lambda (T_N - T)
+        const double rct = Xq[c];  // rho c / tau
+        // Eq. (Lambda_j), explicit in T, from the face fluxes
+        const double Lj = fma(zg.gzn, fn, -zg.gzs * fs);
         double X = 0.0;  // Eq. (source)
         if (g.seg == I.src_layer && s != 0.0) {
           X = I.q0 * s;
@@ -184,18 +229,15 @@ __device__ __forceinline__ void step_fp64_tile(const StepArgs& a, const TileTask
         rc = C;
         rb = rct - A - C;
         rd = fma(rct, T0, Lj + X);
-        le_prev = le;
-        have_le = true;
         if (ENERGY) {
-          const double Vt = g.V2 * etau;  // tau V
-          m = Vt * rct;                   // V rho c
-          if (X != 0.0) eQ = fma(Vt, X, eQ);
+          m = g.V2 * rct;  // V rho c / (etabar tau)
+          if (X != 0.0) eQ = fma(g.V2, X, eQ);
           if (j == 1) {
-            const double f = I.tau * g.V2 * ls * (tS - T0) / zg.eta_s;
+            const double f = -I.tau * g.V2 * fs / zg.eta_s;
             if (I.bc_z0 == CC_DIRICHLET) eD += f; else eN += f;
           }
           if (j == M - 1) {
-            const double f = I.tau * g.V2 * ln * (tN - T0) / zg.eta_n;
+            const double f = I.tau * g.V2 * fn / zg.eta_n;
             if (I.bc_zmax == CC_DIRICHLET) eD += f; else eN += f;
           }
         }
@@ -203,25 +245,23 @@ __device__ __forceinline__ void step_fp64_tile(const StepArgs& a, const TileTask
         // Eq. (cc_first_1)/(cc_first_3) as the row (a, b, c | 0)
         double lmv, lpv;
         if (I.interface_rule == 0) {
-          lmv = lam_eval(I.mat[g.segw], T0);
-          lpv = lam_eval(I.mat[g.seg], T0);
+          lmv = sI[2 * (q * n_if + g.ifo)];
+          lpv = sI[2 * (q * n_if + g.ifo) + 1];
         } else {
-          lmv = g.rw * lam_face(I.mat[g.segw], frule, Tm1, T0);
-          lpv = g.re * lam_face(I.mat[g.seg], frule, T0, Tp1);
+          lmv = g.rw * lw;
+          lpv = g.re * le;
         }
         ra = -lmv * g.he;
         rc = -lpv * g.hw;
         rb = fma(lmv, g.he, lpv * g.hw);
         rd = 0.0;
-        have_le = false;
       } else if (g.cls == RC_AXIS) {  // That_0 = That_1
         ra = 0.0; rb = 1.0; rc = -1.0; rd = 0.0;
-        have_le = false;
       } else {  // r = r_max
         if (I.bc_rmax == CC_DIRICHLET) { ra = 0.0; rb = 1.0; rc = 0.0; rd = I.t_d; }
         else { ra = -1.0; rb = 1.0; rc = 0.0; rd = 0.0; }
-        have_le = false;
       }
+      lw = le;
       if (ENERGY && active) Xq[c] = m;
       if (k < cnt - 1) {
         const double den = (k == 0) ? rb : fma(-ra, pc, rb);
@@ -241,8 +281,6 @@ __device__ __forceinline__ void step_fp64_tile(const StepArgs& a, const TileTask
       } else {
         ae = ra; be = rb; ce = rc; de = rd;
       }
-      Tm1 = T0;
-      T0 = Tp1;
     }
   }
 
@@ -285,7 +323,7 @@ __device__ __forceinline__ void step_fp64_tile(const StepArgs& a, const TileTask
         if (rowM) OM[i] = (I.bc_zmax == CC_DIRICHLET) ? I.t_d : x;
         if (ENERGY) {
           const int c = smem_col(i);
-          eE = fma(Xq[c], x - Tj[c], eE);
+          eE = fma(Xq[c], x - Tj[c], eE);  // V2 rho c (That - T)
           Xq[c] = x;
         }
       }
@@ -308,8 +346,8 @@ __device__ __forceinline__ void step_fp64_tile(const StepArgs& a, const TileTask
     acc.tr += tr;
   }
   if (ENERGY && active) {
-    acc.e[0] += eE;
-    acc.e[1] += eQ;
+    acc.e[0] += etau * eE;
+    acc.e[1] += etau * eQ;
     acc.e[2] += eD;
     acc.e[4] += eN;
   }
@@ -321,20 +359,18 @@ __device__ __forceinline__ void step_fp64_tile(const StepArgs& a, const TileTask
     for (int it = threadIdx.x; it < nl * I.n_if; it += blockDim.x) {
       const int qq = it / I.n_if;
       const int i = I.if_i[it - qq * I.n_if];
-      const double* Tr = sT + (qq + 1) * nrp;
+      const double* Rr = sR + qq * nrp;
       const double* Xr = sX + qq * nrp;
-      const double Ti = Tr[smem_col(i)], x = Xr[smem_col(i)];
+      const double x = Xr[smem_col(i)];
       const double etab = I.zg[j0 + qq].etabar;
       const RowGeo gw = I.rg[i - 1];
-      const double kw = I.tau * gw.V2 * etab * gw.gC *
-                        lam_face(I.mat[gw.seg], frule, Tr[smem_col(i - 1)], Ti);
+      const double kw = I.tau * gw.V2 * etab * gw.gC * Rr[smem_col(i - 1)];
       const double fw = kw * (x - Xr[smem_col(i - 1)]);  // into node i-1
       if (I.rg[i].cls == RC_OUTER) {
         if (I.bc_rmax == CC_DIRICHLET) acc.e[2] += fw; else acc.e[4] += fw;
       } else {
         const RowGeo ge = I.rg[i + 1];
-        const double ke = I.tau * ge.V2 * etab * ge.gA *
-                          lam_face(I.mat[ge.seg], frule, Ti, Tr[smem_col(i + 1)]);
+        const double ke = I.tau * ge.V2 * etab * ge.gA * Rr[smem_col(i)];
         acc.e[3] += fw + ke * (x - Xr[smem_col(i + 1)]);  // and into node i+1
       }
     }

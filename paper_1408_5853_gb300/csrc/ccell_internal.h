@@ -27,7 +27,7 @@ struct RowGeo {
   int cls;     // RC_*
   int seg;     // layer of the segment [r_i, r_{i+1}] (regular node: its layer)
   int segw;    // layer of the segment [r_{i-1}, r_i]
-  int pad;
+  int ifo;     // RC_IFACE / RC_OUTER: position of i in DevInst::if_i (else -1)
 };
 
 // Per axial node j (index j in [0, nz)).
@@ -119,18 +119,31 @@ struct TileTask {
 CC_HOST_DEVICE inline int smem_row_stride(int nr) { return nr + (nr >> 4) + 1; }
 CC_HOST_DEVICE inline int smem_col(int i) { return i + (i >> 4); }
 
-// Dynamic shared memory of one FP64 CTA tile of nl lines: the staged field
-// rows j0-1 .. j0+nl, the axial faces between them, and the new values of
-// the nl lines (read back by the interface energy pass).
-CC_HOST_DEVICE inline int fp64_tile_smem_bytes(int nl, int nr) {
-  return (3 * nl + 3) * smem_row_stride(nr) * (int)sizeof(double);
+// Shared memory of the FP64 CTA tiles, in doubles.  Two staging buffers of
+// stage_elems each (the field rows j0-1 .. j0+nl of the tile in work and of
+// the next one), then per tile of nl lines: the axial face fluxes (nl + 1
+// rows), the radial face conductivities (nl rows), the heat capacities, later
+// the new values (nl rows), and the interface conductivities (2 per line and
+// interface node).
+CC_HOST_DEVICE inline int fp64_stage_elems(int nl, int nr) { return (nl + 2) * smem_row_stride(nr); }
+CC_HOST_DEVICE inline int fp64_tile_smem_bytes(int nl, int nr, int stage_elems) {
+  return (2 * stage_elems + (3 * nl + 1) * smem_row_stride(nr) + 2 * CC_MAX_LAYERS * nl) *
+         (int)sizeof(double);
 }
+// Opt-in limit of dynamic shared memory per block on sm_103.
+constexpr int kMaxTileSmem = 227 * 1024;
 
-// Interface and r_max nodes of one instance, from the row classes.
+// Interface and r_max nodes of one instance, from the row classes (their
+// positions in the list are stored in RowGeo::ifo).
 inline void fill_iface_list(const RowGeo* rg, int nr, DevInst& D) {
   D.n_if = 0;
   for (int i = 0; i < nr && D.n_if < CC_MAX_LAYERS; ++i)
     if (rg[i].cls == RC_IFACE || rg[i].cls == RC_OUTER) D.if_i[D.n_if++] = i;
+}
+inline void number_ifaces(RowGeo* rg, int nr) {
+  int n = 0;
+  for (int i = 0; i < nr; ++i)
+    rg[i].ifo = (rg[i].cls == RC_IFACE || rg[i].cls == RC_OUTER) ? n++ : -1;
 }
 
 // Everything one step launch needs.
@@ -141,6 +154,7 @@ struct StepArgs {
   const TileTask* tiles; // FP64 step: CTA tiles
   int n_tiles;
   int smem_bytes;        // dynamic shared memory of the FP64 tile kernel
+  int stage_elems;       // doubles per staging buffer of the FP64 tile kernel
   int n_inst;
   const void* Tin;       // double* (FP64) or float* (mixed, high part)
   void* Tout;

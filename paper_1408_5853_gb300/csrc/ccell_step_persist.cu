@@ -19,13 +19,14 @@ __global__ void __launch_bounds__(CC_FP64_MAX_THREADS, CC_FP64_MIN_BLOCKS) steps
     EAcc acc;
     eacc_init(acc);
     for (int t = blockIdx.x; t < a.n_tiles; t += gridDim.x)
-      step_fp64_tile<ENERGY, TRACE>(s, a.tiles[t], sm, acc);
+      step_fp64_tile<ENERGY, TRACE, false>(s, a.tiles[t], sm, nullptr, TileTask{0, 0, 0, 0},
+                                           sm + 2 * (size_t)a.stage_elems, acc);
     eacc_flush<ENERGY, TRACE>(s, acc);
     if (!grid_barrier(a.bar, a.bar_extra, a.spin_limit, a.err)) return;
   }
 }
 
-constexpr int kTileSmemMaxP = 160 * 1024;
+constexpr int kTileSmemMaxP = kMaxTileSmem;
 
 template <bool ENERGY, bool TRACE>
 static int launch_fp64_persistent_variant(const StepArgs& a, long long n, cudaStream_t st) {
