@@ -23,7 +23,7 @@ __device__ __forceinline__ double frcp(double d) {
 // Power law lam0 (x / t_ref)^b from the material's table: y = m 2^e with
 // m in [1, 2); the scale row e holds lam0 (k t_ref)^-b 2^(e b) (k = 2 for a
 // face, where y = T_a + T_b, k = 1 for a node, where y = T), and m^b is a
-// degree-5 polynomial in m - c_q on mantissa interval q.  Arguments outside
+// degree-kPowDeg polynomial in m - c_q on mantissa interval q.  Arguments outside
 // the table (or non-finite, or <= 0) take the exact pow path.
 __device__ __forceinline__ double lam_pow(const DevMaterial& M, double y, bool face) {
   const long long bits = __double_as_longlong(y);
@@ -35,11 +35,9 @@ __device__ __forceinline__ double lam_pow(const DevMaterial& M, double y, bool f
                                           (1LL << (51 - kPowBits)));
     const double* P = M.ptab + 2 * kPowNE + q * (kPowDeg + 1);
     const double u = m - c;
-    double r = fma(__ldg(P + 5), u, __ldg(P + 4));
-    r = fma(r, u, __ldg(P + 3));
-    r = fma(r, u, __ldg(P + 2));
-    r = fma(r, u, __ldg(P + 1));
-    r = fma(r, u, __ldg(P + 0));
+    double r = __ldg(P + kPowDeg);
+#pragma unroll
+    for (int k = kPowDeg - 1; k >= 0; --k) r = fma(r, u, __ldg(P + k));
     return r * __ldg(M.ptab + (face ? 0 : kPowNE) + e);
   }
   return M.lam0s * pow((face ? 0.5 * y : y) * M.inv_tref, M.lam_b);

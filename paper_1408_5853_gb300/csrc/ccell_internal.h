@@ -44,9 +44,9 @@ struct ZGeo {
 // Power-law tables: x^b = 2^(e b) * p_q(m - c_q) for x = m 2^e, m in [1, 2),
 // with 2^kPowBits mantissa intervals q of centre c_q and degree-kPowDeg
 // polynomials p_q; binary exponents e in [kPowEmin, kPowEmin + kPowNE).
-constexpr int kPowBits = 7;
+constexpr int kPowBits = 8;
 constexpr int kPowQ = 1 << kPowBits;
-constexpr int kPowDeg = 5;
+constexpr int kPowDeg = 4;
 constexpr int kPowEmin = -2;
 constexpr int kPowNE = 16;
 // per layer: [face scale kPowNE][node scale kPowNE][kPowQ][kPowDeg + 1]

@@ -4,13 +4,13 @@
 // little FP64 throughput, and the time step evaluates three conductivities per
 // node.  Write x = m 2^e with m in [1, 2): x^b = 2^(e b) m^b.  The factor
 // 2^(e b), times the material constant, comes from a table indexed by e; m^b
-// comes from a degree-5 polynomial on one of 128 equal mantissa intervals,
+// comes from a degree-4 polynomial on one of 256 equal mantissa intervals,
 // evaluated in the offset u = m - c_q from the interval centre c_q.  Each
-// polynomial interpolates m^b at the 6 Chebyshev points of its interval
-// (computed in long double); on an interval of half-width 2^-8 the
-// interpolation error is below 1e-17 relative for the exponents of the
-// workloads, so the table value is as accurate as a correctly rounded pow up to
-// the rounding of the evaluation itself.  Every table is checked against powl
+// polynomial interpolates m^b at the 5 Chebyshev points of its interval
+// (computed in long double); on an interval of half-width 2^-9 the
+// interpolation error is at most |d^5 m^b / dm^5| h^5 / (2^4 5!), below 1e-16
+// relative for exponents b in [0, 3], so the table value is as accurate as a
+// correctly rounded pow up to the rounding of the evaluation itself.  Every table is checked against powl
 // at 16 points per interval; a table that misses 4e-16 relative is rejected and
 // the kernel falls back to pow.
 #include <cmath>
