@@ -47,7 +47,6 @@ struct cc_ctx {
   int n_tiles = 0;
   size_t tiles_cap = 0;
   int smem_bytes = 0;
-  int stage_elems = 0;
   void* d_T2 = nullptr;       // ping-pong partner of the caller's field
   float* d_lo = nullptr;      // mixed precision: low-order parts (two buffers)
   double* d_s = nullptr;      // waveform table
@@ -376,27 +375,17 @@ int upload(cc_ctx* c, const std::vector<double>& dts, cudaStream_t st) {
     c->n_tasks = (int)tasks.size();
     // FP64 CTA tiles: (threads / 32) warps x 32/G lines
     std::vector<TileTask> tiles;
-    std::vector<int> lpcs(n);
-    int stage = 0;
+    int smem = 0;
     for (int k = 0; k < n; ++k) {
       const Instance& in = c->inst[k];
       int lpc = (c->threads / 32) * (32 / in.G);
       // fewer lines per tile (idle lanes) if the tile would not fit
-      while (lpc > 1 && fp64_tile_smem_bytes(lpc, in.d.nr, fp64_stage_elems(lpc, in.d.nr)) >
-                            kMaxTileSmem)
-        lpc /= 2;
-      lpcs[k] = lpc;
-      stage = std::max(stage, fp64_stage_elems(std::min(lpc, in.d.nz - 2), in.d.nr));
-    }
-    int smem = 0;
-    for (int k = 0; k < n; ++k) {
-      const Instance& in = c->inst[k];
-      const int lpc = lpcs[k];
+      while (lpc > 1 && fp64_tile_smem_bytes(lpc, in.d.nr) > kMaxTileSmem) lpc /= 2;
       for (int j0 = 1; j0 <= in.d.nz - 2; j0 += lpc) {
         const int nl = std::min(lpc, in.d.nz - 1 - j0);
         tiles.push_back(TileTask{k, j0, nl, 0});
       }
-      smem = std::max(smem, fp64_tile_smem_bytes(std::min(lpc, in.d.nz - 2), in.d.nr, stage));
+      smem = std::max(smem, fp64_tile_smem_bytes(std::min(lpc, in.d.nz - 2), in.d.nr));
     }
     if (smem > kMaxTileSmem) return CC_EUNSUPPORTED;
     if (tiles.size() > c->tiles_cap) {
@@ -414,7 +403,6 @@ int upload(cc_ctx* c, const std::vector<double>& dts, cudaStream_t st) {
       return CC_ECUDA;
     c->n_tiles = (int)tiles.size();
     c->smem_bytes = smem;
-    c->stage_elems = stage;
     c->tasks_dirty = false;
     c->dirty = true;
   }
@@ -637,7 +625,6 @@ int cc_step_n(cc_ctx* c, void* T_dev, int64_t n_steps, double t0, double dt_s, d
   a.tiles = c->d_tiles;
   a.n_tiles = c->n_tiles;
   a.smem_bytes = c->smem_bytes;
-  a.stage_elems = c->stage_elems;
   a.n_inst = n;
   a.s_tab = c->d_s;
   a.trace = trace_dev;
@@ -878,7 +865,6 @@ int adjoint_impl(cc_ctx* c, const void* T0_dev, int64_t n_steps, double t0, doub
   a.tiles = c->d_tiles;
   a.n_tiles = c->n_tiles;
   a.smem_bytes = c->smem_bytes;
-  a.stage_elems = c->stage_elems;
   a.n_inst = n;
   a.s_tab = s_tab;
   a.n_steps = n_steps;

@@ -119,16 +119,11 @@ struct TileTask {
 CC_HOST_DEVICE inline int smem_row_stride(int nr) { return nr + (nr >> 4) + 1; }
 CC_HOST_DEVICE inline int smem_col(int i) { return i + (i >> 4); }
 
-// Shared memory of the FP64 CTA tiles, in doubles.  Two staging buffers of
-// stage_elems each (the field rows j0-1 .. j0+nl of the tile in work and of
-// the next one), then per tile of nl lines: the axial face fluxes (nl + 1
-// rows), the radial face conductivities (nl rows), the heat capacities, later
-// the new values (nl rows), and the interface conductivities (2 per line and
-// interface node).
-CC_HOST_DEVICE inline int fp64_stage_elems(int nl, int nr) { return (nl + 2) * smem_row_stride(nr); }
-CC_HOST_DEVICE inline int fp64_tile_smem_bytes(int nl, int nr, int stage_elems) {
-  return (2 * stage_elems + (3 * nl + 1) * smem_row_stride(nr) + 2 * CC_MAX_LAYERS * nl) *
-         (int)sizeof(double);
+// Shared memory of one FP64 CTA tile of nl lines: the four coefficient rows
+// of every line's tridiagonal system and the heat capacities (nl padded rows
+// each), and four values per line and interface node.
+CC_HOST_DEVICE inline int fp64_tile_smem_bytes(int nl, int nr) {
+  return (5 * nl * smem_row_stride(nr) + 4 * CC_MAX_LAYERS * nl) * (int)sizeof(double);
 }
 // Opt-in limit of dynamic shared memory per block on sm_103.
 constexpr int kMaxTileSmem = 227 * 1024;
@@ -154,7 +149,6 @@ struct StepArgs {
   const TileTask* tiles; // FP64 step: CTA tiles
   int n_tiles;
   int smem_bytes;        // dynamic shared memory of the FP64 tile kernel
-  int stage_elems;       // doubles per staging buffer of the FP64 tile kernel
   int n_inst;
   const void* Tin;       // double* (FP64) or float* (mixed, high part)
   void* Tout;

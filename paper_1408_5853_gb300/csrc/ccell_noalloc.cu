@@ -280,8 +280,7 @@ extern "C" int cc_step_n_noalloc(const cc_geometry_desc* desc, const cc_material
   const int lpc = 4 * (32 / G);  // CTA tiles of the FP64 step: 4 warps, 128 threads
   int n_tiles = 0;
   for (int j0 = 1; j0 <= M - 1; j0 += lpc) h_tile[n_tiles++] = TileTask{0, j0, std::min(lpc, M - j0), 0};
-  const int stage = fp64_stage_elems(std::min(lpc, M - 1), d.nr);
-  const int smem = fp64_tile_smem_bytes(std::min(lpc, M - 1), d.nr, stage);
+  const int smem = fp64_tile_smem_bytes(std::min(lpc, M - 1), d.nr);
 
   std::memset(&h_inst, 0, sizeof h_inst);
   h_inst.nr = d.nr;
@@ -351,7 +350,6 @@ extern "C" int cc_step_n_noalloc(const cc_geometry_desc* desc, const cc_material
   a.tiles = reinterpret_cast<const TileTask*>(base + kOffTile);
   a.n_tiles = n_tiles;
   a.smem_bytes = smem;
-  a.stage_elems = stage;
   a.threads = 128;
   a.n_inst = 1;
   a.s_tab = s_tab;

@@ -91,20 +91,10 @@ int launch_waveform(const DevInst* insts, int n_inst, long long n_steps, double 
 template <bool ENERGY, bool TRACE>
 __global__ void __launch_bounds__(CC_FP64_MAX_THREADS, CC_FP64_MIN_BLOCKS) step_fp64_kernel(const StepArgs a) {
   extern __shared__ double sm[];
-  double* sW = sm + 2 * (size_t)a.stage_elems;
   EAcc acc;
   eacc_init(acc);
-  // the rows of the next tile are copied while the current one is computed
-  if (blockIdx.x < a.n_tiles) stage_rows_async(a, a.tiles[blockIdx.x], sm);
-  int b = 0;
-  for (int t = blockIdx.x; t < a.n_tiles; t += gridDim.x) {
-    const int tn = t + gridDim.x;
-    const TileTask next = tn < a.n_tiles ? a.tiles[tn] : TileTask{0, 0, 0, 0};
-    double* cur = sm + (size_t)b * a.stage_elems;
-    double* nxt = sm + (size_t)(b ^ 1) * a.stage_elems;
-    step_fp64_tile<ENERGY, TRACE, true>(a, a.tiles[t], cur, nxt, next, sW, acc);
-    b ^= 1;
-  }
+  for (int t = blockIdx.x; t < a.n_tiles; t += gridDim.x)
+    step_fp64_tile<ENERGY, TRACE, true>(a, a.tiles[t], sm, acc);
   eacc_flush<ENERGY, TRACE>(a, acc);
 }
 

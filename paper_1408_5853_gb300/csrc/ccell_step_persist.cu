@@ -19,8 +19,7 @@ __global__ void __launch_bounds__(CC_FP64_MAX_THREADS, CC_FP64_MIN_BLOCKS) steps
     EAcc acc;
     eacc_init(acc);
     for (int t = blockIdx.x; t < a.n_tiles; t += gridDim.x)
-      step_fp64_tile<ENERGY, TRACE, false>(s, a.tiles[t], sm, nullptr, TileTask{0, 0, 0, 0},
-                                           sm + 2 * (size_t)a.stage_elems, acc);
+      step_fp64_tile<ENERGY, TRACE, false>(s, a.tiles[t], sm, acc);
     eacc_flush<ENERGY, TRACE>(s, acc);
     if (!grid_barrier(a.bar, a.bar_extra, a.spin_limit, a.err)) return;
   }
