@@ -168,17 +168,22 @@ __device__ __forceinline__ void step_fp64_tile(const StepArgs& a, const TileTask
         const RowGeo& ge = I.rg[ie];
         gwV = gw.V2; gwC = gw.gC; geV = ge.V2; geA = ge.gA;
       }
-      const double* row = Tin + (long long)(j0 - 1 + q0) * nr;  // line j0-1+q0
-      const double Ts = ld_field<CACHED>(row + ic);
-      double Tc = ld_field<CACHED>(row + nr + ic);
+      // T(i, j-1), T(i, j), T(i, j+1) and T(i+1, j) of line j = j0 + q; the
+      // values of the next line are loaded one iteration ahead
+      const double* row = Tin + (long long)(j0 + q0) * nr;  // line j
+      const double Ts = ld_field<CACHED>(row - nr + ic);
+      double Tc = ld_field<CACHED>(row + ic);
+      double Tn = ld_field<CACHED>(row + nr + ic);
+      double Te = ld_field<CACHED>(row + ie);
       double fs = lam_face(Mt, frule, Ts, Tc) * (Tc - Ts);
-#pragma unroll 2
       for (int q = q0; q < q1; ++q) {
         const int j = j0 + q;
-        row += nr;  // line j
-        const double Tn = ld_field<CACHED>(row + nr + ic);
-        double Te = __shfl_down_sync(kFull, Tc, 1);  // T(i+1, j) from the next lane
-        if (lane == 31) Te = ld_field<CACHED>(row + ie);
+        double Tn_next = 0.0, Te_next = 0.0;
+        if (q + 1 < q1) {
+          Tn_next = ld_field<CACHED>(row + 2 * nr + ic);
+          Te_next = ld_field<CACHED>(row + nr + ie);
+        }
+        row += nr;
         const double fn = lam_face(Mt, frule, Tc, Tn) * (Tn - Tc);
         const double le = (ic < N) ? lam_face(Mt, frule, Tc, Te) : 0.0;  // face (i, i+1)
         const double lw = __shfl_up_sync(kFull, le, 1);                  // face (i-1, i)
@@ -246,6 +251,8 @@ __device__ __forceinline__ void step_fp64_tile(const StepArgs& a, const TileTask
           if (ENERGY) SM[o] = m;
         }
         Tc = Tn;
+        Tn = Tn_next;
+        Te = Te_next;
         fs = fn;
       }
     }
