@@ -47,6 +47,9 @@ struct cc_ctx {
   int n_tiles = 0;
   size_t tiles_cap = 0;
   int smem_bytes = 0;
+  int* d_cta = nullptr;       // FP64 step: first tile of each block (n_cta + 1)
+  int n_cta = 0;
+  size_t cta_cap = 0;
   void* d_T2 = nullptr;       // ping-pong partner of the caller's field
   float* d_lo = nullptr;      // mixed precision: low-order parts (two buffers)
   double* d_s = nullptr;      // waveform table
@@ -220,6 +223,10 @@ void free_device(cc_ctx* c) {
   cudaFree(c->d_tiles);
   c->d_tiles = nullptr;
   c->tiles_cap = 0;
+  cudaFree(c->d_cta);
+  c->d_cta = nullptr;
+  c->cta_cap = 0;
+  c->n_cta = 0;
   cudaFree(c->d_T2);
   cudaFree(c->d_lo);
   cudaFree(c->d_s);
@@ -374,18 +381,49 @@ int upload(cc_ctx* c, const std::vector<double>& dts, cudaStream_t st) {
       return CC_ECUDA;
     c->n_tasks = (int)tasks.size();
     // FP64 CTA tiles: (threads / 32) warps x 32/G lines
+    // FP64 CTA tiles: lines of one instance, at most lpc of them.  The blocks
+    // of a launch (its resident capacity) take equal shares of all lines as
+    // ranges of consecutive tiles.
     std::vector<TileTask> tiles;
+    std::vector<int> lpcs(n), cta;
     int smem = 0;
+    long long total_lines = 0;
     for (int k = 0; k < n; ++k) {
       const Instance& in = c->inst[k];
       int lpc = (c->threads / 32) * (32 / in.G);
       // fewer lines per tile (idle lanes) if the tile would not fit
       while (lpc > 1 && fp64_tile_smem_bytes(lpc, in.d.nr) > kMaxTileSmem) lpc /= 2;
-      for (int j0 = 1; j0 <= in.d.nz - 2; j0 += lpc) {
-        const int nl = std::min(lpc, in.d.nz - 1 - j0);
-        tiles.push_back(TileTask{k, j0, nl, 0});
-      }
+      lpcs[k] = lpc;
       smem = std::max(smem, fp64_tile_smem_bytes(std::min(lpc, in.d.nz - 2), in.d.nr));
+      total_lines += in.d.nz - 2;
+    }
+    const int B = (c->precision == CC_FP64 && smem <= kMaxTileSmem)
+                      ? fp64_resident_blocks(c->threads, smem) : 0;
+    if (B > 0) {
+      cta.assign(B + 1, 0);
+      int k = 0, jn = 1;  // next line of instance k
+      long long g = 0;
+      for (int b = 0; b < B; ++b) {
+        cta[b] = (int)tiles.size();
+        const long long g_end = (long long)(b + 1) * total_lines / B;
+        while (g < g_end) {
+          const Instance& in = c->inst[k];
+          const int take = (int)std::min<long long>(g_end - g, in.d.nz - 1 - jn);
+          for (int j = jn; j < jn + take; j += lpcs[k])
+            tiles.push_back(TileTask{k, j, std::min(lpcs[k], jn + take - j), 0});
+          jn += take;
+          g += take;
+          if (jn > in.d.nz - 2) {
+            ++k;
+            jn = 1;
+          }
+        }
+      }
+      cta[B] = (int)tiles.size();
+    } else {
+      for (int k = 0; k < n; ++k)
+        for (int j0 = 1; j0 <= c->inst[k].d.nz - 2; j0 += lpcs[k])
+          tiles.push_back(TileTask{k, j0, std::min(lpcs[k], c->inst[k].d.nz - 1 - j0), 0});
     }
     if (smem > kMaxTileSmem) return CC_EUNSUPPORTED;
     if (tiles.size() > c->tiles_cap) {
@@ -402,6 +440,22 @@ int upload(cc_ctx* c, const std::vector<double>& dts, cudaStream_t st) {
                    cudaMemcpyHostToDevice) != cudaSuccess)
       return CC_ECUDA;
     c->n_tiles = (int)tiles.size();
+    c->n_cta = B;
+    if (B > 0) {
+      if ((size_t)(B + 1) > c->cta_cap) {
+        cudaFree(c->d_cta);
+        c->d_cta = nullptr;
+        c->cta_cap = 0;
+        if (cudaMalloc(&c->d_cta, sizeof(int) * (B + 1)) != cudaSuccess) {
+          cudaGetLastError();
+          return CC_ENOMEM;
+        }
+        c->cta_cap = B + 1;
+      }
+      if (cudaMemcpy(c->d_cta, cta.data(), sizeof(int) * (B + 1), cudaMemcpyHostToDevice) !=
+          cudaSuccess)
+        return CC_ECUDA;
+    }
     c->smem_bytes = smem;
     c->tasks_dirty = false;
     c->dirty = true;
@@ -624,6 +678,8 @@ int cc_step_n(cc_ctx* c, void* T_dev, int64_t n_steps, double t0, double dt_s, d
   a.n_tasks = c->n_tasks;
   a.tiles = c->d_tiles;
   a.n_tiles = c->n_tiles;
+  a.cta_start = c->n_cta > 0 ? c->d_cta : nullptr;
+  a.n_cta = c->n_cta;
   a.smem_bytes = c->smem_bytes;
   a.n_inst = n;
   a.s_tab = c->d_s;
@@ -864,6 +920,8 @@ int adjoint_impl(cc_ctx* c, const void* T0_dev, int64_t n_steps, double t0, doub
   a.n_tasks = c->n_tasks;
   a.tiles = c->d_tiles;
   a.n_tiles = c->n_tiles;
+  a.cta_start = c->n_cta > 0 ? c->d_cta : nullptr;
+  a.n_cta = c->n_cta;
   a.smem_bytes = c->smem_bytes;
   a.n_inst = n;
   a.s_tab = s_tab;

@@ -98,9 +98,14 @@ __device__ __forceinline__ double ld_field(const double* p) {
   else return __ldcg(p);
 }
 
+// One tile.  sm starts with two rows of axial face fluxes: the tile takes the
+// fluxes of the face south of its first line from row par ^ 1 if carry (the
+// previous tile of this block ended on the line before j0), and leaves those
+// north of its last line in row par.
 template <bool ENERGY, bool TRACE, bool CACHED>
 __device__ __forceinline__ void step_fp64_tile(const StepArgs& a, const TileTask tk,
-                                               double* __restrict__ sm, EAcc& acc) {
+                                               double* __restrict__ sm, EAcc& acc, bool carry,
+                                               int par) {
   if (tk.inst != acc.inst) {  // block-uniform
     eacc_flush<ENERGY, TRACE>(a, acc);
     acc.inst = tk.inst;
@@ -115,7 +120,9 @@ __device__ __forceinline__ void step_fp64_tile(const StepArgs& a, const TileTask
   const int frule = I.face_rule;
   const int n_if = I.n_if;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarps = blockDim.x >> 5;
-  double* SA = sm;                         // a, then a' (coupling to the previous separator)
+  const double* cin = sm + (size_t)(par ^ 1) * nrp;  // fluxes south of line j0
+  double* cout = sm + (size_t)par * nrp;             // fluxes north of line j0+nl-1
+  double* SA = sm + 2 * (size_t)nrp;       // a, then a' (coupling to the previous separator)
   double* SB = SA + (size_t)nl * nrp;      // b, then That
   double* SC = SB + (size_t)nl * nrp;      // c, then c'
   double* SD = SC + (size_t)nl * nrp;      // d, then d'
@@ -171,11 +178,16 @@ __device__ __forceinline__ void step_fp64_tile(const StepArgs& a, const TileTask
       // T(i, j-1), T(i, j), T(i, j+1) and T(i+1, j) of line j = j0 + q; the
       // values of the next line are loaded one iteration ahead
       const double* row = Tin + (long long)(j0 + q0) * nr;  // line j
-      const double Ts = ld_field<CACHED>(row - nr + ic);
       double Tc = ld_field<CACHED>(row + ic);
       double Tn = ld_field<CACHED>(row + nr + ic);
       double Te = ld_field<CACHED>(row + ie);
-      double fs = lam_face(Mt, frule, Ts, Tc) * (Tc - Ts);
+      double fs;
+      if (carry && q0 == 0) {
+        fs = cin[smem_col(ic)];
+      } else {
+        const double Ts = ld_field<CACHED>(row - nr + ic);
+        fs = lam_face(Mt, frule, Ts, Tc) * (Tc - Ts);
+      }
       for (int q = q0; q < q1; ++q) {
         const int j = j0 + q;
         double Tn_next = 0.0, Te_next = 0.0;
@@ -242,6 +254,7 @@ __device__ __forceinline__ void step_fp64_tile(const StepArgs& a, const TileTask
           K[2] = I.tau * gwV * zg.etabar * gwC * lw;
           K[3] = I.tau * geV * zg.etabar * geA * le;
         }
+        if (own && q == nl - 1) cout[smem_col(ic)] = fn;
         if (own) {
           const size_t o = (size_t)q * nrp + smem_col(ic);
           SA[o] = ra;
@@ -377,6 +390,26 @@ __device__ __forceinline__ void step_fp64_tile(const StepArgs& a, const TileTask
     if (TRACE) acc.tr += tr;
   }
   __syncthreads();  // the next tile reuses the shared memory
+}
+
+// The tiles of this block: its range, or a stride over all tiles.
+template <bool ENERGY, bool TRACE, bool CACHED>
+__device__ __forceinline__ void fp64_tiles(const StepArgs& a, double* __restrict__ sm, EAcc& acc) {
+  int t0 = blockIdx.x, t1 = a.n_tiles, dt = gridDim.x;
+  if (a.cta_start) {
+    t0 = a.cta_start[blockIdx.x];
+    t1 = a.cta_start[blockIdx.x + 1];
+    dt = 1;
+  }
+  int prev_inst = -1, prev_end = -1, par = 0;
+  for (int t = t0; t < t1; t += dt) {
+    const TileTask tk = a.tiles[t];
+    const bool carry = (tk.inst == prev_inst && tk.j0 == prev_end);
+    step_fp64_tile<ENERGY, TRACE, CACHED>(a, tk, sm, acc, carry, par);
+    prev_inst = tk.inst;
+    prev_end = tk.j0 + tk.nl;
+    par ^= 1;
+  }
 }
 
 // Resident blocks per SM x SMs for a kernel, block size and shared memory.

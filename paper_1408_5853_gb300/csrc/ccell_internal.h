@@ -121,12 +121,14 @@ CC_HOST_DEVICE inline int smem_col(int i) { return i + (i >> 4); }
 
 // Shared memory of one FP64 CTA tile of nl lines: the four coefficient rows
 // of every line's tridiagonal system and the heat capacities (nl padded rows
-// each), and four values per line and interface node.
+// each), two rows of axial face fluxes handed from one tile to the next, and
+// four values per line and interface node.
 CC_HOST_DEVICE inline int fp64_tile_smem_bytes(int nl, int nr) {
-  return (5 * nl * smem_row_stride(nr) + 4 * CC_MAX_LAYERS * nl) * (int)sizeof(double);
+  return ((5 * nl + 2) * smem_row_stride(nr) + 4 * CC_MAX_LAYERS * nl) * (int)sizeof(double);
 }
-// Opt-in limit of dynamic shared memory per block on sm_103.
-constexpr int kMaxTileSmem = 227 * 1024;
+// Largest dynamic shared memory of an FP64 tile: the opt-in limit per block
+// on sm_103 (227 KiB) less room for the kernels' static shared memory.
+constexpr int kMaxTileSmem = 226 * 1024;
 
 // Interface and r_max nodes of one instance, from the row classes (their
 // positions in the list are stored in RowGeo::ifo).
@@ -148,6 +150,9 @@ struct StepArgs {
   int n_tasks;
   const TileTask* tiles; // FP64 step: CTA tiles
   int n_tiles;
+  const int* cta_start;  // FP64 step: tiles [cta_start[b], cta_start[b+1]) of block b, or
+                         // null (blocks stride over the tiles)
+  int n_cta;             // blocks of the FP64 step launch when cta_start is set
   int smem_bytes;        // dynamic shared memory of the FP64 tile kernel
   int n_inst;
   const void* Tin;       // double* (FP64) or float* (mixed, high part)
@@ -201,6 +206,9 @@ int launch_adj_gather(const AdjArgs& a, long long max_nodes, void* stream);
 int launch_adj_seed(const DevInst* insts, int n_inst, const double* trace, const double* target,
                     long long n_steps, double* seed, double* loss, void* stream);
 int launch_step_fp64(const StepArgs& a, void* stream);
+// Resident blocks of the FP64 step kernels (all variants) for a block size and
+// dynamic shared memory: the grid of launches with per-block tile ranges.
+int fp64_resident_blocks(int threads, int smem);
 int launch_step_mixed(const StepArgs& a, void* stream);
 // n steps in one cooperative launch; buffers alternate Tin -> Tout -> Tin ...
 // (and lo_in/lo_out for mixed).  Returns -3 if the grid cannot be co-resident.

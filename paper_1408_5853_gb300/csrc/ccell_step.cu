@@ -87,14 +87,15 @@ int launch_waveform(const DevInst* insts, int n_inst, long long n_steps, double 
   return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }
 
-// Grid-stride over CTA tiles; the grid is sized to the resident capacity.
+// Each block takes its range of tiles (consecutive lines of an instance, so
+// the axial face fluxes of a tile's last line are handed to the next tile) or,
+// without ranges, strides over the tiles.
 template <bool ENERGY, bool TRACE>
 __global__ void __launch_bounds__(CC_FP64_MAX_THREADS, CC_FP64_MIN_BLOCKS) step_fp64_kernel(const StepArgs a) {
   extern __shared__ double sm[];
   EAcc acc;
   eacc_init(acc);
-  for (int t = blockIdx.x; t < a.n_tiles; t += gridDim.x)
-    step_fp64_tile<ENERGY, TRACE, true>(a, a.tiles[t], sm, acc);
+  fp64_tiles<ENERGY, TRACE, true>(a, sm, acc);
   eacc_flush<ENERGY, TRACE>(a, acc);
 }
 
@@ -102,20 +103,34 @@ __global__ void __launch_bounds__(CC_FP64_MAX_THREADS, CC_FP64_MIN_BLOCKS) step_
 constexpr int kTileSmemMax = kMaxTileSmem;
 
 template <bool ENERGY, bool TRACE>
-static void launch_fp64_variant(const StepArgs& a, cudaStream_t st) {
-  static int resident[3] = {0, 0, 0}, resident_smem[3] = {-1, -1, -1};
+static int fp64_variant_resident(int threads, int smem) {
   static bool opted = false;
   if (!opted) {
-    cudaFuncSetAttribute(step_fp64_kernel<ENERGY, TRACE>,
-                         cudaFuncAttributeMaxDynamicSharedMemorySize, kTileSmemMax);
+    if (cudaFuncSetAttribute(step_fp64_kernel<ENERGY, TRACE>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, kTileSmemMax) !=
+        cudaSuccess)
+      cudaGetLastError();  // the launch then reports a tile that does not fit
     opted = true;
   }
+  return resident_blocks(step_fp64_kernel<ENERGY, TRACE>, threads, smem);
+}
+
+int fp64_resident_blocks(int threads, int smem) {
+  int r = fp64_variant_resident<true, true>(threads, smem);
+  r = min(r, fp64_variant_resident<true, false>(threads, smem));
+  r = min(r, fp64_variant_resident<false, true>(threads, smem));
+  return min(r, fp64_variant_resident<false, false>(threads, smem));
+}
+
+template <bool ENERGY, bool TRACE>
+static void launch_fp64_variant(const StepArgs& a, cudaStream_t st) {
+  static int resident[3] = {0, 0, 0}, resident_smem[3] = {-1, -1, -1};
   const int t = a.threads > 0 ? a.threads : 128, si = shape_index(t);
   if (resident_smem[si] != a.smem_bytes) {
-    resident[si] = resident_blocks(step_fp64_kernel<ENERGY, TRACE>, t, a.smem_bytes);
+    resident[si] = fp64_variant_resident<ENERGY, TRACE>(t, a.smem_bytes);
     resident_smem[si] = a.smem_bytes;
   }
-  const int blocks = a.n_tiles < resident[si] ? a.n_tiles : resident[si];
+  const int blocks = a.cta_start ? a.n_cta : (a.n_tiles < resident[si] ? a.n_tiles : resident[si]);
   step_fp64_kernel<ENERGY, TRACE><<<blocks, t, a.smem_bytes, st>>>(a);
 }
 

@@ -18,8 +18,7 @@ __global__ void __launch_bounds__(CC_FP64_MAX_THREADS, CC_FP64_MIN_BLOCKS) steps
     s.Tout = (q & 1) ? const_cast<void*>(a.Tin) : a.Tout;
     EAcc acc;
     eacc_init(acc);
-    for (int t = blockIdx.x; t < a.n_tiles; t += gridDim.x)
-      step_fp64_tile<ENERGY, TRACE, false>(s, a.tiles[t], sm, acc);
+    fp64_tiles<ENERGY, TRACE, false>(s, sm, acc);
     eacc_flush<ENERGY, TRACE>(s, acc);
     if (!grid_barrier(a.bar, a.bar_extra, a.spin_limit, a.err)) return;
   }
@@ -33,7 +32,9 @@ static int launch_fp64_persistent_variant(const StepArgs& a, long long n, cudaSt
   static bool opted = false;
   auto kern = steps_fp64_persistent_kernel<ENERGY, TRACE>;
   if (!opted) {
-    cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, kTileSmemMaxP);
+    if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, kTileSmemMaxP) !=
+        cudaSuccess)
+      cudaGetLastError();  // the launch then reports a tile that does not fit
     opted = true;
   }
   const int t = a.threads > 0 ? a.threads : 128, si = shape_index(t);
@@ -41,7 +42,8 @@ static int launch_fp64_persistent_variant(const StepArgs& a, long long n, cudaSt
     resident[si] = resident_blocks(kern, t, a.smem_bytes);
     resident_smem[si] = a.smem_bytes;
   }
-  const int blocks = a.n_tiles < resident[si] ? a.n_tiles : resident[si];
+  if (a.cta_start && resident[si] < a.n_cta) return -3;
+  const int blocks = a.cta_start ? a.n_cta : (a.n_tiles < resident[si] ? a.n_tiles : resident[si]);
   StepArgs copy = a;
   void* args[] = {&copy, &n};
   const cudaError_t e =
