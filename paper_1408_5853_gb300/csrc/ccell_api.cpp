@@ -381,7 +381,7 @@ int upload(cc_ctx* c, const std::vector<double>& dts, cudaStream_t st) {
       return CC_ECUDA;
     c->n_tasks = (int)tasks.size();
     // FP64 CTA tiles: (threads / 32) warps x 32/G lines
-    // FP64 CTA tiles: lines of one instance, at most lpc of them.  The blocks
+    // CTA tiles of the step kernels: lines of one instance, at most lpc of them.  The blocks
     // of a launch (its resident capacity) take equal shares of all lines as
     // ranges of consecutive tiles.
     std::vector<TileTask> tiles;
@@ -391,14 +391,19 @@ int upload(cc_ctx* c, const std::vector<double>& dts, cudaStream_t st) {
     for (int k = 0; k < n; ++k) {
       const Instance& in = c->inst[k];
       int lpc = (c->threads / 32) * (32 / in.G);
+      auto tile_smem = [&](int nl) {
+        return c->precision == CC_FP64 ? fp64_tile_smem_bytes(nl, in.d.nr)
+                                       : mixed_tile_smem_bytes(nl, in.d.nr);
+      };
       // fewer lines per tile (idle lanes) if the tile would not fit
-      while (lpc > 1 && fp64_tile_smem_bytes(lpc, in.d.nr) > kMaxTileSmem) lpc /= 2;
+      while (lpc > 1 && tile_smem(lpc) > kMaxTileSmem) lpc /= 2;
       lpcs[k] = lpc;
-      smem = std::max(smem, fp64_tile_smem_bytes(std::min(lpc, in.d.nz - 2), in.d.nr));
+      smem = std::max(smem, tile_smem(std::min(lpc, in.d.nz - 2)));
       total_lines += in.d.nz - 2;
     }
-    const int B = (c->precision == CC_FP64 && smem <= kMaxTileSmem)
-                      ? fp64_resident_blocks(c->threads, smem) : 0;
+    const int B = smem > kMaxTileSmem ? 0
+                  : c->precision == CC_FP64 ? fp64_resident_blocks(c->threads, smem)
+                                            : mixed_resident_blocks(c->threads, smem);
     if (B > 0) {
       cta.assign(B + 1, 0);
       int k = 0, jn = 1;  // next line of instance k

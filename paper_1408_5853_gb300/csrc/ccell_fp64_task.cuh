@@ -36,48 +36,6 @@
 
 namespace ccell {
 
-// Energy and trace partial sums of one thread, carried over the tiles of a
-// launch and flushed (warp sums, one atomic per warp and term) when the
-// instance changes, at the end of a step and at the end of the launch.
-struct EAcc {
-  double e[5];  // dE, Q, Phi_D, Phi_I, Phi_N
-  double tr;    // trapezoid-weighted z-sum of That(r_max, z)
-  int inst;     // instance the sums belong to (-1: none yet)
-};
-
-__device__ __forceinline__ void eacc_init(EAcc& c) {
-#pragma unroll
-  for (int k = 0; k < 5; ++k) c.e[k] = 0.0;
-  c.tr = 0.0;
-  c.inst = -1;
-}
-
-// Called by every thread of the block (c.inst is block-uniform).
-template <bool ENERGY, bool TRACE>
-__device__ __forceinline__ void eacc_flush(const StepArgs& a, EAcc& c) {
-  if constexpr (!(ENERGY || TRACE)) return;
-  if (c.inst < 0) return;
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) {
-    if (ENERGY) {
-#pragma unroll
-      for (int k = 0; k < 5; ++k) c.e[k] += __shfl_xor_sync(kFull, c.e[k], o);
-    }
-    if (TRACE) c.tr += __shfl_xor_sync(kFull, c.tr, o);
-  }
-  if ((threadIdx.x & 31) == 0) {
-    if (ENERGY) {
-      double* e = a.energy + (long long)c.inst * 5;
-#pragma unroll
-      for (int k = 0; k < 5; ++k) atomicAdd(e + k, c.e[k]);
-    }
-    if (TRACE) atomicAdd(a.trace + ((long long)c.inst * a.n_steps + a.step) * 2 + 1, c.tr);
-  }
-#pragma unroll
-  for (int k = 0; k < 5; ++k) c.e[k] = 0.0;
-  c.tr = 0.0;
-}
-
 // rho c(T) / tau from the folded material constants
 __device__ __forceinline__ double rct_eval(const DevMaterial& M, double T) {
   if (M.cap_model == 1) {

@@ -126,6 +126,12 @@ CC_HOST_DEVICE inline int smem_col(int i) { return i + (i >> 4); }
 CC_HOST_DEVICE inline int fp64_tile_smem_bytes(int nl, int nr) {
   return ((5 * nl + 2) * smem_row_stride(nr) + 4 * CC_MAX_LAYERS * nl) * (int)sizeof(double);
 }
+// Shared memory of one mixed-precision CTA tile: the same rows in FP32 and
+// kMixIf floats per line and interface node.
+constexpr int kMixIf = 8;
+CC_HOST_DEVICE inline int mixed_tile_smem_bytes(int nl, int nr) {
+  return ((5 * nl + 2) * smem_row_stride(nr) + kMixIf * CC_MAX_LAYERS * nl) * (int)sizeof(float);
+}
 // Largest dynamic shared memory of an FP64 tile: the opt-in limit per block
 // on sm_103 (227 KiB) less room for the kernels' static shared memory.
 constexpr int kMaxTileSmem = 226 * 1024;
@@ -209,6 +215,7 @@ int launch_step_fp64(const StepArgs& a, void* stream);
 // Resident blocks of the FP64 step kernels (all variants) for a block size and
 // dynamic shared memory: the grid of launches with per-block tile ranges.
 int fp64_resident_blocks(int threads, int smem);
+int mixed_resident_blocks(int threads, int smem);
 int launch_step_mixed(const StepArgs& a, void* stream);
 // n steps in one cooperative launch; buffers alternate Tin -> Tout -> Tin ...
 // (and lo_in/lo_out for mixed).  Returns -3 if the grid cannot be co-resident.

@@ -45,265 +45,356 @@ __device__ __forceinline__ float cap32(const DevMaterial& M, float T) {
 }
 
 // ---------------------------------------------------------------------------
-// one warp task
+// one CTA tile of nl consecutive lines (the tile structure of the FP64 step,
+// ccell_fp64_task.cuh): properties and FP32 rows with the lanes over columns,
+// FP64 line solves with the lanes over the rows of a line, then the pair
+// update with the lanes over columns again.
 // ---------------------------------------------------------------------------
-template <bool ENERGY, bool TRACE>
-__device__ __forceinline__ void step_mixed_task(const StepArgs& a, const Task tk, const int lane) {
+template <bool CACHED>
+__device__ __forceinline__ float ld_state(const float* p) {
+  if constexpr (CACHED) return __ldg(p);
+  else return __ldcg(p);
+}
+
+template <bool ENERGY, bool TRACE, bool CACHED>
+__device__ __forceinline__ void step_mixed_tile(const StepArgs& a, const TileTask tk,
+                                                float* __restrict__ sm, EAcc& acc, bool carry,
+                                                int par) {
+  if (tk.inst != acc.inst) {  // block-uniform
+    eacc_flush<ENERGY, TRACE>(a, acc);
+    acc.inst = tk.inst;
+  }
   const DevInst& I = a.insts[tk.inst];
+  const int nr = I.nr, N = nr - 1, M = I.nz - 1;
   const int G = I.G;
   const int lg = __ffs(G) - 1;
-  const int grp = lane >> lg, l = lane & (G - 1);
-  const int nr = I.nr, N = nr - 1, M = I.nz - 1;
-  const int j_req = tk.j0 + grp;
-  const bool active = j_req <= M - 1;
-  const int j = active ? j_req : M - 1;
-  const int i_lo = (l * nr) >> lg;
-  const int i_hi = ((l + 1) * nr) >> lg;
-  const int cnt = i_hi - i_lo;
-
+  const int lpw = 32 >> lg;
+  const int j0 = tk.j0, nl = tk.nl;
+  const int nrp = smem_row_stride(nr);
+  const int frule = I.face_rule;
+  const int n_if = I.n_if;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarps = blockDim.x >> 5;
+  const float* cin = sm + (size_t)(par ^ 1) * nrp;  // axial fluxes south of line j0
+  float* cout = sm + (size_t)par * nrp;             // axial fluxes north of line j0+nl-1
+  float* FA = sm + 2 * (size_t)nrp;        // rows (FP32, delta form)
+  float* FB = FA + (size_t)nl * nrp;       // b, then the new increment dT (FP32)
+  float* FC = FB + (size_t)nl * nrp;
+  float* FD = FC + (size_t)nl * nrp;
+  float* FM = FD + (size_t)nl * nrp;       // V rho c (energy)
+  float* sI = FM + (size_t)nl * nrp;       // per line and interface node: lam_w, lam_e, kw, ke, dTw, dTe
   const float* Hin = static_cast<const float*>(a.Tin) + I.t_off;
   const float* Lin = a.lo_in + I.t_off;
   float* Hout = static_cast<float*>(a.Tout) + I.t_off;
   float* Lout = a.lo_out + I.t_off;
-  const long long rj = (long long)j * nr;
-  const float* Hj = Hin + rj;
-  const float* Lj_ = Lin + rj;
-  const ZGeo zg = I.zg[j];
   const float s = (float)a.s_tab[a.step * a.n_inst + tk.inst];
-  const int frule = I.face_rule;
   const float inv_tau = I.inv_tau_f, tau = I.tau_f;
+  double eQ = 0.0, eD = 0.0, eN = 0.0, eI = 0.0, eE = 0.0, tr = 0.0;
 
-  double cp[kRowsPerLane], ap[kRowsPerLane], dp[kRowsPerLane];
-  float mm[kRowsPerLane];
-  double pc = 0.0, pa = 0.0, pd = 0.0;
-  double Dacc = 0.0, Aacc = 0.0, P = 1.0;
-  double ae = 0.0, be = 1.0, ce = 0.0, de = 0.0;
-  float le_prev = 0.0f;
-  bool have_le = false;
-  double eQ = 0.0, eD = 0.0, eN = 0.0;
-
-  float hm1 = (i_lo > 0) ? __ldcg(Hj + (i_lo - 1)) : 0.0f, lm1 = (i_lo > 0) ? __ldcg(Lj_ + (i_lo - 1)) : 0.0f;
-  float h0 = __ldcg(Hj + (i_lo)), l0 = __ldcg(Lj_ + (i_lo));
-
-  // ---- 1. FP32 rows in delta form, FP64 downward elimination
-#pragma unroll
-  for (int k = 0; k < kRowsPerLane; ++k) {
-    if (k < cnt) {
-      const int i = i_lo + k;
+  // ---- 0a. nodal conductivities of the interface rows, Eq. (cc_first_3)
+  if (I.interface_rule == 0 && n_if > 0) {
+    for (int it = threadIdx.x; it < nl * n_if; it += blockDim.x) {
+      const int q = it / n_if;
+      const int i = I.if_i[it - q * n_if];
       const RowGeo& g = I.rg[i];
-      const int cls = g.cls;
-      const float hp1 = (i < N) ? __ldcg(Hj + (i + 1)) : 0.0f, lp1 = (i < N) ? __ldcg(Lj_ + (i + 1)) : 0.0f;
-      const float dW = (hm1 - h0) + (lm1 - l0);  // T_{i-1} - T_i
-      const float dE = (hp1 - h0) + (lp1 - l0);  // T_{i+1} - T_i
-      float fa, fb, fc, fd, m = 0.0f;
-      if (cls == RC_REGULAR) {
-        const DevMaterial& Mt = I.mat[g.seg];
-        const float hs = __ldcg(Hj + (i - nr)), ls_ = __ldcg(Lj_ + (i - nr)), hn = __ldcg(Hj + (i + nr)), ln_ = __ldcg(Lj_ + (i + nr));
-        const float dS = (hs - h0) + (ls_ - l0), dN = (hn - h0) + (ln_ - l0);
-        const float lw = have_le ? le_prev : lam_face32(Mt, frule, hm1, h0);
-        const float le = lam_face32(Mt, frule, h0, hp1);
-        const float ls = lam_face32(Mt, frule, hs, h0);
-        const float ln = lam_face32(Mt, frule, h0, hn);
-        const float rhoc = Mt.rho_f * cap32(Mt, h0);
-        const float Ljv = fmaf(ln * zg.gzn_f, dN, ls * zg.gzs_f * dS);  // Eq. (Lambda_j)
-        float X = 0.0f;
-        if (g.seg == I.src_layer && s != 0.0f) {
-          X = I.q0_f * s;
-          if (I.g_model == 1) X *= I.g_ref_f * rsqrtf(h0);
-        }
-        const float A = -g.gA_f * lw, C = -g.gC_f * le;
-        fa = A;
-        fc = C;
-        fb = fmaf(rhoc, inv_tau, -A - C);
-        fd = fmaf(-A, dW, fmaf(-C, dE, Ljv + X));
-        le_prev = le;
-        have_le = true;
-        if (ENERGY) {
-          const float V = g.V2_f * zg.etabar_f;
-          m = V * rhoc;
-          eQ += (double)(tau * V * X);
-          if (j == 1) {
-            const double f = (double)(tau * g.V2_f * ls * dS / (float)zg.eta_s);
-            if (I.bc_z0 == CC_DIRICHLET) eD += f; else eN += f;
-          }
-          if (j == M - 1) {
-            const double f = (double)(tau * g.V2_f * ln * dN / (float)zg.eta_n);
-            if (I.bc_zmax == CC_DIRICHLET) eD += f; else eN += f;
-          }
-        }
-      } else if (cls == RC_IFACE) {
-        float lmv, lpv;
-        if (I.interface_rule == 0) {
-          lmv = lam32(I.mat[g.segw], h0);
-          lpv = lam32(I.mat[g.seg], h0);
-        } else {
-          lmv = g.rw_f * lam_face32(I.mat[g.segw], frule, hm1, h0);
-          lpv = g.re_f * lam_face32(I.mat[g.seg], frule, h0, hp1);
-        }
-        fa = -lmv * g.he_f;
-        fc = -lpv * g.hw_f;
-        fb = fmaf(lmv, g.he_f, lpv * g.hw_f);
-        fd = -fmaf(fa, dW, fc * dE);
-        have_le = false;
-      } else if (cls == RC_AXIS) {  // dT_0 - dT_1 = T_1 - T_0
-        fa = 0.0f; fb = 1.0f; fc = -1.0f; fd = dE;
-        have_le = false;
-      } else {
-        if (I.bc_rmax == CC_DIRICHLET) {
-          fa = 0.0f; fb = 1.0f; fc = 0.0f; fd = (I.td_hi - h0) + (I.td_lo - l0);
-        } else {
-          fa = -1.0f; fb = 1.0f; fc = 0.0f; fd = dW;  // dT_N - dT_{N-1} = T_{N-1} - T_N
-        }
-        have_le = false;
+      if (g.cls == RC_IFACE) {
+        const float h = ld_state<CACHED>(Hin + (long long)(j0 + q) * nr + i);
+        sI[kMixIf * it] = lam32(I.mat[g.segw], h);
+        sI[kMixIf * it + 1] = lam32(I.mat[g.seg], h);
       }
-      mm[k] = m;
-      const double ra = fa, rb = fb, rc = fc, rd = fd;  // exact widening
-      if (k < cnt - 1) {
-        const double den = (k == 0) ? rb : fma(-ra, pc, rb);
-        const double r = frcp(den);
-        const double c1 = rc * r;
-        const double a1 = (k == 0) ? ra * r : -ra * pa * r;
-        const double d1 = (k == 0) ? rd * r : fma(-ra, pd, rd) * r;
-        cp[k] = c1;
-        ap[k] = a1;
-        dp[k] = d1;
-        Dacc = fma(P, d1, Dacc);
-        Aacc = fma(P, a1, Aacc);
-        P = -P * c1;
-        pc = c1;
-        pa = a1;
-        pd = d1;
-      } else {
-        ae = ra; be = rb; ce = rc; de = rd;
-      }
-      hm1 = h0; lm1 = l0;
-      h0 = hp1; l0 = lp1;
     }
+    __syncthreads();
   }
 
-  // ---- 2. separators, 3. back substitution (FP64)
-  const double xs = solve_separators(ae, be, ce, de, pa, pc, pd, Dacc, Aacc, P, G, l);
-  const double L = __shfl_up_sync(kFull, xs, 1, G);
+  // ---- 0b. FP32 properties and rows in delta form, lanes over columns
+  // (block b covers columns 31b .. 31b+31; see the FP64 tile)
   {
-    double xn = xs;
-#pragma unroll
-    for (int k = kRowsPerLane - 2; k >= 0; --k) {
-      if (k <= cnt - 2) {
-        const double x = fma(-cp[k], xn, fma(-ap[k], L, dp[k]));
-        dp[k] = x;
-        xn = x;
+    const int nb = (N + 30) / 31;
+    const int n_items = nb * nl;
+    const int end = (int)((long long)(warp + 1) * n_items / nwarps);
+    for (int idx = (int)((long long)warp * n_items / nwarps); idx < end;) {
+      const int b = idx / nl, q0 = idx - b * nl;
+      const int q1 = min(nl, q0 + (end - idx));
+      idx += q1 - q0;
+      const int i = 31 * b + lane;
+      const int ic = i <= N ? i : N;
+      const bool own = (i <= N) && (lane > 0 || b == 0);
+      const RowGeo& g = I.rg[ic];
+      const int cls = g.cls, seg = g.seg;
+      const DevMaterial& Mt = I.mat[seg];
+      const int ie = ic < N ? ic + 1 : ic;
+      const bool edge = (cls == RC_IFACE || cls == RC_OUTER);
+      float gwk = 0.0f, gek = 0.0f;  // tau V2 gC of the west, tau V2 gA of the east neighbour
+      if (ENERGY && edge) {
+        const RowGeo& gw = I.rg[ic - 1];
+        const RowGeo& ge = I.rg[ie];
+        gwk = tau * gw.V2_f * gw.gC_f;
+        gek = tau * ge.V2_f * ge.gA_f;
+      }
+      long long o = (long long)(j0 + q0) * nr;  // line j
+      float hc = ld_state<CACHED>(Hin + o + ic), lc = ld_state<CACHED>(Lin + o + ic);
+      float hn = ld_state<CACHED>(Hin + o + nr + ic), ln = ld_state<CACHED>(Lin + o + nr + ic);
+      float he = ld_state<CACHED>(Hin + o + ie), lE = ld_state<CACHED>(Lin + o + ie);
+      float fs;  // lambda (T - T_S) on the face south of line j
+      if (carry && q0 == 0) {
+        fs = cin[smem_col(ic)];
+      } else {
+        const float hs = ld_state<CACHED>(Hin + o - nr + ic), ls = ld_state<CACHED>(Lin + o - nr + ic);
+        fs = lam_face32(Mt, frule, hs, hc) * ((hc - hs) + (lc - ls));
+      }
+      for (int q = q0; q < q1; ++q) {
+        const int j = j0 + q;
+        float hn2 = 0.0f, ln2 = 0.0f, he2 = 0.0f, lE2 = 0.0f;  // next line, loaded ahead
+        if (q + 1 < q1) {
+          hn2 = ld_state<CACHED>(Hin + o + 2 * nr + ic);
+          ln2 = ld_state<CACHED>(Lin + o + 2 * nr + ic);
+          he2 = ld_state<CACHED>(Hin + o + nr + ie);
+          lE2 = ld_state<CACHED>(Lin + o + nr + ie);
+        }
+        o += nr;
+        const float dN = (hn - hc) + (ln - lc);       // T_{j+1} - T_j
+        const float dE = (he - hc) + (lE - lc);       // T_{i+1} - T_i
+        const float dW = -__shfl_up_sync(kFull, dE, 1);  // T_{i-1} - T_i
+        const float fn = lam_face32(Mt, frule, hc, hn) * dN;
+        const float le = (ic < N) ? lam_face32(Mt, frule, hc, he) : 0.0f;  // face (i, i+1)
+        const float lw = __shfl_up_sync(kFull, le, 1);                     // face (i-1, i)
+        const float rhoc = Mt.rho_f * cap32(Mt, hc);
+        const ZGeo& zg = I.zg[j];
+        float fa, fb, fc, fd, m = 0.0f;
+        if (cls == RC_REGULAR) {
+          const float Ljv = fmaf(zg.gzn_f, fn, -zg.gzs_f * fs);  // Eq. (Lambda_j)
+          float X = 0.0f;
+          if (seg == I.src_layer && s != 0.0f) {
+            X = I.q0_f * s;
+            if (I.g_model == 1) X *= I.g_ref_f * rsqrtf(hc);
+          }
+          const float A = -g.gA_f * lw, C = -g.gC_f * le;
+          fa = A;
+          fc = C;
+          fb = fmaf(rhoc, inv_tau, -A - C);
+          fd = fmaf(-A, dW, fmaf(-C, dE, Ljv + X));
+          if (ENERGY && own) {
+            const float V = g.V2_f * zg.etabar_f;
+            m = V * rhoc;
+            eQ += (double)(tau * V * X);
+            if (j == 1) {
+              const double f = (double)(-tau * g.V2_f * fs / (float)zg.eta_s);
+              if (I.bc_z0 == CC_DIRICHLET) eD += f; else eN += f;
+            }
+            if (j == M - 1) {
+              const double f = (double)(tau * g.V2_f * fn / (float)zg.eta_n);
+              if (I.bc_zmax == CC_DIRICHLET) eD += f; else eN += f;
+            }
+          }
+        } else if (cls == RC_IFACE) {
+          float lmv, lpv;
+          if (I.interface_rule == 0) {
+            lmv = sI[kMixIf * (q * n_if + g.ifo)];
+            lpv = sI[kMixIf * (q * n_if + g.ifo) + 1];
+          } else {
+            lmv = g.rw_f * lw;
+            lpv = g.re_f * le;
+          }
+          fa = -lmv * g.he_f;
+          fc = -lpv * g.hw_f;
+          fb = fmaf(lmv, g.he_f, lpv * g.hw_f);
+          fd = -fmaf(fa, dW, fc * dE);
+        } else if (cls == RC_AXIS) {  // dT_0 - dT_1 = T_1 - T_0
+          fa = 0.0f; fb = 1.0f; fc = -1.0f; fd = dE;
+        } else if (I.bc_rmax == CC_DIRICHLET) {
+          fa = 0.0f; fb = 1.0f; fc = 0.0f; fd = (I.td_hi - hc) + (I.td_lo - lc);
+        } else {  // dT_N - dT_{N-1} = T_{N-1} - T_N
+          fa = -1.0f; fb = 1.0f; fc = 0.0f; fd = dW;
+        }
+        if (ENERGY && own && edge) {
+          // heat-flow coefficients to the regular neighbours and the old
+          // temperature differences across those edges
+          float* K = sI + kMixIf * (q * n_if + g.ifo);
+          K[2] = gwk * zg.etabar_f * lw;
+          K[3] = gek * zg.etabar_f * le;
+          K[4] = -dW;
+          K[5] = -dE;
+        }
+        if (own && q == nl - 1) cout[smem_col(ic)] = fn;
+        if (own) {
+          const size_t w = (size_t)q * nrp + smem_col(ic);
+          FA[w] = fa;
+          FB[w] = fb;
+          FC[w] = fc;
+          FD[w] = fd;
+          if (ENERGY) FM[w] = m;
+        }
+        hc = hn; lc = ln;
+        hn = hn2; ln = ln2;
+        he = he2; lE = lE2;
+        fs = fn;
       }
     }
-#pragma unroll
-    for (int k = 0; k < kRowsPerLane; ++k)
-      if (k == cnt - 1) dp[k] = xs;
   }
-  const double xnext = __shfl_down_sync(kFull, dp[0], 1, G);
+  __syncthreads();
 
-  // ---- 4. pair update, boundary rows, energy, trace
-  double eE = 0.0, eI = 0.0, surf = 0.0;
-  bool bad = false;
-  if (active) {
-    const bool row0 = (j == 1), rowM = (j == M - 1);
+  // ---- 1.-3. FP64 line solves, lanes over the rows of a line
+  {
+    const int grp = lane >> lg, l = lane & (G - 1);
+    const int q_req = warp * lpw + grp;
+    const bool active = q_req < nl;
+    const int q = active ? q_req : nl - 1;
+    const int i_lo = (l * nr) >> lg;
+    const int i_hi = ((l + 1) * nr) >> lg;
+    const int cnt = i_hi - i_lo;
+    const size_t rq = (size_t)q * nrp;
+    double cp[kRowsPerLane], ap[kRowsPerLane], dp[kRowsPerLane];
+    double pc = 0.0, pa = 0.0, pd = 0.0;
+    double Dacc = 0.0, Aacc = 0.0, P = 1.0;
+    double ae = 0.0, be = 1.0, ce = 0.0, de = 0.0;
 #pragma unroll
     for (int k = 0; k < kRowsPerLane; ++k) {
       if (k < cnt) {
-        const int i = i_lo + k;
-        const double x = dp[k];
-        bad |= not_finite(x);
-        const float hi = __ldcg(Hj + (i)), lo = __ldcg(Lj_ + (i));
-        const float v = lo + __double2float_rn(x);
+        const size_t w = rq + smem_col(i_lo + k);
+        const double ra = FA[w], rb = FB[w], rc = FC[w], rd = FD[w];  // exact widening
+        if (k < cnt - 1) {
+          const double den = (k == 0) ? rb : fma(-ra, pc, rb);
+          const double r = frcp(den);
+          const double c1 = rc * r;
+          const double a1 = (k == 0) ? ra * r : -ra * pa * r;
+          const double d1 = (k == 0) ? rd * r : fma(-ra, pd, rd) * r;
+          cp[k] = c1;
+          ap[k] = a1;
+          dp[k] = d1;
+          Dacc = fma(P, d1, Dacc);
+          Aacc = fma(P, a1, Aacc);
+          P = -P * c1;
+          pc = c1;
+          pa = a1;
+          pd = d1;
+        } else {
+          ae = ra; be = rb; ce = rc; de = rd;
+        }
+      }
+    }
+    const double xs = solve_separators(ae, be, ce, de, pa, pc, pd, Dacc, Aacc, P, G, l);
+    const double L = __shfl_up_sync(kFull, xs, 1, G);
+    if (active) {
+      double xn = xs;
+      {
+        const size_t w = rq + smem_col(i_hi - 1);
+        if (ENERGY) eE = fma((double)FM[w], xs, eE);
+        FB[w] = __double2float_rn(xs);
+      }
+#pragma unroll
+      for (int k = kRowsPerLane - 2; k >= 0; --k) {
+        if (k <= cnt - 2) {
+          const size_t w = rq + smem_col(i_lo + k);
+          const double x = fma(-cp[k], xn, fma(-ap[k], L, dp[k]));
+          if (ENERGY) eE = fma((double)FM[w], x, eE);
+          FB[w] = __double2float_rn(x);
+          xn = x;
+        }
+      }
+    }
+  }
+  __syncthreads();
+
+  // ---- 4. pair update, boundary rows, trace, interface energy; lanes over columns
+  {
+    bool bad = false;
+    for (int q = 0; q < nl; ++q) {
+      const int j = j0 + q;
+      const float* Bq = FB + (size_t)q * nrp;
+      const long long rj = (long long)j * nr;
+      for (int i = threadIdx.x; i < nr; i += blockDim.x) {
+        const float x = Bq[smem_col(i)];
+        bad |= !isfinite(x);
+        const float hi = ld_state<CACHED>(Hin + rj + i), lo = ld_state<CACHED>(Lin + rj + i);
+        const float v = lo + x;
         const float h1 = hi + v;
         const float l1 = v - (h1 - hi);  // exact: h1 + l1 = hi + v
         Hout[rj + i] = h1;
         Lout[rj + i] = l1;
-        if (row0) {
+        if (j == 1) {
           Hout[i] = (I.bc_z0 == CC_DIRICHLET) ? I.td_hi : h1;
           Lout[i] = (I.bc_z0 == CC_DIRICHLET) ? I.td_lo : l1;
         }
-        if (rowM) {
+        if (j == M - 1) {
           Hout[(long long)M * nr + i] = (I.bc_zmax == CC_DIRICHLET) ? I.td_hi : h1;
           Lout[(long long)M * nr + i] = (I.bc_zmax == CC_DIRICHLET) ? I.td_lo : l1;
         }
-        if (TRACE && i == N) surf = ((double)hi + (double)lo) + x;
-        if (ENERGY) {
-          eE = fma((double)mm[k], x, eE);
-          const int cls = I.rg[i].cls;
-          if (cls == RC_IFACE || cls == RC_OUTER) {
-            // heat through the edges between this node and its regular
-            // neighbours, at the new temperatures: k (dT_old + d(dT))
-            const double xw = (k == 0) ? L : dp[k > 0 ? k - 1 : 0];
-            const float hw = __ldcg(Hj + (i - 1)), lw_ = __ldcg(Lj_ + (i - 1));
-            const float dT = (hi - hw) + (lo - lw_);
-            const RowGeo& gw = I.rg[i - 1];
-            const float kw = tau * gw.V2_f * zg.etabar_f * gw.gC_f *
-                             lam_face32(I.mat[gw.seg], frule, hw, hi);
-            const double fw = (double)kw * ((double)dT + (x - xw));
-            if (cls == RC_OUTER) {
-              if (I.bc_rmax == CC_DIRICHLET) eD += fw; else eN += fw;
-            } else {
-              const double xe = (k == cnt - 1) ? xnext : dp[k < kRowsPerLane - 1 ? k + 1 : k];
-              const float he = __ldcg(Hj + (i + 1)), le_ = __ldcg(Lj_ + (i + 1));
-              const float dTe = (hi - he) + (lo - le_);
-              const RowGeo& ge = I.rg[i + 1];
-              const float ke = tau * ge.V2_f * zg.etabar_f * ge.gA_f *
-                               lam_face32(I.mat[ge.seg], frule, hi, he);
-              eI += fw + (double)ke * ((double)dTe + (x - xe));
-            }
+        if (TRACE && i == N) {  // That(r_max, z_j)
+          const double surf = ((double)hi + (double)lo) + (double)x;
+          tr = fma(I.zg[j].wnorm, surf, tr);
+          if (j == 1) {
+            const double x0 = (I.bc_z0 == CC_DIRICHLET) ? I.t_d : surf;
+            tr = fma(I.zg[0].wnorm, x0, tr);
+            a.trace[((long long)tk.inst * a.n_steps + a.step) * 2] = x0;
+          }
+          if (j == M - 1) {
+            const double xM = (I.bc_zmax == CC_DIRICHLET) ? I.t_d : surf;
+            tr = fma(I.zg[M].wnorm, xM, tr);
           }
         }
       }
     }
+    if (bad) atomicOr(a.err, 1u);
+    if (ENERGY) {
+      // heat through the edges between each interface (or r_max) node and its
+      // regular neighbours, at the new temperatures: k (dT_old + d(dT))
+      for (int it = threadIdx.x; it < nl * n_if; it += blockDim.x) {
+        const int q = it / n_if;
+        const int i = I.if_i[it - q * n_if];
+        const float* Bq = FB + (size_t)q * nrp;
+        const float* K = sI + kMixIf * it;
+        const double x = Bq[smem_col(i)];
+        const double fw = (double)K[2] * ((double)K[4] + (x - (double)Bq[smem_col(i - 1)]));
+        if (I.rg[i].cls == RC_OUTER) {
+          if (I.bc_rmax == CC_DIRICHLET) eD += fw; else eN += fw;
+        } else {
+          eI += fw + (double)K[3] * ((double)K[5] + (x - (double)Bq[smem_col(i + 1)]));
+        }
+      }
+      acc.e[0] += eE;
+      acc.e[1] += eQ;
+      acc.e[2] += eD;
+      acc.e[3] += eI;
+      acc.e[4] += eN;
+    }
+    if (TRACE) acc.tr += tr;
   }
-  if (bad) atomicOr(a.err, 1u);
+  __syncthreads();  // the next tile reuses the shared memory
+}
 
-  if (ENERGY || TRACE) {
-    double tr = 0.0;
-    if (TRACE && active && l == G - 1) {
-      tr = zg.wnorm * surf;
-      double* trs = a.trace + ((long long)tk.inst * a.n_steps + a.step) * 2;
-      if (j == 1) {
-        const double x0 = (I.bc_z0 == CC_DIRICHLET) ? I.t_d : surf;
-        tr = fma(I.zg[0].wnorm, x0, tr);
-        trs[0] = x0;
-      }
-      if (j == M - 1) {
-        const double xM = (I.bc_zmax == CC_DIRICHLET) ? I.t_d : surf;
-        tr = fma(I.zg[M].wnorm, xM, tr);
-      }
-    }
-    if (!active) { eE = eQ = eD = eI = eN = 0.0; }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-      if (ENERGY) {
-        eE += __shfl_xor_sync(kFull, eE, o);
-        eQ += __shfl_xor_sync(kFull, eQ, o);
-        eD += __shfl_xor_sync(kFull, eD, o);
-        eI += __shfl_xor_sync(kFull, eI, o);
-        eN += __shfl_xor_sync(kFull, eN, o);
-      }
-      if (TRACE) tr += __shfl_xor_sync(kFull, tr, o);
-    }
-    if (lane == 0) {
-      if (ENERGY) {
-        double* e = a.energy + (long long)tk.inst * 5;
-        atomicAdd(e + 0, eE);
-        atomicAdd(e + 1, eQ);
-        atomicAdd(e + 2, eD);
-        atomicAdd(e + 3, eI);
-        atomicAdd(e + 4, eN);
-      }
-      if (TRACE) atomicAdd(a.trace + ((long long)tk.inst * a.n_steps + a.step) * 2 + 1, tr);
-    }
+// The tiles of this block: its range, or a stride over all tiles.
+template <bool ENERGY, bool TRACE, bool CACHED>
+__device__ __forceinline__ void mixed_tiles(const StepArgs& a, float* __restrict__ sm, EAcc& acc) {
+  int t0 = blockIdx.x, t1 = a.n_tiles, dt = gridDim.x;
+  if (a.cta_start) {
+    t0 = a.cta_start[blockIdx.x];
+    t1 = a.cta_start[blockIdx.x + 1];
+    dt = 1;
+  }
+  int prev_inst = -1, prev_end = -1, par = 0;
+  for (int t = t0; t < t1; t += dt) {
+    const TileTask tk = a.tiles[t];
+    const bool carry = (tk.inst == prev_inst && tk.j0 == prev_end);
+    step_mixed_tile<ENERGY, TRACE, CACHED>(a, tk, sm, acc, carry, par);
+    prev_inst = tk.inst;
+    prev_end = tk.j0 + tk.nl;
+    par ^= 1;
   }
 }
 
+// Launch bounds of the mixed-precision step kernels.
+#ifndef CC_MIX_MAX_THREADS
+#define CC_MIX_MAX_THREADS 256
+#endif
+#ifndef CC_MIX_MIN_BLOCKS
+#define CC_MIX_MIN_BLOCKS 1
+#endif
+
 template <class K>
-static int resident_blocks_m(K kernel, int threads) {
+static int resident_blocks_m(K kernel, int threads, int smem) {
   int dev = 0, sms = 0, per_sm = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, threads, 0);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, threads, smem);
   return sms * (per_sm > 0 ? per_sm : 1);
 }
 

@@ -7,20 +7,44 @@
 namespace ccell {
 
 template <bool ENERGY, bool TRACE>
-__global__ void __launch_bounds__(256) step_mixed_kernel(const StepArgs a) {
-  const int lane = threadIdx.x & 31;
-  const int n_warps = (int)((gridDim.x * blockDim.x) >> 5);
-  for (int w = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5); w < a.n_tasks; w += n_warps)
-    step_mixed_task<ENERGY, TRACE>(a, a.tasks[w], lane);
+__global__ void __launch_bounds__(CC_MIX_MAX_THREADS, CC_MIX_MIN_BLOCKS) step_mixed_kernel(const StepArgs a) {
+  extern __shared__ float smf[];
+  EAcc acc;
+  eacc_init(acc);
+  mixed_tiles<ENERGY, TRACE, true>(a, smf, acc);
+  eacc_flush<ENERGY, TRACE>(a, acc);
+}
+
+template <bool ENERGY, bool TRACE>
+static int mixed_variant_resident(int threads, int smem) {
+  static bool opted = false;
+  if (!opted) {
+    if (cudaFuncSetAttribute(step_mixed_kernel<ENERGY, TRACE>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxTileSmem) !=
+        cudaSuccess)
+      cudaGetLastError();  // the launch then reports a tile that does not fit
+    opted = true;
+  }
+  return resident_blocks_m(step_mixed_kernel<ENERGY, TRACE>, threads, smem);
+}
+
+int mixed_resident_blocks(int threads, int smem) {
+  int r = mixed_variant_resident<true, true>(threads, smem);
+  r = min(r, mixed_variant_resident<true, false>(threads, smem));
+  r = min(r, mixed_variant_resident<false, true>(threads, smem));
+  return min(r, mixed_variant_resident<false, false>(threads, smem));
 }
 
 template <bool ENERGY, bool TRACE>
 static void launch_mixed_variant(const StepArgs& a, cudaStream_t st) {
-  static int resident[3] = {0, 0, 0};
+  static int resident[3] = {0, 0, 0}, resident_smem[3] = {-1, -1, -1};
   const int t = a.threads > 0 ? a.threads : 128, si = shape_index_m(t);
-  if (resident[si] == 0) resident[si] = resident_blocks_m(step_mixed_kernel<ENERGY, TRACE>, t);
-  const int need = (a.n_tasks * 32 + t - 1) / t;
-  step_mixed_kernel<ENERGY, TRACE><<<need < resident[si] ? need : resident[si], t, 0, st>>>(a);
+  if (resident_smem[si] != a.smem_bytes) {
+    resident[si] = mixed_variant_resident<ENERGY, TRACE>(t, a.smem_bytes);
+    resident_smem[si] = a.smem_bytes;
+  }
+  const int blocks = a.cta_start ? a.n_cta : (a.n_tiles < resident[si] ? a.n_tiles : resident[si]);
+  step_mixed_kernel<ENERGY, TRACE><<<blocks, t, a.smem_bytes, st>>>(a);
 }
 
 int launch_step_mixed(const StepArgs& a, void* stream) {

@@ -6,10 +6,9 @@
 namespace ccell {
 
 template <bool ENERGY, bool TRACE>
-__global__ void __launch_bounds__(256) steps_mixed_persistent_kernel(const StepArgs a,
+__global__ void __launch_bounds__(CC_MIX_MAX_THREADS, CC_MIX_MIN_BLOCKS) steps_mixed_persistent_kernel(const StepArgs a,
                                                                       long long n) {
-  const int lane = threadIdx.x & 31;
-  const int n_warps = (int)((gridDim.x * blockDim.x) >> 5);
+  extern __shared__ float smf[];
   StepArgs s = a;
   for (long long q = 0; q < n; ++q) {
     s.step = a.step + q;
@@ -17,23 +16,36 @@ __global__ void __launch_bounds__(256) steps_mixed_persistent_kernel(const StepA
     s.Tout = (q & 1) ? const_cast<void*>(a.Tin) : a.Tout;
     s.lo_in = (q & 1) ? a.lo_out : a.lo_in;
     s.lo_out = (q & 1) ? const_cast<float*>(a.lo_in) : a.lo_out;
-    for (int w = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5); w < a.n_tasks; w += n_warps)
-      step_mixed_task<ENERGY, TRACE>(s, a.tasks[w], lane);
+    EAcc acc;
+    eacc_init(acc);
+    mixed_tiles<ENERGY, TRACE, false>(s, smf, acc);
+    eacc_flush<ENERGY, TRACE>(s, acc);
     if (!grid_barrier(a.bar, a.bar_extra, a.spin_limit, a.err)) return;
   }
 }
 
 template <bool ENERGY, bool TRACE>
 static int launch_mixed_persistent_variant(const StepArgs& a, long long n, cudaStream_t st) {
-  static int resident[3] = {0, 0, 0};
-  const int t = a.threads > 0 ? a.threads : 128, si = shape_index_m(t);
+  static int resident[3] = {0, 0, 0}, resident_smem[3] = {-1, -1, -1};
+  static bool opted = false;
   auto kern = steps_mixed_persistent_kernel<ENERGY, TRACE>;
-  if (resident[si] == 0) resident[si] = resident_blocks_m(kern, t);
-  const int need = (a.n_tasks * 32 + t - 1) / t;
-  const int blocks = need < resident[si] ? need : resident[si];
+  if (!opted) {
+    if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxTileSmem) !=
+        cudaSuccess)
+      cudaGetLastError();  // the launch then reports a tile that does not fit
+    opted = true;
+  }
+  const int t = a.threads > 0 ? a.threads : 128, si = shape_index_m(t);
+  if (resident_smem[si] != a.smem_bytes) {
+    resident[si] = resident_blocks_m(kern, t, a.smem_bytes);
+    resident_smem[si] = a.smem_bytes;
+  }
+  if (a.cta_start && resident[si] < a.n_cta) return -3;
+  const int blocks = a.cta_start ? a.n_cta : (a.n_tiles < resident[si] ? a.n_tiles : resident[si]);
   StepArgs copy = a;
   void* args[] = {&copy, &n};
-  const cudaError_t e = cudaLaunchCooperativeKernel((const void*)kern, blocks, t, args, 0, st);
+  const cudaError_t e =
+      cudaLaunchCooperativeKernel((const void*)kern, blocks, t, args, a.smem_bytes, st);
   if (e == cudaErrorCooperativeLaunchTooLarge) {
     cudaGetLastError();
     return -3;
