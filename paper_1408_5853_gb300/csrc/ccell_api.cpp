@@ -62,7 +62,7 @@ struct cc_ctx {
   size_t adj_cap = 0;
   // launch shape: 0 one launch per step, 1 one persistent cooperative launch;
   // threads per block; target rows per lane (sets the lanes per line G)
-  int mode = 0, threads = 128, rows = kRowsPerLane;
+  int mode = 0, threads = 256, rows = kRowsPerLane;
   bool tasks_dirty = true;
   size_t tasks_cap = 0;
   void* d_tune = nullptr;  // autotuner copy of the caller's field

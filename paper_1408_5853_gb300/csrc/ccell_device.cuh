@@ -20,6 +20,21 @@ __device__ __forceinline__ double frcp(double d) {
   return fma(fma(e, e, e), r, r);
 }
 
+// 1/d to about 46 bits (one quadratic Newton step), for line systems whose
+// coefficients carry FP32 accuracy only (the mixed-precision step).
+__device__ __forceinline__ double frcp46(double d) {
+  double r;
+  asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(r) : "d"(d));
+  return fma(r, fma(-d, r, 1.0), r);
+}
+
+// Reciprocal of a line solve: full FP64 (FULL) or frcp46.
+template <bool FULL>
+__device__ __forceinline__ double lrcp(double d) {
+  if constexpr (FULL) return frcp(d);
+  else return frcp46(d);
+}
+
 // Power law lam0 (x / t_ref)^b from the material's table: y = m 2^e with
 // m in [1, 2); the scale row e holds lam0 (k t_ref)^-b 2^(e b) (k = 2 for a
 // face, where y = T_a + T_b, k = 1 for a node, where y = T), and m^b is a
@@ -82,6 +97,7 @@ __device__ __forceinline__ bool not_finite(double x) {
 // Substituting the neighbours' rows gives a tridiagonal system in the G
 // separators, solved by parallel cyclic reduction over warp shuffles.
 // Returns x at this lane's separator.
+template <bool FULL = true>
 __device__ __forceinline__ double solve_separators(double ae, double be, double ce, double de,
                                                    double pa, double pc, double pd, double Dacc,
                                                    double Aacc, double P, int G, int l) {
@@ -93,7 +109,7 @@ __device__ __forceinline__ double solve_separators(double ae, double be, double 
   double ct = -ce * C2n;
   double dt = fma(-ae, pd, de) - ce * D2n;
   for (int d = 1; d < G; d <<= 1) {
-    const double ib = frcp(bt);
+    const double ib = lrcp<FULL>(bt);
     const double am = __shfl_up_sync(kFull, at, d, G);
     const double cm = __shfl_up_sync(kFull, ct, d, G);
     const double dm = __shfl_up_sync(kFull, dt, d, G);
@@ -111,7 +127,7 @@ __device__ __forceinline__ double solve_separators(double ae, double be, double 
     bt = nb;
     dt = nd;
   }
-  return dt * frcp(bt);
+  return dt * lrcp<FULL>(bt);
 }
 
 // Energy and trace partial sums of one thread, carried over the tiles of a
@@ -154,6 +170,83 @@ __device__ __forceinline__ void eacc_flush(const StepArgs& a, EAcc& c) {
 #pragma unroll
   for (int k = 0; k < 5; ++k) c.e[k] = 0.0;
   c.tr = 0.0;
+}
+
+// Phases 1-3 of a CTA tile: the tridiagonal systems of its nl lines, rows
+// (a, b, c | d) in SA .. SD (line q in the padded row q of nrp doubles), solved
+// in place.  Each line is split over G lanes (lane l holds rows
+// [l nr/G, (l+1) nr/G)); every lane eliminates its segment downwards (the
+// forward sweep of Eq. (front_sweep) restricted to the segment, keeping the
+// coupling to the previous segment's last row; c', a', d' overwrite c, a, d),
+// the G separator rows are solved by cyclic reduction with shuffles, and back
+// substitution (Eq. (back_sweep)) leaves the solution of every row in SB.
+// FULL: reciprocals to FP64 accuracy; otherwise to 46 bits (rows of FP32
+// accuracy).
+// For G = 1 this is the Thomas algorithm of the paper with alpha_0 = 1,
+// beta_0 = 0 and x_N = beta_{N-1} / (1 - alpha_{N-1}).
+template <bool FULL>
+__device__ __forceinline__ void solve_tile_lines(double* __restrict__ SA, double* __restrict__ SB,
+                                                 double* __restrict__ SC, double* __restrict__ SD,
+                                                 int nl, int nr, int G) {
+  const int nrp = smem_row_stride(nr);
+  const int lg = __ffs(G) - 1;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int grp = lane >> lg, l = lane & (G - 1);
+  const int q_req = warp * (32 >> lg) + grp;
+  const bool active = q_req < nl;
+  const int q = active ? q_req : nl - 1;  // idle lane groups solve a valid line, store nothing
+  const int i_lo = (l * nr) >> lg;
+  const int i_hi = ((l + 1) * nr) >> lg;
+  const int cnt = i_hi - i_lo;  // 2 .. kRowsPerLane
+  double* A = SA + (size_t)q * nrp;
+  double* B = SB + (size_t)q * nrp;
+  double* C = SC + (size_t)q * nrp;
+  double* D = SD + (size_t)q * nrp;
+  double pc = 0.0, pa = 0.0, pd = 0.0;    // c', a', d' of the previous interior row
+  double Dacc = 0.0, Aacc = 0.0, P = 1.0; // first interior row = Dacc + P x_next - Aacc L
+  double ae = 0.0, be = 1.0, ce = 0.0, de = 0.0;  // separator row
+#pragma unroll
+  for (int k = 0; k < kRowsPerLane; ++k) {
+    if (k < cnt) {
+      const int c = smem_col(i_lo + k);
+      const double ra = A[c], rb = B[c], rc = C[c], rd = D[c];
+      if (k < cnt - 1) {
+        const double den = (k == 0) ? rb : fma(-ra, pc, rb);
+        const double r = lrcp<FULL>(den);
+        const double c1 = rc * r;
+        const double a1 = (k == 0) ? ra * r : -ra * pa * r;
+        const double d1 = (k == 0) ? rd * r : fma(-ra, pd, rd) * r;
+        if (active) {
+          C[c] = c1;
+          A[c] = a1;
+          D[c] = d1;
+        }
+        Dacc = fma(P, d1, Dacc);
+        Aacc = fma(P, a1, Aacc);
+        P = -P * c1;
+        pc = c1;
+        pa = a1;
+        pd = d1;
+      } else {
+        ae = ra; be = rb; ce = rc; de = rd;
+      }
+    }
+  }
+  const double xs = solve_separators<FULL>(ae, be, ce, de, pa, pc, pd, Dacc, Aacc, P, G, l);
+  const double L = __shfl_up_sync(kFull, xs, 1, G);
+  if (active) {
+    double xn = xs;
+    B[smem_col(i_hi - 1)] = xs;
+#pragma unroll
+    for (int k = kRowsPerLane - 2; k >= 0; --k) {
+      if (k <= cnt - 2) {
+        const int c = smem_col(i_lo + k);
+        const double x = fma(-C[c], xn, fma(-A[c], L, D[c]));
+        B[c] = x;
+        xn = x;
+      }
+    }
+  }
 }
 
 // Grid-wide barrier of a cooperative (co-resident) launch with a bounded wait.

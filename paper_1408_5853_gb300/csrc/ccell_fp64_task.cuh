@@ -71,8 +71,6 @@ __device__ __forceinline__ void step_fp64_tile(const StepArgs& a, const TileTask
   const DevInst& I = a.insts[tk.inst];
   const int nr = I.nr, N = nr - 1, M = I.nz - 1;
   const int G = I.G;
-  const int lg = __ffs(G) - 1;
-  const int lpw = 32 >> lg;
   const int j0 = tk.j0, nl = tk.nl;
   const int nrp = smem_row_stride(nr);
   const int frule = I.face_rule;
@@ -231,64 +229,7 @@ __device__ __forceinline__ void step_fp64_tile(const StepArgs& a, const TileTask
   __syncthreads();
 
   // ---- 1.-3. line solves, lanes over the rows of a line
-  {
-    const int grp = lane >> lg, l = lane & (G - 1);
-    const int q_req = warp * lpw + grp;
-    const bool active = q_req < nl;
-    const int q = active ? q_req : nl - 1;  // idle lane groups solve a valid line, store nothing
-    const int i_lo = (l * nr) >> lg;
-    const int i_hi = ((l + 1) * nr) >> lg;
-    const int cnt = i_hi - i_lo;  // 2 .. kRowsPerLane
-    double* A = SA + (size_t)q * nrp;
-    double* B = SB + (size_t)q * nrp;
-    double* C = SC + (size_t)q * nrp;
-    double* D = SD + (size_t)q * nrp;
-    double pc = 0.0, pa = 0.0, pd = 0.0;    // c', a', d' of the previous interior row
-    double Dacc = 0.0, Aacc = 0.0, P = 1.0; // first interior row = Dacc + P x_next - Aacc L
-    double ae = 0.0, be = 1.0, ce = 0.0, de = 0.0;  // separator row
-#pragma unroll
-    for (int k = 0; k < kRowsPerLane; ++k) {
-      if (k < cnt) {
-        const int c = smem_col(i_lo + k);
-        const double ra = A[c], rb = B[c], rc = C[c], rd = D[c];
-        if (k < cnt - 1) {
-          const double den = (k == 0) ? rb : fma(-ra, pc, rb);
-          const double r = frcp(den);
-          const double c1 = rc * r;
-          const double a1 = (k == 0) ? ra * r : -ra * pa * r;
-          const double d1 = (k == 0) ? rd * r : fma(-ra, pd, rd) * r;
-          if (active) {
-            C[c] = c1;
-            A[c] = a1;
-            D[c] = d1;
-          }
-          Dacc = fma(P, d1, Dacc);
-          Aacc = fma(P, a1, Aacc);
-          P = -P * c1;
-          pc = c1;
-          pa = a1;
-          pd = d1;
-        } else {
-          ae = ra; be = rb; ce = rc; de = rd;
-        }
-      }
-    }
-    const double xs = solve_separators(ae, be, ce, de, pa, pc, pd, Dacc, Aacc, P, G, l);
-    const double L = __shfl_up_sync(kFull, xs, 1, G);
-    if (active) {
-      double xn = xs;
-      B[smem_col(i_hi - 1)] = xs;
-#pragma unroll
-      for (int k = kRowsPerLane - 2; k >= 0; --k) {
-        if (k <= cnt - 2) {
-          const int c = smem_col(i_lo + k);
-          const double x = fma(-C[c], xn, fma(-A[c], L, D[c]));
-          B[c] = x;
-          xn = x;
-        }
-      }
-    }
-  }
+  solve_tile_lines<true>(SA, SB, SC, SD, nl, nr, G);
   __syncthreads();
 
   // ---- 4. stores, boundary rows, trace and energy, lanes over columns

@@ -126,11 +126,14 @@ CC_HOST_DEVICE inline int smem_col(int i) { return i + (i >> 4); }
 CC_HOST_DEVICE inline int fp64_tile_smem_bytes(int nl, int nr) {
   return ((5 * nl + 2) * smem_row_stride(nr) + 4 * CC_MAX_LAYERS * nl) * (int)sizeof(double);
 }
-// Shared memory of one mixed-precision CTA tile: the same rows in FP32 and
-// kMixIf floats per line and interface node.
+// Shared memory of one mixed-precision CTA tile: two rows of axial face
+// fluxes handed from tile to tile (FP32), the four rows of every line's
+// system (FP64), then in FP32 the heat capacities and kMixIf floats per line
+// and interface node.
 constexpr int kMixIf = 8;
 CC_HOST_DEVICE inline int mixed_tile_smem_bytes(int nl, int nr) {
-  return ((5 * nl + 2) * smem_row_stride(nr) + kMixIf * CC_MAX_LAYERS * nl) * (int)sizeof(float);
+  return 4 * nl * smem_row_stride(nr) * (int)sizeof(double) +
+         ((nl + 2) * smem_row_stride(nr) + kMixIf * CC_MAX_LAYERS * nl) * (int)sizeof(float);
 }
 // Largest dynamic shared memory of an FP64 tile: the opt-in limit per block
 // on sm_103 (227 KiB) less room for the kernels' static shared memory.

@@ -67,8 +67,6 @@ __device__ __forceinline__ void step_mixed_tile(const StepArgs& a, const TileTas
   const DevInst& I = a.insts[tk.inst];
   const int nr = I.nr, N = nr - 1, M = I.nz - 1;
   const int G = I.G;
-  const int lg = __ffs(G) - 1;
-  const int lpw = 32 >> lg;
   const int j0 = tk.j0, nl = tk.nl;
   const int nrp = smem_row_stride(nr);
   const int frule = I.face_rule;
@@ -76,12 +74,12 @@ __device__ __forceinline__ void step_mixed_tile(const StepArgs& a, const TileTas
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarps = blockDim.x >> 5;
   const float* cin = sm + (size_t)(par ^ 1) * nrp;  // axial fluxes south of line j0
   float* cout = sm + (size_t)par * nrp;             // axial fluxes north of line j0+nl-1
-  float* FA = sm + 2 * (size_t)nrp;        // rows (FP32, delta form)
-  float* FB = FA + (size_t)nl * nrp;       // b, then the new increment dT (FP32)
-  float* FC = FB + (size_t)nl * nrp;
-  float* FD = FC + (size_t)nl * nrp;
-  float* FM = FD + (size_t)nl * nrp;       // V rho c (energy)
-  float* sI = FM + (size_t)nl * nrp;       // per line and interface node: lam_w, lam_e, kw, ke, dTw, dTe
+  double* SA = reinterpret_cast<double*>(sm + 2 * (size_t)nrp);  // rows (delta form, FP32 values widened)
+  double* SB = SA + (size_t)nl * nrp;          // b, then the increment dT
+  double* SC = SB + (size_t)nl * nrp;
+  double* SD = SC + (size_t)nl * nrp;
+  float* FM = reinterpret_cast<float*>(SD + (size_t)nl * nrp);  // V rho c (energy)
+  float* sI = FM + (size_t)nl * nrp;  // per line and interface node: lam_w, lam_e, kw, ke, dTw, dTe
   const float* Hin = static_cast<const float*>(a.Tin) + I.t_off;
   const float* Lin = a.lo_in + I.t_off;
   float* Hout = static_cast<float*>(a.Tout) + I.t_off;
@@ -217,10 +215,10 @@ __device__ __forceinline__ void step_mixed_tile(const StepArgs& a, const TileTas
         if (own && q == nl - 1) cout[smem_col(ic)] = fn;
         if (own) {
           const size_t w = (size_t)q * nrp + smem_col(ic);
-          FA[w] = fa;
-          FB[w] = fb;
-          FC[w] = fc;
-          FD[w] = fd;
+          SA[w] = fa;  // exact widening
+          SB[w] = fb;
+          SC[w] = fc;
+          SD[w] = fd;
           if (ENERGY) FM[w] = m;
         }
         hc = hn; lc = ln;
@@ -233,65 +231,7 @@ __device__ __forceinline__ void step_mixed_tile(const StepArgs& a, const TileTas
   __syncthreads();
 
   // ---- 1.-3. FP64 line solves, lanes over the rows of a line
-  {
-    const int grp = lane >> lg, l = lane & (G - 1);
-    const int q_req = warp * lpw + grp;
-    const bool active = q_req < nl;
-    const int q = active ? q_req : nl - 1;
-    const int i_lo = (l * nr) >> lg;
-    const int i_hi = ((l + 1) * nr) >> lg;
-    const int cnt = i_hi - i_lo;
-    const size_t rq = (size_t)q * nrp;
-    double cp[kRowsPerLane], ap[kRowsPerLane], dp[kRowsPerLane];
-    double pc = 0.0, pa = 0.0, pd = 0.0;
-    double Dacc = 0.0, Aacc = 0.0, P = 1.0;
-    double ae = 0.0, be = 1.0, ce = 0.0, de = 0.0;
-#pragma unroll
-    for (int k = 0; k < kRowsPerLane; ++k) {
-      if (k < cnt) {
-        const size_t w = rq + smem_col(i_lo + k);
-        const double ra = FA[w], rb = FB[w], rc = FC[w], rd = FD[w];  // exact widening
-        if (k < cnt - 1) {
-          const double den = (k == 0) ? rb : fma(-ra, pc, rb);
-          const double r = frcp(den);
-          const double c1 = rc * r;
-          const double a1 = (k == 0) ? ra * r : -ra * pa * r;
-          const double d1 = (k == 0) ? rd * r : fma(-ra, pd, rd) * r;
-          cp[k] = c1;
-          ap[k] = a1;
-          dp[k] = d1;
-          Dacc = fma(P, d1, Dacc);
-          Aacc = fma(P, a1, Aacc);
-          P = -P * c1;
-          pc = c1;
-          pa = a1;
-          pd = d1;
-        } else {
-          ae = ra; be = rb; ce = rc; de = rd;
-        }
-      }
-    }
-    const double xs = solve_separators(ae, be, ce, de, pa, pc, pd, Dacc, Aacc, P, G, l);
-    const double L = __shfl_up_sync(kFull, xs, 1, G);
-    if (active) {
-      double xn = xs;
-      {
-        const size_t w = rq + smem_col(i_hi - 1);
-        if (ENERGY) eE = fma((double)FM[w], xs, eE);
-        FB[w] = __double2float_rn(xs);
-      }
-#pragma unroll
-      for (int k = kRowsPerLane - 2; k >= 0; --k) {
-        if (k <= cnt - 2) {
-          const size_t w = rq + smem_col(i_lo + k);
-          const double x = fma(-cp[k], xn, fma(-ap[k], L, dp[k]));
-          if (ENERGY) eE = fma((double)FM[w], x, eE);
-          FB[w] = __double2float_rn(x);
-          xn = x;
-        }
-      }
-    }
-  }
+  solve_tile_lines<false>(SA, SB, SC, SD, nl, nr, G);
   __syncthreads();
 
   // ---- 4. pair update, boundary rows, trace, interface energy; lanes over columns
@@ -299,11 +239,15 @@ __device__ __forceinline__ void step_mixed_tile(const StepArgs& a, const TileTas
     bool bad = false;
     for (int q = 0; q < nl; ++q) {
       const int j = j0 + q;
-      const float* Bq = FB + (size_t)q * nrp;
+      const double* Bq = SB + (size_t)q * nrp;
+      const float* Mq = FM + (size_t)q * nrp;
       const long long rj = (long long)j * nr;
       for (int i = threadIdx.x; i < nr; i += blockDim.x) {
-        const float x = Bq[smem_col(i)];
-        bad |= !isfinite(x);
+        const int c = smem_col(i);
+        const double xd = Bq[c];
+        bad |= not_finite(xd);
+        if (ENERGY) eE = fma((double)Mq[c], xd, eE);
+        const float x = __double2float_rn(xd);
         const float hi = ld_state<CACHED>(Hin + rj + i), lo = ld_state<CACHED>(Lin + rj + i);
         const float v = lo + x;
         const float h1 = hi + v;
@@ -319,7 +263,7 @@ __device__ __forceinline__ void step_mixed_tile(const StepArgs& a, const TileTas
           Lout[(long long)M * nr + i] = (I.bc_zmax == CC_DIRICHLET) ? I.td_lo : l1;
         }
         if (TRACE && i == N) {  // That(r_max, z_j)
-          const double surf = ((double)hi + (double)lo) + (double)x;
+          const double surf = ((double)hi + (double)lo) + xd;
           tr = fma(I.zg[j].wnorm, surf, tr);
           if (j == 1) {
             const double x0 = (I.bc_z0 == CC_DIRICHLET) ? I.t_d : surf;
@@ -340,14 +284,14 @@ __device__ __forceinline__ void step_mixed_tile(const StepArgs& a, const TileTas
       for (int it = threadIdx.x; it < nl * n_if; it += blockDim.x) {
         const int q = it / n_if;
         const int i = I.if_i[it - q * n_if];
-        const float* Bq = FB + (size_t)q * nrp;
+        const double* Bq = SB + (size_t)q * nrp;
         const float* K = sI + kMixIf * it;
         const double x = Bq[smem_col(i)];
-        const double fw = (double)K[2] * ((double)K[4] + (x - (double)Bq[smem_col(i - 1)]));
+        const double fw = (double)K[2] * ((double)K[4] + (x - Bq[smem_col(i - 1)]));
         if (I.rg[i].cls == RC_OUTER) {
           if (I.bc_rmax == CC_DIRICHLET) eD += fw; else eN += fw;
         } else {
-          eI += fw + (double)K[3] * ((double)K[5] + (x - (double)Bq[smem_col(i + 1)]));
+          eI += fw + (double)K[3] * ((double)K[5] + (x - Bq[smem_col(i + 1)]));
         }
       }
       acc.e[0] += eE;
