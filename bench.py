@@ -121,10 +121,12 @@ def run_ours(args, world, rank, local):
 
     def make(precision):
         sol = ccell.Solver(cfg, precision=precision)
-        if args.launch:
-            sol.set_launch(*[int(v) for v in args.launch.split(",")])
         dt = torch.float64 if precision == ccell.FP64 else torch.float32
         T = torch.tensor(T0.ravel(), dtype=dt, device=dev)
+        if args.launch:
+            sol.set_launch(*[int(v) for v in args.launch.split(",")])
+        else:  # the library's autotuner picks the launch shape (field restored)
+            sol.autotune(T, n_trial=args.tune_steps)
         trace = torch.zeros(2 * n_in, dtype=torch.float64, device=dev)
         energy = torch.zeros(5, dtype=torch.float64, device=dev)
         return sol, T, trace, energy
@@ -207,6 +209,7 @@ def run_ours(args, world, rank, local):
         msm, _ = timed_steps(solm, Tm, trm, enm, args.steps, args.warmup)
         mixed = {"value": nodes * n_in * args.steps * world / (msm / 1e3),
                  "ms_per_step": msm / args.steps,
+                 "launch": dict(zip(("mode", "threads", "rows_per_lane"), solm.get_launch())),
                  "speedup_vs_fp64": (nodes * n_in * args.steps * world / (msm / 1e3)) / value,
                  "hbm_frac_effective": BYTES_PER_NODE_MIXED * nodes * n_in * args.steps * world
                  / (msm / 1e3) / (_peaks()["hbm_gbs"] * 1e9)}
@@ -492,7 +495,9 @@ def main():
     ap.add_argument("--acc-steps", type=int, default=20000,
                     help="steps of the mixed-vs-FP64 accuracy check (0: skip)")
     ap.add_argument("--launch", default="",
-                    help="mode,threads,rows_per_lane of the 512x4096 runs (default: the library's)")
+                    help="mode,threads,rows_per_lane of the 512x4096 runs (default: autotuned)")
+    ap.add_argument("--tune-steps", type=int, default=30,
+                    help="time steps per candidate launch shape of the autotuner")
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     args = ap.parse_args()
     args.parts = set(args.parts.split(","))

@@ -381,13 +381,13 @@ int upload(cc_ctx* c, const std::vector<double>& dts, cudaStream_t st) {
       return CC_ECUDA;
     c->n_tasks = (int)tasks.size();
     // FP64 CTA tiles: (threads / 32) warps x 32/G lines
-    // CTA tiles of the step kernels: lines of one instance, at most lpc of them.  The blocks
-    // of a launch (its resident capacity) take equal shares of all lines as
-    // ranges of consecutive tiles.
+    // CTA tiles of the step kernels: lines of one instance, at most lpc of
+    // them.  The blocks of a launch (its resident capacity) take equal shares
+    // of all nodes as ranges of consecutive tiles.
     std::vector<TileTask> tiles;
     std::vector<int> lpcs(n), cta;
     int smem = 0;
-    long long total_lines = 0;
+    long long total_nodes = 0;  // of the interior lines
     for (int k = 0; k < n; ++k) {
       const Instance& in = c->inst[k];
       int lpc = (c->threads / 32) * (32 / in.G);
@@ -399,7 +399,7 @@ int upload(cc_ctx* c, const std::vector<double>& dts, cudaStream_t st) {
       while (lpc > 1 && tile_smem(lpc) > kMaxTileSmem) lpc /= 2;
       lpcs[k] = lpc;
       smem = std::max(smem, tile_smem(std::min(lpc, in.d.nz - 2)));
-      total_lines += in.d.nz - 2;
+      total_nodes += (long long)in.d.nr * (in.d.nz - 2);
     }
     const int B = smem > kMaxTileSmem ? 0
                   : c->precision == CC_FP64 ? fp64_resident_blocks(c->threads, smem)
@@ -410,14 +410,15 @@ int upload(cc_ctx* c, const std::vector<double>& dts, cudaStream_t st) {
       long long g = 0;
       for (int b = 0; b < B; ++b) {
         cta[b] = (int)tiles.size();
-        const long long g_end = (long long)(b + 1) * total_lines / B;
-        while (g < g_end) {
+        const long long g_end = (long long)(b + 1) * total_nodes / B;
+        while (g < g_end && k < n) {
           const Instance& in = c->inst[k];
-          const int take = (int)std::min<long long>(g_end - g, in.d.nz - 1 - jn);
+          const int take = (int)std::min<long long>((g_end - g + in.d.nr - 1) / in.d.nr,
+                                                    in.d.nz - 1 - jn);
           for (int j = jn; j < jn + take; j += lpcs[k])
             tiles.push_back(TileTask{k, j, std::min(lpcs[k], jn + take - j), 0});
           jn += take;
-          g += take;
+          g += (long long)take * in.d.nr;
           if (jn > in.d.nz - 2) {
             ++k;
             jn = 1;

@@ -235,34 +235,43 @@ __device__ __forceinline__ void step_fp64_tile(const StepArgs& a, const TileTask
   // ---- 4. stores, boundary rows, trace and energy, lanes over columns
   {
     bool bad = false;
-    for (int q = 0; q < nl; ++q) {
+    // threads over the nl x nr nodes of the tile, line by line (all threads
+    // stay busy when nr is below the block size)
+    int q = threadIdx.x / nr, i = threadIdx.x - q * nr, qe = -1;
+    double eEq = 0.0;
+    for (; q < nl;) {
       const int j = j0 + q;
-      const double* Bq = SB + (size_t)q * nrp;
-      double* Oj = Tout + (long long)j * nr;
-      double eEq = 0.0;
-      for (int i = threadIdx.x; i < nr; i += blockDim.x) {
-        const int c = smem_col(i);
-        const double x = Bq[c];
-        bad |= not_finite(x);
-        Oj[i] = x;
-        if (j == 1) Tout[i] = (I.bc_z0 == CC_DIRICHLET) ? I.t_d : x;
-        if (j == M - 1) Tout[(long long)M * nr + i] = (I.bc_zmax == CC_DIRICHLET) ? I.t_d : x;
-        if (ENERGY) eEq = fma(SM[(size_t)q * nrp + c], x - ld_field<CACHED>(Tin + (long long)j * nr + i), eEq);
-        if (TRACE && i == N) {  // That(r_max, z_j)
-          tr = fma(I.zg[j].wnorm, x, tr);
-          if (j == 1) {
-            const double x0 = (I.bc_z0 == CC_DIRICHLET) ? I.t_d : x;
-            tr = fma(I.zg[0].wnorm, x0, tr);
-            a.trace[((long long)tk.inst * a.n_steps + a.step) * 2] = x0;
-          }
-          if (j == M - 1) {
-            const double xM = (I.bc_zmax == CC_DIRICHLET) ? I.t_d : x;
-            tr = fma(I.zg[M].wnorm, xM, tr);
-          }
+      if (ENERGY && q != qe) {  // per-line factor etabar tau of the capacities
+        if (qe >= 0) eE = fma(I.zg[j0 + qe].etabar * I.tau, eEq, eE);
+        eEq = 0.0;
+        qe = q;
+      }
+      const int c = smem_col(i);
+      const double x = SB[(size_t)q * nrp + c];
+      bad |= not_finite(x);
+      Tout[(long long)j * nr + i] = x;
+      if (j == 1) Tout[i] = (I.bc_z0 == CC_DIRICHLET) ? I.t_d : x;
+      if (j == M - 1) Tout[(long long)M * nr + i] = (I.bc_zmax == CC_DIRICHLET) ? I.t_d : x;
+      if (ENERGY) eEq = fma(SM[(size_t)q * nrp + c], x - ld_field<CACHED>(Tin + (long long)j * nr + i), eEq);
+      if (TRACE && i == N) {  // That(r_max, z_j)
+        tr = fma(I.zg[j].wnorm, x, tr);
+        if (j == 1) {
+          const double x0 = (I.bc_z0 == CC_DIRICHLET) ? I.t_d : x;
+          tr = fma(I.zg[0].wnorm, x0, tr);
+          a.trace[((long long)tk.inst * a.n_steps + a.step) * 2] = x0;
+        }
+        if (j == M - 1) {
+          const double xM = (I.bc_zmax == CC_DIRICHLET) ? I.t_d : x;
+          tr = fma(I.zg[M].wnorm, xM, tr);
         }
       }
-      if (ENERGY) eE = fma(I.zg[j].etabar * I.tau, eEq, eE);
+      i += blockDim.x;
+      while (i >= nr) {
+        i -= nr;
+        ++q;
+      }
     }
+    if (ENERGY && qe >= 0) eE = fma(I.zg[j0 + qe].etabar * I.tau, eEq, eE);
     if (bad) atomicOr(a.err, 1u);
     if (ENERGY) {
       // heat through the radial edges between each interface (or r_max) node

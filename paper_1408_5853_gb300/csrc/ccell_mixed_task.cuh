@@ -237,44 +237,47 @@ __device__ __forceinline__ void step_mixed_tile(const StepArgs& a, const TileTas
   // ---- 4. pair update, boundary rows, trace, interface energy; lanes over columns
   {
     bool bad = false;
-    for (int q = 0; q < nl; ++q) {
+    // threads over the nl x nr nodes of the tile, line by line
+    int q = threadIdx.x / nr, i = threadIdx.x - q * nr;
+    for (; q < nl;) {
       const int j = j0 + q;
-      const double* Bq = SB + (size_t)q * nrp;
-      const float* Mq = FM + (size_t)q * nrp;
       const long long rj = (long long)j * nr;
-      for (int i = threadIdx.x; i < nr; i += blockDim.x) {
-        const int c = smem_col(i);
-        const double xd = Bq[c];
-        bad |= not_finite(xd);
-        if (ENERGY) eE = fma((double)Mq[c], xd, eE);
-        const float x = __double2float_rn(xd);
-        const float hi = ld_state<CACHED>(Hin + rj + i), lo = ld_state<CACHED>(Lin + rj + i);
-        const float v = lo + x;
-        const float h1 = hi + v;
-        const float l1 = v - (h1 - hi);  // exact: h1 + l1 = hi + v
-        Hout[rj + i] = h1;
-        Lout[rj + i] = l1;
+      const int c = smem_col(i);
+      const double xd = SB[(size_t)q * nrp + c];
+      bad |= not_finite(xd);
+      if (ENERGY) eE = fma((double)FM[(size_t)q * nrp + c], xd, eE);
+      const float x = __double2float_rn(xd);
+      const float hi = ld_state<CACHED>(Hin + rj + i), lo = ld_state<CACHED>(Lin + rj + i);
+      const float v = lo + x;
+      const float h1 = hi + v;
+      const float l1 = v - (h1 - hi);  // exact: h1 + l1 = hi + v
+      Hout[rj + i] = h1;
+      Lout[rj + i] = l1;
+      if (j == 1) {
+        Hout[i] = (I.bc_z0 == CC_DIRICHLET) ? I.td_hi : h1;
+        Lout[i] = (I.bc_z0 == CC_DIRICHLET) ? I.td_lo : l1;
+      }
+      if (j == M - 1) {
+        Hout[(long long)M * nr + i] = (I.bc_zmax == CC_DIRICHLET) ? I.td_hi : h1;
+        Lout[(long long)M * nr + i] = (I.bc_zmax == CC_DIRICHLET) ? I.td_lo : l1;
+      }
+      if (TRACE && i == N) {  // That(r_max, z_j)
+        const double surf = ((double)hi + (double)lo) + xd;
+        tr = fma(I.zg[j].wnorm, surf, tr);
         if (j == 1) {
-          Hout[i] = (I.bc_z0 == CC_DIRICHLET) ? I.td_hi : h1;
-          Lout[i] = (I.bc_z0 == CC_DIRICHLET) ? I.td_lo : l1;
+          const double x0 = (I.bc_z0 == CC_DIRICHLET) ? I.t_d : surf;
+          tr = fma(I.zg[0].wnorm, x0, tr);
+          a.trace[((long long)tk.inst * a.n_steps + a.step) * 2] = x0;
         }
         if (j == M - 1) {
-          Hout[(long long)M * nr + i] = (I.bc_zmax == CC_DIRICHLET) ? I.td_hi : h1;
-          Lout[(long long)M * nr + i] = (I.bc_zmax == CC_DIRICHLET) ? I.td_lo : l1;
+          const double xM = (I.bc_zmax == CC_DIRICHLET) ? I.t_d : surf;
+          tr = fma(I.zg[M].wnorm, xM, tr);
         }
-        if (TRACE && i == N) {  // That(r_max, z_j)
-          const double surf = ((double)hi + (double)lo) + xd;
-          tr = fma(I.zg[j].wnorm, surf, tr);
-          if (j == 1) {
-            const double x0 = (I.bc_z0 == CC_DIRICHLET) ? I.t_d : surf;
-            tr = fma(I.zg[0].wnorm, x0, tr);
-            a.trace[((long long)tk.inst * a.n_steps + a.step) * 2] = x0;
-          }
-          if (j == M - 1) {
-            const double xM = (I.bc_zmax == CC_DIRICHLET) ? I.t_d : surf;
-            tr = fma(I.zg[M].wnorm, xM, tr);
-          }
-        }
+      }
+      i += blockDim.x;
+      while (i >= nr) {
+        i -= nr;
+        ++q;
       }
     }
     if (bad) atomicOr(a.err, 1u);
