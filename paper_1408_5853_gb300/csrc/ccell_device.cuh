@@ -180,8 +180,8 @@ __device__ __forceinline__ void eacc_flush(const StepArgs& a, EAcc& c) {
 // coupling to the previous segment's last row; c', a', d' overwrite c, a, d),
 // the G separator rows are solved by cyclic reduction with shuffles, and back
 // substitution (Eq. (back_sweep)) leaves the solution of every row in SB.
-// FULL: reciprocals to FP64 accuracy; otherwise to 46 bits (rows of FP32
-// accuracy).
+// FULL: reciprocals to FP64 accuracy; otherwise to 46 bits for rows of FP32
+// accuracy that are scaled to a unit diagonal (b is not read).
 // For G = 1 this is the Thomas algorithm of the paper with alpha_0 = 1,
 // beta_0 = 0 and x_N = beta_{N-1} / (1 - alpha_{N-1}).
 template <bool FULL>
@@ -209,7 +209,7 @@ __device__ __forceinline__ void solve_tile_lines(double* __restrict__ SA, double
   for (int k = 0; k < kRowsPerLane; ++k) {
     if (k < cnt) {
       const int c = smem_col(i_lo + k);
-      const double ra = A[c], rb = B[c], rc = C[c], rd = D[c];
+      const double ra = A[c], rb = FULL ? B[c] : 1.0, rc = C[c], rd = D[c];
       if (k < cnt - 1) {
         const double den = (k == 0) ? rb : fma(-ra, pc, rb);
         const double r = lrcp<FULL>(den);

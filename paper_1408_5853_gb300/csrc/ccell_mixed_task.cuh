@@ -215,10 +215,12 @@ __device__ __forceinline__ void step_mixed_tile(const StepArgs& a, const TileTas
         if (own && q == nl - 1) cout[smem_col(ic)] = fn;
         if (own) {
           const size_t w = (size_t)q * nrp + smem_col(ic);
-          SA[w] = fa;  // exact widening
-          SB[w] = fb;
-          SC[w] = fc;
-          SD[w] = fd;
+          // the row divided by its diagonal in FP32 (the solve takes b = 1),
+          // then widened exactly
+          const float ib = __fdividef(1.0f, fb);
+          SA[w] = fa * ib;
+          SC[w] = fc * ib;
+          SD[w] = fd * ib;
           if (ENERGY) FM[w] = m;
         }
         hc = hn; lc = ln;
@@ -231,7 +233,7 @@ __device__ __forceinline__ void step_mixed_tile(const StepArgs& a, const TileTas
   __syncthreads();
 
   // ---- 1.-3. FP64 line solves, lanes over the rows of a line
-  solve_tile_lines<false>(SA, SB, SC, SD, nl, nr, G);
+  solve_tile_lines<false>(SA, SB, SC, SD, nl, nr, G);  // unit diagonal
   __syncthreads();
 
   // ---- 4. pair update, boundary rows, trace, interface energy; lanes over columns
