@@ -455,6 +455,149 @@ int or_step_n(const or_problem* p, double* T, long n_steps, double t0, double ta
   return 0;
 }
 
+/* ------------------------------------------------------------------ */
+/* ADI variant (Peaceman-Rachford), implicit in both directions        */
+/* ------------------------------------------------------------------ */
+/*
+ * The paper mentions the Alternating Direction Implicit method (Section 3,
+ * after Eq. (stability_condition)) as the unconditionally stable alternative
+ * to its scheme.  Reading taken (A19): the Peaceman-Rachford splitting of
+ * Eq. (scheme_eq) over two half steps of tau/2, with the operators of
+ * Eqs. (Lambda_i), (Lambda_j) and the source of Eq. (source), all material
+ * properties and X frozen at (T^n, t_n):
+ *   half step 1:  rho c (T* - T^n)/(tau/2)      = Lambda_i[T*]      + Lambda_j[T^n]     + X
+ *   half step 2:  rho c (T^n+1 - T*)/(tau/2)    = Lambda_i[T*]      + Lambda_j[T^n+1]   + X
+ * Half step 1 is the paper's step with tau/2 (radial lines, interface rows
+ * and closures as there).  Half step 2 is a tridiagonal system along z for
+ * each column i of regular nodes (rows j = 1..M-1; T_0 = T_1 or T_D and
+ * T_M = T_D or T_M-1 folded in); then the columns of non-regular nodes take
+ * their radial relations with the new neighbours -- axis T_0 = T_1, r_max
+ * Neumann T_N = T_N-1 or Dirichlet T_D, interface nodes the row of
+ * Eq. (cc_first_3) (lambda* at T^n) -- and the axial boundary rows are set as
+ * in the paper's step.  trace as in or_step_n; no energy terms.
+ */
+int or_step_adi_n(const or_problem* p, double* T, long n_steps, double t0, double tau,
+                  double* trace) {
+  const int N = p->nr - 1, M = p->nz - 1, nr = p->nr;
+  const size_t nn = (size_t)nr * (M + 1);
+  double* r = (double*)malloc(sizeof(double) * (N + 1));
+  double* z = (double*)malloc(sizeof(double) * (M + 1));
+  int* cls = (int*)malloc(sizeof(int) * (N + 1));
+  int* seg = (int*)malloc(sizeof(int) * (N + 1));
+  double* Ts = (double*)malloc(sizeof(double) * nn);  /* T*     */
+  double* Tn = (double*)malloc(sizeof(double) * nn);  /* T^n+1  */
+  if (!r || !z || !cls || !seg || !Ts || !Tn || or_grid(p, r, z, cls, seg)) {
+    free(r); free(z); free(cls); free(seg); free(Ts); free(Tn);
+    return -1;
+  }
+  const double h = 0.5 * tau;
+  for (long n = 0; n < n_steps; n++) {
+    const double tn = t0 + (double)n * tau;
+    const double s = or_waveform(p, tn);
+    /* half step 1: the paper's step with tau/2 */
+    memcpy(Ts, T, sizeof(double) * nn);
+    if (or_step_n(p, Ts, 1, tn, h, NULL, NULL)) {
+      free(r); free(z); free(cls); free(seg); free(Ts); free(Tn);
+      return -1;
+    }
+    memcpy(Tn, Ts, sizeof(double) * nn);
+    /* half step 2: one tridiagonal system in j per column of regular nodes */
+#pragma omp parallel
+    {
+      double* a = (double*)malloc(sizeof(double) * (M + 1));
+      double* b = (double*)malloc(sizeof(double) * (M + 1));
+      double* c = (double*)malloc(sizeof(double) * (M + 1));
+      double* f = (double*)malloc(sizeof(double) * (M + 1));
+#pragma omp for schedule(static)
+      for (int i = 1; i <= N - 1; i++) {
+        if (cls[i] != OR_REGULAR) continue;
+        const int m = seg[i];
+        const double h_w = r[i] - r[i - 1], h_e = r[i + 1] - r[i];
+        const double hbar = 0.5 * (h_e + h_w);
+        const double r_w = 0.5 * (r[i] + r[i - 1]), r_e = 0.5 * (r[i] + r[i + 1]);
+        for (int j = 1; j <= M - 1; j++) {
+          const double* Tj = T + (size_t)j * nr;        /* T^n, line j   */
+          const double* Sj = Ts + (size_t)j * nr;       /* T*,  line j   */
+          const double eta_s = z[j] - z[j - 1], eta_n = z[j + 1] - z[j];
+          const double etabar = 0.5 * (eta_n + eta_s);
+          const double T0 = Tj[i];
+          const double rc = p->rho[m] * cap_m(p, m, T0);
+          const double lw = lam_face(p, m, Tj[i - 1], T0);
+          const double le = lam_face(p, m, T0, Tj[i + 1]);
+          const double ls = lam_face(p, m, T[(size_t)(j - 1) * nr + i], T0);
+          const double ln = lam_face(p, m, T0, T[(size_t)(j + 1) * nr + i]);
+          /* Eq. (Lambda_i) applied to T*, explicit here */
+          const double Li = (r_e * le * (Sj[i + 1] - Sj[i]) / h_e -
+                             r_w * lw * (Sj[i] - Sj[i - 1]) / h_w) / (r[i] * hbar);
+          /* Eq. (Lambda_j) applied to T^n+1: coefficients of T_j-1, T_j+1 */
+          a[j] = -ls / (eta_s * etabar);
+          c[j] = -ln / (eta_n * etabar);
+          b[j] = rc / h - a[j] - c[j];
+          f[j] = rc / h * Sj[i] + Li + source(p, m, T0, s);
+        }
+        /* z closures folded into the first and last rows */
+        if (p->bc_z0) { f[1] -= a[1] * p->t_dirichlet; } else { b[1] += a[1]; }
+        if (p->bc_zmax) { f[M - 1] -= c[M - 1] * p->t_dirichlet; } else { b[M - 1] += c[M - 1]; }
+        /* Thomas algorithm in j */
+        for (int j = 2; j <= M - 1; j++) {
+          const double w = a[j] / b[j - 1];
+          b[j] -= w * c[j - 1];
+          f[j] -= w * f[j - 1];
+        }
+        double x = f[M - 1] / b[M - 1];
+        Tn[(size_t)(M - 1) * nr + i] = x;
+        for (int j = M - 2; j >= 1; j--) {
+          x = (f[j] - c[j] * x) / b[j];
+          Tn[(size_t)j * nr + i] = x;
+        }
+      }
+      free(a); free(b); free(c); free(f);
+    }
+    /* radial relations of the non-regular columns with the new values */
+    for (int j = 1; j <= M - 1; j++) {
+      double* Hj = Tn + (size_t)j * nr;
+      const double* Tj = T + (size_t)j * nr;
+      for (int i = 1; i <= N - 1; i++) {
+        if (cls[i] != OR_IFACE) continue;
+        const int mi = seg[i - 1], mo = seg[i];
+        const double h_w = r[i] - r[i - 1], h_e = r[i + 1] - r[i];
+        double lm, lp;
+        if (p->interface_rule == 0) {
+          lm = lam_m(p, mi, Tj[i]);
+          lp = lam_m(p, mo, Tj[i]);
+        } else {
+          lm = 0.5 * (r[i] + r[i - 1]) * lam_face(p, mi, Tj[i - 1], Tj[i]);
+          lp = 0.5 * (r[i] + r[i + 1]) * lam_face(p, mo, Tj[i], Tj[i + 1]);
+        }
+        /* lm (T_i - T_i-1)/h_i = lp (T_i+1 - T_i)/h_i+1, Eq. (cc_first_1) */
+        Hj[i] = (lm * h_e * Hj[i - 1] + lp * h_w * Hj[i + 1]) / (lm * h_e + lp * h_w);
+      }
+      Hj[0] = Hj[1];
+      Hj[N] = p->bc_rmax ? p->t_dirichlet : Hj[N - 1];
+    }
+    /* axial boundary rows */
+    for (int i = 0; i <= N; i++) {
+      Tn[i] = p->bc_z0 ? p->t_dirichlet : Tn[(size_t)nr + i];
+      Tn[(size_t)M * nr + i] = p->bc_zmax ? p->t_dirichlet : Tn[(size_t)(M - 1) * nr + i];
+    }
+    memcpy(T, Tn, sizeof(double) * nn);
+    if (trace) {
+      double wsum = 0.0, acc = 0.0;
+      for (int j = 0; j <= M; j++) {
+        double w = 0.0;
+        if (j > 0) w += 0.5 * (z[j] - z[j - 1]);
+        if (j < M) w += 0.5 * (z[j + 1] - z[j]);
+        wsum += w;
+        acc += w * T[(size_t)j * nr + N];
+      }
+      trace[2 * n] = T[N];
+      trace[2 * n + 1] = acc / wsum;
+    }
+  }
+  free(r); free(z); free(cls); free(seg); free(Ts); free(Tn);
+  return 0;
+}
+
 int or_num_threads(void) {
 #ifdef _OPENMP
   return omp_get_max_threads();

@@ -91,6 +91,8 @@ def _load():
         lib.or_grid.restype = ctypes.c_int
         lib.or_step_n.argtypes = [P, dp, ctypes.c_long, ctypes.c_double, ctypes.c_double, dp, dp]
         lib.or_step_n.restype = ctypes.c_int
+        lib.or_step_adi_n.argtypes = [P, dp, ctypes.c_long, ctypes.c_double, ctypes.c_double, dp]
+        lib.or_step_adi_n.restype = ctypes.c_int
         lib.or_tau_stab.argtypes = [P, ctypes.c_double, ctypes.c_double, ctypes.c_int]
         lib.or_tau_stab.restype = ctypes.c_double
         lib.or_waveform.argtypes = [P, ctypes.c_double]
@@ -188,6 +190,23 @@ def step_n(cfg: dict, T: np.ndarray, n_steps: int, t0: float, dt: float,
     if rc != 0:
         raise ValueError("oracle rejected the problem")
     return T, trace, energy
+
+
+def step_adi_n(cfg: dict, T: np.ndarray, n_steps: int, t0: float, dt: float,
+               want_trace: bool = True):
+    """Run n_steps of the Peaceman-Rachford ADI variant (two half steps of
+    dt/2: implicit in r, then implicit in z).  Returns (T_new, trace[n,2] or None)."""
+    lib = _load()
+    p = problem(cfg)
+    T = np.ascontiguousarray(T, dtype=np.float64).copy()
+    if T.shape != (cfg["nz"], cfg["nr"]):
+        raise ValueError(f"T must have shape (nz, nr) = {(cfg['nz'], cfg['nr'])}")
+    trace = np.zeros((n_steps, 2)) if want_trace else None
+    rc = lib.or_step_adi_n(ctypes.byref(p), _dp(T), int(n_steps), float(t0), float(dt),
+                           _dp(trace) if trace is not None else None)
+    if rc != 0:
+        raise ValueError("oracle rejected the problem")
+    return T, trace
 
 
 def n_params(cfg: dict) -> int:

@@ -55,6 +55,19 @@ MUTATIONS = {
         ("return 0.5 * (1.0 - th * th) / p->edge_w;", "return -0.5 * (1.0 - th * th) / p->edge_w;"),
     "adjoint: Neumann row z=0 not folded into line 1":
         ("if (!p->bc_z0) mu[(size_t)nr + i] += mu[i];", "(void)0;"),
+    # ADI variant
+    "ADI: radial term of the second half step partly at T^n":
+        ("const double Li = (r_e * le * (Sj[i + 1] - Sj[i]) / h_e -",
+         "const double Li = (r_e * le * (Tj[i + 1] - Tj[i]) / h_e -"),
+    "ADI: full time step in the second half step's diagonal":
+        ("b[j] = rc / h - a[j] - c[j];", "b[j] = rc / tau - a[j] - c[j];"),
+    "ADI: source dropped from the second half step":
+        ("f[j] = rc / h * Sj[i] + Li + source(p, m, T0, s);", "f[j] = rc / h * Sj[i] + Li;"),
+    "ADI: Neumann closure at z = 0 not folded":
+        ("} else { b[1] += a[1]; }", "} else { (void)0; }"),
+    "ADI: interface cell widths swapped":
+        ("Hj[i] = (lm * h_e * Hj[i - 1] + lp * h_w * Hj[i + 1])",
+         "Hj[i] = (lm * h_w * Hj[i - 1] + lp * h_e * Hj[i + 1])"),
 }
 
 
@@ -71,6 +84,7 @@ def test_pins_catch_mutation(name, tmp_path):
                     "-o", str(so), "-lm"], check=True, capture_output=True)
     env = dict(os.environ, CCELL_ORACLE_SO=str(so))
     res = subprocess.run([sys.executable, "-m", "pytest", "-x", "-q",
+                          os.path.join(ROOT, "tests", "test_oracle_adi.py"),
                           os.path.join(ROOT, "tests", "test_oracle_pins.py"),
                           os.path.join(ROOT, "tests", "test_oracle_adjoint.py")],
                          env=env, capture_output=True, text=True, cwd=ROOT)
