@@ -187,7 +187,29 @@ int cc_set_dt(cc_ctx* ctx, int32_t instance, double dt_s);
 int cc_step_n(cc_ctx* ctx, void* T_dev, int64_t n_steps, double t0_s, double dt_s,
               double* trace_dev, double* energy_dev, void* stream);
 
-/* Launch shape of cc_step_n (the numerics do not depend on it):
+/*
+ * ADI variant (Peaceman-Rachford), the scheme the paper names as the
+ * unconditionally stable alternative to its own (Section 3, after
+ * Eq. (stability_condition)): each step is two half steps of dt/2 with the
+ * material properties and the source frozen at (T^n, t_n),
+ *   rho c (T* - T^n)/(dt/2)    = Lambda_i[T*] + Lambda_j[T^n]   + X   (implicit in r)
+ *   rho c (T^n+1 - T*)/(dt/2)  = Lambda_i[T*] + Lambda_j[T^n+1] + X   (implicit in z)
+ * The first is the step of cc_step_n at dt/2; the second is one tridiagonal
+ * system along z per column of regular nodes, after which the axis, r_max
+ * and interface columns take their radial relations (interface: Eq.
+ * (cc_first_3) with lambda* at T^n) and the axial boundary rows are set.
+ * There is no stability bound on dt (no CC_EUNSTABLE); accuracy is second
+ * order in dt for frozen coefficients.
+ *   T_dev      in/out double field of all instances (FP64 contexts only).
+ *   trace_dev  NULL or double[n_instances][n_steps][2] as in cc_step_n.
+ * No energy terms.  The first call sizes the ADI scratch (about 24 bytes
+ * per node plus 24 bytes per node of the column solves).
+ * Errors: CC_EINVAL, CC_EUNSUPPORTED (CC_MIXED context), CC_ESTATE,
+ * CC_ECUDA, CC_ENOMEM.  Asynchronous; cc_sync reports deferred failures. */
+int cc_step_adi_n(cc_ctx* ctx, void* T_dev, int64_t n_steps, double t0_s, double dt_s,
+                  double* trace_dev, void* stream);
+
+/* Launch shape of cc_step_n (the numerics do not depend on it):/* Launch shape of cc_step_n (the numerics do not depend on it):
  *   mode 0: one kernel launch per time step; mode 1: all steps of a call in
  *   one cooperative (co-resident) launch with a grid barrier between steps
  *   (bounded wait: a barrier that does not complete within ~seconds ends the

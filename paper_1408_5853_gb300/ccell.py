@@ -6,7 +6,7 @@ this module loads the CUDA library and fails loudly if it is missing; there is
 no CPU fallback.
 
 Low-level functions carry the C names (``cc_create_geometry``,
-``cc_set_materials``, ``cc_set_source``, ``cc_set_dt``, ``cc_step_n``,
+``cc_set_materials``, ``cc_set_source``, ``cc_set_dt``, ``cc_step_n``, ``cc_step_adi_n``,
 ``cc_sync``, ``cc_adjoint``, ``cc_adjoint_vjp``, ``cc_set_launch``, ``cc_get_launch``,
 ``cc_autotune``, ``cc_destroy``, ``cc_step_n_noalloc``, ``cc_query_grid``,
 ``cc_tau_stab``, ``cc_status_string``, ``cc_kernel_launches``).  ``Solver``
@@ -82,6 +82,7 @@ def _load():
     lib.cc_set_source.argtypes = [vp, _i, ctypes.POINTER(Source)]
     lib.cc_set_dt.argtypes = [vp, _i, _d]
     lib.cc_step_n.argtypes = [vp, vp, ctypes.c_int64, _d, _d, vp, vp, vp]
+    lib.cc_step_adi_n.argtypes = [vp, vp, ctypes.c_int64, _d, _d, vp, vp]
     lib.cc_sync.argtypes = [vp, vp]
     lib.cc_adjoint.argtypes = [vp, vp, ctypes.c_int64, _d, _d, vp, _i, vp, vp, vp, vp]
     lib.cc_destroy.argtypes = [vp]
@@ -103,8 +104,8 @@ def _load():
     lib.cc_adjoint_vjp.argtypes = [vp, vp, ctypes.c_int64, _d, _d, vp, _i, vp, vp, vp]
     lib.cc_adjoint_vjp.restype = ctypes.c_int
     for name in ("cc_create_geometry", "cc_set_materials", "cc_set_source", "cc_set_dt",
-                 "cc_step_n", "cc_sync", "cc_adjoint", "cc_destroy", "cc_query_grid",
-                 "cc_tau_stab"):
+                 "cc_step_n", "cc_step_adi_n", "cc_sync", "cc_adjoint", "cc_destroy",
+                 "cc_query_grid", "cc_tau_stab"):
         getattr(lib, name).restype = ctypes.c_int
     _lib = lib
     return lib
@@ -144,6 +145,12 @@ def cc_set_source(ctx, instance: int, source: Source) -> None:
 
 def cc_set_dt(ctx, instance: int, dt: float) -> None:
     _check(_load().cc_set_dt(ctx, instance, float(dt)), "cc_set_dt")
+
+
+def cc_step_adi_n(ctx, T_ptr: int, n_steps: int, t0: float, dt: float, trace_ptr,
+                  stream_ptr) -> None:
+    _check(_load().cc_step_adi_n(ctx, T_ptr, int(n_steps), float(t0), float(dt), trace_ptr,
+                                 stream_ptr), "cc_step_adi_n")
 
 
 def cc_step_n(ctx, T_ptr: int, n_steps: int, t0: float, dt: float, trace_ptr, energy_ptr,
@@ -314,6 +321,22 @@ class Solver:
         cc_step_n(self.ctx, T.data_ptr(), n_steps, t0, dt,
                   trace.data_ptr() if trace is not None else None,
                   energy.data_ptr() if energy is not None else None, st.cuda_stream)
+
+    def step_adi(self, T, n_steps: int, t0: float = 0.0, dt: float = 0.0, trace=None,
+                 stream=None) -> None:
+        """Advance the FP64 field ``T`` in place by n_steps steps of the ADI
+        variant (no stability bound on dt)."""
+        import torch
+        if not (T.is_cuda and T.is_contiguous() and T.dtype == torch.float64
+                and T.numel() == self.total):
+            raise ValueError("T must be a contiguous CUDA float64 tensor of the context's size")
+        if trace is not None and not (trace.is_cuda and trace.is_contiguous()
+                                      and trace.dtype == torch.float64
+                                      and trace.numel() == 2 * n_steps * len(self.cfgs)):
+            raise ValueError("trace must be contiguous CUDA float64 of the right size")
+        st = stream if stream is not None else torch.cuda.current_stream()
+        cc_step_adi_n(self.ctx, T.data_ptr(), n_steps, t0, dt,
+                      trace.data_ptr() if trace is not None else None, st.cuda_stream)
 
     def set_launch(self, mode: int, threads: int = 128, rows_per_lane: int = 16) -> None:
         cc_set_launch(self.ctx, mode, threads, rows_per_lane)

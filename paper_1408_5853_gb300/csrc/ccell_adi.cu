@@ -1,0 +1,181 @@
+// ADI variant of the time step (Peaceman-Rachford), the scheme the paper
+// names as the unconditionally stable alternative to its own (Section 3,
+// after Eq. (stability_condition)).  Two half steps of tau/2, properties and
+// source frozen at (T^n, t_n):
+//   rho c (T* - T^n)/(tau/2)     = Lambda_i[T*] + Lambda_j[T^n]     + X   (radial lines)
+//   rho c (T^n+1 - T*)/(tau/2)   = Lambda_i[T*] + Lambda_j[T^n+1]   + X   (axial columns)
+// The first half step is the tile kernel of the paper's step at tau/2; it
+// also leaves rho c/(tau/2), Lambda_j[T^n] and the axial face conductivities
+// of the regular nodes.  Subtracting the two equations, the second becomes
+//   rho c/(tau/2) T^n+1 - Lambda_j[T^n+1] = rho c/(tau/2) (2 T* - T^n) - Lambda_j[T^n],
+// one tridiagonal system along z per column of regular nodes (this file),
+// split over the lanes of a warp like the radial lines.  Then the non-regular
+// columns take their radial relations with the new values (axis, r_max,
+// interface rows of Eq. (cc_first_3) with lambda* at T^n), the axial
+// boundary rows are set, and the surface trace is formed.
+#include <cuda_runtime.h>
+
+#include "ccell_device.cuh"
+
+namespace ccell {
+
+__global__ void __launch_bounds__(128) adi_axial_kernel(const AdiArgs a) {
+  const int lane = threadIdx.x & 31;
+  const int n_warps = (int)((gridDim.x * blockDim.x) >> 5);
+  for (int w = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5); w < a.n_tasks; w += n_warps) {
+    const AdiTask tk = a.tasks[w];
+    const DevInst& I = a.insts[tk.inst];
+    const int nr = I.nr, M = I.nz - 1, L = M - 1;  // rows j = 1 .. M-1
+    int G = 32;
+    while (G > 1 && L < 2 * G) G >>= 1;
+    const int lg = __ffs(G) - 1;
+    const int grp = lane >> lg, l = lane & (G - 1);  // groups > 0 repeat group 0, store nothing
+    const int lo = 1 + ((l * L) >> lg), hi = 1 + (((l + 1) * L) >> lg);
+    const int cnt = hi - lo;  // >= 2
+    const long long col = I.t_off + tk.i;
+    const size_t plane = (size_t)a.n_tasks * a.rows_max * 32;
+    double* Cp = a.scr + ((size_t)w * a.rows_max) * 32 + lane;
+    double* Ap = Cp + plane;
+    double* Dp = Ap + plane;
+    double pc = 0.0, pa = 0.0, pd = 0.0;
+    double Dacc = 0.0, Aacc = 0.0, P = 1.0;
+    double ae = 0.0, be = 1.0, ce = 0.0, de = 0.0;
+    for (int k = 0; k < cnt; ++k) {
+      const int j = lo + k;
+      const long long o = col + (long long)j * nr;
+      const ZGeo& zg = I.zg[j];
+      const double rct = a.rct[o];
+      double ra = -zg.gzs * a.lamz[o - nr];  // face (j-1, j)
+      double rc = -zg.gzn * a.lamz[o];       // face (j, j+1)
+      double rb = rct - ra - rc;
+      double rd = fma(rct, 2.0 * a.Tx[o] - a.Tn[o], -a.lj[o]);
+      if (j == 1) {  // T_0 = T_1 or T_D folded into the row
+        if (I.bc_z0 == CC_DIRICHLET) rd = fma(-ra, I.t_d, rd); else rb += ra;
+        ra = 0.0;
+      }
+      if (j == M - 1) {  // T_M = T_D or T_M-1
+        if (I.bc_zmax == CC_DIRICHLET) rd = fma(-rc, I.t_d, rd); else rb += rc;
+        rc = 0.0;
+      }
+      if (k < cnt - 1) {
+        const double den = (k == 0) ? rb : fma(-ra, pc, rb);
+        const double r = frcp(den);
+        const double c1 = rc * r;
+        const double a1 = (k == 0) ? ra * r : -ra * pa * r;
+        const double d1 = (k == 0) ? rd * r : fma(-ra, pd, rd) * r;
+        Cp[(size_t)k * 32] = c1;
+        Ap[(size_t)k * 32] = a1;
+        Dp[(size_t)k * 32] = d1;
+        Dacc = fma(P, d1, Dacc);
+        Aacc = fma(P, a1, Aacc);
+        P = -P * c1;
+        pc = c1;
+        pa = a1;
+        pd = d1;
+      } else {
+        ae = ra; be = rb; ce = rc; de = rd;
+      }
+    }
+    const double xs = solve_separators(ae, be, ce, de, pa, pc, pd, Dacc, Aacc, P, G, l);
+    const double Lp = __shfl_up_sync(kFull, xs, 1, G);
+    // every group has read its rows before group 0 overwrites T* (same warp)
+    __syncwarp();
+    if (grp == 0) {
+      bool bad = not_finite(xs);
+      a.Tx[col + (long long)(hi - 1) * nr] = xs;
+      double xn = xs;
+      for (int k = cnt - 2; k >= 0; --k) {
+        const double x = fma(-Cp[(size_t)k * 32], xn, fma(-Ap[(size_t)k * 32], Lp, Dp[(size_t)k * 32]));
+        bad |= not_finite(x);
+        a.Tx[col + (long long)(lo + k) * nr] = x;
+        xn = x;
+      }
+      if (bad) atomicOr(a.err, 1u);
+    }
+  }
+}
+
+// One block per instance: non-regular columns, axial boundary rows, trace.
+__global__ void __launch_bounds__(256) adi_finish_kernel(const AdiArgs a) {
+  const int k = blockIdx.x;
+  const DevInst& I = a.insts[k];
+  const int nr = I.nr, N = nr - 1, M = I.nz - 1;
+  const double* Tn = a.Tn + I.t_off;
+  double* X = a.Tx + I.t_off;
+  bool bad = false;
+  // interface nodes: lm (T_i - T_i-1)/h_i = lp (T_i+1 - T_i)/h_i+1, lambda at T^n
+  const int n_if = I.n_if;
+  for (int it = threadIdx.x; it < (M - 1) * n_if; it += blockDim.x) {
+    const int jj = it / n_if;
+    const int i = I.if_i[it - jj * n_if];
+    const RowGeo& g = I.rg[i];
+    if (g.cls != RC_IFACE) continue;
+    const long long o = (long long)(jj + 1) * nr + i;
+    double lm, lp;
+    if (I.interface_rule == 0) {
+      lm = lam_eval(I.mat[g.segw], Tn[o]);
+      lp = lam_eval(I.mat[g.seg], Tn[o]);
+    } else {
+      lm = g.rw * lam_face(I.mat[g.segw], I.face_rule, Tn[o - 1], Tn[o]);
+      lp = g.re * lam_face(I.mat[g.seg], I.face_rule, Tn[o], Tn[o + 1]);
+    }
+    const double x = fma(lm * g.he, X[o - 1], lp * g.hw * X[o + 1]) / fma(lm, g.he, lp * g.hw);
+    bad |= not_finite(x);
+    X[o] = x;
+  }
+  // axis and r_max columns
+  for (int j = 1 + threadIdx.x; j <= M - 1; j += blockDim.x) {
+    const long long o = (long long)j * nr;
+    X[o] = X[o + 1];
+    X[o + N] = (I.bc_rmax == CC_DIRICHLET) ? I.t_d : X[o + N - 1];
+  }
+  if (bad) atomicOr(a.err, 1u);
+  __syncthreads();
+  // axial boundary rows
+  for (int i = threadIdx.x; i < nr; i += blockDim.x) {
+    X[i] = (I.bc_z0 == CC_DIRICHLET) ? I.t_d : X[nr + i];
+    X[(long long)M * nr + i] = (I.bc_zmax == CC_DIRICHLET) ? I.t_d : X[(long long)(M - 1) * nr + i];
+  }
+  __syncthreads();
+  if (a.trace) {  // That(r_max, z_0) and the trapezoid-weighted mean over z
+    __shared__ double part[32];
+    double s = 0.0;
+    for (int j = threadIdx.x; j <= M; j += blockDim.x) s = fma(I.zg[j].wnorm, X[(long long)j * nr + N], s);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(kFull, s, o);
+    if ((threadIdx.x & 31) == 0) part[threadIdx.x >> 5] = s;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double t = 0.0;
+      for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += part[w];
+      double* tr = a.trace + ((long long)k * a.n_steps + a.step) * 2;
+      tr[0] = X[N];
+      tr[1] = t;
+    }
+  }
+}
+
+int launch_adi_axial(const AdiArgs& a, void* stream) {
+  constexpr int threads = 128;
+  static int resident = 0;
+  if (resident == 0) {
+    int dev = 0, sms = 0, per_sm = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, adi_axial_kernel, threads, 0);
+    resident = sms * (per_sm > 0 ? per_sm : 1);
+  }
+  const int need = (a.n_tasks * 32 + threads - 1) / threads;
+  if (need > 0)
+    adi_axial_kernel<<<need < resident ? need : resident, threads, 0, (cudaStream_t)stream>>>(a);
+  count_launch();
+  return cudaGetLastError() == cudaSuccess ? 0 : -1;
+}
+
+int launch_adi_finish(const AdiArgs& a, void* stream) {
+  adi_finish_kernel<<<a.n_inst, 256, 0, (cudaStream_t)stream>>>(a);
+  count_launch();
+  return cudaGetLastError() == cudaSuccess ? 0 : -1;
+}
+
+}  // namespace ccell

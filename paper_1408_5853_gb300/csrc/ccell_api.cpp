@@ -66,6 +66,11 @@ struct cc_ctx {
   bool tasks_dirty = true;
   size_t tasks_cap = 0;
   void* d_tune = nullptr;  // autotuner copy of the caller's field
+  // ADI variant: column tasks and scratch, built on first use
+  AdiTask* d_adi_tasks = nullptr;
+  int n_adi_tasks = 0, adi_rows = 0;
+  double* d_adi = nullptr;
+  size_t adi_scratch = 0;
 };
 
 namespace {
@@ -237,6 +242,12 @@ void free_device(cc_ctx* c) {
   c->adj_cap = 0;
   cudaFree(c->d_tune);
   c->d_tune = nullptr;
+  cudaFree(c->d_adi_tasks);
+  c->d_adi_tasks = nullptr;
+  c->n_adi_tasks = 0;
+  cudaFree(c->d_adi);
+  c->d_adi = nullptr;
+  c->adi_scratch = 0;
   c->tasks_cap = 0;
   c->d_inst = nullptr;
   c->d_rg = nullptr;
@@ -738,6 +749,127 @@ int cc_step_n(cc_ctx* c, void* T_dev, int64_t n_steps, double t0, double dt_s, d
   }
   if (n_steps & 1) {
     if (cudaMemcpyAsync(T_dev, c->d_T2, elem * c->total_nodes, cudaMemcpyDeviceToDevice, st) !=
+        cudaSuccess)
+      return CC_ECUDA;
+  }
+  return CC_OK;
+}
+
+int cc_step_adi_n(cc_ctx* c, void* T_dev, int64_t n_steps, double t0, double dt_s,
+                  double* trace_dev, void* stream) {
+  if (!c || !T_dev || n_steps < 0 || !std::isfinite(t0)) return CC_EINVAL;
+  if (c->failed) return CC_ESTATE;
+  if (c->precision != CC_FP64) return CC_EUNSUPPORTED;
+  if (n_steps == 0) return CC_OK;
+  const int n = (int)c->inst.size();
+  std::vector<double> half(n);
+  for (int k = 0; k < n; ++k) {
+    Instance& in = c->inst[k];
+    if (!in.mat_set) return CC_ESTATE;
+    const double dt = dt_s > 0.0 ? dt_s : in.dt;
+    if (!(dt > 0.0) || !std::isfinite(dt)) return CC_EINVAL;
+    half[k] = 0.5 * dt;
+  }
+  cudaStream_t st = (cudaStream_t)stream;
+  int rc = upload(c, half, st);  // the tables fold rho / (dt/2)
+  if (rc != CC_OK) return rc;
+  if (!c->d_adi_tasks) {  // columns of regular nodes, one warp each
+    std::vector<AdiTask> tasks;
+    int rows = 0;
+    for (int k = 0; k < n; ++k) {
+      const Instance& in = c->inst[k];
+      const int L = in.d.nz - 2;
+      int G = 32;
+      while (G > 1 && L < 2 * G) G >>= 1;
+      rows = std::max(rows, (L + G - 1) / G);
+      for (int i = 0; i < in.d.nr; ++i)
+        if (in.cls[i] == RC_REGULAR) tasks.push_back(AdiTask{k, i});
+    }
+    if (cudaMalloc(&c->d_adi_tasks, sizeof(AdiTask) * std::max<size_t>(1, tasks.size())) !=
+        cudaSuccess) {
+      cudaGetLastError();
+      return CC_ENOMEM;
+    }
+    if (!tasks.empty() &&
+        cudaMemcpy(c->d_adi_tasks, tasks.data(), sizeof(AdiTask) * tasks.size(),
+                   cudaMemcpyHostToDevice) != cudaSuccess)
+      return CC_ECUDA;
+    c->n_adi_tasks = (int)tasks.size();
+    c->adi_rows = rows;
+  }
+  const size_t nodes = (size_t)c->total_nodes;
+  const size_t need = 3 * nodes + 3 * (size_t)c->n_adi_tasks * c->adi_rows * 32;
+  if (need > c->adi_scratch) {
+    cudaFree(c->d_adi);
+    c->d_adi = nullptr;
+    c->adi_scratch = 0;
+    if (cudaMalloc(&c->d_adi, sizeof(double) * need) != cudaSuccess) {
+      cudaGetLastError();
+      return CC_ENOMEM;
+    }
+    c->adi_scratch = need;
+  }
+  // waveform at the half steps; step m uses entry 2m, t_m = t0 + m dt
+  const long long n_half = 2 * n_steps;
+  if (c->s_cap < n_half * n) {
+    cudaFree(c->d_s);
+    c->d_s = nullptr;
+    c->s_cap = 0;
+    if (cudaMalloc(&c->d_s, sizeof(double) * n_half * n) != cudaSuccess) {
+      cudaGetLastError();
+      return CC_ENOMEM;
+    }
+    c->s_cap = n_half * n;
+  }
+  if (launch_waveform(c->d_inst, n, n_half, t0, c->d_s, stream)) return CC_ECUDA;
+  if (trace_dev &&
+      cudaMemsetAsync(trace_dev, 0, sizeof(double) * 2 * n_steps * n, st) != cudaSuccess)
+    return CC_ECUDA;
+  StepArgs a{};
+  a.insts = c->d_inst;
+  a.tasks = c->d_tasks;
+  a.n_tasks = c->n_tasks;
+  a.tiles = c->d_tiles;
+  a.n_tiles = c->n_tiles;
+  a.cta_start = c->n_cta > 0 ? c->d_cta : nullptr;
+  a.n_cta = c->n_cta;
+  a.smem_bytes = c->smem_bytes;
+  a.n_inst = n;
+  a.s_tab = c->d_s;
+  a.n_steps = n_half;
+  a.err = c->d_err;
+  a.threads = c->threads;
+  a.adi_rct = c->d_adi;
+  a.adi_lj = c->d_adi + nodes;
+  a.adi_lamz = c->d_adi + 2 * nodes;
+  AdiArgs z{};
+  z.insts = c->d_inst;
+  z.n_inst = n;
+  z.tasks = c->d_adi_tasks;
+  z.n_tasks = c->n_adi_tasks;
+  z.rows_max = c->adi_rows;
+  z.rct = a.adi_rct;
+  z.lj = a.adi_lj;
+  z.lamz = a.adi_lamz;
+  z.scr = c->d_adi + 3 * nodes;
+  z.trace = trace_dev;
+  z.n_steps = n_steps;
+  z.err = c->d_err;
+  void* bufs[2] = {T_dev, c->d_T2};
+  for (long long m = 0; m < n_steps; ++m) {
+    // half step 1: the step of cc_step_n at dt/2, T^n -> T*
+    a.step = 2 * m;
+    a.Tin = bufs[m & 1];
+    a.Tout = bufs[(m + 1) & 1];
+    if (launch_step_fp64(a, stream)) return CC_ECUDA;
+    // half step 2: columns along z, T* -> T^n+1 in place; then the rest
+    z.Tn = static_cast<const double*>(bufs[m & 1]);
+    z.Tx = static_cast<double*>(bufs[(m + 1) & 1]);
+    z.step = m;
+    if (launch_adi_axial(z, stream) || launch_adi_finish(z, stream)) return CC_ECUDA;
+  }
+  if (n_steps & 1) {
+    if (cudaMemcpyAsync(T_dev, c->d_T2, sizeof(double) * nodes, cudaMemcpyDeviceToDevice, st) !=
         cudaSuccess)
       return CC_ECUDA;
   }

@@ -142,7 +142,9 @@ __device__ __forceinline__ void step_fp64_tile(const StepArgs& a, const TileTask
         fs = cin[smem_col(ic)];
       } else {
         const double Ts = ld_field<CACHED>(row - nr + ic);
-        fs = lam_face(Mt, frule, Ts, Tc) * (Tc - Ts);
+        const double ls = lam_face(Mt, frule, Ts, Tc);
+        fs = ls * (Tc - Ts);
+        if (a.adi_lamz && own && j0 + q0 == 1) a.adi_lamz[I.t_off + ic] = ls;  // face (0, 1)
       }
       for (int q = q0; q < q1; ++q) {
         const int j = j0 + q;
@@ -152,7 +154,8 @@ __device__ __forceinline__ void step_fp64_tile(const StepArgs& a, const TileTask
           Te_next = ld_field<CACHED>(row + nr + ie);
         }
         row += nr;
-        const double fn = lam_face(Mt, frule, Tc, Tn) * (Tn - Tc);
+        const double ln = lam_face(Mt, frule, Tc, Tn);  // face (j, j+1)
+        const double fn = ln * (Tn - Tc);
         const double le = (ic < N) ? lam_face(Mt, frule, Tc, Te) : 0.0;  // face (i, i+1)
         const double lw = __shfl_up_sync(kFull, le, 1);                  // face (i-1, i)
         const double rct = rct_eval(Mt, Tc);                             // rho c / tau
@@ -172,6 +175,12 @@ __device__ __forceinline__ void step_fp64_tile(const StepArgs& a, const TileTask
           rc = C;
           rb = rct - A - C;
           rd = fma(rct, Tc, Lj + X);
+          if (a.adi_lj && own) {  // for the axial half step of the ADI variant
+            const long long o = I.t_off + (long long)j * nr + ic;
+            a.adi_rct[o] = rct;
+            a.adi_lj[o] = Lj;
+            a.adi_lamz[o] = ln;
+          }
           if (ENERGY && own) {
             m = g.V2 * rct;  // V rho c / (etabar tau)
             if (X != 0.0) eQ = fma(zg.etabar * I.tau * g.V2, X, eQ);

@@ -174,6 +174,11 @@ struct StepArgs {
   long long n_steps;
   double* energy;        // [n_inst][5] or null
   unsigned* err;         // error word: bit0 non-finite, bit1 barrier timeout
+  // ADI variant, first half step (or null): rho c / tau, Lambda_j[T] and the
+  // axial face conductivity lambda_{i,j+1/2} at the regular nodes, [node]
+  double* adi_rct;
+  double* adi_lj;
+  double* adi_lamz;
   // launch shape
   int threads;           // threads per block (64, 128 or 256)
   // persistent launches: grid barrier state [count, generation], bounded wait
@@ -205,6 +210,32 @@ struct AdjArgs {
   double* grad;          // [sum_k (2 + 2 L_k)]
   const int* n_layers;   // per instance
 };
+
+// ADI variant, axial half step: one warp per column of regular nodes.
+struct AdiTask {
+  int inst;
+  int i;
+};
+
+struct AdiArgs {
+  const DevInst* insts;
+  int n_inst;
+  const AdiTask* tasks;
+  int n_tasks;
+  int rows_max;          // rows per lane of the longest column segment
+  const double* Tn;      // T^n, all instances
+  double* Tx;            // T* in, T^{n+1} out
+  const double* rct;     // rho c / (tau/2) at T^n, [node]
+  const double* lj;      // Lambda_j[T^n], [node]
+  const double* lamz;    // lambda_{i,j+1/2} at T^n, [node]
+  double* scr;           // [3][n_tasks][rows_max][32]: c', a', d' of the column solves
+  double* trace;         // [n_inst][n_steps][2] or null
+  long long step;
+  long long n_steps;
+  unsigned* err;
+};
+int launch_adi_axial(const AdiArgs& a, void* stream);
+int launch_adi_finish(const AdiArgs& a, void* stream);
 
 // kernels (ccell_step.cu)
 int launch_waveform(const DevInst* insts, int n_inst, long long n_steps, double t0,
