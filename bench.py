@@ -225,6 +225,8 @@ def run_ours(args, world, rank, local):
     batched = run_batched(args, dev) if "batched" in args.parts else {"skipped": True}
     adjoint = run_adjoint(args, dev) if "adjoint" in args.parts else {"skipped": True}
     paper = run_paper(args, dev) if "paper" in args.parts else {"skipped": True}
+    adi = (run_adi(args, dev, ms / (args.steps * n_in)) if "adi" in args.parts
+           else {"skipped": True})
 
     if rank != 0:
         return None
@@ -261,6 +263,7 @@ def run_ours(args, world, rank, local):
         "batched": batched,
         "adjoint": adjoint,
         "paper_cell": paper,
+        "adi": adi,
         "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": int(hT.numel() * 8),
                 "d2h_bytes_per_step": int(hOut.numel() * 8 + hTr.numel() * 8)},
         "gpu_launches": int(launches),
@@ -401,6 +404,58 @@ def run_paper(args, dev) -> dict:
             "projected_25ms_run_s": nodes * 1e5 / rate}
 
 
+def run_adi(args, dev, main_ms_per_time_step: float) -> dict:
+    """ADI variant (Peaceman-Rachford, implicit in r and z) on the 512x4096
+    workload at dt = 0.25 us, the time step that workload is configured with
+    (625 x the explicit bound of the paper's scheme): time per step, and the
+    simulated time per wall second against the paper's scheme at its stable
+    0.4 ns.  Accuracy cost: both from the same field over args.adi_check_us
+    microseconds across the end of a heater pulse, max |dT| between them."""
+    import torch
+
+    from paper_1408_5853_gb300 import ccell, inputs
+    cfg = inputs.production_case()
+    nodes = cfg["nr"] * cfg["nz"]
+    T0 = inputs.initial_field(cfg, "smooth", seed=0)
+    dt = 2.5e-7
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    sol = ccell.Solver(cfg)
+    T = torch.tensor(T0.ravel(), dtype=torch.float64, device=dev)
+    tr = torch.zeros(2 * args.adi_steps, dtype=torch.float64, device=dev)
+    sol.step_adi(T, 5, 0.0, dt)  # warm-up, sizes the scratch
+    sol.sync()
+    flush.fill_(1.0)
+    l0 = ccell.cc_kernel_launches()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    sol.step_adi(T, args.adi_steps, 5 * dt, dt, tr)
+    e1.record()
+    torch.cuda.synchronize()
+    launches = ccell.cc_kernel_launches() - l0
+    sol.sync()
+    ms = e0.elapsed_time(e1) / args.adi_steps
+    # accuracy against the paper's scheme over the same simulated interval
+    t_span = args.adi_check_us * 1e-6
+    t0 = 1.0e-3 - 0.5 * t_span
+    Ta = torch.tensor(T0.ravel(), dtype=torch.float64, device=dev)
+    Tm = Ta.clone()
+    sol.step_adi(Ta, int(round(t_span / dt)), t0, dt)
+    solm = ccell.Solver(cfg)
+    solm.step(Tm, int(round(t_span / cfg["dt"])), t0, cfg["dt"], None, None)
+    solm.sync()
+    sol.sync()
+    err = float((Ta - Tm).abs().max().item())
+    solm.close()
+    sol.close()
+    return {"dt_s": dt, "value": nodes / (ms / 1e3), "unit": "node-updates/s",
+            "ms_per_step": ms, "launches_per_step": launches / args.adi_steps,
+            "simulated_s_per_wall_s": dt / (ms / 1e3),
+            "paper_scheme_simulated_s_per_wall_s": cfg["dt"] / (main_ms_per_time_step / 1e3),
+            "check": {"simulated_us": args.adi_check_us,
+                      "max_dT_vs_paper_scheme_K": err,
+                      "paper_scheme_dt_s": cfg["dt"]}}
+
+
 def mixed_accuracy(cfg, T0, n, dev) -> dict:
     """Mixed path against the FP64 path (itself parity-checked against the
     oracle to 1e-9 K) from the same FP32-rounded field, n steps from t = 0
@@ -488,7 +543,10 @@ def main():
     ap.add_argument("--ref-inner", type=int, default=60, help="time steps per reference step")
     ap.add_argument("--cpu-sample-steps", type=int, default=300)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--parts", default="fp64,mixed,batched,adjoint,paper",
+    ap.add_argument("--adi-steps", type=int, default=200, help="timed ADI steps")
+    ap.add_argument("--adi-check-us", type=float, default=10.0,
+                    help="simulated microseconds of the ADI accuracy check")
+    ap.add_argument("--parts", default="fp64,mixed,batched,adjoint,paper,adi",
                     help="comma list of extra parts to run besides the FP64 headline")
     ap.add_argument("--batch-instances", type=int, default=256)
     ap.add_argument("--batch-inner", type=int, default=20, help="time steps per batched replay")

@@ -40,13 +40,17 @@ __global__ void __launch_bounds__(128) adi_axial_kernel(const AdiArgs a) {
     double pc = 0.0, pa = 0.0, pd = 0.0;
     double Dacc = 0.0, Aacc = 0.0, P = 1.0;
     double ae = 0.0, be = 1.0, ce = 0.0, de = 0.0;
+    double ls = a.lamz[col + (long long)(lo - 1) * nr];  // face (j-1, j), carried down
+#pragma unroll 4
     for (int k = 0; k < cnt; ++k) {
       const int j = lo + k;
       const long long o = col + (long long)j * nr;
       const ZGeo& zg = I.zg[j];
       const double rct = a.rct[o];
-      double ra = -zg.gzs * a.lamz[o - nr];  // face (j-1, j)
-      double rc = -zg.gzn * a.lamz[o];       // face (j, j+1)
+      const double ln = a.lamz[o];           // face (j, j+1)
+      double ra = -zg.gzs * ls;
+      double rc = -zg.gzn * ln;
+      ls = ln;
       double rb = rct - ra - rc;
       double rd = fma(rct, 2.0 * a.Tx[o] - a.Tn[o], -a.lj[o]);
       if (j == 1) {  // T_0 = T_1 or T_D folded into the row
@@ -95,22 +99,31 @@ __global__ void __launch_bounds__(128) adi_axial_kernel(const AdiArgs a) {
   }
 }
 
-// One block per instance: non-regular columns, axial boundary rows, trace.
+// Lines per block of the completion kernel.
+constexpr int kFinishLines = 16;
+
+// Blocks over (line range, instance): the non-regular columns of the lines,
+// then the axial boundary rows (by the blocks owning lines 1 and M-1) and the
+// trace (block partial sums, one atomic per block).
 __global__ void __launch_bounds__(256) adi_finish_kernel(const AdiArgs a) {
-  const int k = blockIdx.x;
+  const int k = blockIdx.y;
   const DevInst& I = a.insts[k];
   const int nr = I.nr, N = nr - 1, M = I.nz - 1;
+  const int j_lo = 1 + blockIdx.x * kFinishLines;
+  if (j_lo > M - 1) return;  // block-uniform
+  const int j_hi = min(M - 1, j_lo + kFinishLines - 1);
+  const int nj = j_hi - j_lo + 1;
   const double* Tn = a.Tn + I.t_off;
   double* X = a.Tx + I.t_off;
   bool bad = false;
   // interface nodes: lm (T_i - T_i-1)/h_i = lp (T_i+1 - T_i)/h_i+1, lambda at T^n
   const int n_if = I.n_if;
-  for (int it = threadIdx.x; it < (M - 1) * n_if; it += blockDim.x) {
+  for (int it = threadIdx.x; it < nj * n_if; it += blockDim.x) {
     const int jj = it / n_if;
     const int i = I.if_i[it - jj * n_if];
     const RowGeo& g = I.rg[i];
     if (g.cls != RC_IFACE) continue;
-    const long long o = (long long)(jj + 1) * nr + i;
+    const long long o = (long long)(j_lo + jj) * nr + i;
     double lm, lp;
     if (I.interface_rule == 0) {
       lm = lam_eval(I.mat[g.segw], Tn[o]);
@@ -124,23 +137,30 @@ __global__ void __launch_bounds__(256) adi_finish_kernel(const AdiArgs a) {
     X[o] = x;
   }
   // axis and r_max columns
-  for (int j = 1 + threadIdx.x; j <= M - 1; j += blockDim.x) {
+  for (int j = j_lo + threadIdx.x; j <= j_hi; j += blockDim.x) {
     const long long o = (long long)j * nr;
     X[o] = X[o + 1];
     X[o + N] = (I.bc_rmax == CC_DIRICHLET) ? I.t_d : X[o + N - 1];
   }
   if (bad) atomicOr(a.err, 1u);
   __syncthreads();
-  // axial boundary rows
-  for (int i = threadIdx.x; i < nr; i += blockDim.x) {
-    X[i] = (I.bc_z0 == CC_DIRICHLET) ? I.t_d : X[nr + i];
-    X[(long long)M * nr + i] = (I.bc_zmax == CC_DIRICHLET) ? I.t_d : X[(long long)(M - 1) * nr + i];
-  }
-  __syncthreads();
+  // axial boundary rows, from lines 1 and M-1 (complete now)
+  if (j_lo == 1)
+    for (int i = threadIdx.x; i < nr; i += blockDim.x)
+      X[i] = (I.bc_z0 == CC_DIRICHLET) ? I.t_d : X[nr + i];
+  if (j_hi == M - 1)
+    for (int i = threadIdx.x; i < nr; i += blockDim.x)
+      X[(long long)M * nr + i] = (I.bc_zmax == CC_DIRICHLET) ? I.t_d : X[(long long)(M - 1) * nr + i];
   if (a.trace) {  // That(r_max, z_0) and the trapezoid-weighted mean over z
-    __shared__ double part[32];
+    __syncthreads();
+    __shared__ double part[8];
     double s = 0.0;
-    for (int j = threadIdx.x; j <= M; j += blockDim.x) s = fma(I.zg[j].wnorm, X[(long long)j * nr + N], s);
+    for (int j = j_lo + threadIdx.x; j <= j_hi; j += blockDim.x)
+      s = fma(I.zg[j].wnorm, X[(long long)j * nr + N], s);
+    if (threadIdx.x == 0) {
+      if (j_lo == 1) s = fma(I.zg[0].wnorm, X[N], s);
+      if (j_hi == M - 1) s = fma(I.zg[M].wnorm, X[(long long)M * nr + N], s);
+    }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(kFull, s, o);
     if ((threadIdx.x & 31) == 0) part[threadIdx.x >> 5] = s;
@@ -149,8 +169,8 @@ __global__ void __launch_bounds__(256) adi_finish_kernel(const AdiArgs a) {
       double t = 0.0;
       for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += part[w];
       double* tr = a.trace + ((long long)k * a.n_steps + a.step) * 2;
-      tr[0] = X[N];
-      tr[1] = t;
+      if (j_lo == 1) tr[0] = X[N];
+      atomicAdd(tr + 1, t);
     }
   }
 }
@@ -173,7 +193,8 @@ int launch_adi_axial(const AdiArgs& a, void* stream) {
 }
 
 int launch_adi_finish(const AdiArgs& a, void* stream) {
-  adi_finish_kernel<<<a.n_inst, 256, 0, (cudaStream_t)stream>>>(a);
+  const dim3 grid((unsigned)((a.lines_max + kFinishLines - 1) / kFinishLines), (unsigned)a.n_inst);
+  adi_finish_kernel<<<grid, 256, 0, (cudaStream_t)stream>>>(a);
   count_launch();
   return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }

@@ -412,9 +412,13 @@ int upload(cc_ctx* c, const std::vector<double>& dts, cudaStream_t st) {
       smem = std::max(smem, tile_smem(std::min(lpc, in.d.nz - 2)));
       total_nodes += (long long)in.d.nr * (in.d.nz - 2);
     }
+    // the grid of the launch mode in use: per-step or cooperative kernels
     const int B = smem > kMaxTileSmem ? 0
-                  : c->precision == CC_FP64 ? fp64_resident_blocks(c->threads, smem)
-                                            : mixed_resident_blocks(c->threads, smem);
+                  : c->precision == CC_FP64
+                      ? (c->mode == 1 ? fp64_persistent_resident_blocks(c->threads, smem)
+                                      : fp64_resident_blocks(c->threads, smem))
+                      : (c->mode == 1 ? mixed_persistent_resident_blocks(c->threads, smem)
+                                      : mixed_resident_blocks(c->threads, smem));
     if (B > 0) {
       cta.assign(B + 1, 0);
       int k = 0, jn = 1;  // next line of instance k
@@ -848,6 +852,7 @@ int cc_step_adi_n(cc_ctx* c, void* T_dev, int64_t n_steps, double t0, double dt_
   z.tasks = c->d_adi_tasks;
   z.n_tasks = c->n_adi_tasks;
   z.rows_max = c->adi_rows;
+  for (int k = 0; k < n; ++k) z.lines_max = std::max(z.lines_max, c->inst[k].d.nz - 2);
   z.rct = a.adi_rct;
   z.lj = a.adi_lj;
   z.lamz = a.adi_lamz;
@@ -880,7 +885,7 @@ int cc_set_launch(cc_ctx* c, int32_t mode, int32_t threads, int32_t rows_per_lan
   if (!c || (mode != 0 && mode != 1) || (threads != 64 && threads != 128 && threads != 256) ||
       rows_per_lane < 2 || rows_per_lane > kRowsPerLane)
     return CC_EINVAL;
-  if (rows_per_lane != c->rows || threads != c->threads) c->tasks_dirty = true;
+  if (rows_per_lane != c->rows || threads != c->threads || mode != c->mode) c->tasks_dirty = true;
   c->mode = mode;
   c->threads = threads;
   c->rows = rows_per_lane;

@@ -223,6 +223,7 @@ struct AdiArgs {
   const AdiTask* tasks;
   int n_tasks;
   int rows_max;          // rows per lane of the longest column segment
+  int lines_max;         // largest nz - 2 over the instances
   const double* Tn;      // T^n, all instances
   double* Tx;            // T* in, T^{n+1} out
   const double* rct;     // rho c / (tau/2) at T^n, [node]
@@ -250,6 +251,9 @@ int launch_step_fp64(const StepArgs& a, void* stream);
 // dynamic shared memory: the grid of launches with per-block tile ranges.
 int fp64_resident_blocks(int threads, int smem);
 int mixed_resident_blocks(int threads, int smem);
+// The same for the persistent (cooperative) kernels.
+int fp64_persistent_resident_blocks(int threads, int smem);
+int mixed_persistent_resident_blocks(int threads, int smem);
 int launch_step_mixed(const StepArgs& a, void* stream);
 // n steps in one cooperative launch; buffers alternate Tin -> Tout -> Tin ...
 // (and lo_in/lo_out for mixed).  Returns -3 if the grid cannot be co-resident.

@@ -53,6 +53,22 @@ static int launch_mixed_persistent_variant(const StepArgs& a, long long n, cudaS
   return e == cudaSuccess ? 0 : -1;
 }
 
+template <bool ENERGY, bool TRACE>
+static int mixed_persistent_variant_resident(int threads, int smem) {
+  auto kern = steps_mixed_persistent_kernel<ENERGY, TRACE>;
+  if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxTileSmem) !=
+      cudaSuccess)
+    cudaGetLastError();
+  return resident_blocks_m(kern, threads, smem);
+}
+
+int mixed_persistent_resident_blocks(int threads, int smem) {
+  int r = mixed_persistent_variant_resident<true, true>(threads, smem);
+  r = min(r, mixed_persistent_variant_resident<true, false>(threads, smem));
+  r = min(r, mixed_persistent_variant_resident<false, true>(threads, smem));
+  return min(r, mixed_persistent_variant_resident<false, false>(threads, smem));
+}
+
 int launch_steps_mixed_persistent(const StepArgs& a, long long n, void* stream) {
   cudaStream_t st = (cudaStream_t)stream;
   const bool E = a.energy != nullptr, T = a.trace != nullptr;

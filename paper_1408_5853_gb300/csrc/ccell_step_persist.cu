@@ -55,6 +55,22 @@ static int launch_fp64_persistent_variant(const StepArgs& a, long long n, cudaSt
   return e == cudaSuccess ? 0 : -1;
 }
 
+template <bool ENERGY, bool TRACE>
+static int fp64_persistent_variant_resident(int threads, int smem) {
+  auto kern = steps_fp64_persistent_kernel<ENERGY, TRACE>;
+  if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, kTileSmemMaxP) !=
+      cudaSuccess)
+    cudaGetLastError();
+  return resident_blocks(kern, threads, smem);
+}
+
+int fp64_persistent_resident_blocks(int threads, int smem) {
+  int r = fp64_persistent_variant_resident<true, true>(threads, smem);
+  r = min(r, fp64_persistent_variant_resident<true, false>(threads, smem));
+  r = min(r, fp64_persistent_variant_resident<false, true>(threads, smem));
+  return min(r, fp64_persistent_variant_resident<false, false>(threads, smem));
+}
+
 int launch_steps_fp64_persistent(const StepArgs& a, long long n, void* stream) {
   cudaStream_t st = (cudaStream_t)stream;
   const bool E = a.energy != nullptr, T = a.trace != nullptr;
