@@ -9,7 +9,7 @@
 // of the regular nodes.  Subtracting the two equations, the second becomes
 //   rho c/(tau/2) T^n+1 - Lambda_j[T^n+1] = rho c/(tau/2) (2 T* - T^n) - Lambda_j[T^n],
 // one tridiagonal system along z per column of regular nodes (this file),
-// split over the lanes of a warp like the radial lines.  Then the non-regular
+// split over the threads of a block.  Then the non-regular
 // columns take their radial relations with the new values (axis, r_max,
 // interface rows of Eq. (cc_first_3) with lambda* at T^n), the axial
 // boundary rows are set, and the surface trace is formed.
@@ -19,35 +19,39 @@
 
 namespace ccell {
 
-__global__ void __launch_bounds__(128) adi_axial_kernel(const AdiArgs a) {
-  const int lane = threadIdx.x & 31;
-  const int n_warps = (int)((gridDim.x * blockDim.x) >> 5);
-  for (int w = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5); w < a.n_tasks; w += n_warps) {
+// One block per column of regular nodes.  Each thread eliminates its run of
+// rows downwards (c', a', d' to global scratch, coalesced over the threads),
+// the S separator rows are solved by cyclic reduction through shared memory,
+// and each thread substitutes back.  The same partitioned elimination as the
+// radial lines (solve_tile_lines), with the separators spread over the block.
+__global__ void __launch_bounds__(kAdiLanes) adi_axial_kernel(const AdiArgs a) {
+  __shared__ double sA[kAdiLanes], sB[kAdiLanes], sC[kAdiLanes], sI[kAdiLanes];
+  const int s = threadIdx.x;
+  for (int w = blockIdx.x; w < a.n_tasks; w += gridDim.x) {
     const AdiTask tk = a.tasks[w];
     const DevInst& I = a.insts[tk.inst];
     const int nr = I.nr, M = I.nz - 1, L = M - 1;  // rows j = 1 .. M-1
-    int G = 32;
-    while (G > 1 && L < 2 * G) G >>= 1;
-    const int lg = __ffs(G) - 1;
-    const int grp = lane >> lg, l = lane & (G - 1);  // groups > 0 repeat group 0, store nothing
-    const int lo = 1 + ((l * L) >> lg), hi = 1 + (((l + 1) * L) >> lg);
-    const int cnt = hi - lo;  // >= 2
+    int S = kAdiLanes;
+    while (S > 1 && L < 2 * S) S >>= 1;
+    const bool act = s < S;
+    const int lo = 1 + (int)(((long long)s * L) / S), hi = 1 + (int)(((long long)(s + 1) * L) / S);
+    const int cnt = act ? hi - lo : 0;  // >= 1
     const long long col = I.t_off + tk.i;
-    const size_t plane = (size_t)a.n_tasks * a.rows_max * 32;
-    double* Cp = a.scr + ((size_t)w * a.rows_max) * 32 + lane;
+    const size_t plane = (size_t)a.n_tasks * a.rows_max * kAdiLanes;
+    double* Cp = a.scr + ((size_t)w * a.rows_max) * kAdiLanes + s;
     double* Ap = Cp + plane;
     double* Dp = Ap + plane;
     double pc = 0.0, pa = 0.0, pd = 0.0;
     double Dacc = 0.0, Aacc = 0.0, P = 1.0;
     double ae = 0.0, be = 1.0, ce = 0.0, de = 0.0;
-    double ls = a.lamz[col + (long long)(lo - 1) * nr];  // face (j-1, j), carried down
+    double ls = act ? a.lamz[col + (long long)(lo - 1) * nr] : 0.0;  // face (j-1, j), carried
 #pragma unroll 4
     for (int k = 0; k < cnt; ++k) {
       const int j = lo + k;
       const long long o = col + (long long)j * nr;
       const ZGeo& zg = I.zg[j];
       const double rct = a.rct[o];
-      const double ln = a.lamz[o];           // face (j, j+1)
+      const double ln = a.lamz[o];  // face (j, j+1)
       double ra = -zg.gzs * ls;
       double rc = -zg.gzn * ln;
       ls = ln;
@@ -67,9 +71,9 @@ __global__ void __launch_bounds__(128) adi_axial_kernel(const AdiArgs a) {
         const double c1 = rc * r;
         const double a1 = (k == 0) ? ra * r : -ra * pa * r;
         const double d1 = (k == 0) ? rd * r : fma(-ra, pd, rd) * r;
-        Cp[(size_t)k * 32] = c1;
-        Ap[(size_t)k * 32] = a1;
-        Dp[(size_t)k * 32] = d1;
+        Cp[(size_t)k * kAdiLanes] = c1;
+        Ap[(size_t)k * kAdiLanes] = a1;
+        Dp[(size_t)k * kAdiLanes] = d1;
         Dacc = fma(P, d1, Dacc);
         Aacc = fma(P, a1, Aacc);
         P = -P * c1;
@@ -80,16 +84,52 @@ __global__ void __launch_bounds__(128) adi_axial_kernel(const AdiArgs a) {
         ae = ra; be = rb; ce = rc; de = rd;
       }
     }
-    const double xs = solve_separators(ae, be, ce, de, pa, pc, pd, Dacc, Aacc, P, G, l);
-    const double Lp = __shfl_up_sync(kFull, xs, 1, G);
-    // every group has read its rows before group 0 overwrites T* (same warp)
-    __syncwarp();
-    if (grp == 0) {
+    // separator rows in the separators of the neighbouring segments: the
+    // first interior row of segment s+1 is Dacc + P x_{s+1} - Aacc x_s
+    sA[s] = Dacc;
+    sB[s] = Aacc;
+    sC[s] = P;
+    __syncthreads();
+    const int sn = (s + 1 < S) ? s + 1 : s;  // the last separator has c = 0
+    double at = -ae * pa;
+    double bt = fma(-ae, pc, be) - ce * sB[sn];
+    double ct = ce * sC[sn];
+    double dt = fma(-ae, pd, de) - ce * sA[sn];
+    __syncthreads();
+    // parallel cyclic reduction over the S separators
+    for (int d = 1; d < S; d <<= 1) {
+      const double ib = frcp(bt);
+      sA[s] = at; sB[s] = ct; sC[s] = dt; sI[s] = ib;
+      __syncthreads();
+      double al = 0.0, ga = 0.0, am = 0.0, cm = 0.0, dm = 0.0, apv = 0.0, cpv = 0.0, dpv = 0.0;
+      if (act && s >= d) {
+        al = -at * sI[s - d];
+        am = sA[s - d]; cm = sB[s - d]; dm = sC[s - d];
+      }
+      if (act && s + d < S) {
+        ga = -ct * sI[s + d];
+        apv = sA[s + d]; cpv = sB[s + d]; dpv = sC[s + d];
+      }
+      __syncthreads();
+      const double nb = fma(ga, apv, fma(al, cm, bt));
+      const double nd = fma(ga, dpv, fma(al, dm, dt));
+      at = al * am;
+      ct = ga * cpv;
+      bt = nb;
+      dt = nd;
+    }
+    const double xs = dt * frcp(bt);
+    sA[s] = xs;
+    __syncthreads();
+    const double Lp = (s > 0) ? sA[s - 1] : 0.0;
+    __syncthreads();  // the shared arrays are reused by the next column
+    if (act) {
       bool bad = not_finite(xs);
       a.Tx[col + (long long)(hi - 1) * nr] = xs;
       double xn = xs;
       for (int k = cnt - 2; k >= 0; --k) {
-        const double x = fma(-Cp[(size_t)k * 32], xn, fma(-Ap[(size_t)k * 32], Lp, Dp[(size_t)k * 32]));
+        const double x = fma(-Cp[(size_t)k * kAdiLanes], xn,
+                             fma(-Ap[(size_t)k * kAdiLanes], Lp, Dp[(size_t)k * kAdiLanes]));
         bad |= not_finite(x);
         a.Tx[col + (long long)(lo + k) * nr] = x;
         xn = x;
@@ -176,18 +216,8 @@ __global__ void __launch_bounds__(256) adi_finish_kernel(const AdiArgs a) {
 }
 
 int launch_adi_axial(const AdiArgs& a, void* stream) {
-  constexpr int threads = 128;
-  static int resident = 0;
-  if (resident == 0) {
-    int dev = 0, sms = 0, per_sm = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, adi_axial_kernel, threads, 0);
-    resident = sms * (per_sm > 0 ? per_sm : 1);
-  }
-  const int need = (a.n_tasks * 32 + threads - 1) / threads;
-  if (need > 0)
-    adi_axial_kernel<<<need < resident ? need : resident, threads, 0, (cudaStream_t)stream>>>(a);
+  if (a.n_tasks > 0)
+    adi_axial_kernel<<<a.n_tasks, kAdiLanes, 0, (cudaStream_t)stream>>>(a);
   count_launch();
   return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }

@@ -783,9 +783,9 @@ int cc_step_adi_n(cc_ctx* c, void* T_dev, int64_t n_steps, double t0, double dt_
     for (int k = 0; k < n; ++k) {
       const Instance& in = c->inst[k];
       const int L = in.d.nz - 2;
-      int G = 32;
-      while (G > 1 && L < 2 * G) G >>= 1;
-      rows = std::max(rows, (L + G - 1) / G);
+      int S = kAdiLanes;  // segments of a column
+      while (S > 1 && L < 2 * S) S >>= 1;
+      rows = std::max(rows, (L + S - 1) / S);
       for (int i = 0; i < in.d.nr; ++i)
         if (in.cls[i] == RC_REGULAR) tasks.push_back(AdiTask{k, i});
     }
@@ -802,7 +802,7 @@ int cc_step_adi_n(cc_ctx* c, void* T_dev, int64_t n_steps, double t0, double dt_
     c->adi_rows = rows;
   }
   const size_t nodes = (size_t)c->total_nodes;
-  const size_t need = 3 * nodes + 3 * (size_t)c->n_adi_tasks * c->adi_rows * 32;
+  const size_t need = 3 * nodes + 3 * (size_t)c->n_adi_tasks * c->adi_rows * kAdiLanes;
   if (need > c->adi_scratch) {
     cudaFree(c->d_adi);
     c->d_adi = nullptr;

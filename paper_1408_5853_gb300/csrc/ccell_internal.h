@@ -211,7 +211,9 @@ struct AdjArgs {
   const int* n_layers;   // per instance
 };
 
-// ADI variant, axial half step: one warp per column of regular nodes.
+// ADI variant, axial half step: one block of kAdiLanes threads per column of
+// regular nodes, each thread a run of rows.
+constexpr int kAdiLanes = 128;
 struct AdiTask {
   int inst;
   int i;
@@ -229,7 +231,7 @@ struct AdiArgs {
   const double* rct;     // rho c / (tau/2) at T^n, [node]
   const double* lj;      // Lambda_j[T^n], [node]
   const double* lamz;    // lambda_{i,j+1/2} at T^n, [node]
-  double* scr;           // [3][n_tasks][rows_max][32]: c', a', d' of the column solves
+  double* scr;           // [3][n_tasks][rows_max][kAdiLanes]: c', a', d' of the column solves
   double* trace;         // [n_inst][n_steps][2] or null
   long long step;
   long long n_steps;
