@@ -86,7 +86,10 @@ __device__ __forceinline__ void step_mixed_tile(const StepArgs& a, const TileTas
   float* Lout = a.lo_out + I.t_off;
   const float s = (float)a.s_tab[a.step * a.n_inst + tk.inst];
   const float inv_tau = I.inv_tau_f, tau = I.tau_f;
-  double eQ = 0.0, eD = 0.0, eN = 0.0, eI = 0.0, eE = 0.0, tr = 0.0;
+  double eD = 0.0, eN = 0.0, eI = 0.0, tr = 0.0;
+  // stored and injected heat: FP32 partial sums over this thread's nodes of
+  // the tile (a few dozen terms), added to the FP64 accumulators once per tile
+  float eQf = 0.0f, eEf = 0.0f;
 
   // ---- 0a. nodal conductivities of the interface rows, Eq. (cc_first_3)
   if (I.interface_rule == 0 && n_if > 0) {
@@ -173,7 +176,7 @@ __device__ __forceinline__ void step_mixed_tile(const StepArgs& a, const TileTas
           if (ENERGY && own) {
             const float V = g.V2_f * zg.etabar_f;
             m = V * rhoc;
-            eQ += (double)(tau * V * X);
+            eQf = fmaf(tau * V, X, eQf);
             if (j == 1) {
               const double f = (double)(-tau * g.V2_f * fs / (float)zg.eta_s);
               if (I.bc_z0 == CC_DIRICHLET) eD += f; else eN += f;
@@ -247,8 +250,8 @@ __device__ __forceinline__ void step_mixed_tile(const StepArgs& a, const TileTas
       const int c = smem_col(i);
       const double xd = SB[(size_t)q * nrp + c];
       bad |= not_finite(xd);
-      if (ENERGY) eE = fma((double)FM[(size_t)q * nrp + c], xd, eE);
       const float x = __double2float_rn(xd);
+      if (ENERGY) eEf = fmaf(FM[(size_t)q * nrp + c], x, eEf);
       const float hi = ld_state<CACHED>(Hin + rj + i), lo = ld_state<CACHED>(Lin + rj + i);
       const float v = lo + x;
       const float h1 = hi + v;
@@ -299,8 +302,8 @@ __device__ __forceinline__ void step_mixed_tile(const StepArgs& a, const TileTas
           eI += fw + (double)K[3] * ((double)K[5] + (x - Bq[smem_col(i + 1)]));
         }
       }
-      acc.e[0] += eE;
-      acc.e[1] += eQ;
+      acc.e[0] += (double)eEf;
+      acc.e[1] += (double)eQf;
       acc.e[2] += eD;
       acc.e[3] += eI;
       acc.e[4] += eN;
