@@ -17,7 +17,8 @@
 //  adj_gather_kernel  per node: dJ/dT^n from xi of the node's own row and of
 //                     the four neighbouring rows that read its temperature
 //                     (no atomics on the field), plus the parameter terms of
-//                     its own row (block-reduced, one atomic per block).
+//                     its own row (shuffle sums per warp, shared sums per
+//                     block, one global atomic per block and parameter).
 #include <cuda_runtime.h>
 
 #include "ccell_device.cuh"
@@ -246,6 +247,11 @@ __global__ void __launch_bounds__(256) adj_gather_kernel(const AdjArgs a) {
   const int L = a.n_layers[inst];
   if (threadIdx.x < kGradMax) sg[threadIdx.x] = 0.0;
   __syncthreads();
+  // this node's parameter terms: q0, t_on, lam_scale[mL], cap_scale[mC]
+  // (a second lam_scale term at mL2 for interface rows); summed over the warp
+  // per parameter below, so that the block's shared sums see one add per warp
+  double pq = 0.0, pt = 0.0, pl = 0.0, pl2 = 0.0, pc = 0.0;
+  int mL = -1, mL2 = -1, mC = -1;
   const long long node = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (node < (long long)nr * I.nz) {
     const int j = (int)(node / nr), i = (int)(node - (long long)j * nr);
@@ -319,11 +325,13 @@ __global__ void __launch_bounds__(256) adj_gather_kernel(const AdjArgs a) {
         // parameters of this row
         const double lam_part =
             fma(g.gC * lE, ge, fma(g.gA * lW, gw, fma(lN * zg.gzn, dN, -lS * zg.gzs * dS)));
-        atomicAdd(&sg[2 + m], xi * lam_part * Mt.inv_lam_scale);
-        atomicAdd(&sg[2 + L + m], xi * rct * (T - yi) * Mt.inv_cap_scale);
+        pl = xi * lam_part * Mt.inv_lam_scale;
+        mL = m;
+        pc = xi * rct * (T - yi) * Mt.inv_cap_scale;
+        mC = m;
         if (heat) {
-          atomicAdd(&sg[0], xi * a.s_tab[sidx] * gT);
-          atomicAdd(&sg[1], xi * I.q0 * a.ds_tab[sidx] * gT);
+          pq = xi * a.s_tab[sidx] * gT;
+          pt = xi * I.q0 * a.ds_tab[sidx] * gT;
         }
       }
     } else if (g.cls == RC_IFACE && line) {
@@ -343,10 +351,25 @@ __global__ void __launch_bounds__(256) adj_gather_kernel(const AdjArgs a) {
         dlp = g.re * lEa;
       }
       acc = fma(xi, fma(dlm * g.he, gw, dlp * g.hw * ge), acc);
-      atomicAdd(&sg[2 + mi], xi * lm * g.he * gw * I.mat[mi].inv_lam_scale);
-      atomicAdd(&sg[2 + mo], xi * lp * g.hw * ge * I.mat[mo].inv_lam_scale);
+      pl = xi * lm * g.he * gw * I.mat[mi].inv_lam_scale;
+      mL = mi;
+      pl2 = xi * lp * g.hw * ge * I.mat[mo].inv_lam_scale;
+      mL2 = mo;
     }
     a.lam_out[I.t_off + rj + i] = acc;
+  }
+  // warp sums per parameter (the block is warp-uniform here)
+  for (int p = 0; p < 2 + 2 * L; ++p) {
+    double v;
+    if (p == 0) v = pq;
+    else if (p == 1) v = pt;
+    else if (p < 2 + L) v = (mL == p - 2 ? pl : 0.0) + (mL2 == p - 2 ? pl2 : 0.0);
+    else v = (mC == p - 2 - L) ? pc : 0.0;
+    if (__any_sync(kFull, v != 0.0)) {
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(kFull, v, o);
+      if ((threadIdx.x & 31) == 0) atomicAdd(&sg[p], v);
+    }
   }
   __syncthreads();
   if (threadIdx.x < 2 + 2 * L && sg[threadIdx.x] != 0.0)
