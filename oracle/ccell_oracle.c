@@ -75,6 +75,10 @@ typedef struct {
   double edge_w;                   /* s, tanh edge width                 */
   int g_model;                     /* 0: g = 1, 1: g = g_ref/sqrt(T)     */
   double g_ref;
+  /* stepped outline (reading A20): 0 = rectangle; k >= 1: beyond z_step
+   * only the k innermost layers continue */
+  int step_layers;
+  double z_step;                   /* metres                             */
 } or_problem;
 
 /* ------------------------------------------------------------------ */
@@ -161,6 +165,42 @@ int or_grid(const or_problem* p, double* r, double* z, int* rclass, int* seg) {
     for (int j = 0; j <= M; j++) z[j] = ((double)j - lo) * eta;
   }
   return 0;
+}
+
+/* Stepped outline of the domain, r in [0, r_max(z)], z in [0, z_max(r)]
+ * (Section 2; reading A20).  The paper's cell has its outer layers only on
+ * z in [0, z_0] (the working surface r = r_max, Section 5); beyond z_0 the
+ * inner layers continue alone to the thermostat end z_max.  Here: the lines
+ * j with z_j > z_step (j >= j_narrow) hold only the step_layers innermost
+ * layers; their outer node is the interface node i_step that starts layer
+ * step_layers, and it takes the r_max closure; nodes i > i_step of those
+ * lines lie outside the domain.  A rectangle gives j_narrow = nz, i_step = N.
+ * Returns 0, or -1 for an outline this scheme does not take (vertex
+ * placement only; line 1 must be a full-width line). */
+int or_outline(const or_problem* p, const double* z, const int* rclass, int* i_step,
+               int* j_narrow) {
+  const int N = p->nr - 1, M = p->nz - 1;
+  *i_step = N;
+  *j_narrow = p->nz;
+  if (p->step_layers == 0) return 0;
+  if (p->step_layers < 0 || p->step_layers >= p->n_layers || p->placement != 0) return -1;
+  int k = 0;
+  for (int i = 1; i < N; i++)
+    if (rclass[i] == OR_IFACE && ++k == p->step_layers) { *i_step = i; break; }
+  if (k != p->step_layers) return -1;
+  /* a node on the step face belongs to the full-width part */
+  const double zs = p->z_step + 1e-9 * p->length;
+  for (int j = 0; j <= M; j++)
+    if (z[j] > zs) { *j_narrow = j; break; }
+  if (*j_narrow < 2) return -1;
+  return 0;
+}
+
+/* 1 if the outline is a rectangle (no narrow line): the ADI variant and the
+ * adjoint take rectangles only */
+static int rect_outline(const or_problem* p, const double* z, const int* cls) {
+  int i_step, j_narrow;
+  return or_outline(p, z, cls, &i_step, &j_narrow) == 0 && j_narrow == p->nz;
 }
 
 /* ------------------------------------------------------------------ */
@@ -298,7 +338,9 @@ int or_step_n(const or_problem* p, double* T, long n_steps, double t0, double ta
   int* seg = (int*)malloc(sizeof(int) * (N + 1));
   double* Th = (double*)malloc(sizeof(double) * (size_t)nr * (M + 1));
   double* part = (double*)malloc(sizeof(double) * 5 * (size_t)(M + 1)); /* per line */
-  if (!r || !z || !cls || !seg || !Th || !part || or_grid(p, r, z, cls, seg)) {
+  int i_step = 0, j_narrow = 0;
+  if (!r || !z || !cls || !seg || !Th || !part || or_grid(p, r, z, cls, seg) ||
+      or_outline(p, z, cls, &i_step, &j_narrow)) {
     free(r); free(z); free(cls); free(seg); free(Th); free(part);
     return -1;
   }
@@ -321,11 +363,15 @@ int or_step_n(const or_problem* p, double* T, long n_steps, double t0, double ta
         double* Thj = Th + (size_t)j * nr;
         const double eta_s = z[j] - z[j - 1], eta_n = z[j + 1] - z[j];
         const double etabar = 0.5 * (eta_n + eta_s);
+        /* outer node of this line; lines j +- 1 narrower than this one
+         * close the axial faces of the columns beyond their outer node */
+        const int Nj = (j >= j_narrow) ? i_step : N;
+        const int wide_s = (j - 1 < j_narrow), wide_n = (j + 1 < j_narrow);
 
         /* forward sweep, Eqs. (front_sweep), (ABC), (cc_first_3) */
         alpha[0] = 1.0;                     /* Eq. (alphabeta_ini) */
         beta[0] = 0.0;
-        for (int i = 1; i <= N - 1; i++) {
+        for (int i = 1; i <= Nj - 1; i++) {
           const double h_w = r[i] - r[i - 1], h_e = r[i + 1] - r[i];
           if (cls[i] == OR_IFACE) {
             const int mi = seg[i - 1], mo = seg[i];
@@ -353,11 +399,14 @@ int or_step_n(const or_problem* p, double* T, long n_steps, double t0, double ta
           const double r_w = 0.5 * (r[i] + r[i - 1]), r_e = 0.5 * (r[i] + r[i + 1]);
           const double lw = lam_face(p, m, Tj[i - 1], T0);
           const double le = lam_face(p, m, T0, Tj[i + 1]);
-          const double ls = lam_face(p, m, Ts[i], T0);
-          const double ln = lam_face(p, m, T0, Tn[i]);
           const double rc = p->rho[m] * cap_m(p, m, T0);
-          /* Eq. (Lambda_j), explicit in T */
-          const double Lj = (ln * (Tn[i] - T0) / eta_n - ls * (T0 - Ts[i]) / eta_s) / etabar;
+          /* Eq. (Lambda_j), explicit in T; no heat crosses a face to a node
+           * outside the domain (Eq. (boundcond)) */
+          const double fn = (wide_n || i <= i_step)
+                                ? lam_face(p, m, T0, Tn[i]) * (Tn[i] - T0) / eta_n : 0.0;
+          const double fs = (wide_s || i <= i_step)
+                                ? lam_face(p, m, Ts[i], T0) * (T0 - Ts[i]) / eta_s : 0.0;
+          const double Lj = (fn - fs) / etabar;
           const double X = source(p, m, T0, s);
           /* Eq. (ABC) */
           const double A = -r_w * lw / (r[i] * hbar * h_w);
@@ -369,17 +418,20 @@ int or_step_n(const or_problem* p, double* T, long n_steps, double t0, double ta
           beta[i] = (F - A * beta[i - 1]) / den;
         }
         /* Eq. (T_ini_for_back_sweep) or the Dirichlet value */
-        Thj[N] = (p->bc_rmax == 0) ? beta[N - 1] / (1.0 - alpha[N - 1]) : p->t_dirichlet;
-        for (int i = N - 1; i >= 0; i--) Thj[i] = alpha[i] * Thj[i + 1] + beta[i]; /* Eq. (back_sweep) */
+        Thj[Nj] = (p->bc_rmax == 0) ? beta[Nj - 1] / (1.0 - alpha[Nj - 1]) : p->t_dirichlet;
+        for (int i = Nj - 1; i >= 0; i--) Thj[i] = alpha[i] * Thj[i + 1] + beta[i]; /* Eq. (back_sweep) */
+        for (int i = Nj + 1; i <= N; i++) Thj[i] = Tj[i];  /* outside the domain */
       }
       free(alpha);
       free(beta);
     }
 
-    /* axial boundary rows */
+    /* axial boundary rows (line 0 always has the full width) */
+    const int NM = (M >= j_narrow) ? i_step : N;
     for (int i = 0; i <= N; i++) {
       Th[i] = p->bc_z0 ? p->t_dirichlet : Th[(size_t)nr + i];
-      Th[(size_t)M * nr + i] = p->bc_zmax ? p->t_dirichlet : Th[(size_t)(M - 1) * nr + i];
+      Th[(size_t)M * nr + i] = (i > NM) ? T[(size_t)M * nr + i]
+                               : p->bc_zmax ? p->t_dirichlet : Th[(size_t)(M - 1) * nr + i];
     }
 
     /* energy terms of this step, per line then summed in line order */
@@ -393,7 +445,8 @@ int or_step_n(const or_problem* p, double* T, long n_steps, double t0, double ta
         const double eta_s = z[j] - z[j - 1], eta_n = z[j + 1] - z[j];
         const double etabar = 0.5 * (eta_n + eta_s);
         double e[5] = {0, 0, 0, 0, 0}, c[5] = {0, 0, 0, 0, 0};
-        for (int i = 1; i <= N - 1; i++) {
+        const int Nj = (j >= j_narrow) ? i_step : N;
+        for (int i = 1; i <= Nj - 1; i++) {
           if (cls[i] != OR_REGULAR) continue;
           const int m = seg[i];
           const double h_w = r[i] - r[i - 1], h_e = r[i + 1] - r[i];
@@ -408,10 +461,11 @@ int or_step_n(const or_problem* p, double* T, long n_steps, double t0, double ta
                        (Hj[i - 1] - Hj[i]) / h_w;
             kadd(cls[i - 1] == OR_IFACE ? &e[3] : &e[4], cls[i - 1] == OR_IFACE ? &c[3] : &c[4], f);
           }
-          if (cls[i + 1] != OR_REGULAR) {
+          const int ce = (i + 1 == Nj) ? OR_OUTER : cls[i + 1];  /* outer node of the line */
+          if (ce != OR_REGULAR) {
             double f = tau * two_pi * etabar * r_e * lam_face(p, m, Tj[i], Tj[i + 1]) *
                        (Hj[i + 1] - Hj[i]) / h_e;
-            int k = (cls[i + 1] == OR_IFACE) ? 3 : (p->bc_rmax ? 2 : 4);
+            int k = (ce == OR_IFACE) ? 3 : (p->bc_rmax ? 2 : 4);
             kadd(&e[k], &c[k], f);
           }
           /* axial edges to the boundary rows (explicit fluxes) */
@@ -421,7 +475,7 @@ int or_step_n(const or_problem* p, double* T, long n_steps, double t0, double ta
             int k = p->bc_z0 ? 2 : 4;
             kadd(&e[k], &c[k], f);
           }
-          if (j == M - 1) {
+          if (j == M - 1 && i <= NM) {
             double f = tau * two_pi * r[i] * hbar * lam_face(p, m, Tj[i], Tn[i]) *
                        (Tn[i] - Tj[i]) / eta_n;
             int k = p->bc_zmax ? 2 : 4;
@@ -437,11 +491,12 @@ int or_step_n(const or_problem* p, double* T, long n_steps, double t0, double ta
     memcpy(T, Th, sizeof(double) * (size_t)nr * (M + 1));
 
     if (trace) {
+      /* trapezoid over the r = r_max surface, the full-width lines */
       double wsum = 0.0, acc = 0.0;
-      for (int j = 0; j <= M; j++) {
+      for (int j = 0; j <= M && j < j_narrow; j++) {
         double w = 0.0;
         if (j > 0) w += 0.5 * (z[j] - z[j - 1]);
-        if (j < M) w += 0.5 * (z[j + 1] - z[j]);
+        if (j < M && j + 1 < j_narrow) w += 0.5 * (z[j + 1] - z[j]);
         wsum += w;
         acc += w * T[(size_t)j * nr + N];
       }
@@ -486,7 +541,8 @@ int or_step_adi_n(const or_problem* p, double* T, long n_steps, double t0, doubl
   int* seg = (int*)malloc(sizeof(int) * (N + 1));
   double* Ts = (double*)malloc(sizeof(double) * nn);  /* T*     */
   double* Tn = (double*)malloc(sizeof(double) * nn);  /* T^n+1  */
-  if (!r || !z || !cls || !seg || !Ts || !Tn || or_grid(p, r, z, cls, seg)) {
+  if (!r || !z || !cls || !seg || !Ts || !Tn || or_grid(p, r, z, cls, seg) ||
+      !rect_outline(p, z, cls)) {
     free(r); free(z); free(cls); free(seg); free(Ts); free(Tn);
     return -1;
   }
@@ -714,7 +770,8 @@ int or_step_vjp(const or_problem* p, const double* x, const double* y, double* m
   double* xi = (double*)malloc(sizeof(double) * (N + 1));
   double* cw = (double*)malloc(sizeof(double) * (N + 1));
   double* dw = (double*)malloc(sizeof(double) * (N + 1));
-  if (!r || !z || !cls || !seg || !a || !b || !c || !xi || !cw || !dw || or_grid(p, r, z, cls, seg)) {
+  if (!r || !z || !cls || !seg || !a || !b || !c || !xi || !cw || !dw || or_grid(p, r, z, cls, seg) ||
+      !rect_outline(p, z, cls)) {
     free(r); free(z); free(cls); free(seg); free(a); free(b); free(c); free(xi); free(cw); free(dw);
     return -1;
   }
@@ -870,7 +927,7 @@ int or_adjoint(const or_problem* p, const double* T0, long n_steps, double t0, d
   int* seg = (int*)malloc(sizeof(int) * (N + 1));
   int rc = -1;
   if (!ck || !seg_states || !trace || !lam || !lam2 || !w || !r || !z || !cls || !seg ||
-      or_grid(p, r, z, cls, seg))
+      or_grid(p, r, z, cls, seg) || !rect_outline(p, z, cls))
     goto done;
   {
     double wsum = 0.0;

@@ -76,6 +76,8 @@ class Problem(ctypes.Structure):
         ("edge_w", ctypes.c_double),
         ("g_model", ctypes.c_int),
         ("g_ref", ctypes.c_double),
+        ("step_layers", ctypes.c_int),
+        ("z_step", ctypes.c_double),
     ]
 
 
@@ -89,6 +91,8 @@ def _load():
         ip = ctypes.POINTER(ctypes.c_int)
         lib.or_grid.argtypes = [P, dp, dp, ip, ip]
         lib.or_grid.restype = ctypes.c_int
+        lib.or_outline.argtypes = [P, dp, ip, ip, ip]
+        lib.or_outline.restype = ctypes.c_int
         lib.or_step_n.argtypes = [P, dp, ctypes.c_long, ctypes.c_double, ctypes.c_double, dp, dp]
         lib.or_step_n.restype = ctypes.c_int
         lib.or_step_adi_n.argtypes = [P, dp, ctypes.c_long, ctypes.c_double, ctypes.c_double, dp]
@@ -153,6 +157,10 @@ def problem(cfg: dict) -> Problem:
         p.edge_w = src.get("edge_w", 0.0)
         p.g_model = src.get("g_model", 0)
         p.g_ref = src.get("g_ref", 0.0)
+    step = cfg.get("step")
+    if step is not None:
+        p.step_layers = step["layers"]
+        p.z_step = step["z"]
     return p
 
 
@@ -168,6 +176,20 @@ def grid(cfg: dict) -> dict:
     if rc != 0:
         raise ValueError("oracle rejected the grid description")
     return {"r": r, "z": z, "rclass": cls, "seg": seg}
+
+
+def outline(cfg: dict) -> tuple:
+    """(i_step, j_narrow) of the stepped outline: the lines j >= j_narrow end at
+    the radial node i_step; a rectangle gives (nr - 1, nz)."""
+    lib = _load()
+    p = problem(cfg)
+    g = grid(cfg)
+    i_step = np.zeros(1, dtype=np.int32)
+    j_narrow = np.zeros(1, dtype=np.int32)
+    if lib.or_outline(ctypes.byref(p), _dp(g["z"]), _ip(g["rclass"]), _ip(i_step),
+                      _ip(j_narrow)) != 0:
+        raise ValueError("oracle rejected the outline")
+    return int(i_step[0]), int(j_narrow[0])
 
 
 def step_n(cfg: dict, T: np.ndarray, n_steps: int, t0: float, dt: float,

@@ -1,0 +1,66 @@
+"""The C ABI on a machine without a GPU: the library loads, exports every
+function include/ccell.h declares, and its host-only queries (grid, stepped
+outline, status strings) agree with the oracle's grid and outline."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+from oracle import oracle
+from paper_1408_5853_gb300 import ccell, inputs
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "ccell.h")
+
+
+def declared_functions():
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", " ", text, flags=re.S)  # drop comments
+    text = re.sub(r"//[^\n]*", " ", text)
+    return sorted(set(re.findall(r"\b(cc_[a-z0-9_]+)\s*\(", text)))
+
+
+def test_library_exports_every_declared_function():
+    names = declared_functions()
+    assert len(names) >= 15, names
+    lib = ctypes.CDLL(ccell.library_path())
+    missing = [n for n in names if not hasattr(lib, n)]
+    assert not missing, missing
+
+
+def test_status_strings():
+    for code in range(0, -9, -1):
+        s = ccell.cc_status_string(code)
+        assert s and "unknown" not in s.lower(), (code, s)
+
+
+@pytest.mark.parametrize("case", ["small", "production", "paper"])
+def test_host_grid_matches_oracle_grid(case):
+    cfg = {"small": inputs.small_case(q0=1.0), "production": inputs.production_case(),
+           "paper": inputs.paper_case(128, 301)}[case]
+    r, z, cls = ccell.cc_query_grid(ccell.geometry_desc(cfg))
+    g = oracle.grid(cfg)
+    np.testing.assert_allclose(r, g["r"], rtol=1e-15, atol=0.0)
+    np.testing.assert_allclose(z, g["z"], rtol=1e-15, atol=0.0)
+    assert np.array_equal(np.asarray(cls), g["rclass"])
+
+
+@pytest.mark.parametrize("layers,z_step", [(1, 4e-3), (2, 6e-3), (3, 9.99e-3), (1, 20e-3)])
+def test_host_outline_matches_oracle_outline(layers, z_step):
+    cfg = inputs.small_case(q0=1.0)
+    cfg["step"] = dict(layers=layers, z=z_step)
+    assert ccell.cc_query_outline(ccell.geometry_desc(cfg)) == oracle.outline(cfg)
+
+
+def test_outline_rejections():
+    cfg = inputs.small_case(q0=1.0)
+    for step in (dict(layers=4, z=5e-3),       # as many layers as the cylinder
+                 dict(layers=1, z=0.01e-3),    # line 1 would be narrow
+                 dict(layers=-1, z=5e-3)):
+        cfg["step"] = step
+        with pytest.raises(ccell.CCError):
+            ccell.cc_query_outline(ccell.geometry_desc(cfg))
+        with pytest.raises(ValueError):
+            oracle.outline(cfg)

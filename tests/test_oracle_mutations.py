@@ -18,9 +18,9 @@ MUTATIONS = {
     "wrong face radius in A (r_e for r_w)":
         ("const double A = -r_w * lw", "const double A = -r_e * lw"),
     "sign of the south flux in Lambda_j":
-        ("- ls * (T0 - Ts[i]) / eta_s", "+ ls * (T0 - Ts[i]) / eta_s"),
+        ("const double Lj = (fn - fs) / etabar;", "const double Lj = (fn + fs) / etabar;"),
     "north face conductivity from the south neighbour":
-        ("const double ln = lam_face(p, m, T0, Tn[i]);", "const double ln = lam_face(p, m, T0, Ts[i]);"),
+        ("? lam_face(p, m, T0, Tn[i]) * (Tn[i] - T0) / eta_n", "? lam_face(p, m, T0, Ts[i]) * (Tn[i] - T0) / eta_n"),
     "face conductivity at one node instead of the face mean":
         ("return lam_m(p, m, 0.5 * (Ta + Tb));", "return lam_m(p, m, Ta);"),
     "heat capacity saturation squared instead of cubed":
@@ -33,7 +33,7 @@ MUTATIONS = {
     "source term dropped from F":
         ("F = rc / tau * T0 + Lj + X;", "F = rc / tau * T0 + Lj;"),
     "Neumann closure at r_max dropped":
-        ("beta[N - 1] / (1.0 - alpha[N - 1])", "beta[N - 1]"),
+        ("beta[Nj - 1] / (1.0 - alpha[Nj - 1])", "beta[Nj - 1]"),
     "sign of alpha in the forward sweep":
         ("alpha[i] = -C / den;", "alpha[i] = C / den;"),
     "stability bound with eta instead of eta^2":
@@ -55,6 +55,20 @@ MUTATIONS = {
         ("return 0.5 * (1.0 - th * th) / p->edge_w;", "return -0.5 * (1.0 - th * th) / p->edge_w;"),
     "adjoint: Neumann row z=0 not folded into line 1":
         ("if (!p->bc_z0) mu[(size_t)nr + i] += mu[i];", "(void)0;"),
+    # stepped outline
+    "outline: axial face to an outside node left open":
+        ("(wide_n || i <= i_step)", "(1)"),
+    "outline: narrow lines solved over the full width":
+        ("const int Nj = (j >= j_narrow) ? i_step : N;\n        const int wide_s",
+         "const int Nj = N;\n        const int wide_s"),
+    "outline: trace over every line":
+        ("for (int j = 0; j <= M && j < j_narrow; j++) {", "for (int j = 0; j <= M; j++) {"),
+    "outline: Dirichlet row reset beyond the step":
+        ("Th[(size_t)M * nr + i] = (i > NM) ?", "Th[(size_t)M * nr + i] = (i > N) ?"),
+    "outline: narrow line's outer edge booked as an interface edge":
+        ("const int ce = (i + 1 == Nj) ? OR_OUTER : cls[i + 1];", "const int ce = cls[i + 1];"),
+    "outline: heat booked through the closed face at z_max":
+        ("if (j == M - 1 && i <= NM) {", "if (j == M - 1) {"),
     # ADI variant
     "ADI: radial term of the second half step partly at T^n":
         ("const double Li = (r_e * le * (Sj[i + 1] - Sj[i]) / h_e -",
@@ -84,6 +98,7 @@ def test_pins_catch_mutation(name, tmp_path):
                     "-o", str(so), "-lm"], check=True, capture_output=True)
     env = dict(os.environ, CCELL_ORACLE_SO=str(so))
     res = subprocess.run([sys.executable, "-m", "pytest", "-x", "-q",
+                          os.path.join(ROOT, "tests", "test_oracle_outline.py"),
                           os.path.join(ROOT, "tests", "test_oracle_adi.py"),
                           os.path.join(ROOT, "tests", "test_oracle_pins.py"),
                           os.path.join(ROOT, "tests", "test_oracle_adjoint.py")],
