@@ -88,6 +88,19 @@ enum { CC_FP64 = 0, CC_MIXED = 1 };
  *               conductivities (conserves energy exactly).
  *   t_guard_lo_K, t_guard_hi_K  temperature range over which the stability
  *               guard minimises rho c / lambda (0, 0 = [t_dirichlet, 100 K]).
+ *   step_layers, z_step_m  stepped outline r in [0, r_max(z)] of Section 2
+ *               (the paper's cell has its outer layers on z in [0, z_0]
+ *               only, Section 5).  0: rectangle.  k in [1, n_layers): the
+ *               lines with z_j > z_step_m (a line on the step face counts
+ *               as below it) hold only the k innermost layers; their outer
+ *               node is the interface node that starts layer k and takes
+ *               the r_max condition bc_rmax; no heat crosses the step face
+ *               (Eq. (boundcond)); the nodes outside the domain keep their
+ *               values and must be finite.  Vertex placement only; line 1
+ *               must keep the full width (else CC_EINVAL).  The surface
+ *               trace averages over the full-width lines (r = r_max).
+ *               cc_step_adi_n and the adjoint take rectangles only
+ *               (CC_EUNSUPPORTED).
  */
 typedef struct {
   int32_t n_layers;
@@ -101,6 +114,8 @@ typedef struct {
   int32_t face_rule;
   int32_t interface_rule;
   double t_guard_lo_K, t_guard_hi_K;
+  int32_t step_layers;
+  double z_step_m;
 } cc_geometry_desc;
 
 /*
@@ -285,7 +300,8 @@ int cc_destroy(cc_ctx* ctx);
  * scratch (tables, work list, waveform table, error word, and the ping-pong
  * partner of T_dev) lives in a file-scope static device array of about
  * 9.5 MiB that every GPU loading the library holds until the process exits.
- *   desc        geometry (precision must be CC_FP64); materials[n_layers];
+ *   desc        geometry (precision must be CC_FP64, a rectangle:
+ *               step_layers 0, else CC_EUNSUPPORTED); materials[n_layers];
  *               source (layer -1 for none).  Same meaning as cc_create_geometry,
  *               cc_set_materials and cc_set_source.
  *   T_dev       caller-owned device double[nz][nr], advanced in place.
@@ -312,6 +328,11 @@ int cc_step_n_noalloc(const cc_geometry_desc* desc, const cc_material* materials
 /* Node positions and radial classes of one descriptor: r[nr], z[nz],
  * rclass[nr] (0 axis, 1 regular, 2 layer interface, 3 outer boundary). */
 int cc_query_grid(const cc_geometry_desc* desc, double* r, double* z, int32_t* rclass);
+
+/* Stepped outline of one descriptor: the lines j >= *j_narrow end at the
+ * radial node *i_step (a rectangle gives nr - 1 and nz).  CC_EINVAL for an
+ * outline the scheme does not take. */
+int cc_query_outline(const cc_geometry_desc* desc, int32_t* i_step, int32_t* j_narrow);
 
 /* Stability bound of Eq. (stability_condition) for one instance:
  * (min_j eta_j^2 / 2) * min over layers and the guard range of rho c/lambda. */

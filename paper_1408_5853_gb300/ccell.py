@@ -8,7 +8,7 @@ no CPU fallback.
 Low-level functions carry the C names (``cc_create_geometry``,
 ``cc_set_materials``, ``cc_set_source``, ``cc_set_dt``, ``cc_step_n``, ``cc_step_adi_n``,
 ``cc_sync``, ``cc_adjoint``, ``cc_adjoint_vjp``, ``cc_set_launch``, ``cc_get_launch``,
-``cc_autotune``, ``cc_destroy``, ``cc_step_n_noalloc``, ``cc_query_grid``,
+``cc_autotune``, ``cc_destroy``, ``cc_step_n_noalloc``, ``cc_query_grid``, ``cc_query_outline``,
 ``cc_tau_stab``, ``cc_status_string``, ``cc_kernel_launches``).  ``Solver``
 builds a context from the problem dicts of ``inputs``.
 """
@@ -37,6 +37,7 @@ class GeometryDesc(ctypes.Structure):
         ("length_m", _d), ("bc_rmax", _i), ("bc_z0", _i), ("bc_zmax", _i),
         ("t_dirichlet_K", _d), ("placement", _i), ("precision", _i), ("face_rule", _i),
         ("interface_rule", _i), ("t_guard_lo_K", _d), ("t_guard_hi_K", _d),
+        ("step_layers", _i), ("z_step_m", _d),
     ]
 
 
@@ -87,6 +88,8 @@ def _load():
     lib.cc_adjoint.argtypes = [vp, vp, ctypes.c_int64, _d, _d, vp, _i, vp, vp, vp, vp]
     lib.cc_destroy.argtypes = [vp]
     lib.cc_query_grid.argtypes = [ctypes.POINTER(GeometryDesc), dp, dp, ctypes.POINTER(_i)]
+    lib.cc_query_outline.argtypes = [ctypes.POINTER(GeometryDesc), ctypes.POINTER(_i),
+                                     ctypes.POINTER(_i)]
     lib.cc_tau_stab.argtypes = [vp, _i, dp]
     lib.cc_status_string.argtypes = [ctypes.c_int]
     lib.cc_status_string.restype = ctypes.c_char_p
@@ -105,7 +108,7 @@ def _load():
     lib.cc_adjoint_vjp.restype = ctypes.c_int
     for name in ("cc_create_geometry", "cc_set_materials", "cc_set_source", "cc_set_dt",
                  "cc_step_n", "cc_step_adi_n", "cc_sync", "cc_adjoint", "cc_destroy",
-                 "cc_query_grid", "cc_tau_stab"):
+                 "cc_query_grid", "cc_query_outline", "cc_tau_stab"):
         getattr(lib, name).restype = ctypes.c_int
     _lib = lib
     return lib
@@ -220,6 +223,15 @@ def cc_query_grid(desc: GeometryDesc):
     return r, z, cls
 
 
+def cc_query_outline(desc: GeometryDesc) -> tuple:
+    """(i_step, j_narrow) of a stepped outline: the lines j >= j_narrow end at
+    the radial node i_step; a rectangle gives (nr - 1, nz)."""
+    i_step, j_narrow = _i(0), _i(0)
+    _check(_load().cc_query_outline(ctypes.byref(desc), ctypes.byref(i_step),
+                                    ctypes.byref(j_narrow)), "cc_query_outline")
+    return i_step.value, j_narrow.value
+
+
 def cc_tau_stab(ctx, instance: int) -> float:
     out = _d()
     _check(_load().cc_tau_stab(ctx, instance, ctypes.byref(out)), "cc_tau_stab")
@@ -244,6 +256,9 @@ def geometry_desc(cfg: dict, precision: int = FP64) -> GeometryDesc:
     d.interface_rule = cfg.get("interface_rule", 0)
     lo, hi = cfg.get("t_guard", (0.0, 0.0))
     d.t_guard_lo_K, d.t_guard_hi_K = lo, hi
+    step = cfg.get("step")
+    if step is not None:
+        d.step_layers, d.z_step_m = step["layers"], step["z"]
     return d
 
 

@@ -24,6 +24,7 @@ struct Instance {
   double dt = 0.0;
   std::vector<double> r, z;
   std::vector<int> cls, seg;
+  int j_narrow = 0, i_step = 0;  // stepped outline (rectangle: nz, nr - 1)
   int G = 1;
   long long t_off = 0;
 };
@@ -89,6 +90,8 @@ int valid_desc(const cc_geometry_desc& d) {
   if (d.placement == 1 && d.n_layers != 1) return CC_EINVAL;
   if (d.placement == 0 && d.nr - 1 < 2 * d.n_layers) return CC_EINVAL;
   if (!std::isfinite(d.t_dirichlet_K)) return CC_EINVAL;
+  if (d.step_layers < 0 || d.step_layers >= d.n_layers) return CC_EINVAL;
+  if (d.step_layers > 0 && (d.placement != 0 || !std::isfinite(d.z_step_m))) return CC_EINVAL;
   return CC_OK;
 }
 
@@ -158,6 +161,32 @@ void build_grid(const cc_geometry_desc& d, std::vector<double>& r, std::vector<d
   }
   cls[0] = RC_AXIS;
   cls[N] = RC_OUTER;
+}
+
+// Stepped outline r in [0, r_max(z)] (Section 2): the lines with
+// z_j > z_step (a node on the step face counts as below it) keep only the
+// step_layers innermost layers and end at the interface node that starts
+// layer step_layers.  Line 1 must keep the full width.
+int build_outline(const cc_geometry_desc& d, const std::vector<double>& z,
+                  const std::vector<int>& cls, int& i_step, int& j_narrow) {
+  const int N = d.nr - 1, M = d.nz - 1;
+  i_step = N;
+  j_narrow = d.nz;
+  if (d.step_layers == 0) return CC_OK;
+  int k = 0;
+  for (int i = 1; i < N; ++i)
+    if (cls[i] == RC_IFACE && ++k == d.step_layers) {
+      i_step = i;
+      break;
+    }
+  if (k != d.step_layers) return CC_EINVAL;
+  const double zs = d.z_step_m + 1e-9 * d.length_m;
+  for (int j = 0; j <= M; ++j)
+    if (z[j] > zs) {
+      j_narrow = j;
+      break;
+    }
+  return j_narrow < 2 ? CC_EINVAL : CC_OK;
 }
 
 // Lanes per line: the smallest power of two giving at most `rows` rows per
@@ -325,11 +354,12 @@ int upload(cc_ctx* c, const std::vector<double>& dts, cudaStream_t st) {
         rg.push_back(g);
       }
       number_ifaces(rg.data() + rg.size() - in.d.nr, in.d.nr);
+      // trapezoid weights of the r = r_max surface (the full-width lines)
       double wsum = 0.0;
       std::vector<double> w(M + 1, 0.0);
-      for (int j = 0; j <= M; ++j) {
+      for (int j = 0; j <= M && j < in.j_narrow; ++j) {
         if (j > 0) w[j] += 0.5 * (in.z[j] - in.z[j - 1]);
-        if (j < M) w[j] += 0.5 * (in.z[j + 1] - in.z[j]);
+        if (j < M && j + 1 < in.j_narrow) w[j] += 0.5 * (in.z[j + 1] - in.z[j]);
         wsum += w[j];
       }
       for (int j = 0; j <= M; ++j) {
@@ -500,6 +530,8 @@ int upload(cc_ctx* c, const std::vector<double>& dts, cudaStream_t st) {
     D.src_layer = in.src.layer;
     D.waveform = in.src.waveform;
     D.g_model = in.src.g_model;
+    D.j_narrow = in.j_narrow;
+    D.i_step = in.i_step;
     D.t_off = in.t_off;
     D.t_d = in.d.t_dirichlet_K;
     D.tau = dts[k];
@@ -600,6 +632,10 @@ int cc_create_geometry(const cc_geometry_desc* desc, int32_t n_instances, cc_ctx
     Instance in;
     in.d = desc[k];
     build_grid(in.d, in.r, in.z, in.cls, in.seg);
+    if (build_outline(in.d, in.z, in.cls, in.i_step, in.j_narrow) != CC_OK) {
+      delete c;
+      return CC_EINVAL;
+    }
     in.G = choose_lanes(in.d.nr);
     in.t_off = off;
     in.src.layer = -1;
@@ -769,6 +805,7 @@ int cc_step_adi_n(cc_ctx* c, void* T_dev, int64_t n_steps, double t0, double dt_
   std::vector<double> half(n);
   for (int k = 0; k < n; ++k) {
     Instance& in = c->inst[k];
+    if (in.j_narrow < in.d.nz) return CC_EUNSUPPORTED;  // rectangles only
     if (!in.mat_set) return CC_ESTATE;
     const double dt = dt_s > 0.0 ? dt_s : in.dt;
     if (!(dt > 0.0) || !std::isfinite(dt)) return CC_EINVAL;
@@ -1000,6 +1037,7 @@ int adjoint_impl(cc_ctx* c, const void* T0_dev, int64_t n_steps, double t0, doub
   std::vector<double> dts(n);
   for (int k = 0; k < n; ++k) {
     Instance& in = c->inst[k];
+    if (in.j_narrow < in.d.nz) return CC_EUNSUPPORTED;  // rectangles only
     if (!in.mat_set) return CC_ESTATE;
     dts[k] = dt_s > 0.0 ? dt_s : in.dt;
     if (!(dts[k] > 0.0)) return CC_EINVAL;
@@ -1179,6 +1217,21 @@ int cc_query_grid(const cc_geometry_desc* d, double* r, double* z, int32_t* rcla
   if (z) std::memcpy(z, zz.data(), sizeof(double) * zz.size());
   if (rclass)
     for (size_t i = 0; i < cls.size(); ++i) rclass[i] = cls[i];
+  return CC_OK;
+}
+
+int cc_query_outline(const cc_geometry_desc* d, int32_t* i_step, int32_t* j_narrow) {
+  if (!d || !i_step || !j_narrow) return CC_EINVAL;
+  const int v = valid_desc(*d);
+  if (v != CC_OK) return v;
+  std::vector<double> rr, zz;
+  std::vector<int> cls, seg;
+  build_grid(*d, rr, zz, cls, seg);
+  int is = 0, jn = 0;
+  const int o = build_outline(*d, zz, cls, is, jn);
+  if (o != CC_OK) return o;
+  *i_step = is;
+  *j_narrow = jn;
   return CC_OK;
 }
 

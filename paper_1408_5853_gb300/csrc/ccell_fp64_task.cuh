@@ -59,8 +59,9 @@ __device__ __forceinline__ double ld_field(const double* p) {
 // One tile.  sm starts with two rows of axial face fluxes: the tile takes the
 // fluxes of the face south of its first line from row par ^ 1 if carry (the
 // previous tile of this block ended on the line before j0), and leaves those
-// north of its last line in row par.
-template <bool ENERGY, bool TRACE, bool CACHED>
+// north of its last line in row par.  STP: the tile holds a line of a stepped
+// outline that is narrow or borders a narrow one (other tiles skip the checks).
+template <bool ENERGY, bool TRACE, bool CACHED, bool STP>
 __device__ __forceinline__ void step_fp64_tile(const StepArgs& a, const TileTask tk,
                                                double* __restrict__ sm, EAcc& acc, bool carry,
                                                int par) {
@@ -155,13 +156,15 @@ __device__ __forceinline__ void step_fp64_tile(const StepArgs& a, const TileTask
         }
         row += nr;
         const double ln = lam_face(Mt, frule, Tc, Tn);  // face (j, j+1)
-        const double fn = ln * (Tn - Tc);
+        // no heat through a face to a node outside a stepped outline
+        const double fn = (STP && j + 1 >= I.j_narrow && ic > I.i_step) ? 0.0 : ln * (Tn - Tc);
+        const int cls = STP ? line_class(I, g.cls, ic, j) : g.cls;
         const double le = (ic < N) ? lam_face(Mt, frule, Tc, Te) : 0.0;  // face (i, i+1)
         const double lw = __shfl_up_sync(kFull, le, 1);                  // face (i-1, i)
         const double rct = rct_eval(Mt, Tc);                             // rho c / tau
         const ZGeo& zg = I.zg[j];
         double ra, rb, rc, rd, m = 0.0;
-        if (g.cls == RC_REGULAR) {
+        if (cls == RC_REGULAR) {
           // Eq. (Lambda_j), explicit in T, from the face fluxes
           const double Lj = fma(zg.gzn, fn, -zg.gzs * fs);
           double X = 0.0;  // Eq. (source)
@@ -193,7 +196,7 @@ __device__ __forceinline__ void step_fp64_tile(const StepArgs& a, const TileTask
               if (I.bc_zmax == CC_DIRICHLET) eD += f; else eN += f;
             }
           }
-        } else if (g.cls == RC_IFACE) {
+        } else if (cls == RC_IFACE) {
           // Eq. (cc_first_1)/(cc_first_3) as the row (a, b, c | 0)
           double lmv, lpv;
           if (I.interface_rule == 0) {
@@ -207,17 +210,20 @@ __device__ __forceinline__ void step_fp64_tile(const StepArgs& a, const TileTask
           rc = -lpv * g.hw;
           rb = fma(lmv, g.he, lpv * g.hw);
           rd = 0.0;
-        } else if (g.cls == RC_AXIS) {  // That_0 = That_1
+        } else if (cls == RC_AXIS) {  // That_0 = That_1
           ra = 0.0; rb = 1.0; rc = -1.0; rd = 0.0;
-        } else {  // r = r_max
+        } else if (!STP || cls == RC_OUTER) {  // r = r_max, or the outer node of a narrow line
           if (I.bc_rmax == CC_DIRICHLET) { ra = 0.0; rb = 1.0; rc = 0.0; rd = I.t_d; }
           else { ra = -1.0; rb = 1.0; rc = 0.0; rd = 0.0; }
+        } else {  // outside the domain: a decoupled row, the old value is stored
+          ra = 0.0; rb = 1.0; rc = 0.0; rd = 0.0;
         }
         if (ENERGY && own && edge) {
           // heat-flow coefficients to the regular neighbours (faces at T^n)
+          const bool in = !STP || cls != RC_OUTSIDE;
           double* K = sI + 4 * (q * n_if + g.ifo);
-          K[2] = I.tau * gwV * zg.etabar * gwC * lw;
-          K[3] = I.tau * geV * zg.etabar * geA * le;
+          K[2] = in ? I.tau * gwV * zg.etabar * gwC * lw : 0.0;
+          K[3] = in ? I.tau * geV * zg.etabar * geA * le : 0.0;
         }
         if (own && q == nl - 1) cout[smem_col(ic)] = fn;
         if (own) {
@@ -258,9 +264,14 @@ __device__ __forceinline__ void step_fp64_tile(const StepArgs& a, const TileTask
       const int c = smem_col(i);
       const double x = SB[(size_t)q * nrp + c];
       bad |= not_finite(x);
-      Tout[(long long)j * nr + i] = x;
+      // nodes outside a stepped outline keep their values
+      Tout[(long long)j * nr + i] = (STP && j >= I.j_narrow && i > I.i_step)
+                                        ? ld_field<CACHED>(Tin + (long long)j * nr + i) : x;
       if (j == 1) Tout[i] = (I.bc_z0 == CC_DIRICHLET) ? I.t_d : x;
-      if (j == M - 1) Tout[(long long)M * nr + i] = (I.bc_zmax == CC_DIRICHLET) ? I.t_d : x;
+      if (j == M - 1)
+        Tout[(long long)M * nr + i] = (STP && M >= I.j_narrow && i > I.i_step)
+                                          ? ld_field<CACHED>(Tin + (long long)M * nr + i)
+                                          : (I.bc_zmax == CC_DIRICHLET) ? I.t_d : x;
       if (ENERGY) eEq = fma(SM[(size_t)q * nrp + c], x - ld_field<CACHED>(Tin + (long long)j * nr + i), eEq);
       if (TRACE && i == N) {  // That(r_max, z_j)
         tr = fma(I.zg[j].wnorm, x, tr);
@@ -292,9 +303,10 @@ __device__ __forceinline__ void step_fp64_tile(const StepArgs& a, const TileTask
         const double* K = sI + 4 * it;
         const double x = Bq[smem_col(i)];
         const double fw = K[2] * (x - Bq[smem_col(i - 1)]);  // into node i-1
-        if (I.rg[i].cls == RC_OUTER) {
+        const int cls = STP ? line_class(I, I.rg[i].cls, i, j0 + q) : I.rg[i].cls;
+        if (cls == RC_OUTER) {
           if (I.bc_rmax == CC_DIRICHLET) eD += fw; else eN += fw;
-        } else {
+        } else if (!STP || cls == RC_IFACE) {
           eI += fw + K[3] * (x - Bq[smem_col(i + 1)]);  // and into node i+1
         }
       }
@@ -322,7 +334,10 @@ __device__ __forceinline__ void fp64_tiles(const StepArgs& a, double* __restrict
   for (int t = t0; t < t1; t += dt) {
     const TileTask tk = a.tiles[t];
     const bool carry = (tk.inst == prev_inst && tk.j0 == prev_end);
-    step_fp64_tile<ENERGY, TRACE, CACHED>(a, tk, sm, acc, carry, par);
+    if (tk.j0 + tk.nl >= a.insts[tk.inst].j_narrow)
+      step_fp64_tile<ENERGY, TRACE, CACHED, true>(a, tk, sm, acc, carry, par);
+    else
+      step_fp64_tile<ENERGY, TRACE, CACHED, false>(a, tk, sm, acc, carry, par);
     prev_inst = tk.inst;
     prev_end = tk.j0 + tk.nl;
     par ^= 1;

@@ -7,7 +7,7 @@
 
 namespace ccell {
 
-enum : int { RC_AXIS = 0, RC_REGULAR = 1, RC_IFACE = 2, RC_OUTER = 3 };
+enum : int { RC_AXIS = 0, RC_REGULAR = 1, RC_IFACE = 2, RC_OUTER = 3, RC_OUTSIDE = 4 };
 
 // Largest number of rows one lane eliminates sequentially; a line of nr rows
 // is split over G lanes (G a power of two, G <= 32), so nr <= 32 * kRowsPerLane.
@@ -79,6 +79,9 @@ struct DevInst {
   int bc_rmax, bc_z0, bc_zmax;
   int face_rule, interface_rule;
   int src_layer, waveform, g_model;
+  // stepped outline: the lines j >= j_narrow end at the radial node i_step
+  // (class RC_OUTER there, RC_OUTSIDE beyond); a rectangle has j_narrow = nz
+  int j_narrow, i_step;
   int pad0;
   int n_if;              // interface and r_max nodes (classes RC_IFACE, RC_OUTER) ...
   int if_i[CC_MAX_LAYERS];  // ... their radial indices, ascending
@@ -92,6 +95,15 @@ struct DevInst {
   const ZGeo* zg;        // [nz]
   DevMaterial mat[CC_MAX_LAYERS];
 };
+
+// Class of radial node i on line j: the node's own class, except on the
+// narrow lines of a stepped outline.
+#ifdef __CUDACC__
+__device__ __forceinline__ int line_class(const DevInst& I, int cls, int i, int j) {
+  if (j >= I.j_narrow && i >= I.i_step) return i == I.i_step ? RC_OUTER : RC_OUTSIDE;
+  return cls;
+}
+#endif
 
 // One warp's work: 32/G consecutive lines of one instance.
 struct Task {

@@ -56,7 +56,9 @@ __device__ __forceinline__ float ld_state(const float* p) {
   else return __ldcg(p);
 }
 
-template <bool ENERGY, bool TRACE, bool CACHED>
+// STP: the tile holds a line of a stepped outline that is narrow or borders a
+// narrow one (other tiles skip the checks).
+template <bool ENERGY, bool TRACE, bool CACHED, bool STP>
 __device__ __forceinline__ void step_mixed_tile(const StepArgs& a, const TileTask tk,
                                                 float* __restrict__ sm, EAcc& acc, bool carry,
                                                 int par) {
@@ -120,10 +122,10 @@ __device__ __forceinline__ void step_mixed_tile(const StepArgs& a, const TileTas
       const int ic = i <= N ? i : N;
       const bool own = (i <= N) && (lane > 0 || b == 0);
       const RowGeo& g = I.rg[ic];
-      const int cls = g.cls, seg = g.seg;
+      const int cls0 = g.cls, seg = g.seg;
       const DevMaterial& Mt = I.mat[seg];
       const int ie = ic < N ? ic + 1 : ic;
-      const bool edge = (cls == RC_IFACE || cls == RC_OUTER);
+      const bool edge = (cls0 == RC_IFACE || cls0 == RC_OUTER);
       float gwk = 0.0f, gek = 0.0f;  // tau V2 gC of the west, tau V2 gA of the east neighbour
       if (ENERGY && edge) {
         const RowGeo& gw = I.rg[ic - 1];
@@ -155,7 +157,10 @@ __device__ __forceinline__ void step_mixed_tile(const StepArgs& a, const TileTas
         const float dN = (hn - hc) + (ln - lc);       // T_{j+1} - T_j
         const float dE = (he - hc) + (lE - lc);       // T_{i+1} - T_i
         const float dW = -__shfl_up_sync(kFull, dE, 1);  // T_{i-1} - T_i
-        const float fn = lam_face32(Mt, frule, hc, hn) * dN;
+        // no heat through a face to a node outside a stepped outline
+        const float fn = (STP && j + 1 >= I.j_narrow && ic > I.i_step)
+                             ? 0.0f : lam_face32(Mt, frule, hc, hn) * dN;
+        const int cls = STP ? line_class(I, cls0, ic, j) : cls0;
         const float le = (ic < N) ? lam_face32(Mt, frule, hc, he) : 0.0f;  // face (i, i+1)
         const float lw = __shfl_up_sync(kFull, le, 1);                     // face (i-1, i)
         const float rhoc = Mt.rho_f * cap32(Mt, hc);
@@ -201,7 +206,9 @@ __device__ __forceinline__ void step_mixed_tile(const StepArgs& a, const TileTas
           fd = -fmaf(fa, dW, fc * dE);
         } else if (cls == RC_AXIS) {  // dT_0 - dT_1 = T_1 - T_0
           fa = 0.0f; fb = 1.0f; fc = -1.0f; fd = dE;
-        } else if (I.bc_rmax == CC_DIRICHLET) {
+        } else if (STP && cls == RC_OUTSIDE) {  // outside the domain: decoupled, dT = 0
+          fa = 0.0f; fb = 1.0f; fc = 0.0f; fd = 0.0f;
+        } else if (I.bc_rmax == CC_DIRICHLET) {  // r = r_max or a narrow line's outer node
           fa = 0.0f; fb = 1.0f; fc = 0.0f; fd = (I.td_hi - hc) + (I.td_lo - lc);
         } else {  // dT_N - dT_{N-1} = T_{N-1} - T_N
           fa = -1.0f; fb = 1.0f; fc = 0.0f; fd = dW;
@@ -209,11 +216,12 @@ __device__ __forceinline__ void step_mixed_tile(const StepArgs& a, const TileTas
         if (ENERGY && own && edge) {
           // heat-flow coefficients to the regular neighbours and the old
           // temperature differences across those edges
+          const bool in = !STP || cls != RC_OUTSIDE;
           float* K = sI + kMixIf * (q * n_if + g.ifo);
-          K[2] = gwk * zg.etabar_f * lw;
-          K[3] = gek * zg.etabar_f * le;
-          K[4] = -dW;
-          K[5] = -dE;
+          K[2] = in ? gwk * zg.etabar_f * lw : 0.0f;
+          K[3] = in ? gek * zg.etabar_f * le : 0.0f;
+          K[4] = in ? -dW : 0.0f;
+          K[5] = in ? -dE : 0.0f;
         }
         if (own && q == nl - 1) cout[smem_col(ic)] = fn;
         if (own) {
@@ -254,8 +262,12 @@ __device__ __forceinline__ void step_mixed_tile(const StepArgs& a, const TileTas
       if (ENERGY) eEf = fmaf(FM[(size_t)q * nrp + c], x, eEf);
       const float hi = ld_state<CACHED>(Hin + rj + i), lo = ld_state<CACHED>(Lin + rj + i);
       const float v = lo + x;
-      const float h1 = hi + v;
-      const float l1 = v - (h1 - hi);  // exact: h1 + l1 = hi + v
+      float h1 = hi + v;
+      float l1 = v - (h1 - hi);  // exact: h1 + l1 = hi + v
+      if (STP && j >= I.j_narrow && i > I.i_step) {  // outside a stepped outline: unchanged
+        h1 = hi;
+        l1 = lo;
+      }
       Hout[rj + i] = h1;
       Lout[rj + i] = l1;
       if (j == 1) {
@@ -263,8 +275,14 @@ __device__ __forceinline__ void step_mixed_tile(const StepArgs& a, const TileTas
         Lout[i] = (I.bc_z0 == CC_DIRICHLET) ? I.td_lo : l1;
       }
       if (j == M - 1) {
-        Hout[(long long)M * nr + i] = (I.bc_zmax == CC_DIRICHLET) ? I.td_hi : h1;
-        Lout[(long long)M * nr + i] = (I.bc_zmax == CC_DIRICHLET) ? I.td_lo : l1;
+        const long long rM = (long long)M * nr + i;
+        if (STP && M >= I.j_narrow && i > I.i_step) {
+          Hout[rM] = ld_state<CACHED>(Hin + rM);
+          Lout[rM] = ld_state<CACHED>(Lin + rM);
+        } else {
+          Hout[rM] = (I.bc_zmax == CC_DIRICHLET) ? I.td_hi : h1;
+          Lout[rM] = (I.bc_zmax == CC_DIRICHLET) ? I.td_lo : l1;
+        }
       }
       if (TRACE && i == N) {  // That(r_max, z_j)
         const double surf = ((double)hi + (double)lo) + xd;
@@ -296,9 +314,10 @@ __device__ __forceinline__ void step_mixed_tile(const StepArgs& a, const TileTas
         const float* K = sI + kMixIf * it;
         const double x = Bq[smem_col(i)];
         const double fw = (double)K[2] * ((double)K[4] + (x - Bq[smem_col(i - 1)]));
-        if (I.rg[i].cls == RC_OUTER) {
+        const int cls = STP ? line_class(I, I.rg[i].cls, i, j0 + q) : I.rg[i].cls;
+        if (cls == RC_OUTER) {
           if (I.bc_rmax == CC_DIRICHLET) eD += fw; else eN += fw;
-        } else {
+        } else if (!STP || cls == RC_IFACE) {
           eI += fw + (double)K[3] * ((double)K[5] + (x - Bq[smem_col(i + 1)]));
         }
       }
@@ -326,7 +345,10 @@ __device__ __forceinline__ void mixed_tiles(const StepArgs& a, float* __restrict
   for (int t = t0; t < t1; t += dt) {
     const TileTask tk = a.tiles[t];
     const bool carry = (tk.inst == prev_inst && tk.j0 == prev_end);
-    step_mixed_tile<ENERGY, TRACE, CACHED>(a, tk, sm, acc, carry, par);
+    if (tk.j0 + tk.nl >= a.insts[tk.inst].j_narrow)
+      step_mixed_tile<ENERGY, TRACE, CACHED, true>(a, tk, sm, acc, carry, par);
+    else
+      step_mixed_tile<ENERGY, TRACE, CACHED, false>(a, tk, sm, acc, carry, par);
     prev_inst = tk.inst;
     prev_end = tk.j0 + tk.nl;
     par ^= 1;

@@ -163,6 +163,7 @@ int validate(const cc_geometry_desc& d, const cc_material* mat, const cc_source&
       !ok01(d.placement) || !ok01(d.face_rule) || !ok01(d.interface_rule))
     return CC_EINVAL;
   if (d.placement == 1 && d.n_layers != 1) return CC_EINVAL;
+  if (d.step_layers != 0) return CC_EUNSUPPORTED;  // rectangles only
   if (d.placement == 0 && d.nr - 1 < 2 * d.n_layers) return CC_EINVAL;
   if (!(d.length_m > 0.0) || !std::isfinite(d.t_dirichlet_K)) return CC_EINVAL;
   for (int m = 0; m < d.n_layers; ++m) {
@@ -294,6 +295,8 @@ extern "C" int cc_step_n_noalloc(const cc_geometry_desc* desc, const cc_material
   h_inst.src_layer = source->layer;
   h_inst.waveform = source->waveform;
   h_inst.g_model = source->g_model;
+  h_inst.j_narrow = d.nz;  // rectangle
+  h_inst.i_step = d.nr - 1;
   h_inst.t_d = d.t_dirichlet_K;
   h_inst.tau = dt_s;
   h_inst.inv_tau = 1.0 / dt_s;

@@ -142,14 +142,15 @@ def adjoint_case(nr: int = 256, nz: int = 1024, dt: float = 6.25e-9) -> dict:
 _GOLDEN = os.path.join(os.path.dirname(_HERE), "tests", "golden", "paper_material_fits.json")
 
 
-def paper_case(nr: int = 256, nz: int = 201) -> dict:
-    """The paper's cryogenic cell (Section 5) on a rectangular r-z domain:
-    copper core 1.2 mm, insulator 0.05 mm, graphite heater 0.05 mm, outer
-    insulator 1 um; length 5 cm; polynomial fits of c_V and lambda (Tables
-    a_coefs, b_coefs), converted from cgs to SI; Joule source
-    chi(T) I(t)^2 / S_2^2 with chi = 1.8 / sqrt(T) Ohm cm, I0 = 363 mA and the
-    transient turn-on (waveform 2); 1 ms pulse every 25 ms; T0 = 4.2 K.
-    The non-rectangular outline of the paper's figure is not reproduced."""
+def paper_case(nr: int = 256, nz: int = 201, stepped: bool = False) -> dict:
+    """The paper's cryogenic cell (Section 5): copper core 1.2 mm, insulator
+    0.05 mm, graphite heater 0.05 mm, outer insulator 1 um; length 5 cm;
+    polynomial fits of c_V and lambda (Tables a_coefs, b_coefs), converted
+    from cgs to SI; Joule source chi(T) I(t)^2 / S_2^2 with chi = 1.8 / sqrt(T)
+    Ohm cm, I0 = 363 mA and the transient turn-on (waveform 2); 1 ms pulse
+    every 25 ms; T0 = 4.2 K.  Rectangular r-z domain, or with `stepped` the
+    outer layers on z <= z_0 = 4 cm only and the copper core alone up to the
+    helium end (the working surface r = r_max spans z in [0, z_0])."""
     with open(_GOLDEN) as f:
         fit = json.load(f)
     r_cm = fit["radii_cm"]
@@ -171,6 +172,8 @@ def paper_case(nr: int = 256, nz: int = 201) -> dict:
                source=dict(layer=2, q0=q0, t_period=run["t_prd_s"], t_on=run["t_src_s"],
                            t_start=0.0, waveform=2, edge_w=run["tau_s"], g_model=1, g_ref=1.0),
                dt=run["tau_s"], t_guard=(run["T0_K"], 60.0))
+    if stepped:
+        cfg["step"] = dict(layers=1, z=fit["z_cm"]["z0"] * 1e-2)
     cfg["name"] = f"paper cryogenic cell {nr}x{nz} (polynomial materials, transient source)"
     return cfg
 
