@@ -9,11 +9,12 @@
 // sum_i xi_i d r_i / d(.), r_i = f_i - (a_i y_{i-1} + b_i y_i + c_i y_{i+1})
 // at fixed y = That.
 //
-//  adj_line_kernel    per line: rebuild (a, b, c) at T^n, then solve the
-//                     transposed system with the same segment elimination and
-//                     shuffle cyclic reduction as the forward solve
-//                     (mu includes the loss seed of step n and the folded
-//                     axial boundary rows).
+//  adj_tile_kernel    per CTA tile of lines: rebuild (a, b, c) at T^n with
+//                     the lanes over columns, then solve the transposed
+//                     systems in shared memory with the segment elimination
+//                     and shuffle cyclic reduction of the forward step (mu
+//                     includes the loss seed of step n and the folded axial
+//                     boundary rows).
 //  adj_gather_kernel  per node: dJ/dT^n from xi of the node's own row and of
 //                     the four neighbouring rows that read its temperature
 //                     (no atomics on the field), plus the parameter terms of
@@ -72,164 +73,156 @@ __device__ __forceinline__ void cap_d(const DevMaterial& M, double T, double& c,
 }
 
 // ---------------------------------------------------------------------------
-// transposed line solve
+// transposed line solves, one CTA tile of nl lines at a time
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ void adj_line_task(const AdjArgs& a, const Task tk, const int lane) {
-  const DevInst& I = a.insts[tk.inst];
-  const int G = I.G;
-  const int lg = __ffs(G) - 1;
-  const int grp = lane >> lg, l = lane & (G - 1);
-  const int nr = I.nr, N = nr - 1, M = I.nz - 1;
-  const int j_req = tk.j0 + grp;
-  const bool active = j_req <= M - 1;
-  const int j = active ? j_req : M - 1;
-  const int i_lo = (l * nr) >> lg;
-  const int i_hi = ((l + 1) * nr) >> lg;
-  const int cnt = i_hi - i_lo;
-  const long long rj = (long long)j * nr;
-  const double* Tj = a.x + I.t_off + rj;
-  double* Sa = a.sa + I.t_off + rj;
-  double* Sb = a.sb + I.t_off + rj;
-  double* Sc = a.sc + I.t_off + rj;
-  const int frule = I.face_rule;
-
-  // pass 1: the rows of the forward step at T^n
-  {
-    double Tm1 = (i_lo > 0) ? Tj[i_lo - 1] : 0.0;
-    double T0 = Tj[i_lo];
-    double le_prev = 0.0;
-    bool have_le = false;
-#pragma unroll
-    for (int k = 0; k < kRowsPerLane; ++k) {
-      if (k < cnt) {
-        const int i = i_lo + k;
-        const RowGeo& g = I.rg[i];
-        const double Tp1 = (i < N) ? Tj[i + 1] : 0.0;
-        double ra, rb, rc;
-        if (g.cls == RC_REGULAR) {
-          const DevMaterial& Mt = I.mat[g.seg];
-          const double lw = have_le ? le_prev : lam_face(Mt, frule, Tm1, T0);
-          const double le = lam_face(Mt, frule, T0, Tp1);
-          const double rct = Mt.rho * cap_eval(Mt, T0) * I.inv_tau;
-          ra = -g.gA * lw;
-          rc = -g.gC * le;
-          rb = rct - ra - rc;
-          le_prev = le;
-          have_le = true;
-        } else if (g.cls == RC_IFACE) {
-          double lm, lp;
-          if (I.interface_rule == 0) {
-            lm = lam_eval(I.mat[g.segw], T0);
-            lp = lam_eval(I.mat[g.seg], T0);
-          } else {
-            lm = g.rw * lam_face(I.mat[g.segw], frule, Tm1, T0);
-            lp = g.re * lam_face(I.mat[g.seg], frule, T0, Tp1);
-          }
-          ra = -lm * g.he;
-          rc = -lp * g.hw;
-          rb = fma(lm, g.he, lp * g.hw);
-          have_le = false;
-        } else if (g.cls == RC_AXIS) {
-          ra = 0.0; rb = 1.0; rc = -1.0;
-          have_le = false;
-        } else {
-          ra = (I.bc_rmax == CC_DIRICHLET) ? 0.0 : -1.0;
-          rb = 1.0;
-          rc = 0.0;
-          have_le = false;
-        }
-        if (active) {
-          Sa[i] = ra;
-          Sb[i] = rb;
-          Sc[i] = rc;
-        }
-        Tm1 = T0;
-        T0 = Tp1;
-      }
+// Forward row (a, b, c) of node i on a line at T^n: Eq. (ABC) for regular
+// nodes, Eq. (cc_first_3) for interface nodes, the closures at the axis and
+// at r_max.  lw, le: face conductivities (i-1, i) and (i, i+1).
+__device__ __forceinline__ void forward_row(const DevInst& I, const RowGeo& g, double T0,
+                                            double lw, double le, double& ra, double& rb,
+                                            double& rc) {
+  if (g.cls == RC_REGULAR) {
+    const DevMaterial& Mt = I.mat[g.seg];
+    const double rct = Mt.rho * cap_eval(Mt, T0) * I.inv_tau;
+    ra = -g.gA * lw;
+    rc = -g.gC * le;
+    rb = rct - ra - rc;
+  } else if (g.cls == RC_IFACE) {
+    double lm, lp;
+    if (I.interface_rule == 0) {
+      lm = lam_eval(I.mat[g.segw], T0);
+      lp = lam_eval(I.mat[g.seg], T0);
+    } else {
+      lm = g.rw * lw;
+      lp = g.re * le;
     }
-  }
-  __syncwarp();
-
-  // pass 2: M^T xi = mu, rows (c_{i-1}, b_i, a_{i+1} | mu_i)
-  const double* Lam = a.lam + I.t_off;
-  const double sd = a.seed[(long long)tk.inst * a.n_steps + a.step];
-  const bool fold0 = (j == 1) && (I.bc_z0 == CC_NEUMANN);
-  const bool foldM = (j == M - 1) && (I.bc_zmax == CC_NEUMANN);
-  const double wj = I.zg[j].wnorm, w0 = I.zg[0].wnorm, wM = I.zg[M].wnorm;
-
-  double cp[kRowsPerLane], ap[kRowsPerLane], dp[kRowsPerLane];
-  double pc = 0.0, pa = 0.0, pd = 0.0;
-  double Dacc = 0.0, Aacc = 0.0, P = 1.0;
-  double ae = 0.0, be = 1.0, ce = 0.0, de = 0.0;
-#pragma unroll
-  for (int k = 0; k < kRowsPerLane; ++k) {
-    if (k < cnt) {
-      const int i = i_lo + k;
-      const double ra = (i > 0) ? Sc[i - 1] : 0.0;
-      const double rb = Sb[i];
-      const double rc = (i < N) ? Sa[i + 1] : 0.0;
-      double rd = Lam[rj + i];
-      if (i == N) rd = fma(sd, wj, rd);
-      if (fold0) rd += Lam[i] + ((i == N) ? sd * w0 : 0.0);
-      if (foldM) rd += Lam[(long long)M * nr + i] + ((i == N) ? sd * wM : 0.0);
-      if (k < cnt - 1) {
-        const double den = (k == 0) ? rb : fma(-ra, pc, rb);
-        const double r = frcp(den);
-        const double c1 = rc * r;
-        const double a1 = (k == 0) ? ra * r : -ra * pa * r;
-        const double d1 = (k == 0) ? rd * r : fma(-ra, pd, rd) * r;
-        cp[k] = c1;
-        ap[k] = a1;
-        dp[k] = d1;
-        Dacc = fma(P, d1, Dacc);
-        Aacc = fma(P, a1, Aacc);
-        P = -P * c1;
-        pc = c1;
-        pa = a1;
-        pd = d1;
-      } else {
-        ae = ra; be = rb; ce = rc; de = rd;
-      }
-    }
-  }
-  const double xs = solve_separators(ae, be, ce, de, pa, pc, pd, Dacc, Aacc, P, G, l);
-  const double L = __shfl_up_sync(kFull, xs, 1, G);
-  double xn = xs;
-#pragma unroll
-  for (int k = kRowsPerLane - 2; k >= 0; --k) {
-    if (k <= cnt - 2) {
-      const double x = fma(-cp[k], xn, fma(-ap[k], L, dp[k]));
-      dp[k] = x;
-      xn = x;
-    }
-  }
-  if (active) {
-    double* XI = a.xi + I.t_off + rj;
-#pragma unroll
-    for (int k = 0; k < kRowsPerLane; ++k)
-      if (k < cnt) XI[i_lo + k] = (k == cnt - 1) ? xs : dp[k];
+    ra = -lm * g.he;
+    rc = -lp * g.hw;
+    rb = fma(lm, g.he, lp * g.hw);
+  } else if (g.cls == RC_AXIS) {
+    ra = 0.0; rb = 1.0; rc = -1.0;
+  } else {
+    ra = (I.bc_rmax == CC_DIRICHLET) ? 0.0 : -1.0;
+    rb = 1.0;
+    rc = 0.0;
   }
 }
 
-__global__ void __launch_bounds__(128) adj_line_kernel(const AdjArgs a) {
-  const int lane = threadIdx.x & 31;
-  const int n_warps = (int)((gridDim.x * blockDim.x) >> 5);
-  for (int w = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5); w < a.n_tasks; w += n_warps)
-    adj_line_task(a, a.tasks[w], lane);
+// The transposed system M^T xi = mu of line j has rows (c_{i-1}, b_i, a_{i+1} |
+// mu_i).  Rows are assembled with the lanes over columns: block b of a warp
+// covers columns 30b .. 30b+31, lanes 1..30 own columns 30b+1 .. 30b+30 (and
+// lane 0 the axis for b = 0); lane 0 hands c of its column to lane 1 and lane
+// 31 hands a of its column to lane 30.  Each radial face conductivity is
+// evaluated once per lane (the west face comes from the left lane).  The
+// systems are then solved with the segment elimination and shuffle cyclic
+// reduction of the forward step, and xi is stored with the threads over the
+// nodes of the tile.
+__global__ void __launch_bounds__(CC_ADJ_MAX_THREADS) adj_tile_kernel(const AdjArgs a) {
+  extern __shared__ double sm[];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarps = blockDim.x >> 5;
+  for (int t = blockIdx.x; t < a.n_tiles; t += gridDim.x) {
+    const TileTask tk = a.tiles[t];
+    const DevInst& I = a.insts[tk.inst];
+    const int nr = I.nr, N = nr - 1, M = I.nz - 1;
+    const int j0 = tk.j0, nl = tk.nl;
+    const int nrp = smem_row_stride(nr);
+    const int frule = I.face_rule;
+    double* SA = sm;
+    double* SB = SA + (size_t)nl * nrp;
+    double* SC = SB + (size_t)nl * nrp;
+    double* SD = SC + (size_t)nl * nrp;
+    const double* X = a.x + I.t_off;
+    const double* Lam = a.lam + I.t_off;
+    const double sd = a.seed[(long long)tk.inst * a.n_steps + a.step];
+    const double w0 = I.zg[0].wnorm, wM = I.zg[M].wnorm;
+    {
+      const int nb = (N + 29) / 30;
+      const int n_items = nb * nl;
+      const int end = (int)((long long)(warp + 1) * n_items / nwarps);
+      for (int idx = (int)((long long)warp * n_items / nwarps); idx < end;) {
+        const int b = idx / nl, q0 = idx - b * nl;
+        const int q1 = min(nl, q0 + (end - idx));
+        idx += q1 - q0;
+        const int i = 30 * b + lane;
+        const int ic = i <= N ? i : N;
+        const bool own = (i <= N) && ((lane >= 1 && lane <= 30) || (b == 0 && lane == 0));
+        const RowGeo g = I.rg[ic];
+        const DevMaterial& Mt = I.mat[g.seg];
+        const int ie = ic < N ? ic + 1 : ic;
+        const double* row = X + (long long)(j0 + q0) * nr;
+        double Tc = __ldg(row + ic), Te = __ldg(row + ie);
+        for (int q = q0; q < q1; ++q) {
+          const int j = j0 + q;
+          double Tc_next = 0.0, Te_next = 0.0;
+          if (q + 1 < q1) {
+            Tc_next = __ldg(row + nr + ic);
+            Te_next = __ldg(row + nr + ie);
+          }
+          row += nr;
+          const double le = (ic < N) ? lam_face(Mt, frule, Tc, Te) : 0.0;  // face (i, i+1)
+          const double lw = __shfl_up_sync(kFull, le, 1);                  // face (i-1, i)
+          double fa, fb, fc;
+          forward_row(I, g, Tc, lw, le, fa, fb, fc);
+          const double cw = __shfl_up_sync(kFull, fc, 1);    // c_{i-1}
+          const double ae = __shfl_down_sync(kFull, fa, 1);  // a_{i+1}
+          if (own) {
+            const long long rj = (long long)j * nr;
+            double rd = __ldg(Lam + rj + ic);
+            if (ic == N) rd = fma(sd, I.zg[j].wnorm, rd);
+            if (j == 1 && I.bc_z0 == CC_NEUMANN) rd += __ldg(Lam + ic) + ((ic == N) ? sd * w0 : 0.0);
+            if (j == M - 1 && I.bc_zmax == CC_NEUMANN)
+              rd += __ldg(Lam + (long long)M * nr + ic) + ((ic == N) ? sd * wM : 0.0);
+            const size_t o = (size_t)q * nrp + smem_col(ic);
+            SA[o] = (ic > 0) ? cw : 0.0;
+            SB[o] = fb;
+            SC[o] = (ic < N) ? ae : 0.0;
+            SD[o] = rd;
+          }
+          Tc = Tc_next;
+          Te = Te_next;
+        }
+      }
+    }
+    __syncthreads();
+    solve_tile_lines<true>(SA, SB, SC, SD, nl, nr, I.G);
+    __syncthreads();
+    {
+      double* XI = a.xi + I.t_off;
+      int q = threadIdx.x / nr, i = threadIdx.x - q * nr;
+      for (; q < nl;) {
+        XI[(long long)(j0 + q) * nr + i] = SB[(size_t)q * nrp + smem_col(i)];
+        i += blockDim.x;
+        while (i >= nr) {
+          i -= nr;
+          ++q;
+        }
+      }
+    }
+    __syncthreads();  // the next tile reuses the shared memory
+  }
 }
 
 int launch_adj_line(const AdjArgs& a, void* stream) {
-  constexpr int threads = 128;
-  static int resident = 0;
-  if (resident == 0) {
+  static int resident = 0, resident_smem = -1, resident_threads = -1;
+  static bool opted = false;
+  if (!opted) {
+    if (cudaFuncSetAttribute(adj_tile_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             kMaxTileSmem) != cudaSuccess)
+      cudaGetLastError();  // the launch then reports a tile that does not fit
+    opted = true;
+  }
+  if (resident_smem != a.smem_bytes || resident_threads != a.threads) {
     int dev = 0, sms = 0, per_sm = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, adj_line_kernel, threads, 0);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, adj_tile_kernel, a.threads,
+                                                  a.smem_bytes);
     resident = sms * (per_sm > 0 ? per_sm : 1);
+    resident_smem = a.smem_bytes;
+    resident_threads = a.threads;
   }
-  const int need = (a.n_tasks * 32 + threads - 1) / threads;
-  adj_line_kernel<<<need < resident ? need : resident, threads, 0, (cudaStream_t)stream>>>(a);
+  const int blocks = a.n_tiles < resident ? a.n_tiles : resident;
+  adj_tile_kernel<<<blocks, a.threads, a.smem_bytes, (cudaStream_t)stream>>>(a);
   count_launch();
   return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }
@@ -238,125 +231,153 @@ int launch_adj_line(const AdjArgs& a, void* stream) {
 // per-node gather of dJ/dT^n and of the parameter terms
 // ---------------------------------------------------------------------------
 constexpr int kGradMax = 2 + 2 * CC_MAX_LAYERS;
+constexpr int kGatherLines = 8;  // lines per thread: the axial face is carried down
 
+// Warp task (column block cb, line block jb): lane l holds column 31 cb + l
+// (lane 0 of cb > 0 only supplies its east face to lane 1) on the lines
+// 8 jb .. 8 jb + 7.  Every face conductivity and its derivatives are
+// evaluated once per face: the east face per lane (the west face comes from
+// the left lane), the north face per line (the south face is the previous
+// line's north face).
 __global__ void __launch_bounds__(256) adj_gather_kernel(const AdjArgs a) {
   __shared__ double sg[kGradMax];
   const int inst = blockIdx.y;
   const DevInst& I = a.insts[inst];
   const int nr = I.nr, N = nr - 1, M = I.nz - 1;
   const int L = a.n_layers[inst];
+  const int lane = threadIdx.x & 31;
   if (threadIdx.x < kGradMax) sg[threadIdx.x] = 0.0;
   __syncthreads();
-  // this node's parameter terms: q0, t_on, lam_scale[mL], cap_scale[mC]
-  // (a second lam_scale term at mL2 for interface rows); summed over the warp
-  // per parameter below, so that the block's shared sums see one add per warp
+  // this column's parameter terms over its lines: q0, t_on, lam_scale[mL],
+  // cap_scale[mC] (a second lam_scale term at mL2 for interface columns);
+  // summed over the warp per parameter below
   double pq = 0.0, pt = 0.0, pl = 0.0, pl2 = 0.0, pc = 0.0;
   int mL = -1, mL2 = -1, mC = -1;
-  const long long node = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  if (node < (long long)nr * I.nz) {
-    const int j = (int)(node / nr), i = (int)(node - (long long)j * nr);
+  const int ncb = (N + 30) / 31, njb = (M + kGatherLines) / kGatherLines;
+  const int w = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+  if (w < ncb * njb) {  // warp-uniform
+    const int cb = w % ncb, jb = w / ncb;
+    const int i = 31 * cb + lane;
+    const int ic = i <= N ? i : N;
+    const bool own = (i <= N) && (lane > 0 || cb == 0);
     const double* X = a.x + I.t_off;
     const double* Y = a.y + I.t_off;
     const double* XI = a.xi + I.t_off;
-    const long long rj = (long long)j * nr;
-    const double T = X[rj + i];
-    const RowGeo& g = I.rg[i];
+    const RowGeo g = I.rg[ic];
     const int frule = I.face_rule;
-    const bool line = (j >= 1 && j <= M - 1);  // own row belongs to a solved line
     const double tau_inv = I.inv_tau;
-    double acc = 0.0;
-    // radial faces (i-1, i) of material seg[i-1] and (i, i+1) of material seg[i]
-    double lW = 0.0, lWa = 0.0, lWb = 0.0, lE = 0.0, lEa = 0.0, lEb = 0.0;
-    if (i >= 1) lam_face_d(I.mat[I.rg[i - 1].seg], frule, X[rj + i - 1], T, lW, lWa, lWb);
-    if (i <= N - 1) lam_face_d(I.mat[g.seg], frule, T, X[rj + i + 1], lE, lEa, lEb);
-    const double yi = Y[rj + i];
-    // rows i-1 and i+1 of the same line
-    if (line) {
-      if (i >= 1) {
-        const RowGeo& gw = I.rg[i - 1];
-        const double xw = XI[rj + i - 1], dy = yi - Y[rj + i - 1];
-        if (gw.cls == RC_REGULAR) acc = fma(xw * gw.gC * lWb, dy, acc);
-        else if (gw.cls == RC_IFACE && I.interface_rule == 1)
-          acc = fma(xw * gw.re * lWb * gw.hw, dy, acc);
-      }
-      if (i <= N - 1) {
-        const RowGeo& ge = I.rg[i + 1];
-        const double xe = XI[rj + i + 1], dy = yi - Y[rj + i + 1];
-        if (ge.cls == RC_REGULAR) acc = fma(xe * ge.gA * lEa, dy, acc);
-        else if (ge.cls == RC_IFACE && I.interface_rule == 1)
-          acc = fma(xe * ge.rw * lEa * ge.he, dy, acc);
-      }
-    }
-    if (g.cls == RC_REGULAR) {
-      const int m = g.seg;
-      const DevMaterial& Mt = I.mat[m];
-      // axial faces (j-1, j) and (j, j+1)
-      double lS = 0.0, lSa = 0.0, lSb = 0.0, lN = 0.0, lNa = 0.0, lNb = 0.0;
-      const double Ts = (j >= 1) ? X[rj - nr + i] : 0.0, Tn = (j <= M - 1) ? X[rj + nr + i] : 0.0;
-      if (j >= 1) lam_face_d(Mt, frule, Ts, T, lS, lSa, lSb);
-      if (j <= M - 1) lam_face_d(Mt, frule, T, Tn, lN, lNa, lNb);
-      // rows (i, j+1) and (i, j-1) read T through their south / north faces
-      if (j + 1 >= 1 && j + 1 <= M - 1)
-        acc = fma(XI[rj + nr + i] * I.zg[j + 1].gzs, fma(-lNa, Tn - T, lN), acc);
-      if (j - 1 >= 1 && j - 1 <= M - 1)
-        acc = fma(XI[rj - nr + i] * I.zg[j - 1].gzn, fma(lSb, T - Ts, lS), acc);
-      if (line) {
-        const double xi = XI[rj + i];
-        const ZGeo& zg = I.zg[j];
-        double c, dc;
-        cap_d(Mt, T, c, dc);
-        const double rct = Mt.rho * c * tau_inv, drct = Mt.rho * dc * tau_inv;
-        const double gw = Y[rj + i - 1] - yi, ge = Y[rj + i + 1] - yi;
-        const double dN = Tn - T, dS = T - Ts;
-        double d0 = fma(drct, T - yi, rct);
-        d0 = fma(fma(lNa, dN, -lN), zg.gzn, d0);
-        d0 = fma(-fma(lSb, dS, lS), zg.gzs, d0);
-        d0 = fma(g.gA * lWb, gw, d0);
-        d0 = fma(g.gC * lEa, ge, d0);
-        const bool heat = (m == I.src_layer);
-        const long long sidx = a.step * a.n_inst + inst;
-        double gT = 1.0, dgT = 0.0;
-        if (heat && I.g_model == 1) {
-          gT = I.g_ref * rsqrt(T);
-          dgT = -0.5 * gT * frcp(T);
+    const bool regular = (g.cls == RC_REGULAR);
+    const DevMaterial& Mt = I.mat[g.seg];
+    const int j_lo = kGatherLines * jb;
+    const int j_hi = min(j_lo + kGatherLines - 1, M);
+    double Ts = (j_lo >= 1) ? X[(long long)(j_lo - 1) * nr + ic] : 0.0;
+    double T = X[(long long)j_lo * nr + ic];
+    double lS = 0.0, lSa = 0.0, lSb = 0.0;  // face (j-1, j) of a regular column
+    if (regular && j_lo >= 1) lam_face_d(Mt, frule, Ts, T, lS, lSa, lSb);
+    for (int j = j_lo; j <= j_hi; ++j) {  // same lines for the whole warp
+      const long long rj = (long long)j * nr;
+      const double Tn = (j <= M - 1) ? X[rj + nr + ic] : 0.0;
+      // radial faces (i, i+1) of material seg[i], (i-1, i) from the left lane
+      double lE = 0.0, lEa = 0.0, lEb = 0.0;
+      if (ic <= N - 1) lam_face_d(Mt, frule, T, X[rj + ic + 1], lE, lEa, lEb);
+      double lW = __shfl_up_sync(kFull, lE, 1);
+      double lWb = __shfl_up_sync(kFull, lEb, 1);
+      if (i == 0) lW = lWb = 0.0;
+      // axial face (j, j+1) of a regular column
+      double lN = 0.0, lNa = 0.0, lNb = 0.0;
+      if (regular && j <= M - 1) lam_face_d(Mt, frule, T, Tn, lN, lNa, lNb);
+      if (own) {
+        const bool line = (j >= 1 && j <= M - 1);  // own row belongs to a solved line
+        const double yi = Y[rj + ic];
+        double acc = 0.0;
+        // rows i-1 and i+1 of the same line
+        if (line) {
+          if (ic >= 1) {
+            const RowGeo& gw = I.rg[ic - 1];
+            const double xw = XI[rj + ic - 1], dy = yi - Y[rj + ic - 1];
+            if (gw.cls == RC_REGULAR) acc = fma(xw * gw.gC * lWb, dy, acc);
+            else if (gw.cls == RC_IFACE && I.interface_rule == 1)
+              acc = fma(xw * gw.re * lWb * gw.hw, dy, acc);
+          }
+          if (ic <= N - 1) {
+            const RowGeo& ge = I.rg[ic + 1];
+            const double xe = XI[rj + ic + 1], dy = yi - Y[rj + ic + 1];
+            if (ge.cls == RC_REGULAR) acc = fma(xe * ge.gA * lEa, dy, acc);
+            else if (ge.cls == RC_IFACE && I.interface_rule == 1)
+              acc = fma(xe * ge.rw * lEa * ge.he, dy, acc);
+          }
         }
-        if (heat) d0 = fma(I.q0 * a.s_tab[sidx], dgT, d0);
-        acc = fma(xi, d0, acc);
-        // parameters of this row
-        const double lam_part =
-            fma(g.gC * lE, ge, fma(g.gA * lW, gw, fma(lN * zg.gzn, dN, -lS * zg.gzs * dS)));
-        pl = xi * lam_part * Mt.inv_lam_scale;
-        mL = m;
-        pc = xi * rct * (T - yi) * Mt.inv_cap_scale;
-        mC = m;
-        if (heat) {
-          pq = xi * a.s_tab[sidx] * gT;
-          pt = xi * I.q0 * a.ds_tab[sidx] * gT;
+        if (regular) {
+          const int m = g.seg;
+          // rows (i, j+1) and (i, j-1) read T through their south / north faces
+          if (j + 1 >= 1 && j + 1 <= M - 1)
+            acc = fma(XI[rj + nr + ic] * I.zg[j + 1].gzs, fma(-lNa, Tn - T, lN), acc);
+          if (j - 1 >= 1 && j - 1 <= M - 1)
+            acc = fma(XI[rj - nr + ic] * I.zg[j - 1].gzn, fma(lSb, T - Ts, lS), acc);
+          if (line) {
+            const double xi = XI[rj + ic];
+            const ZGeo& zg = I.zg[j];
+            double c, dc;
+            cap_d(Mt, T, c, dc);
+            const double rct = Mt.rho * c * tau_inv, drct = Mt.rho * dc * tau_inv;
+            const double gw = Y[rj + ic - 1] - yi, ge = Y[rj + ic + 1] - yi;
+            const double dN = Tn - T, dS = T - Ts;
+            double d0 = fma(drct, T - yi, rct);
+            d0 = fma(fma(lNa, dN, -lN), zg.gzn, d0);
+            d0 = fma(-fma(lSb, dS, lS), zg.gzs, d0);
+            d0 = fma(g.gA * lWb, gw, d0);
+            d0 = fma(g.gC * lEa, ge, d0);
+            const bool heat = (m == I.src_layer);
+            const long long sidx = a.step * a.n_inst + inst;
+            double gT = 1.0, dgT = 0.0;
+            if (heat && I.g_model == 1) {
+              gT = I.g_ref * rsqrt(T);
+              dgT = -0.5 * gT * frcp(T);
+            }
+            if (heat) d0 = fma(I.q0 * a.s_tab[sidx], dgT, d0);
+            acc = fma(xi, d0, acc);
+            // parameters of this row
+            const double lam_part =
+                fma(g.gC * lE, ge, fma(g.gA * lW, gw, fma(lN * zg.gzn, dN, -lS * zg.gzs * dS)));
+            pl = fma(xi * lam_part, Mt.inv_lam_scale, pl);
+            mL = m;
+            pc = fma(xi * rct * (T - yi), Mt.inv_cap_scale, pc);
+            mC = m;
+            if (heat) {
+              pq = fma(xi * a.s_tab[sidx], gT, pq);
+              pt = fma(xi * I.q0 * a.ds_tab[sidx], gT, pt);
+            }
+          }
+        } else if (g.cls == RC_IFACE && line) {
+          const double xi = XI[rj + ic];
+          const int mi = g.segw, mo = g.seg;
+          const double gw = Y[rj + ic - 1] - yi, ge = Y[rj + ic + 1] - yi;
+          double lm, lp, dlm, dlp;
+          if (I.interface_rule == 0) {
+            lm = lam_eval(I.mat[mi], T);
+            lp = lam_eval(I.mat[mo], T);
+            dlm = dlam_node(I.mat[mi], T, lm);
+            dlp = dlam_node(I.mat[mo], T, lp);
+          } else {
+            lm = g.rw * lW;
+            lp = g.re * lE;
+            dlm = g.rw * lWb;
+            dlp = g.re * lEa;
+          }
+          acc = fma(xi, fma(dlm * g.he, gw, dlp * g.hw * ge), acc);
+          pl = fma(xi * lm * g.he * gw, I.mat[mi].inv_lam_scale, pl);
+          mL = mi;
+          pl2 = fma(xi * lp * g.hw * ge, I.mat[mo].inv_lam_scale, pl2);
+          mL2 = mo;
         }
+        a.lam_out[I.t_off + rj + ic] = acc;
       }
-    } else if (g.cls == RC_IFACE && line) {
-      const double xi = XI[rj + i];
-      const int mi = g.segw, mo = g.seg;
-      const double gw = Y[rj + i - 1] - yi, ge = Y[rj + i + 1] - yi;
-      double lm, lp, dlm, dlp;
-      if (I.interface_rule == 0) {
-        lm = lam_eval(I.mat[mi], T);
-        lp = lam_eval(I.mat[mo], T);
-        dlm = dlam_node(I.mat[mi], T, lm);
-        dlp = dlam_node(I.mat[mo], T, lp);
-      } else {
-        lm = g.rw * lW;
-        lp = g.re * lE;
-        dlm = g.rw * lWb;
-        dlp = g.re * lEa;
-      }
-      acc = fma(xi, fma(dlm * g.he, gw, dlp * g.hw * ge), acc);
-      pl = xi * lm * g.he * gw * I.mat[mi].inv_lam_scale;
-      mL = mi;
-      pl2 = xi * lp * g.hw * ge * I.mat[mo].inv_lam_scale;
-      mL2 = mo;
+      Ts = T;
+      T = Tn;
+      lS = lN;
+      lSa = lNa;
+      lSb = lNb;
     }
-    a.lam_out[I.t_off + rj + i] = acc;
   }
   // warp sums per parameter (the block is warp-uniform here)
   for (int p = 0; p < 2 + 2 * L; ++p) {
@@ -368,7 +389,7 @@ __global__ void __launch_bounds__(256) adj_gather_kernel(const AdjArgs a) {
     if (__any_sync(kFull, v != 0.0)) {
 #pragma unroll
       for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(kFull, v, o);
-      if ((threadIdx.x & 31) == 0) atomicAdd(&sg[p], v);
+      if (lane == 0) atomicAdd(&sg[p], v);
     }
   }
   __syncthreads();
@@ -376,9 +397,10 @@ __global__ void __launch_bounds__(256) adj_gather_kernel(const AdjArgs a) {
     atomicAdd(a.grad + a.grad_off[inst] + threadIdx.x, sg[threadIdx.x]);
 }
 
-int launch_adj_gather(const AdjArgs& a, long long max_nodes, void* stream) {
+int launch_adj_gather(const AdjArgs& a, int max_nr, int max_nz, void* stream) {
   const int threads = 256;
-  const dim3 grid((unsigned)((max_nodes + threads - 1) / threads), (unsigned)a.n_inst);
+  const long long warps = (long long)((max_nr - 1 + 30) / 31) * ((max_nz + kGatherLines - 1) / kGatherLines);
+  const dim3 grid((unsigned)((warps * 32 + threads - 1) / threads), (unsigned)a.n_inst);
   adj_gather_kernel<<<grid, threads, 0, (cudaStream_t)stream>>>(a);
   count_launch();
   return cudaGetLastError() == cudaSuccess ? 0 : -1;

@@ -1049,19 +1049,20 @@ int adjoint_impl(cc_ctx* c, const void* T0_dev, int64_t n_steps, double t0, doub
   const long long K = ckpt > 0 ? ckpt : 256;
   const long long n_ck = (n_steps + K - 1) / K;
   const size_t nodes = (size_t)c->total_nodes;
-  long long max_nodes = 0;
+  int max_nr = 0, max_nz = 0;
   std::vector<long long> goff(n);
   std::vector<int> nl(n);
   long long gsum = 0;
   for (int k = 0; k < n; ++k) {
-    max_nodes = std::max(max_nodes, (long long)c->inst[k].d.nr * c->inst[k].d.nz);
+    max_nr = std::max(max_nr, c->inst[k].d.nr);
+    max_nz = std::max(max_nz, c->inst[k].d.nz);
     goff[k] = gsum;
     nl[k] = c->inst[k].d.n_layers;
     gsum += 2 + 2 * nl[k];
   }
-  // scratch layout (doubles): checkpoints, segment states, lam x2, xi, sa, sb, sc,
+  // scratch layout (doubles): checkpoints, segment states, lam x2, xi,
   // trace, seed, s, ds, grad offsets and layer counts
-  const size_t need = nodes * (size_t)(n_ck + K + 1 + 6) + (size_t)n * n_steps * 5 + 2 * (size_t)n + 8;
+  const size_t need = nodes * (size_t)(n_ck + K + 1 + 3) + (size_t)n * n_steps * 5 + 2 * (size_t)n + 8;
   if (c->adj_cap < need) {
     cudaFree(c->d_adj);
     c->d_adj = nullptr;
@@ -1078,9 +1079,6 @@ int adjoint_impl(cc_ctx* c, const void* T0_dev, int64_t n_steps, double t0, doub
   double* lamA = p; p += nodes;
   double* lamB = p; p += nodes;
   double* xi = p; p += nodes;
-  double* sa = p; p += nodes;
-  double* sb = p; p += nodes;
-  double* sc = p; p += nodes;
   double* trace = p; p += (size_t)n * n_steps * 2;
   double* seed = p; p += (size_t)n * n_steps;
   double* s_tab = p; p += (size_t)n * n_steps;
@@ -1092,7 +1090,8 @@ int adjoint_impl(cc_ctx* c, const void* T0_dev, int64_t n_steps, double t0, doub
       cudaMemsetAsync(trace, 0, sizeof(double) * 2 * n * n_steps, st) ||
       cudaMemsetAsync(lamA, 0, sizeof(double) * nodes, st) ||
       cudaMemsetAsync(grad_dev, 0, sizeof(double) * gsum, st) ||
-      cudaMemcpyAsync(segs, T0_dev, sizeof(double) * nodes, cudaMemcpyDeviceToDevice, st))
+      cudaMemcpyAsync(segs + nodes * ((n_ck - 1) * K & 1), T0_dev, sizeof(double) * nodes,
+                      cudaMemcpyDeviceToDevice, st))
     return CC_ECUDA;
   if (launch_waveform(c->d_inst, n, n_steps, t0, s_tab, stream, ds_tab)) return CC_ECUDA;
   StepArgs a{};
@@ -1109,16 +1108,20 @@ int adjoint_impl(cc_ctx* c, const void* T0_dev, int64_t n_steps, double t0, doub
   a.n_steps = n_steps;
   a.err = c->d_err;
   a.threads = c->threads;
-  // forward sweep with checkpoints (slots 0 and 1 of the segment buffer)
+  // forward sweep with checkpoints: slots 0 and 1 of the segment buffer in
+  // turn, arranged so that the last segment starts in slot 0 and keeps all
+  // its states (it needs no recompute)
+  const long long lo_last = (n_ck - 1) * K;
+  auto slot = [&](long long s) { return s >= lo_last ? s - lo_last : (s + lo_last) & 1; };
   for (long long s = 0; s < n_steps; ++s) {
-    double* cur = segs + nodes * (s & 1);
-    if (s % K == 0 &&
+    double* cur = segs + nodes * slot(s);
+    if (s % K == 0 && s < lo_last &&
         cudaMemcpyAsync(ck + nodes * (s / K), cur, sizeof(double) * nodes, cudaMemcpyDeviceToDevice,
                         st))
       return CC_ECUDA;
     a.step = s;
     a.Tin = cur;
-    a.Tout = segs + nodes * ((s + 1) & 1);
+    a.Tout = segs + nodes * slot(s + 1);
     a.trace = trace;
     if (launch_step_fp64(a, stream)) return CC_ECUDA;
   }
@@ -1132,12 +1135,11 @@ int adjoint_impl(cc_ctx* c, const void* T0_dev, int64_t n_steps, double t0, doub
   // reverse sweep, one checkpoint segment at a time
   AdjArgs b{};
   b.insts = c->d_inst;
-  b.tasks = c->d_tasks;
-  b.n_tasks = c->n_tasks;
+  b.tiles = c->d_tiles;
+  b.n_tiles = c->n_tiles;
+  b.threads = c->threads;
+  b.smem_bytes = c->smem_bytes;  // FP64 tiles: five rows and more per line
   b.n_inst = n;
-  b.sa = sa;
-  b.sb = sb;
-  b.sc = sc;
   b.xi = xi;
   b.seed = seed;
   b.s_tab = s_tab;
@@ -1149,9 +1151,10 @@ int adjoint_impl(cc_ctx* c, const void* T0_dev, int64_t n_steps, double t0, doub
   a.trace = nullptr;
   for (long long k = n_ck - 1; k >= 0; --k) {
     const long long lo = k * K, hi = std::min(lo + K, (long long)n_steps);
-    if (cudaMemcpyAsync(segs, ck + nodes * k, sizeof(double) * nodes, cudaMemcpyDeviceToDevice, st))
-      return CC_ECUDA;
-    for (long long s = lo; s < hi; ++s) {
+    for (long long s = lo; s < hi && k < n_ck - 1; ++s) {  // recompute the segment
+      if (s == lo && cudaMemcpyAsync(segs, ck + nodes * k, sizeof(double) * nodes,
+                                     cudaMemcpyDeviceToDevice, st))
+        return CC_ECUDA;
       a.step = s;
       a.Tin = segs + nodes * (s - lo);
       a.Tout = segs + nodes * (s - lo + 1);
@@ -1163,7 +1166,7 @@ int adjoint_impl(cc_ctx* c, const void* T0_dev, int64_t n_steps, double t0, doub
       b.y = segs + nodes * (s - lo + 1);
       b.lam = lamA;
       b.lam_out = lamB;
-      if (launch_adj_line(b, stream) || launch_adj_gather(b, max_nodes, stream)) return CC_ECUDA;
+      if (launch_adj_line(b, stream) || launch_adj_gather(b, max_nr, max_nz, stream)) return CC_ECUDA;
       std::swap(lamA, lamB);
     }
   }

@@ -200,18 +200,20 @@ struct StepArgs {
 };
 
 // Reverse sweep of the adjoint (ccell_adjoint.cu).
+#ifndef CC_ADJ_MAX_THREADS
+#define CC_ADJ_MAX_THREADS 256
+#endif
 struct AdjArgs {
   const DevInst* insts;
-  const Task* tasks;
-  int n_tasks;
+  const TileTask* tiles;  // CTA tiles of lines (those of the step kernels)
+  int n_tiles;
+  int threads;            // block size the tiles were cut for
+  int smem_bytes;         // >= 4 rows of nl x nrp doubles
   int n_inst;
   const double* x;       // T^n, all instances
   const double* y;       // T^{n+1}
   const double* lam;     // dJ/dT^{n+1} (without the seed of step n)
   double* lam_out;       // dJ/dT^n
-  double* sa;            // row coefficients of the step, [node]
-  double* sb;
-  double* sc;
   double* xi;            // M^{-T} mu, [node]
   const double* seed;    // [n_inst][n_steps]: dJ/dSbar_n
   const double* s_tab;   // [n_steps][n_inst] waveform
@@ -257,7 +259,7 @@ int launch_waveform(const DevInst* insts, int n_inst, long long n_steps, double 
                     double* s_tab, void* stream, double* ds_tab = nullptr);
 // adjoint (ccell_adjoint.cu)
 int launch_adj_line(const AdjArgs& a, void* stream);
-int launch_adj_gather(const AdjArgs& a, long long max_nodes, void* stream);
+int launch_adj_gather(const AdjArgs& a, int max_nr, int max_nz, void* stream);
 int launch_adj_seed(const DevInst* insts, int n_inst, const double* trace, const double* target,
                     long long n_steps, double* seed, double* loss, void* stream);
 int launch_step_fp64(const StepArgs& a, void* stream);

@@ -167,3 +167,19 @@ def test_gpu_adjoint_256x1024_short_horizon():
     assert abs(lg[0] - lo) <= 1e-10 * lo
     assert np.max(np.abs(gg - go)) <= 1e-8 * np.max(np.abs(go)), (gg, go)
     assert np.max(np.abs(dg.reshape(T0.shape) - do)) <= 1e-8 * np.max(np.abs(do))
+
+
+@pytest.mark.parametrize("ckpt", [1, 7, 37, 59, 60, 1000])
+def test_gpu_adjoint_checkpoint_invariance(ckpt):
+    """The gradient does not depend on the checkpoint interval: many segments,
+    a last segment starting at an odd step (37, 59), one segment (60, 1000)."""
+    cfg = _case()
+    n = 60
+    t0 = 1.0e-3 - 30 * cfg["dt"]
+    T0 = inputs.initial_field(cfg, "smooth", seed=6)
+    target = inputs.target_waveform(cfg, t0 + cfg["dt"] * np.arange(1, n + 1))
+    lo, go, do = oracle.adjoint(cfg, T0, n, t0, cfg["dt"], target, ckpt=16)
+    lg, gg, dg = _gpu_adjoint([cfg], [T0], n, t0, [target], ckpt=ckpt)
+    assert abs(lg[0] - lo) <= 1e-10 * lo
+    assert np.max(np.abs(gg - go)) <= 1e-8 * np.max(np.abs(go)), (gg, go)
+    assert np.max(np.abs(dg.reshape(T0.shape) - do)) <= 1e-8 * np.max(np.abs(do))
