@@ -39,7 +39,7 @@ FLOPS_PER_NODE_FP64 = 150     # FP64 operations per node-update (2 power laws ~ 
 # on the 512x4096 workload, from the ncu capture summarised in
 # profiles/step_fp64_kernel_512x4096.md (cache flushed before the launch).  Valid only for the
 # kernel as captured there: reset to None when the kernel changes.
-STEP_FP64_TRAFFIC_512x4096 = 17.213952e6 + 0.0
+STEP_FP64_TRAFFIC_512x4096 = 17.251328e6 + 1.536e3
 FP64_PEAK_TFLOPS = 152 * 4 * 0.5 * 2 * 2.07e9 / 1e12   # SMs x SMSPs x DFMA lanes/clk x 2 x max clock
 L2_FLUSH_BYTES = 256 << 20
 
