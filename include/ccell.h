@@ -299,7 +299,7 @@ int cc_destroy(cc_ctx* ctx);
  * first use.  This call allocates nothing, on the device or the host: its
  * scratch (tables, work list, waveform table, error word, and the ping-pong
  * partner of T_dev) lives in a file-scope static device array of about
- * 9.5 MiB that every GPU loading the library holds until the process exits.
+ * 9.4 MiB that every GPU loading the library holds until the process exits.
  *   desc        geometry (precision must be CC_FP64, a rectangle:
  *               step_layers 0, else CC_EUNSUPPORTED); materials[n_layers];
  *               source (layer -1 for none).  Same meaning as cc_create_geometry,

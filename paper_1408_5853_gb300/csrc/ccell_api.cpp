@@ -42,8 +42,6 @@ struct cc_ctx {
   DevInst* d_inst = nullptr;
   RowGeo* d_rg = nullptr;
   ZGeo* d_zg = nullptr;
-  Task* d_tasks = nullptr;
-  int n_tasks = 0;
   TileTask* d_tiles = nullptr;
   int n_tiles = 0;
   size_t tiles_cap = 0;
@@ -65,7 +63,6 @@ struct cc_ctx {
   // threads per block; target rows per lane (sets the lanes per line G)
   int mode = 0, threads = 256, rows = kRowsPerLane;
   bool tasks_dirty = true;
-  size_t tasks_cap = 0;
   void* d_tune = nullptr;  // autotuner copy of the caller's field
   // ADI variant: column tasks and scratch, built on first use
   AdiTask* d_adi_tasks = nullptr;
@@ -253,7 +250,6 @@ void free_device(cc_ctx* c) {
   cudaFree(c->d_inst);
   cudaFree(c->d_rg);
   cudaFree(c->d_zg);
-  cudaFree(c->d_tasks);
   cudaFree(c->d_tiles);
   c->d_tiles = nullptr;
   c->tiles_cap = 0;
@@ -277,11 +273,9 @@ void free_device(cc_ctx* c) {
   cudaFree(c->d_adi);
   c->d_adi = nullptr;
   c->adi_scratch = 0;
-  c->tasks_cap = 0;
   c->d_inst = nullptr;
   c->d_rg = nullptr;
   c->d_zg = nullptr;
-  c->d_tasks = nullptr;
   c->d_T2 = nullptr;
   c->d_lo = nullptr;
   c->d_s = nullptr;
@@ -395,32 +389,17 @@ int upload(cc_ctx* c, const std::vector<double>& dts, cudaStream_t st) {
     // Lanes per line from the rows-per-lane policy; when the lines of all
     // instances give fewer than kMinWarpTasks warp tasks, use more lanes per
     // line (fewer rows per lane) so that every SM sub-partition has work.
-    constexpr int kMinWarpTasks = 2048;
-    std::vector<Task> tasks;
+    constexpr long long kMinWarpTasks = 2048;
     for (int rows = c->rows;; rows /= 2) {
-      tasks.clear();
+      long long warp_tasks = 0;  // 32/G lines each
       for (int k = 0; k < n; ++k) {
         Instance& in = c->inst[k];
         in.G = choose_lanes(in.d.nr, rows);
         const int lpw = 32 / in.G;
-        for (int j0 = 1; j0 <= in.d.nz - 2; j0 += lpw) tasks.push_back(Task{k, j0});
+        warp_tasks += (in.d.nz - 2 + lpw - 1) / lpw;
       }
-      if ((int)tasks.size() >= kMinWarpTasks || rows <= 4) break;
+      if (warp_tasks >= kMinWarpTasks || rows <= 4) break;
     }
-    if (tasks.size() > c->tasks_cap) {
-      cudaFree(c->d_tasks);
-      c->d_tasks = nullptr;
-      c->tasks_cap = 0;
-      if (cudaMalloc(&c->d_tasks, sizeof(Task) * tasks.size()) != cudaSuccess) {
-        cudaGetLastError();
-        return CC_ENOMEM;
-      }
-      c->tasks_cap = tasks.size();
-    }
-    if (cudaMemcpy(c->d_tasks, tasks.data(), sizeof(Task) * tasks.size(),
-                   cudaMemcpyHostToDevice) != cudaSuccess)
-      return CC_ECUDA;
-    c->n_tasks = (int)tasks.size();
     // FP64 CTA tiles: (threads / 32) warps x 32/G lines
     // CTA tiles of the step kernels: lines of one instance, at most lpc of
     // them.  The blocks of a launch (its resident capacity) take equal shares
@@ -731,8 +710,6 @@ int cc_step_n(cc_ctx* c, void* T_dev, int64_t n_steps, double t0, double dt_s, d
   const size_t elem = c->precision == CC_FP64 ? sizeof(double) : sizeof(float);
   StepArgs a{};
   a.insts = c->d_inst;
-  a.tasks = c->d_tasks;
-  a.n_tasks = c->n_tasks;
   a.tiles = c->d_tiles;
   a.n_tiles = c->n_tiles;
   a.cta_start = c->n_cta > 0 ? c->d_cta : nullptr;
@@ -756,7 +733,7 @@ int cc_step_n(cc_ctx* c, void* T_dev, int64_t n_steps, double t0, double dt_s, d
   }
   void* bufs[2] = {T_dev, c->d_T2};
   if (c->precision == CC_MIXED) {
-    if (launch_mixed_init(c->d_inst, n, c->d_tasks, c->n_tasks, c->d_lo, c->total_nodes, stream))
+    if (launch_mixed_init(c->d_lo, c->total_nodes, stream))
       return CC_ECUDA;
   }
   bool done = false;
@@ -868,8 +845,6 @@ int cc_step_adi_n(cc_ctx* c, void* T_dev, int64_t n_steps, double t0, double dt_
     return CC_ECUDA;
   StepArgs a{};
   a.insts = c->d_inst;
-  a.tasks = c->d_tasks;
-  a.n_tasks = c->n_tasks;
   a.tiles = c->d_tiles;
   a.n_tiles = c->n_tiles;
   a.cta_start = c->n_cta > 0 ? c->d_cta : nullptr;
@@ -1096,8 +1071,6 @@ int adjoint_impl(cc_ctx* c, const void* T0_dev, int64_t n_steps, double t0, doub
   if (launch_waveform(c->d_inst, n, n_steps, t0, s_tab, stream, ds_tab)) return CC_ECUDA;
   StepArgs a{};
   a.insts = c->d_inst;
-  a.tasks = c->d_tasks;
-  a.n_tasks = c->n_tasks;
   a.tiles = c->d_tiles;
   a.n_tiles = c->n_tiles;
   a.cta_start = c->n_cta > 0 ? c->d_cta : nullptr;

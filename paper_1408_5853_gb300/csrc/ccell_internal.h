@@ -105,12 +105,6 @@ __device__ __forceinline__ int line_class(const DevInst& I, int cls, int i, int 
 }
 #endif
 
-// One warp's work: 32/G consecutive lines of one instance.
-struct Task {
-  int inst;
-  int j0;
-};
-
 // One CTA's work in the FP64 step: nl consecutive lines starting at j0
 // (nl <= warps per CTA x 32/G).
 struct TileTask {
@@ -167,8 +161,6 @@ inline void number_ifaces(RowGeo* rg, int nr) {
 // Everything one step launch needs.
 struct StepArgs {
   const DevInst* insts;
-  const Task* tasks;
-  int n_tasks;
   const TileTask* tiles; // FP64 step: CTA tiles
   int n_tiles;
   const int* cta_start;  // FP64 step: tiles [cta_start[b], cta_start[b+1]) of block b, or
@@ -275,8 +267,7 @@ int launch_step_mixed(const StepArgs& a, void* stream);
 // (and lo_in/lo_out for mixed).  Returns -3 if the grid cannot be co-resident.
 int launch_steps_fp64_persistent(const StepArgs& a, long long n, void* stream);
 int launch_steps_mixed_persistent(const StepArgs& a, long long n, void* stream);
-int launch_mixed_init(const DevInst* insts, int n_inst, const Task* tasks, int n_tasks,
-                      float* lo, long long n_total, void* stream);
+int launch_mixed_init(float* lo, long long n_total, void* stream);
 int launch_boundary_trace_zero(double* trace, long long n, void* stream);
 long long kernel_launch_count();
 // Host: fill one power-law table for exponent b and scales; returns false if

@@ -41,8 +41,7 @@ constexpr size_t kOffInst = 0;
 constexpr size_t kOffErr = align256(kOffInst + sizeof(DevInst));
 constexpr size_t kOffRg = align256(kOffErr + sizeof(unsigned));
 constexpr size_t kOffZg = align256(kOffRg + sizeof(RowGeo) * CC_NOALLOC_MAX_NR);
-constexpr size_t kOffTask = align256(kOffZg + sizeof(ZGeo) * CC_NOALLOC_MAX_NZ);
-constexpr size_t kOffTile = align256(kOffTask + sizeof(Task) * CC_NOALLOC_MAX_NZ);
+constexpr size_t kOffTile = align256(kOffZg + sizeof(ZGeo) * CC_NOALLOC_MAX_NZ);
 constexpr size_t kOffS = align256(kOffTile + sizeof(TileTask) * CC_NOALLOC_MAX_NZ);
 constexpr size_t kOffT2 = align256(kOffS + sizeof(double) * CC_NOALLOC_MAX_STEPS);
 constexpr size_t kScratchBytes = align256(kOffT2 + sizeof(double) * CC_NOALLOC_MAX_NODES);
@@ -57,7 +56,6 @@ unsigned char* g_dev_ptr[kMaxDevices];  // device address of the array, per devi
 DevInst h_inst;
 RowGeo h_rg[CC_NOALLOC_MAX_NR];
 ZGeo h_zg[CC_NOALLOC_MAX_NZ];
-Task h_task[CC_NOALLOC_MAX_NZ];
 TileTask h_tile[CC_NOALLOC_MAX_NZ];
 double h_r[CC_NOALLOC_MAX_NR], h_z[CC_NOALLOC_MAX_NZ];
 int h_cls[CC_NOALLOC_MAX_NR], h_seg[CC_NOALLOC_MAX_NR];
@@ -276,8 +274,6 @@ extern "C" int cc_step_n_noalloc(const cc_geometry_desc* desc, const cc_material
   }
   int G = 1;
   while (G < 32 && (d.nr + G - 1) / G > kRowsPerLane) G <<= 1;
-  int n_tasks = 0;
-  for (int j0 = 1; j0 <= M - 1; j0 += 32 / G) h_task[n_tasks++] = Task{0, j0};
   const int lpc = 4 * (32 / G);  // CTA tiles of the FP64 step: 4 warps, 128 threads
   int n_tiles = 0;
   for (int j0 = 1; j0 <= M - 1; j0 += lpc) h_tile[n_tiles++] = TileTask{0, j0, std::min(lpc, M - j0), 0};
@@ -333,8 +329,6 @@ extern "C" int cc_step_n_noalloc(const cc_geometry_desc* desc, const cc_material
   if (cudaMemcpyAsync(base + kOffInst, &h_inst, sizeof h_inst, cudaMemcpyHostToDevice, st) ||
       cudaMemcpyAsync(base + kOffRg, h_rg, sizeof(RowGeo) * d.nr, cudaMemcpyHostToDevice, st) ||
       cudaMemcpyAsync(base + kOffZg, h_zg, sizeof(ZGeo) * d.nz, cudaMemcpyHostToDevice, st) ||
-      cudaMemcpyAsync(base + kOffTask, h_task, sizeof(Task) * n_tasks, cudaMemcpyHostToDevice,
-                      st) ||
       cudaMemcpyAsync(base + kOffTile, h_tile, sizeof(TileTask) * n_tiles, cudaMemcpyHostToDevice,
                       st) ||
       cudaMemsetAsync(base + kOffErr, 0, sizeof(unsigned), st))
@@ -348,8 +342,6 @@ extern "C" int cc_step_n_noalloc(const cc_geometry_desc* desc, const cc_material
   if (launch_waveform(dinst, 1, n_steps, t0_s, s_tab, stream)) return CC_ECUDA;
   StepArgs a{};
   a.insts = dinst;
-  a.tasks = reinterpret_cast<const Task*>(base + kOffTask);
-  a.n_tasks = n_tasks;
   a.tiles = reinterpret_cast<const TileTask*>(base + kOffTile);
   a.n_tiles = n_tiles;
   a.smem_bytes = smem;

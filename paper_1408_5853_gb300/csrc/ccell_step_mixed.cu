@@ -59,8 +59,7 @@ int launch_step_mixed(const StepArgs& a, void* stream) {
 }
 
 // The low parts of the first state buffer start at zero for every call.
-int launch_mixed_init(const DevInst*, int, const Task*, int, float* lo, long long n_total,
-                      void* stream) {
+int launch_mixed_init(float* lo, long long n_total, void* stream) {
   return cudaMemsetAsync(lo, 0, sizeof(float) * n_total, (cudaStream_t)stream) == cudaSuccess
              ? 0 : -1;
 }
