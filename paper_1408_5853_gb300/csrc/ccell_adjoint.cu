@@ -202,7 +202,7 @@ __global__ void __launch_bounds__(CC_ADJ_MAX_THREADS) adj_tile_kernel(const AdjA
   }
 }
 
-int launch_adj_line(const AdjArgs& a, void* stream) {
+int launch_adj_tile(const AdjArgs& a, void* stream) {
   static int resident = 0, resident_smem = -1, resident_threads = -1;
   static bool opted = false;
   if (!opted) {

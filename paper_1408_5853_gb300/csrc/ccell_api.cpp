@@ -1139,7 +1139,7 @@ int adjoint_impl(cc_ctx* c, const void* T0_dev, int64_t n_steps, double t0, doub
       b.y = segs + nodes * (s - lo + 1);
       b.lam = lamA;
       b.lam_out = lamB;
-      if (launch_adj_line(b, stream) || launch_adj_gather(b, max_nr, max_nz, stream)) return CC_ECUDA;
+      if (launch_adj_tile(b, stream) || launch_adj_gather(b, max_nr, max_nz, stream)) return CC_ECUDA;
       std::swap(lamA, lamB);
     }
   }

@@ -250,7 +250,7 @@ int launch_adi_finish(const AdiArgs& a, void* stream);
 int launch_waveform(const DevInst* insts, int n_inst, long long n_steps, double t0,
                     double* s_tab, void* stream, double* ds_tab = nullptr);
 // adjoint (ccell_adjoint.cu)
-int launch_adj_line(const AdjArgs& a, void* stream);
+int launch_adj_tile(const AdjArgs& a, void* stream);
 int launch_adj_gather(const AdjArgs& a, int max_nr, int max_nz, void* stream);
 int launch_adj_seed(const DevInst* insts, int n_inst, const double* trace, const double* target,
                     long long n_steps, double* seed, double* loss, void* stream);

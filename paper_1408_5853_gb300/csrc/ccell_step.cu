@@ -1,23 +1,17 @@
 // Time-step kernels of the explicit-implicit scheme (Section 3 of Ayriyan et
 // al., arXiv:1408.5853) for sm_103a.
 //
-// One warp task covers 32/G consecutive axial lines j of one instance; each
-// line is owned by G lanes, lane l holding a contiguous segment of rows
-// i in [l*nr/G, (l+1)*nr/G).  Per time step and line:
-//   1. every lane assembles its rows of the tridiagonal system of Eq. (ABC)
-//      (regular nodes), the interface rows of Eq. (cc_first_1) and the
-//      closures of Eq. (first_oder_bc), evaluating lambda(T) and c(T) in
-//      registers (Eqs. (Lambda_i), (Lambda_j), (source));
-//   2. it eliminates the segment's interior rows downwards (the forward
-//      sweep of Eq. (front_sweep) restricted to the segment, keeping the
-//      coupling to the previous segment's last row), and accumulates the
-//      expression of its first interior row in terms of the two segment
-//      separators;
-//   3. the G separator rows form a tridiagonal system solved by parallel
-//      cyclic reduction with warp shuffles;
-//   4. back substitution (Eq. (back_sweep)) inside each segment.
-// For G = 1 this is exactly the Thomas algorithm of the paper with
-// alpha_0 = 1, beta_0 = 0 and That_N = beta_{N-1}/(1 - alpha_{N-1}).
+// One launch per time step.  A block works on CTA tiles of consecutive axial
+// lines of one instance (ccell_fp64_task.cuh): properties and the rows of
+// Eq. (ABC), the interface rows of Eq. (cc_first_1) and the closures of
+// Eq. (first_oder_bc) are assembled in shared memory with the lanes over
+// columns; each line is then solved over G lanes (segment elimination, the
+// forward sweep of Eq. (front_sweep) restricted to a segment; cyclic
+// reduction of the G separator rows with warp shuffles; back substitution,
+// Eq. (back_sweep)).  For G = 1 this is exactly the Thomas algorithm of the
+// paper with alpha_0 = 1, beta_0 = 0 and That_N = beta_{N-1}/(1 - alpha_{N-1}).
+// The blocks of a launch take equal shares of all nodes as ranges of tiles.
+// This file also holds the waveform table kernel and the launch counter.
 #include <cuda_runtime.h>
 
 #include <atomic>

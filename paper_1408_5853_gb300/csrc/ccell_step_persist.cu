@@ -1,5 +1,5 @@
 // FP64 time step, all steps of a call in one cooperative launch (see
-// ccell_step.cu for the scheme and ccell_fp64_task.cuh for one warp task).
+// ccell_step.cu for the scheme and ccell_fp64_task.cuh for one CTA tile).
 #include <cuda_runtime.h>
 
 #include "ccell_fp64_task.cuh"
