@@ -64,3 +64,64 @@ def test_outline_rejections():
             ccell.cc_query_outline(ccell.geometry_desc(cfg))
         with pytest.raises(ValueError):
             oracle.outline(cfg)
+
+
+@pytest.mark.parametrize("case", ["small", "production", "paper"])
+def test_host_stability_bound_matches_oracle(case):
+    """cc_tau_stab (host side of the guard of Eq. (stability_condition)) equals
+    the oracle's bound over the same temperature range."""
+    cfg = {"small": inputs.small_case(q0=1.0), "production": inputs.production_case(),
+           "paper": inputs.paper_case(128, 301)}[case]
+    lo, hi = (4.2, 20.0) if case == "paper" else (cfg["t_dirichlet"], 100.0)
+    cfg["t_guard"] = (lo, hi)
+    sol = ccell.Solver(cfg)          # no device work until the first step
+    try:
+        got = sol.tau_stab(0)
+    finally:
+        sol.close()
+    want = oracle.tau_stab(cfg, lo, hi, 257)
+    assert abs(got - want) <= 1e-12 * want, (got, want)
+
+
+def test_descriptor_and_material_validation():
+    cfg = inputs.small_case(q0=1.0)
+    bad_descs = []
+    for field, value in (("nr", 2), ("nz", 2), ("nr", 513), ("length_m", -1.0),
+                         ("bc_rmax", 2), ("placement", 1), ("face_rule", 3)):
+        d = ccell.geometry_desc(cfg)
+        setattr(d, field, value)
+        bad_descs.append((field, d))
+    for field, d in bad_descs:
+        with pytest.raises(ccell.CCError):
+            ccell.cc_create_geometry([d])
+    ctx = ccell.cc_create_geometry([ccell.geometry_desc(cfg)])
+    try:
+        mats = ccell.materials(cfg)
+        mats[1].rho = 0.0
+        with pytest.raises(ccell.CCError):
+            ccell.cc_set_materials(ctx, 0, mats)
+        with pytest.raises(ccell.CCError):
+            ccell.cc_set_materials(ctx, 5, ccell.materials(cfg))   # no such instance
+        src = ccell.source(cfg)
+        src.layer = 7
+        with pytest.raises(ccell.CCError):
+            ccell.cc_set_source(ctx, 0, src)
+        with pytest.raises(ccell.CCError) as e:
+            ccell.cc_tau_stab(ctx, 0)                               # materials not set yet
+        assert e.value.status == ccell.CC_ESTATE
+    finally:
+        ccell.cc_destroy(ctx)
+
+
+def test_launch_shape_validation_and_round_trip():
+    cfg = inputs.small_case(q0=1.0)
+    sol = ccell.Solver(cfg)
+    try:
+        for shape in ((1, 64, 4), (0, 256, 16), (1, 128, 8)):
+            sol.set_launch(*shape)
+            assert ccell.cc_get_launch(sol.ctx) == shape
+        for bad in ((2, 128, 16), (0, 96, 16), (0, 128, 1), (0, 128, 32)):
+            with pytest.raises(ccell.CCError):
+                sol.set_launch(*bad)
+    finally:
+        sol.close()
