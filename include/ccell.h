@@ -219,7 +219,8 @@ int cc_step_n(cc_ctx* ctx, void* T_dev, int64_t n_steps, double t0_s, double dt_
  *   trace_dev  NULL or double[n_instances][n_steps][2] as in cc_step_n.
  * No energy terms.  The first call sizes the ADI scratch (about 24 bytes
  * per node plus 24 bytes per node of the column solves).
- * Errors: CC_EINVAL, CC_EUNSUPPORTED (CC_MIXED context), CC_ESTATE,
+ * Errors: CC_EINVAL, CC_EUNSUPPORTED (CC_MIXED context or a stepped
+ * outline), CC_ESTATE,
  * CC_ECUDA, CC_ENOMEM.  Asynchronous; cc_sync reports deferred failures. */
 int cc_step_adi_n(cc_ctx* ctx, void* T_dev, int64_t n_steps, double t0_s, double dt_s,
                   double* trace_dev, void* stream);
@@ -255,8 +256,11 @@ int cc_sync(cc_ctx* ctx, void* stream);
  * loss J = sum_n dt (Sbar_n - target_n)^2, Sbar_n the z-mean surface
  * temperature after step n (trace column 1).  Returns J and dJ/dtheta for
  * theta = (q0, t_on, lam_scale[0..L-1], cap_scale[0..L-1]) per instance,
- * plus dJ/dT0 if dT0_dev is not NULL.  Checkpoints every ckpt_every steps and
- * recomputes in between.
+ * plus dJ/dT0 if dT0_dev is not NULL.  Checkpoints every ckpt_every steps
+ * (<= 0: 256) and recomputes in between; the forward sweep keeps every state
+ * of the last segment, which needs no recompute.  Device scratch, owned by
+ * the context: ceil(n_steps / ckpt_every) + ckpt_every + 4 fields plus 5 doubles
+ * per instance and step.
  *   T0_dev      initial field (not modified); target_dev double[n_inst][n_steps]
  *   loss_dev    double[n_inst]; grad_dev: for each instance in order, 2 + 2 n_layers
  *               doubles (q0, t_on, lam_scale[0..L-1], cap_scale[0..L-1])
@@ -265,7 +269,8 @@ int cc_sync(cc_ctx* ctx, void* stream);
  * recomputed state, solves the transposed line systems, and gathers the
  * derivatives through lambda(T), c(T), X and the interface rows.  The
  * t_on derivative is nonzero only for the smoothed waveform (waveform 1).
- * Errors as cc_step_n; CC_EUNSUPPORTED for CC_MIXED contexts. */
+ * Errors as cc_step_n; CC_EUNSUPPORTED for CC_MIXED contexts and for a
+ * stepped outline (step_layers > 0 with a narrow line). */
 int cc_adjoint(cc_ctx* ctx, const void* T0_dev, int64_t n_steps, double t0_s, double dt_s,
                const double* target_dev, int32_t ckpt_every, double* loss_dev,
                double* grad_dev, void* dT0_dev, void* stream);
