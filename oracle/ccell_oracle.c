@@ -16,7 +16,7 @@
  * outer closures Eqs. (first_oder_bc), (alphabeta_ini), (T_ini_for_back_sweep)
  * and the layer-interface rows Eqs. (cc_first_1)-(cc_first_3).
  *
- * Readings of points the paper leaves open (each also listed in the design doc):
+ * Readings of points the paper leaves open (the labels are used below):
  *   A1 face conductivity lambda_{i+1/2,j} = lambda_m((T_ij + T_i+1,j)/2)
  *      (face_rule 0); face_rule 1 = mean of the two nodal values.
  *   A2 boundary conditions per face are flags: default Neumann at r=r_max and
@@ -27,7 +27,13 @@
  *      Interface nodes carry no heat capacity, no axial term, no source.
  *   A4 X and the waveform s(t) are evaluated at (T^n, t_n), t_n = t0 + n*tau;
  *      the rectangular pulse uses the half-open windows of Eq. (period).
+ *   A5 the transient p^2(t) of Eq. (transient_function) with the exponent
+ *      read as negative (or_waveform).
  *   A13 no FMA contraction: build with -ffp-contract=off.
+ *   A19 ADI variant: Peaceman-Rachford over two half steps of tau/2
+ *      (or_step_adi_n).
+ *   A20 stepped outline r in [0, r_max(z)]: beyond z_step only the inner
+ *      layers continue, the step face is insulated (or_outline).
  *
  * Array layout: T[j*nr + i], i = 0..nr-1 radial (contiguous), j = 0..nz-1
  * axial; a line j is one contiguous row of nr values.

@@ -2,7 +2,7 @@
 
 Checks of the reading of the printed tables, kept in tests/golden with their
 citation: the conductivity table only makes sense with its columns read as
-b4..b0 (reading A7) -- then the outer insulator's row is the constant
+b4..b0 -- then the outer insulator's row is the constant
 1e-3 W/(cm K) the text states and every fit is positive over 4.2-60 K.  The
 heat-capacity table read as printed has the graphite fit turn negative near
 22 K, inside the stated 4.2-60 K range; this is recorded, and runs of the paper
