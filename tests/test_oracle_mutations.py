@@ -40,6 +40,23 @@ MUTATIONS = {
         ("if (e * e < eta2) eta2 = e * e;", "if (e < eta2) eta2 = e;"),
     "rectangle pulse closed interval":
         ("return (phi < p->t_on) ? 1.0 : 0.0;", "return (phi <= p->t_on) ? 1.0 : 0.0;"),
+    "Dirichlet row at z = 0 copied from line 1":
+        ("Th[i] = p->bc_z0 ? p->t_dirichlet : Th[(size_t)nr + i];", "Th[i] = Th[(size_t)nr + i];"),
+    "sign of the heat through a Dirichlet z = 0 face":
+        ("(Ts[i] - Tj[i]) / eta_s;", "(Tj[i] - Ts[i]) / eta_s;"),
+    "Dirichlet value at r_max dropped":
+        ("beta[Nj - 1] / (1.0 - alpha[Nj - 1]) : p->t_dirichlet;", "beta[Nj - 1] / (1.0 - alpha[Nj - 1]) : 0.0;"),
+    "conductivity scale dropped":
+        ("b[4] * T * T * T * T;\n    }\n  }\n  return p->lam_scale[m] * v;",
+         "b[4] * T * T * T * T;\n    }\n  }\n  return v;"),
+    "polynomial heat capacity read in reverse order":
+        ("v = a[0] + a[1] * T + a[2] * T * T + a[3] * T * T * T;",
+         "v = a[3] + a[2] * T + a[1] * T * T + a[0] * T * T * T;"),
+    "resistivity 1/T instead of 1/sqrt(T)":
+        ("double g = (p->g_model == 1) ? p->g_ref / sqrt(T) : 1.0;",
+         "double g = (p->g_model == 1) ? p->g_ref / T : 1.0;"),
+    "transient sub-step tau* = tau":
+        ("return 1.0 - exp(-phi / (7.0 * (p->edge_w / 100.0)));", "return 1.0 - exp(-phi / (7.0 * p->edge_w));"),
     # discrete adjoint
     "adjoint: lambda term of the north flux derivative dropped":
         ("d0 += (ln_a * dN - ln) / eta_n / etabar", "d0 += (ln_a * dN) / eta_n / etabar"),
@@ -101,6 +118,7 @@ def test_pins_catch_mutation(name, tmp_path):
                           os.path.join(ROOT, "tests", "test_oracle_outline.py"),
                           os.path.join(ROOT, "tests", "test_oracle_adi.py"),
                           os.path.join(ROOT, "tests", "test_oracle_pins.py"),
-                          os.path.join(ROOT, "tests", "test_oracle_adjoint.py")],
+                          os.path.join(ROOT, "tests", "test_oracle_adjoint.py"),
+                          os.path.join(ROOT, "tests", "test_paper_model.py")],
                          env=env, capture_output=True, text=True, cwd=ROOT)
     assert res.returncode != 0, f"pins did not catch: {name}\n{res.stdout[-2000:]}"

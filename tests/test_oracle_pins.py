@@ -126,6 +126,21 @@ def test_axial_steady_state_exact():
     assert np.max(np.abs(T1 - T)) < 1e-12 * np.max(T)
 
 
+def test_axial_steady_state_dirichlet_both_ends():
+    """Constant lambda, uniform source, Dirichlet at z=0 and z=L (nodes on both
+    faces): T = T_D + X z (L - z) / (2 lambda) is reproduced by one step to
+    rounding."""
+    lam, X, L, TD = 3.0, 50.0, 1.0, 20.0
+    cfg = single_layer(6, 17, L=L, lam=lam, placement=1, bc=(0, 1, 1), t_d=TD, q0=X)
+    z = oracle.grid(cfg)["z"]
+    assert z[0] == 0.0 and abs(z[-1] - L) < 1e-15
+    Tz = TD + X * z * (L - z) / (2 * lam)
+    T = np.repeat(Tz[:, None], cfg["nr"], axis=1)
+    tau = 0.4 * oracle.tau_stab(cfg, 20.0, 40.0)
+    T1, _, _ = oracle.step_n(cfg, T, 3, 0.0, tau)
+    assert np.max(np.abs(T1 - T)) < 1e-12 * np.max(T)
+
+
 def _kirchhoff_error(M, b=1.2):
     lam0, Tr, X, L, TD = 2.0, 20.0, 400.0, 1.0, 20.0
     cfg = single_layer(3, M + 1, L=L, lam=lam0, lam_model=1, lam_b=b, t_ref=Tr,
@@ -215,23 +230,29 @@ def test_two_layer_interface_first_order(rule):
 
 
 # ----------------------------------------------------------------------------
-def _uniform_heating(tau):
+def _uniform_heating(tau, cap_model=1):
     c0, theta, Tr, rho, X = 5.0, 60.0, 20.0, 7900.0, 4.0e7
-    cfg = single_layer(5, 5, lam=10.0, rho=rho, c=c0, cap_model=1, theta=theta, t_ref=Tr,
-                       placement=0, bc=(0, 0, 0), q0=X)
+    poly = [0.5, 0.1, 0.005, 1e-4]      # c = a0 + a1 T + a2 T^2 + a3 T^3 (Eq. (poly_cap))
+    cfg = single_layer(5, 5, lam=10.0, rho=rho, c=c0, cap_model=cap_model, theta=theta,
+                       t_ref=Tr, placement=0, bc=(0, 0, 0), q0=X)
+    cfg["layers"][0]["cap_poly"] = poly
     t_end = 2e-3
     n = int(round(t_end / tau))
     T1, _, _ = oracle.step_n(cfg, np.full((5, 5), 20.0), n, 0.0, t_end / n,
                              want_trace=False, want_energy=False)
-    cap = lambda T: c0 * (T / Tr) ** 3 / (1 + (T / theta) ** 3)
+    if cap_model == 1:
+        cap = lambda T: c0 * (T / Tr) ** 3 / (1 + (T / theta) ** 3)
+    else:
+        cap = lambda T: poly[0] + poly[1] * T + poly[2] * T ** 2 + poly[3] * T ** 3
     sol = integrate.solve_ivp(lambda t, y: [X / (rho * cap(y[0]))], (0, t_end), [20.0],
                               rtol=1e-12, atol=1e-12)
     return T1[2, 2], sol.y[0, -1]
 
 
-def test_uniform_heating_temperature_dependent_capacity():
-    a, exact = _uniform_heating(2e-6)
-    b, _ = _uniform_heating(1e-6)
+@pytest.mark.parametrize("cap_model", [1, 2])
+def test_uniform_heating_temperature_dependent_capacity(cap_model):
+    a, exact = _uniform_heating(2e-6, cap_model)
+    b, _ = _uniform_heating(1e-6, cap_model)
     assert abs(b - exact) < 0.6 * abs(a - exact)       # first order in tau
     rich = 2 * b - a                                    # Richardson limit
     assert abs(rich - exact) < 1e-4 * abs(exact - 20.0), (a, b, rich, exact)
@@ -265,6 +286,23 @@ def test_energy_identity_multilayer(interface_rule, face_rule):
         assert abs(PI) <= 1e-12 * abs(Q)      # conservative interface rows
     else:
         assert abs(PI) > 1e-9 * abs(Q)        # first-order interface defect
+
+
+def test_energy_identity_dirichlet_both_ends():
+    """Heat leaves through both Dirichlet faces z = 0 and z = z_max; the
+    identity dE = Q + PhiD + PhiI + PhiN still closes to 1e-12."""
+    cfg = inputs.small_case()
+    cfg.update(bc_z0=1, interface_rule=1)
+    T = inputs.initial_field(cfg, "smooth", seed=8)
+    T[:, 0] = T[:, 1]
+    T[:, -1] = T[:, -2]
+    T[0] = 20.0
+    T[-1] = 20.0
+    _, _, e = oracle.step_n(cfg, T, 600, 0.0, cfg["dt"])
+    dE, Q, PD, PI, PN = e
+    assert abs(dE - Q - PD - PI - PN) <= 1e-12 * max(abs(Q), abs(dE))
+    assert PD < -1e-3 * abs(Q)                # the warm field loses heat at both ends
+    assert abs(PN) <= 1e-12 * abs(Q) and abs(PI) <= 1e-12 * abs(Q)
 
 
 def test_boundary_closures():
