@@ -68,9 +68,11 @@ def _two_layer_case(nr=10, nz=12):
 
 
 def test_adi_fixed_point_is_the_steady_state_of_the_scheme():
-    for rule in (0, 1):
+    # both interface rules; Dirichlet on every face (heat leaves at r_max and z = 0 too)
+    for rule, bcs in ((0, (0, 0, 1)), (1, (0, 0, 1)), (0, (1, 1, 1))):
         cfg = _two_layer_case()
         cfg["interface_rule"] = rule
+        cfg["bc_rmax"], cfg["bc_z0"], cfg["bc_zmax"] = bcs
         ts = oracle.tau_stab(cfg, 20.0, 60.0)
         T = np.full((cfg["nz"], cfg["nr"]), 20.0)
         # the paper's scheme, small steps, to convergence
@@ -90,7 +92,7 @@ def test_adi_fixed_point_is_the_steady_state_of_the_scheme():
                 Ta = Tn
                 break
             Ta = Tn
-        assert Tm.max() > 25.0  # the source heats well above the Dirichlet value
+        assert Tm.max() > 22.0  # the source heats well above the Dirichlet value
         assert np.abs(Ta - Tm).max() < 1e-9 * Tm.max(), (rule, np.abs(Ta - Tm).max())
 
 

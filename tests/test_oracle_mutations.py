@@ -55,6 +55,12 @@ MUTATIONS = {
     "resistivity 1/T instead of 1/sqrt(T)":
         ("double g = (p->g_model == 1) ? p->g_ref / sqrt(T) : 1.0;",
          "double g = (p->g_model == 1) ? p->g_ref / T : 1.0;"),
+    "minimum of one cell per layer instead of two":
+        ("if (n[m] < 2) n[m] = 2;", "if (n[m] < 1) n[m] = 1;"),
+    "ADI: sign of the Dirichlet z = 0 value folded into the first row":
+        ("if (p->bc_z0) { f[1] -= a[1] * p->t_dirichlet; }", "if (p->bc_z0) { f[1] += a[1] * p->t_dirichlet; }"),
+    "ADI: Dirichlet r_max column taken as Neumann":
+        ("Hj[N] = p->bc_rmax ? p->t_dirichlet : Hj[N - 1];", "Hj[N] = Hj[N - 1];"),
     "transient sub-step tau* = tau":
         ("return 1.0 - exp(-phi / (7.0 * (p->edge_w / 100.0)));", "return 1.0 - exp(-phi / (7.0 * p->edge_w));"),
     # discrete adjoint

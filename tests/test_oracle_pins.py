@@ -64,6 +64,11 @@ def test_grid_partition_hand_derived():
     assert list(np.nonzero(g["rclass"] == 2)[0]) == [160, 192, 272, 431]
     z = g["z"]
     assert z[0] == 0.0 and abs(z[-1] - 10e-3) < 1e-18
+    # the paper's cell, 64 nodes over 1.2/0.05/0.05/0.001 mm: ideal 58.11/2.42/2.42/0.05
+    # -> floors 58/2/2/0, the 1 um insulator raised to the minimum of 2 cells (64),
+    # the surplus cell taken from the largest layer: 57/2/2/2
+    g = oracle.grid(inputs.paper_case(64, 41))
+    assert list(np.nonzero(g["rclass"] == 2)[0]) == [57, 59, 61]
 
 
 def test_rectangular_waveform_half_open():
