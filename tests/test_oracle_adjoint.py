@@ -15,11 +15,12 @@ from oracle import oracle
 from paper_1408_5853_gb300 import inputs
 
 
-def _case(nr=14, nz=9, rule=0, face=0, g_model=0, bc_rmax=0):
+def _case(nr=14, nz=9, rule=0, face=0, g_model=0, bc_rmax=0, bc_z=(0, 1)):
     cfg = inputs.adjoint_case(nr=nr, nz=nz)
     cfg["layers"] = cfg["layers"][:3]
     cfg["source"].update(layer=2, g_model=g_model, g_ref=4.0, edge_w=20e-6)
-    cfg.update(interface_rule=rule, face_rule=face, bc_rmax=bc_rmax)
+    cfg.update(interface_rule=rule, face_rule=face, bc_rmax=bc_rmax, bc_z0=bc_z[0],
+               bc_zmax=bc_z[1])
     cfg["dt"] = 0.5 * oracle.tau_stab(cfg, 20.0, 100.0)
     return cfg
 
@@ -44,9 +45,12 @@ def _perturb(cfg, k, h):
     return c, h * base
 
 
-@pytest.mark.parametrize("rule,face,g_model,bc_rmax", [(0, 0, 0, 0), (1, 0, 1, 0), (0, 1, 0, 1)])
-def test_step_vjp_dot_product(rule, face, g_model, bc_rmax):
-    cfg = _case(rule=rule, face=face, g_model=g_model, bc_rmax=bc_rmax)
+@pytest.mark.parametrize("rule,face,g_model,bc_rmax,bc_z", [
+    (0, 0, 0, 0, (0, 1)), (1, 0, 1, 0, (0, 1)), (0, 1, 0, 1, (0, 1)),
+    (0, 0, 0, 0, (1, 0)),     # Dirichlet z = 0, Neumann z = z_max
+])
+def test_step_vjp_dot_product(rule, face, g_model, bc_rmax, bc_z):
+    cfg = _case(rule=rule, face=face, g_model=g_model, bc_rmax=bc_rmax, bc_z=bc_z)
     rng = np.random.default_rng(11)
     x = inputs.initial_field(cfg, "smooth", seed=4) + 0.3 * rng.random((cfg["nz"], cfg["nr"]))
     tn = 1.0e-3 - 5e-6        # on the falling tanh edge: d s / d t_on != 0

@@ -92,6 +92,13 @@ MUTATIONS = {
         ("const int ce = (i + 1 == Nj) ? OR_OUTER : cls[i + 1];", "const int ce = cls[i + 1];"),
     "outline: heat booked through the closed face at z_max":
         ("if (j == M - 1 && i <= NM) {", "if (j == M - 1) {"),
+    "adjoint: Neumann row z = z_max not folded into line M-1":
+        ("if (!p->bc_zmax) mu[(size_t)(M - 1) * nr + i] += mu[(size_t)M * nr + i];", "(void)0;"),
+    "adjoint: cap_scale partial with the wrong sign":
+        ("gbar[2 + L + m] += X * rc / tau * (T0 - yj[i]) / p->cap_scale[m];",
+         "gbar[2 + L + m] += X * rc / tau * (yj[i] - T0) / p->cap_scale[m];"),
+    "adjoint: derivative of the resistivity dropped":
+        ("if (m == p->src_layer) d0 += p->q0 * s * src_dg(p, T0);", "(void)0;"),
     # ADI variant
     "ADI: radial term of the second half step partly at T^n":
         ("const double Li = (r_e * le * (Sj[i + 1] - Sj[i]) / h_e -",
