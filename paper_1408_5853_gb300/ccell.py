@@ -359,9 +359,16 @@ class Solver:
     def get_launch(self) -> tuple:
         return cc_get_launch(self.ctx)
 
+    def _check_field(self, T, dtype=None) -> None:
+        """T must be this context's contiguous CUDA field (no CPU fallback)."""
+        if not (T.is_cuda and T.is_contiguous() and T.dtype == (dtype or self.dtype)
+                and T.numel() == self.total):
+            raise ValueError("T must be a contiguous CUDA tensor of the context's dtype and size")
+
     def autotune(self, T, n_trial: int = 3, stream=None) -> float:
         """Pick the fastest launch shape on field T (restored); returns ms per step."""
         import torch
+        self._check_field(T)
         st = stream if stream is not None else torch.cuda.current_stream()
         return cc_autotune(self.ctx, T.data_ptr(), n_trial, st.cuda_stream)
 
@@ -392,6 +399,9 @@ class Solver:
         """Loss sum_n dt (Sbar_n - target_n)^2 per instance, its gradient
         (per instance: q0, t_on, lam_scale[], cap_scale[]) and optionally dJ/dT0."""
         import torch
+        self._check_field(T0, torch.float64)
+        if target.numel() != n_steps * len(self.cfgs):
+            raise ValueError("target must hold n_steps values per instance")
         dev = T0.device
         st = stream if stream is not None else torch.cuda.current_stream()
         loss = torch.zeros(len(self.cfgs), dtype=torch.float64, device=dev)

@@ -125,3 +125,19 @@ def test_launch_shape_validation_and_round_trip():
                 sol.set_launch(*bad)
     finally:
         sol.close()
+
+
+def test_no_cpu_fallback():
+    """The binding refuses host tensors: every step of the path runs on the GPU."""
+    torch = pytest.importorskip("torch")
+    cfg = inputs.small_case(q0=1.0)
+    sol = ccell.Solver(cfg)
+    try:
+        T = torch.tensor(inputs.initial_field(cfg).ravel())         # host memory
+        target = torch.zeros(4, dtype=torch.float64)
+        for call in (lambda: sol.step(T, 2), lambda: sol.step_adi(T, 2),
+                     lambda: sol.autotune(T), lambda: sol.adjoint(T, 4, 0.0, 0.0, target)):
+            with pytest.raises(ValueError):
+                call()
+    finally:
+        sol.close()
