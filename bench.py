@@ -19,6 +19,7 @@ from __future__ import annotations
 import argparse
 import json
 import os
+import platform
 import statistics
 import subprocess
 import sys
@@ -487,18 +488,50 @@ def mixed_accuracy(cfg, T0, n, dev) -> dict:
             "energy_identity_rel": ident(em), "energy_identity_rel_fp64": ident(ed)}
 
 
+def _cpu_model() -> str:
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.lower().startswith("model name:"):
+                return line.split(":", 1)[1].strip()
+    except (OSError, subprocess.SubprocessError):
+        pass
+    try:
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                key = line.split(":")[0].strip().lower()
+                if key in ("model name", "cpu part", "hardware"):
+                    return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    return platform.processor() or platform.machine()
+
+
 def cpu_baseline(sample_steps: int) -> dict:
-    """The FP64 oracle, as it stands, on the host cores for a bounded sample."""
+    """The FP64 oracle, as it stands, on the host cores for a bounded sample;
+    also one thread on a sample 1/16 of the size."""
     from oracle import oracle
     from paper_1408_5853_gb300 import inputs
     cfg = inputs.production_case()
+    nodes = cfg["nr"] * cfg["nz"]
     T0 = inputs.initial_field(cfg, "smooth", seed=0)
+    cores = oracle.num_threads()
     t = time.perf_counter()
     oracle.step_n(cfg, T0, sample_steps, 0.0, cfg["dt"])
     s = time.perf_counter() - t
-    return {"value": cfg["nr"] * cfg["nz"] * sample_steps / s, "unit": UNIT,
-            "cores": oracle.num_threads(), "kind": "oracle",
-            "sample": f"{sample_steps} time steps of the 512x4096 workload ({s:.1f} s)"}
+    one_steps = max(1, sample_steps // 16)
+    oracle.set_threads(1)
+    try:
+        t = time.perf_counter()
+        oracle.step_n(cfg, T0, one_steps, 0.0, cfg["dt"])
+        s1 = time.perf_counter() - t
+    finally:
+        oracle.set_threads(cores)
+    return {"value": nodes * sample_steps / s, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"{sample_steps} time steps of the 512x4096 workload ({s:.1f} s)",
+            "single_thread": {"value": nodes * one_steps / s1, "unit": UNIT, "cores": 1,
+                              "sample": f"{one_steps} time steps ({s1:.1f} s)"},
+            "cpu_model": _cpu_model(), "nproc": os.cpu_count()}
 
 
 def run_reference(args, world, rank):
@@ -531,7 +564,8 @@ def run_reference(args, world, rank):
                    "precision": "fp64"},
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": oracle.num_threads(),
                          "kind": "oracle",
-                         "sample": f"{n_in} time steps of the 512x4096 workload per bench step"},
+                         "sample": f"{n_in} time steps of the 512x4096 workload per bench step",
+                         "cpu_model": _cpu_model(), "nproc": os.cpu_count()},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
 
