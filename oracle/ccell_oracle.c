@@ -323,6 +323,107 @@ static void kadd(double* s, double* c, double x) {
 }
 
 /* ------------------------------------------------------------------ */
+/* the tridiagonal system of one line                                  */
+/* ------------------------------------------------------------------ */
+/*
+ * Rows (a, b, c | f) of the system for That on line j (1 <= j <= M-1) from
+ * the field T at waveform value s: row i reads
+ *   a_i That_{i-1} + b_i That_i + c_i That_{i+1} = f_i,   i = 0..Nj,
+ * with Eq. (ABC) for regular nodes, the interface condition Eq. (cc_first_1)
+ * written as a row for interface nodes, That_0 = That_1 at the axis
+ * (Eq. (first_oder_bc)) and, at the outer node Nj of the line, That_Nj =
+ * That_Nj-1 (Neumann) or the Dirichlet value.
+ */
+static void line_rows(const or_problem* p, const double* T, int j, double s, double tau,
+                      const double* r, const double* z, const int* cls, const int* seg,
+                      int Nj, int i_step, int j_narrow, double* a, double* b, double* c,
+                      double* f) {
+  const int nr = p->nr;
+  const double* Tj = T + (size_t)j * nr;
+  const double* Ts = T + (size_t)(j - 1) * nr;  /* line j-1 */
+  const double* Tn = T + (size_t)(j + 1) * nr;  /* line j+1 */
+  const double eta_s = z[j] - z[j - 1], eta_n = z[j + 1] - z[j];
+  const double etabar = 0.5 * (eta_n + eta_s);
+  /* lines j +- 1 narrower than this one close the axial faces of the
+   * columns beyond their outer node */
+  const int wide_s = (j - 1 < j_narrow), wide_n = (j + 1 < j_narrow);
+  a[0] = 0.0; b[0] = 1.0; c[0] = -1.0; f[0] = 0.0;
+  for (int i = 1; i <= Nj - 1; i++) {
+    const double h_w = r[i] - r[i - 1], h_e = r[i + 1] - r[i];
+    if (cls[i] == OR_IFACE) {
+      const int mi = seg[i - 1], mo = seg[i];
+      double lm, lp;                  /* lambda*_m, lambda*_m+1 */
+      if (p->interface_rule == 0) {
+        /* Eq. (cc_first_1): lambda*_m (T_i* - T_i*-1)/h_i* =
+         * lambda*_m+1 (T_i*+1 - T_i*)/h_i*+1, lambda* at T_i*,j */
+        lm = lam_m(p, mi, Tj[i]);
+        lp = lam_m(p, mo, Tj[i]);
+      } else {
+        /* same row with the r-weighted face conductivities of the
+         * neighbouring regular rows: flux continuity that conserves */
+        lm = 0.5 * (r[i] + r[i - 1]) * lam_face(p, mi, Tj[i - 1], Tj[i]);
+        lp = 0.5 * (r[i] + r[i + 1]) * lam_face(p, mo, Tj[i], Tj[i + 1]);
+      }
+      /* times h_i* h_i*+1 */
+      a[i] = -lm * h_e;
+      c[i] = -lp * h_w;
+      b[i] = lm * h_e + lp * h_w;
+      f[i] = 0.0;
+      continue;
+    }
+    const int m = seg[i];
+    const double T0 = Tj[i];
+    const double hbar = 0.5 * (h_e + h_w);
+    const double r_w = 0.5 * (r[i] + r[i - 1]), r_e = 0.5 * (r[i] + r[i + 1]);
+    const double lw = lam_face(p, m, Tj[i - 1], T0);
+    const double le = lam_face(p, m, T0, Tj[i + 1]);
+    const double rc = p->rho[m] * cap_m(p, m, T0);
+    /* Eq. (Lambda_j), explicit in T; no heat crosses a face to a node
+     * outside the domain (Eq. (boundcond)) */
+    const double fn = (wide_n || i <= i_step)
+                          ? lam_face(p, m, T0, Tn[i]) * (Tn[i] - T0) / eta_n : 0.0;
+    const double fs = (wide_s || i <= i_step)
+                          ? lam_face(p, m, Ts[i], T0) * (T0 - Ts[i]) / eta_s : 0.0;
+    const double Lj = (fn - fs) / etabar;
+    const double X = source(p, m, T0, s);
+    /* Eq. (ABC) */
+    const double A = -r_w * lw / (r[i] * hbar * h_w);
+    const double C = -r_e * le / (r[i] * hbar * h_e);
+    const double B = (r_w * lw / h_w + r_e * le / h_e) / (r[i] * hbar) + rc / tau;
+    const double F = rc / tau * T0 + Lj + X;
+    a[i] = A;
+    b[i] = B;
+    c[i] = C;
+    f[i] = F;
+  }
+  if (p->bc_rmax == 0) { a[Nj] = -1.0; b[Nj] = 1.0; c[Nj] = 0.0; f[Nj] = 0.0; }
+  else { a[Nj] = 0.0; b[Nj] = 1.0; c[Nj] = 0.0; f[Nj] = p->t_dirichlet; }
+}
+
+/* Test access to line_rows: the rows of line j (1 <= j <= nz-2) for the
+ * field T at time t with step tau, *n_rows = Nj + 1 (the rows the sweep of
+ * or_step_n solves).  Returns 0, or -1 on an invalid problem or line. */
+int or_line_rows(const or_problem* p, const double* T, int j, double t, double tau, double* a,
+                 double* b, double* c, double* f, int* n_rows) {
+  const int N = p->nr - 1, M = p->nz - 1;
+  if (j < 1 || j > M - 1) return -1;
+  double* r = (double*)malloc(sizeof(double) * (N + 1));
+  double* z = (double*)malloc(sizeof(double) * (M + 1));
+  int* cls = (int*)malloc(sizeof(int) * (N + 1));
+  int* seg = (int*)malloc(sizeof(int) * (N + 1));
+  int i_step = 0, j_narrow = 0, rc = -1;
+  if (r && z && cls && seg && or_grid(p, r, z, cls, seg) == 0 &&
+      or_outline(p, z, cls, &i_step, &j_narrow) == 0) {
+    const int Nj = (j >= j_narrow) ? i_step : N;
+    line_rows(p, T, j, or_waveform(p, t), tau, r, z, cls, seg, Nj, i_step, j_narrow, a, b, c, f);
+    *n_rows = Nj + 1;
+    rc = 0;
+  }
+  free(r); free(z); free(cls); free(seg);
+  return rc;
+}
+
+/* ------------------------------------------------------------------ */
 /* n time steps                                                        */
 /* ------------------------------------------------------------------ */
 /*
@@ -361,75 +462,41 @@ int or_step_n(const or_problem* p, double* T, long n_steps, double t0, double ta
     {
       double* alpha = (double*)malloc(sizeof(double) * (N + 1));
       double* beta = (double*)malloc(sizeof(double) * (N + 1));
+      double* ra = (double*)malloc(sizeof(double) * (N + 1));  /* rows of line j */
+      double* rb = (double*)malloc(sizeof(double) * (N + 1));
+      double* rcv = (double*)malloc(sizeof(double) * (N + 1));
+      double* rf = (double*)malloc(sizeof(double) * (N + 1));
 #pragma omp for schedule(static)
       for (int j = 1; j <= M - 1; j++) {
         const double* Tj = T + (size_t)j * nr;
-        const double* Ts = T + (size_t)(j - 1) * nr;  /* line j-1 */
-        const double* Tn = T + (size_t)(j + 1) * nr;  /* line j+1 */
         double* Thj = Th + (size_t)j * nr;
-        const double eta_s = z[j] - z[j - 1], eta_n = z[j + 1] - z[j];
-        const double etabar = 0.5 * (eta_n + eta_s);
-        /* outer node of this line; lines j +- 1 narrower than this one
-         * close the axial faces of the columns beyond their outer node */
+        /* outer node of this line (a narrower line ends at i_step) */
         const int Nj = (j >= j_narrow) ? i_step : N;
-        const int wide_s = (j - 1 < j_narrow), wide_n = (j + 1 < j_narrow);
+        line_rows(p, T, j, s, tau, r, z, cls, seg, Nj, i_step, j_narrow, ra, rb, rcv, rf);
 
-        /* forward sweep, Eqs. (front_sweep), (ABC), (cc_first_3) */
+        /* forward sweep, Eqs. (front_sweep), (cc_first_3) */
         alpha[0] = 1.0;                     /* Eq. (alphabeta_ini) */
         beta[0] = 0.0;
         for (int i = 1; i <= Nj - 1; i++) {
-          const double h_w = r[i] - r[i - 1], h_e = r[i + 1] - r[i];
           if (cls[i] == OR_IFACE) {
-            const int mi = seg[i - 1], mo = seg[i];
-            double lm, lp;                  /* lambda*_m, lambda*_m+1 */
-            if (p->interface_rule == 0) {
-              /* Eq. (cc_first_1): lambda*_m (T_i* - T_i*-1)/h_i* =
-               * lambda*_m+1 (T_i*+1 - T_i*)/h_i*+1, lambda* at T_i*,j */
-              lm = lam_m(p, mi, Tj[i]);
-              lp = lam_m(p, mo, Tj[i]);
-            } else {
-              /* same row with the r-weighted face conductivities of the
-               * neighbouring regular rows: flux continuity that conserves */
-              lm = 0.5 * (r[i] + r[i - 1]) * lam_face(p, mi, Tj[i - 1], Tj[i]);
-              lp = 0.5 * (r[i] + r[i + 1]) * lam_face(p, mo, Tj[i], Tj[i + 1]);
-            }
-            /* Eq. (cc_first_3) */
-            const double den = lp * h_w + lm * h_e * (1.0 - alpha[i - 1]);
-            alpha[i] = lp * h_w / den;
-            beta[i] = lm * h_e * beta[i - 1] / den;
+            /* Eq. (cc_first_3), with lambda*_m h_i*+1 = -a and
+             * lambda*_m+1 h_i* = -c of the interface row */
+            const double lmh = -ra[i], lph = -rcv[i];
+            const double den = lph + lmh * (1.0 - alpha[i - 1]);
+            alpha[i] = lph / den;
+            beta[i] = lmh * beta[i - 1] / den;
             continue;
           }
-          const int m = seg[i];
-          const double T0 = Tj[i];
-          const double hbar = 0.5 * (h_e + h_w);
-          const double r_w = 0.5 * (r[i] + r[i - 1]), r_e = 0.5 * (r[i] + r[i + 1]);
-          const double lw = lam_face(p, m, Tj[i - 1], T0);
-          const double le = lam_face(p, m, T0, Tj[i + 1]);
-          const double rc = p->rho[m] * cap_m(p, m, T0);
-          /* Eq. (Lambda_j), explicit in T; no heat crosses a face to a node
-           * outside the domain (Eq. (boundcond)) */
-          const double fn = (wide_n || i <= i_step)
-                                ? lam_face(p, m, T0, Tn[i]) * (Tn[i] - T0) / eta_n : 0.0;
-          const double fs = (wide_s || i <= i_step)
-                                ? lam_face(p, m, Ts[i], T0) * (T0 - Ts[i]) / eta_s : 0.0;
-          const double Lj = (fn - fs) / etabar;
-          const double X = source(p, m, T0, s);
-          /* Eq. (ABC) */
-          const double A = -r_w * lw / (r[i] * hbar * h_w);
-          const double C = -r_e * le / (r[i] * hbar * h_e);
-          const double B = (r_w * lw / h_w + r_e * le / h_e) / (r[i] * hbar) + rc / tau;
-          const double F = rc / tau * T0 + Lj + X;
-          const double den = B + A * alpha[i - 1];
-          alpha[i] = -C / den;
-          beta[i] = (F - A * beta[i - 1]) / den;
+          const double den = rb[i] + ra[i] * alpha[i - 1];
+          alpha[i] = -rcv[i] / den;
+          beta[i] = (rf[i] - ra[i] * beta[i - 1]) / den;
         }
         /* Eq. (T_ini_for_back_sweep) or the Dirichlet value */
         Thj[Nj] = (p->bc_rmax == 0) ? beta[Nj - 1] / (1.0 - alpha[Nj - 1]) : p->t_dirichlet;
         for (int i = Nj - 1; i >= 0; i--) Thj[i] = alpha[i] * Thj[i + 1] + beta[i]; /* Eq. (back_sweep) */
         for (int i = Nj + 1; i <= N; i++) Thj[i] = Tj[i];  /* outside the domain */
       }
-      free(alpha);
-      free(beta);
+      free(alpha); free(beta); free(ra); free(rb); free(rcv); free(rf);
     }
 
     /* axial boundary rows (line 0 always has the full width) */

@@ -93,6 +93,9 @@ def _load():
         lib.or_grid.restype = ctypes.c_int
         lib.or_outline.argtypes = [P, dp, ip, ip, ip]
         lib.or_outline.restype = ctypes.c_int
+        lib.or_line_rows.argtypes = [P, dp, ctypes.c_int, ctypes.c_double, ctypes.c_double, dp,
+                                     dp, dp, dp, ip]
+        lib.or_line_rows.restype = ctypes.c_int
         lib.or_step_n.argtypes = [P, dp, ctypes.c_long, ctypes.c_double, ctypes.c_double, dp, dp]
         lib.or_step_n.restype = ctypes.c_int
         lib.or_step_adi_n.argtypes = [P, dp, ctypes.c_long, ctypes.c_double, ctypes.c_double, dp]
@@ -190,6 +193,21 @@ def outline(cfg: dict) -> tuple:
                       _ip(j_narrow)) != 0:
         raise ValueError("oracle rejected the outline")
     return int(i_step[0]), int(j_narrow[0])
+
+
+def line_rows(cfg: dict, T: np.ndarray, j: int, t: float, dt: float) -> tuple:
+    """Rows (a, b, c, f) of the tridiagonal system of line j that one step from
+    T at time t solves (row i: a_i x_{i-1} + b_i x_i + c_i x_{i+1} = f_i)."""
+    lib = _load()
+    p = problem(cfg)
+    T = np.ascontiguousarray(T, dtype=np.float64)
+    a, b, c, f = (np.zeros(cfg["nr"]) for _ in range(4))
+    n = np.zeros(1, dtype=np.int32)
+    if lib.or_line_rows(ctypes.byref(p), _dp(T), int(j), float(t), float(dt), _dp(a), _dp(b),
+                        _dp(c), _dp(f), _ip(n)) != 0:
+        raise ValueError("oracle rejected the line")
+    k = int(n[0])
+    return a[:k], b[:k], c[:k], f[:k]
 
 
 def step_n(cfg: dict, T: np.ndarray, n_steps: int, t0: float, dt: float,

@@ -26,16 +26,19 @@ MUTATIONS = {
     "heat capacity saturation squared instead of cubed":
         ("(1.0 + y * y * y)", "(1.0 + y * y)"),
     "density dropped from rho c":
-        ("const double rc = p->rho[m] * cap_m(p, m, T0);\n          /* Eq. (Lambda_j)",
-         "const double rc = cap_m(p, m, T0);\n          /* Eq. (Lambda_j)"),
-    "interface beta with the wrong cell width":
-        ("beta[i] = lm * h_e * beta[i - 1] / den;", "beta[i] = lm * h_w * beta[i - 1] / den;"),
+        ("const double rc = p->rho[m] * cap_m(p, m, T0);\n    /* Eq. (Lambda_j)",
+         "const double rc = cap_m(p, m, T0);\n    /* Eq. (Lambda_j)"),
+    "interface row with the cell widths swapped":
+        ("a[i] = -lm * h_e;\n      c[i] = -lp * h_w;\n      b[i] = lm * h_e + lp * h_w;",
+         "a[i] = -lm * h_w;\n      c[i] = -lp * h_e;\n      b[i] = lm * h_w + lp * h_e;"),
+    "interface recursion with the cell widths swapped":
+        ("const double lmh = -ra[i], lph = -rcv[i];", "const double lmh = -rcv[i], lph = -ra[i];"),
     "source term dropped from F":
         ("F = rc / tau * T0 + Lj + X;", "F = rc / tau * T0 + Lj;"),
     "Neumann closure at r_max dropped":
         ("beta[Nj - 1] / (1.0 - alpha[Nj - 1])", "beta[Nj - 1]"),
     "sign of alpha in the forward sweep":
-        ("alpha[i] = -C / den;", "alpha[i] = C / den;"),
+        ("alpha[i] = -rcv[i] / den;", "alpha[i] = rcv[i] / den;"),
     "stability bound with eta instead of eta^2":
         ("if (e * e < eta2) eta2 = e * e;", "if (e < eta2) eta2 = e;"),
     "rectangle pulse closed interval":
@@ -82,8 +85,8 @@ MUTATIONS = {
     "outline: axial face to an outside node left open":
         ("(wide_n || i <= i_step)", "(1)"),
     "outline: narrow lines solved over the full width":
-        ("const int Nj = (j >= j_narrow) ? i_step : N;\n        const int wide_s",
-         "const int Nj = N;\n        const int wide_s"),
+        ("const int Nj = (j >= j_narrow) ? i_step : N;\n        line_rows(",
+         "const int Nj = N;\n        line_rows("),
     "outline: trace over every line":
         ("for (int j = 0; j <= M && j < j_narrow; j++) {", "for (int j = 0; j <= M; j++) {"),
     "outline: Dirichlet row reset beyond the step":

@@ -310,6 +310,39 @@ def test_energy_identity_dirichlet_both_ends():
     assert abs(PN) <= 1e-12 * abs(Q) and abs(PI) <= 1e-12 * abs(Q)
 
 
+@pytest.mark.parametrize("variant", ["plain", "interface_rule_1", "rmax_dirichlet", "stepped"])
+def test_line_sweep_equals_dense_solve(variant):
+    """Brute force for the line solve: the sweep of Eqs. (front_sweep),
+    (cc_first_3), (back_sweep) with its closures returns, on every line of a
+    16-node cylinder with three interfaces, the dense solution (numpy, partial
+    pivoting) of the rows it was given; the axis closure is exact."""
+    cfg = inputs.small_case()
+    cfg.update(nr=16, nz=10)
+    if variant == "interface_rule_1":
+        cfg["interface_rule"] = 1
+    elif variant == "rmax_dirichlet":
+        cfg["bc_rmax"] = 1
+    elif variant == "stepped":
+        cfg["step"] = dict(layers=2, z=5e-3)
+    cfg["dt"] = 0.5 * oracle.tau_stab(cfg, 20.0, 100.0)
+    assert list(np.nonzero(oracle.grid(cfg)["rclass"] == 2)[0]) == [5, 7, 10]
+    T = inputs.initial_field(cfg, "smooth", seed=2)
+    t = 1e-3 - 0.5 * cfg["dt"]                      # inside the pulse: the source is on
+    T1, _, _ = oracle.step_n(cfg, T, 1, t, cfg["dt"], want_trace=False, want_energy=False)
+    for j in range(1, cfg["nz"] - 1):
+        a, b, c, f = oracle.line_rows(cfg, T, j, t, cfg["dt"])
+        n = len(b)
+        A = np.diag(b) + np.diag(a[1:], -1) + np.diag(c[:-1], 1)
+        assert a[0] == 0.0 and c[-1] == 0.0
+        x = np.linalg.solve(A, f)
+        assert np.max(np.abs(T1[j, :n] - x)) < 1e-11, (j, np.max(np.abs(T1[j, :n] - x)))
+        assert T1[j, 0] == T1[j, 1]
+        if variant != "rmax_dirichlet":
+            assert abs(T1[j, n - 1] - T1[j, n - 2]) < 1e-11
+    if variant == "stepped":
+        assert len(oracle.line_rows(cfg, T, cfg["nz"] - 2, t, cfg["dt"])[1]) == 8
+
+
 def test_boundary_closures():
     cfg = inputs.small_case()
     T = inputs.initial_field(cfg, "smooth", seed=1)
