@@ -4,6 +4,7 @@ Each case plants one mistake in a copy of ``oracle/ccell_oracle.c`` (on the
 CPU, in a temporary directory), builds it, and runs the pin suite against that
 build; the suite has to fail.
 """
+import concurrent.futures as cf
 import os
 import shutil
 import subprocess
@@ -118,23 +119,53 @@ MUTATIONS = {
 }
 
 
-@pytest.mark.parametrize("name", sorted(MUTATIONS))
-def test_pins_catch_mutation(name, tmp_path):
-    old, new = MUTATIONS[name]
+PIN_FILES = ["test_oracle_outline.py", "test_oracle_adi.py", "test_oracle_pins.py",
+             "test_oracle_adjoint.py", "test_paper_model.py"]
+
+
+CONTROL = "(no mutation)"
+
+
+def _run_mutant(name, workdir):
+    """Build one mutant (or the unchanged oracle for CONTROL) and run the pin
+    suite against it; returns (returncode, output)."""
+    old, new = MUTATIONS.get(name, ("", ""))
     src = open(SRC).read()
-    assert src.count(old) == 1, f"mutation anchor not found once: {old!r}"
-    mut = tmp_path / "mutant.c"
-    mut.write_text(src.replace(old, new))
-    so = tmp_path / "libmutant.so"
+    if name != CONTROL and src.count(old) != 1:
+        return None, f"mutation anchor not found once: {old!r}"
+    d = os.path.join(workdir, str(len(name)) + "_" + str(abs(hash(name))))
+    os.makedirs(d)
+    mut, so = os.path.join(d, "mutant.c"), os.path.join(d, "libmutant.so")
+    with open(mut, "w") as f:
+        f.write(src.replace(old, new) if name != CONTROL else src)
     cc = shutil.which("gcc") or shutil.which("cc")
-    subprocess.run([cc, "-O2", "-std=c11", "-ffp-contract=off", "-fPIC", "-shared", str(mut),
-                    "-o", str(so), "-lm"], check=True, capture_output=True)
-    env = dict(os.environ, CCELL_ORACLE_SO=str(so))
-    res = subprocess.run([sys.executable, "-m", "pytest", "-x", "-q",
-                          os.path.join(ROOT, "tests", "test_oracle_outline.py"),
-                          os.path.join(ROOT, "tests", "test_oracle_adi.py"),
-                          os.path.join(ROOT, "tests", "test_oracle_pins.py"),
-                          os.path.join(ROOT, "tests", "test_oracle_adjoint.py"),
-                          os.path.join(ROOT, "tests", "test_paper_model.py")],
+    subprocess.run([cc, "-O2", "-std=c11", "-ffp-contract=off", "-fPIC", "-shared", mut,
+                    "-o", so, "-lm"], check=True, capture_output=True)
+    # one thread per mutant: the mutants run side by side
+    env = dict(os.environ, CCELL_ORACLE_SO=so, OMP_NUM_THREADS="1")
+    res = subprocess.run([sys.executable, "-m", "pytest", "-x", "-q", "-p", "no:cacheprovider"]
+                         + [os.path.join(ROOT, "tests", f) for f in PIN_FILES],
                          env=env, capture_output=True, text=True, cwd=ROOT)
-    assert res.returncode != 0, f"pins did not catch: {name}\n{res.stdout[-2000:]}"
+    return res.returncode, res.stdout[-2000:]
+
+
+@pytest.fixture(scope="module")
+def mutant_results(tmp_path_factory):
+    workdir = str(tmp_path_factory.mktemp("mutants"))
+    workers = max(1, min(8, os.cpu_count() or 1))
+    with cf.ThreadPoolExecutor(workers) as ex:
+        futures = {name: ex.submit(_run_mutant, name, workdir)
+                   for name in list(MUTATIONS) + [CONTROL]}
+        return {name: fut.result() for name, fut in futures.items()}
+
+
+def test_unchanged_oracle_passes_the_same_runner(mutant_results):
+    rc, out = mutant_results[CONTROL]
+    assert rc == 0, f"the pin suite fails on the unchanged oracle in this runner:\n{out}"
+
+
+@pytest.mark.parametrize("name", sorted(MUTATIONS))
+def test_pins_catch_mutation(name, mutant_results):
+    rc, out = mutant_results[name]
+    assert rc is not None, out
+    assert rc != 0, f"pins did not catch: {name}\n{out}"
