@@ -334,6 +334,19 @@ int cc_step_n_noalloc(const cc_geometry_desc* desc, const cc_material* materials
  * rclass[nr] (0 axis, 1 regular, 2 layer interface, 3 outer boundary). */
 int cc_query_grid(const cc_geometry_desc* desc, double* r, double* z, int32_t* rclass);
 
+/* CTA tiles the step kernels use for a set of instances (all of one
+ * precision) with `threads` per block and the rows-per-lane policy of
+ * cc_set_launch: tiles[3 t .. 3 t + 2] = (instance, first line j0, lines nl)
+ * for t < min(*n_tiles, max_tiles); with n_blocks > 0 blocks, cta[b] ..
+ * cta[b+1] (cta: int32[n_blocks + 1] or NULL) are the tiles of block b, an
+ * equal share of all interior nodes (a launch uses its resident block
+ * count); lanes[k] (or NULL): lanes G per line of instance k; *smem_bytes
+ * (or NULL): dynamic shared memory of the largest tile.  CC_EINVAL for
+ * invalid arguments or when max_tiles is too small (*n_tiles is then set). */
+int cc_query_tiles(const cc_geometry_desc* descs, int32_t n_instances, int32_t threads,
+                   int32_t rows_per_lane, int32_t n_blocks, int32_t* tiles, int32_t max_tiles,
+                   int32_t* n_tiles, int32_t* cta, int32_t* lanes, int32_t* smem_bytes);
+
 /* Stepped outline of one descriptor: the lines j >= *j_narrow end at the
  * radial node *i_step (a rectangle gives nr - 1 and nz).  CC_EINVAL for an
  * outline the scheme does not take. */

@@ -9,6 +9,7 @@ Low-level functions carry the C names (``cc_create_geometry``,
 ``cc_set_materials``, ``cc_set_source``, ``cc_set_dt``, ``cc_step_n``, ``cc_step_adi_n``,
 ``cc_sync``, ``cc_adjoint``, ``cc_adjoint_vjp``, ``cc_set_launch``, ``cc_get_launch``,
 ``cc_autotune``, ``cc_destroy``, ``cc_step_n_noalloc``, ``cc_query_grid``, ``cc_query_outline``,
+``cc_query_tiles``,
 ``cc_tau_stab``, ``cc_status_string``, ``cc_kernel_launches``).  ``Solver``
 builds a context from the problem dicts of ``inputs``.
 """
@@ -90,6 +91,10 @@ def _load():
     lib.cc_query_grid.argtypes = [ctypes.POINTER(GeometryDesc), dp, dp, ctypes.POINTER(_i)]
     lib.cc_query_outline.argtypes = [ctypes.POINTER(GeometryDesc), ctypes.POINTER(_i),
                                      ctypes.POINTER(_i)]
+    ip = ctypes.POINTER(_i)
+    lib.cc_query_tiles.argtypes = [ctypes.POINTER(GeometryDesc), _i, _i, _i, _i, ip, _i, ip, ip,
+                                   ip, ip]
+    lib.cc_query_tiles.restype = ctypes.c_int
     lib.cc_tau_stab.argtypes = [vp, _i, dp]
     lib.cc_status_string.argtypes = [ctypes.c_int]
     lib.cc_status_string.restype = ctypes.c_char_p
@@ -221,6 +226,27 @@ def cc_query_grid(desc: GeometryDesc):
                                  z.ctypes.data_as(ctypes.POINTER(_d)),
                                  cls.ctypes.data_as(ctypes.POINTER(_i))), "cc_query_grid")
     return r, z, cls
+
+
+def cc_query_tiles(descs, threads: int, rows_per_lane: int, n_blocks: int):
+    """CTA tiles of the step kernels for these descriptors: (tiles[n, 3] =
+    (instance, j0, nl), cta[n_blocks + 1] or None, lanes per instance,
+    shared-memory bytes of the largest tile)."""
+    arr = (GeometryDesc * len(descs))(*descs)
+    n = _i(0)
+    _check(_load().cc_query_tiles(arr, len(descs), threads, rows_per_lane, n_blocks, None, 0,
+                                  ctypes.byref(n), None, None, None), "cc_query_tiles")
+    tiles = np.zeros((max(n.value, 1), 3), dtype=np.int32)
+    cta = np.zeros(n_blocks + 1, dtype=np.int32)
+    lanes = np.zeros(len(descs), dtype=np.int32)
+    smem = _i(0)
+    ip = ctypes.POINTER(_i)
+    _check(_load().cc_query_tiles(arr, len(descs), threads, rows_per_lane, n_blocks,
+                                  tiles.ctypes.data_as(ip), n.value, ctypes.byref(n),
+                                  cta.ctypes.data_as(ip) if n_blocks > 0 else None,
+                                  lanes.ctypes.data_as(ip), ctypes.byref(smem)),
+           "cc_query_tiles")
+    return tiles[:n.value], (cta if n_blocks > 0 else None), lanes, smem.value
 
 
 def cc_query_outline(desc: GeometryDesc) -> tuple:

@@ -285,6 +285,85 @@ void free_device(cc_ctx* c) {
 }
 
 // Allocate device memory (first use) and upload the per-instance tables.
+// Lanes per line of every instance from the rows-per-lane policy; when the
+// lines of all instances give fewer than kMinWarpTasks warp tasks (32/G
+// lines each), use more lanes per line (fewer rows per lane) so that every
+// SM sub-partition has work.
+void choose_instance_lanes(std::vector<Instance>& inst, int rows_policy) {
+  constexpr long long kMinWarpTasks = 2048;
+  for (int rows = rows_policy;; rows /= 2) {
+    long long warp_tasks = 0;
+    for (Instance& in : inst) {
+      in.G = choose_lanes(in.d.nr, rows);
+      const int lpw = 32 / in.G;
+      warp_tasks += (in.d.nz - 2 + lpw - 1) / lpw;
+    }
+    if (warp_tasks >= kMinWarpTasks || rows <= 4) break;
+  }
+}
+
+// Lines per CTA tile of every instance, (threads / 32) warps x 32/G lines,
+// halved until the tile fits in shared memory; returns the largest tile's
+// shared memory (above kMaxTileSmem if even one line does not fit).
+int tile_lines(const std::vector<Instance>& inst, int threads, int precision,
+               std::vector<int>& lpcs) {
+  lpcs.assign(inst.size(), 1);
+  int smem = 0;
+  for (size_t k = 0; k < inst.size(); ++k) {
+    const Instance& in = inst[k];
+    int lpc = (threads / 32) * (32 / in.G);
+    auto tile_smem = [&](int nl) {
+      return precision == CC_FP64 ? fp64_tile_smem_bytes(nl, in.d.nr)
+                                  : mixed_tile_smem_bytes(nl, in.d.nr);
+    };
+    // fewer lines per tile (idle lanes) if the tile would not fit
+    while (lpc > 1 && tile_smem(lpc) > kMaxTileSmem) lpc /= 2;
+    lpcs[k] = lpc;
+    smem = std::max(smem, tile_smem(std::min(lpc, in.d.nz - 2)));
+  }
+  return smem;
+}
+
+// CTA tiles of the step kernels: lines of one instance, at most lpcs[k] of
+// them.  With B > 0 blocks, block b takes an equal share of all interior
+// nodes as the consecutive tiles [cta[b], cta[b+1]); with B = 0 the tiles
+// are cut per instance and the blocks stride over them (cta stays empty).
+void cut_tiles(const std::vector<Instance>& inst, const std::vector<int>& lpcs, int B,
+               std::vector<TileTask>& tiles, std::vector<int>& cta) {
+  const int n = (int)inst.size();
+  tiles.clear();
+  cta.clear();
+  long long total_nodes = 0;  // of the interior lines
+  for (const Instance& in : inst) total_nodes += (long long)in.d.nr * (in.d.nz - 2);
+  if (B > 0) {
+    cta.assign(B + 1, 0);
+    int k = 0, jn = 1;  // next line of instance k
+    long long g = 0;
+    for (int b = 0; b < B; ++b) {
+      cta[b] = (int)tiles.size();
+      const long long g_end = (long long)(b + 1) * total_nodes / B;
+      while (g < g_end && k < n) {
+        const Instance& in = inst[k];
+        const int take = (int)std::min<long long>((g_end - g + in.d.nr - 1) / in.d.nr,
+                                                  in.d.nz - 1 - jn);
+        for (int j = jn; j < jn + take; j += lpcs[k])
+          tiles.push_back(TileTask{k, j, std::min(lpcs[k], jn + take - j), 0});
+        jn += take;
+        g += (long long)take * in.d.nr;
+        if (jn > in.d.nz - 2) {
+          ++k;
+          jn = 1;
+        }
+      }
+    }
+    cta[B] = (int)tiles.size();
+  } else {
+    for (int k = 0; k < n; ++k)
+      for (int j0 = 1; j0 <= inst[k].d.nz - 2; j0 += lpcs[k])
+        tiles.push_back(TileTask{k, j0, std::min(lpcs[k], inst[k].d.nz - 1 - j0), 0});
+  }
+}
+
 int upload(cc_ctx* c, const std::vector<double>& dts, cudaStream_t st) {
   const int n = (int)c->inst.size();
   if (c->device < 0) {
@@ -386,41 +465,9 @@ int upload(cc_ctx* c, const std::vector<double>& dts, cudaStream_t st) {
     if (cur != c->device) return CC_EINVAL;
   }
   if (c->tasks_dirty) {
-    // Lanes per line from the rows-per-lane policy; when the lines of all
-    // instances give fewer than kMinWarpTasks warp tasks, use more lanes per
-    // line (fewer rows per lane) so that every SM sub-partition has work.
-    constexpr long long kMinWarpTasks = 2048;
-    for (int rows = c->rows;; rows /= 2) {
-      long long warp_tasks = 0;  // 32/G lines each
-      for (int k = 0; k < n; ++k) {
-        Instance& in = c->inst[k];
-        in.G = choose_lanes(in.d.nr, rows);
-        const int lpw = 32 / in.G;
-        warp_tasks += (in.d.nz - 2 + lpw - 1) / lpw;
-      }
-      if (warp_tasks >= kMinWarpTasks || rows <= 4) break;
-    }
-    // FP64 CTA tiles: (threads / 32) warps x 32/G lines
-    // CTA tiles of the step kernels: lines of one instance, at most lpc of
-    // them.  The blocks of a launch (its resident capacity) take equal shares
-    // of all nodes as ranges of consecutive tiles.
-    std::vector<TileTask> tiles;
-    std::vector<int> lpcs(n), cta;
-    int smem = 0;
-    long long total_nodes = 0;  // of the interior lines
-    for (int k = 0; k < n; ++k) {
-      const Instance& in = c->inst[k];
-      int lpc = (c->threads / 32) * (32 / in.G);
-      auto tile_smem = [&](int nl) {
-        return c->precision == CC_FP64 ? fp64_tile_smem_bytes(nl, in.d.nr)
-                                       : mixed_tile_smem_bytes(nl, in.d.nr);
-      };
-      // fewer lines per tile (idle lanes) if the tile would not fit
-      while (lpc > 1 && tile_smem(lpc) > kMaxTileSmem) lpc /= 2;
-      lpcs[k] = lpc;
-      smem = std::max(smem, tile_smem(std::min(lpc, in.d.nz - 2)));
-      total_nodes += (long long)in.d.nr * (in.d.nz - 2);
-    }
+    choose_instance_lanes(c->inst, c->rows);
+    std::vector<int> lpcs;
+    const int smem = tile_lines(c->inst, c->threads, c->precision, lpcs);
     // the grid of the launch mode in use: per-step or cooperative kernels
     const int B = smem > kMaxTileSmem ? 0
                   : c->precision == CC_FP64
@@ -428,33 +475,9 @@ int upload(cc_ctx* c, const std::vector<double>& dts, cudaStream_t st) {
                                       : fp64_resident_blocks(c->threads, smem))
                       : (c->mode == 1 ? mixed_persistent_resident_blocks(c->threads, smem)
                                       : mixed_resident_blocks(c->threads, smem));
-    if (B > 0) {
-      cta.assign(B + 1, 0);
-      int k = 0, jn = 1;  // next line of instance k
-      long long g = 0;
-      for (int b = 0; b < B; ++b) {
-        cta[b] = (int)tiles.size();
-        const long long g_end = (long long)(b + 1) * total_nodes / B;
-        while (g < g_end && k < n) {
-          const Instance& in = c->inst[k];
-          const int take = (int)std::min<long long>((g_end - g + in.d.nr - 1) / in.d.nr,
-                                                    in.d.nz - 1 - jn);
-          for (int j = jn; j < jn + take; j += lpcs[k])
-            tiles.push_back(TileTask{k, j, std::min(lpcs[k], jn + take - j), 0});
-          jn += take;
-          g += (long long)take * in.d.nr;
-          if (jn > in.d.nz - 2) {
-            ++k;
-            jn = 1;
-          }
-        }
-      }
-      cta[B] = (int)tiles.size();
-    } else {
-      for (int k = 0; k < n; ++k)
-        for (int j0 = 1; j0 <= c->inst[k].d.nz - 2; j0 += lpcs[k])
-          tiles.push_back(TileTask{k, j0, std::min(lpcs[k], c->inst[k].d.nz - 1 - j0), 0});
-    }
+    std::vector<TileTask> tiles;
+    std::vector<int> cta;
+    cut_tiles(c->inst, lpcs, B, tiles, cta);
     if (smem > kMaxTileSmem) return CC_EUNSUPPORTED;
     if (tiles.size() > c->tiles_cap) {
       cudaFree(c->d_tiles);
@@ -1194,6 +1217,40 @@ int cc_query_grid(const cc_geometry_desc* d, double* r, double* z, int32_t* rcla
   if (rclass)
     for (size_t i = 0; i < cls.size(); ++i) rclass[i] = cls[i];
   return CC_OK;
+}
+
+int cc_query_tiles(const cc_geometry_desc* descs, int32_t n_instances, int32_t threads,
+                   int32_t rows_per_lane, int32_t n_blocks, int32_t* tiles, int32_t max_tiles,
+                   int32_t* n_tiles, int32_t* cta, int32_t* lanes, int32_t* smem_bytes) {
+  if (!descs || n_instances < 1 || !n_tiles || n_blocks < 0 || max_tiles < 0 ||
+      (threads != 64 && threads != 128 && threads != 256) || rows_per_lane < 2 ||
+      rows_per_lane > kRowsPerLane)
+    return CC_EINVAL;
+  std::vector<Instance> inst(n_instances);
+  for (int k = 0; k < n_instances; ++k) {
+    const int v = valid_desc(descs[k]);
+    if (v != CC_OK) return v;
+    if (descs[k].precision != descs[0].precision) return CC_EINVAL;
+    inst[k].d = descs[k];
+  }
+  choose_instance_lanes(inst, rows_per_lane);
+  std::vector<int> lpcs, cv;
+  std::vector<TileTask> tv;
+  const int smem = tile_lines(inst, threads, descs[0].precision, lpcs);
+  cut_tiles(inst, lpcs, n_blocks, tv, cv);
+  *n_tiles = (int32_t)tv.size();
+  if (tiles)
+    for (size_t t = 0; t < tv.size() && (int)t < max_tiles; ++t) {
+      tiles[3 * t] = tv[t].inst;
+      tiles[3 * t + 1] = tv[t].j0;
+      tiles[3 * t + 2] = tv[t].nl;
+    }
+  if (cta && n_blocks > 0)
+    for (int b = 0; b <= n_blocks; ++b) cta[b] = cv[b];
+  if (lanes)
+    for (int k = 0; k < n_instances; ++k) lanes[k] = inst[k].G;
+  if (smem_bytes) *smem_bytes = smem;
+  return (int)tv.size() > max_tiles && tiles ? CC_EINVAL : CC_OK;
 }
 
 int cc_query_outline(const cc_geometry_desc* d, int32_t* i_step, int32_t* j_narrow) {

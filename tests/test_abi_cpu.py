@@ -141,3 +141,32 @@ def test_no_cpu_fallback():
                 call()
     finally:
         sol.close()
+
+
+@pytest.mark.parametrize("threads,rows,blocks,precision", [
+    (256, 16, 152, 0), (128, 16, 304, 1), (64, 4, 456, 1), (256, 8, 0, 0), (128, 16, 7, 0)])
+def test_tile_partition_covers_every_line_once(threads, rows, blocks, precision):
+    """Host logic of the step launches: the CTA tiles of a ragged batch cover
+    every interior line of every instance exactly once, within the tile's
+    lanes and shared memory, and n blocks take contiguous tile ranges of equal
+    node shares (within one line)."""
+    cfgs = inputs.batched_cases(seed=1, n=24)
+    descs = [ccell.geometry_desc(c, precision) for c in cfgs]
+    tiles, cta, lanes, smem = ccell.cc_query_tiles(descs, threads, rows, blocks)
+    assert 0 < smem <= 226 * 1024
+    for k, c in enumerate(cfgs):
+        G = int(lanes[k])
+        assert G in (1, 2, 4, 8, 16, 32) and -(-c["nr"] // G) <= 16
+        mine = tiles[tiles[:, 0] == k]
+        lines = np.concatenate([np.arange(j0, j0 + nl) for _, j0, nl in mine])
+        assert np.array_equal(np.sort(lines), np.arange(1, c["nz"] - 1)), k
+        assert mine[:, 2].min() >= 1 and mine[:, 2].max() <= (threads // 32) * (32 // G)
+    if blocks:
+        assert cta[0] == 0 and cta[-1] == len(tiles) and np.all(np.diff(cta) >= 0)
+        nr = np.array([c["nr"] for c in cfgs])
+        per_tile = nr[tiles[:, 0]] * tiles[:, 2]
+        total = int(per_tile.sum())
+        assert total == sum(c["nr"] * (c["nz"] - 2) for c in cfgs)
+        share = total / blocks
+        block_nodes = [int(per_tile[cta[b]:cta[b + 1]].sum()) for b in range(blocks)]
+        assert max(abs(x - share) for x in block_nodes) < nr.max() + 1, (min(block_nodes), share)
