@@ -8,8 +8,9 @@ import numpy as np
 
 
 def run_gpu(cfgs, T0_list, n_steps, t0=0.0, dt=0.0, precision=0, want_trace=True,
-            want_energy=True, chunks=None):
-    """Run n_steps on the GPU for the instances `cfgs` from fields `T0_list`.
+            want_energy=True, chunks=None, launch=None):
+    """Run n_steps on the GPU for the instances `cfgs` from fields `T0_list`
+    (launch: (mode, threads, rows_per_lane) or the library's default).
 
     Returns (list of fields, trace[n_inst, n_steps, 2], energy[n_inst, 5])."""
     import torch
@@ -17,6 +18,8 @@ def run_gpu(cfgs, T0_list, n_steps, t0=0.0, dt=0.0, precision=0, want_trace=True
     if isinstance(cfgs, dict):
         cfgs, T0_list = [cfgs], [T0_list]
     sol = ccell.Solver(cfgs, precision=precision)
+    if launch is not None:
+        sol.set_launch(*launch)
     dtype = torch.float64 if precision == ccell.FP64 else torch.float32
     flat = np.concatenate([np.asarray(T, dtype=np.float64).ravel() for T in T0_list])
     T = torch.tensor(flat, dtype=dtype, device="cuda")
