@@ -65,6 +65,22 @@ MUTATIONS = {
         ("if (p->bc_z0) { f[1] -= a[1] * p->t_dirichlet; }", "if (p->bc_z0) { f[1] += a[1] * p->t_dirichlet; }"),
     "ADI: Dirichlet r_max column taken as Neumann":
         ("Hj[N] = p->bc_rmax ? p->t_dirichlet : Hj[N - 1];", "Hj[N] = Hj[N - 1];"),
+    "stored heat with the capacity at That":
+        ("kadd(&e[0], &c[0], V * p->rho[m] * cap_m(p, m, Tj[i]) * (Hj[i] - Tj[i]));",
+         "kadd(&e[0], &c[0], V * p->rho[m] * cap_m(p, m, Hj[i]) * (Hj[i] - Tj[i]));"),
+    "heat through the z = 0 face always booked as Dirichlet":
+        ("int k = p->bc_z0 ? 2 : 4;", "int k = 2;"),
+    "rectangle pulses before t_start":
+        ("  if (p->waveform == 0) {\n    if (u < 0.0) return 0.0;",
+         "  if (p->waveform == 0) {\n    if (u < -1.0) return 0.0;"),
+    "tanh edges of the current period only":
+        ("  double k = floor((u - 0.5 * p->t_on) / p->t_period + 0.5);\n  if (k < 0.0) k = 0.0;\n"
+         "  double phi = u - k * p->t_period;\n  return 0.5",
+         "  double k = floor(u / p->t_period);\n  if (k < 0.0) k = 0.0;\n"
+         "  double phi = u - k * p->t_period;\n  return 0.5"),
+    "trace surface value from line 1":
+        ("      trace[2 * n] = T[N];\n      trace[2 * n + 1] = acc / wsum;\n    }\n  }\n  if (energy)",
+         "      trace[2 * n] = T[(size_t)nr + N];\n      trace[2 * n + 1] = acc / wsum;\n    }\n  }\n  if (energy)"),
     "transient sub-step tau* = tau":
         ("return 1.0 - exp(-phi / (7.0 * (p->edge_w / 100.0)));", "return 1.0 - exp(-phi / (7.0 * p->edge_w));"),
     # discrete adjoint

@@ -77,7 +77,9 @@ def test_rectangular_waveform_half_open():
     assert w(0.0) == 1.0 and w(0.999e-3) == 1.0
     assert w(1.0e-3) == 0.0 and w(9.999e-3) == 0.0
     assert w(10.0e-3) == 1.0 and w(10.5e-3) == 1.0 and w(11.0e-3 + 1e-12) == 0.0
-    assert w(-1e-9) == 0.0
+    assert w(-1e-9) == 0.0 and w(-9.5e-3) == 0.0      # no pulse before the first one
+    cfg["source"]["t_start"] = 2e-3
+    assert w(1.5e-3) == 0.0 and w(2e-3) == 1.0 and w(2.999e-3) == 1.0 and w(3e-3) == 0.0
 
 
 def test_tanh_waveform_smooth_edges():
@@ -89,6 +91,9 @@ def test_tanh_waveform_smooth_edges():
     assert abs(w(5e-3)) < 1e-12 and abs(w(10e-3) - 0.5) < 1e-12
     # continuous across the wrap point between pulses
     assert abs(w(5.5e-3 - 1e-12) - w(5.5e-3 + 1e-12)) < 1e-12
+    # before the second pulse the rising edge of that pulse is the nearest one
+    ew = cfg["source"]["edge_w"]
+    assert abs(w(10e-3 - 2 * ew) - 0.5 * (1.0 + math.tanh(-2.0))) < 1e-12
 
 
 def test_transient_turn_on_waveform():
@@ -343,6 +348,20 @@ def test_line_sweep_equals_dense_solve(variant):
         assert len(oracle.line_rows(cfg, T, cfg["nz"] - 2, t, cfg["dt"])[1]) == 8
 
 
+def test_no_dirichlet_face_no_dirichlet_flux():
+    """With Neumann on every face (a start with T_0 != T_1 at z = 0), no heat
+    is booked as Dirichlet flux and the identity still closes."""
+    cfg = inputs.small_case()
+    cfg.update(bc_zmax=0, interface_rule=1)
+    T = inputs.initial_field(cfg, "smooth", seed=9)
+    T[1] += 0.5                                # T_0 != T_1: heat through the ghost edge
+    _, _, e = oracle.step_n(cfg, T, 1, 0.0, cfg["dt"])
+    dE, Q, PD, PI, PN = e
+    assert PD == 0.0
+    assert abs(PN) > 1e-6 * abs(Q)
+    assert abs(dE - Q - PD - PI - PN) <= 1e-12 * max(abs(Q), abs(dE))
+
+
 def test_boundary_closures():
     cfg = inputs.small_case()
     T = inputs.initial_field(cfg, "smooth", seed=1)
@@ -352,6 +371,9 @@ def test_boundary_closures():
     assert np.array_equal(T1[0], T1[1])                # Neumann z = 0
     assert np.all(T1[-1] == 20.0)                      # Dirichlet z = z_max
     assert tr[-1, 0] == T1[0, -1]
+    cfg["bc_z0"] = 1                                   # Dirichlet z = 0: the trace's
+    T1, tr, _ = oracle.step_n(cfg, T, 3, 0.0, cfg["dt"])  # surface value is T_D
+    assert np.all(T1[0] == 20.0) and np.all(tr[:, 0] == 20.0)
 
 
 # ----------------------------------------------------------------------------
