@@ -81,6 +81,11 @@ MUTATIONS = {
     "trace surface value from line 1":
         ("      trace[2 * n] = T[N];\n      trace[2 * n + 1] = acc / wsum;\n    }\n  }\n  if (energy)",
          "      trace[2 * n] = T[(size_t)nr + N];\n      trace[2 * n + 1] = acc / wsum;\n    }\n  }\n  if (energy)"),
+    "outline with line 1 narrow accepted":
+        ("if (*j_narrow < 2) return -1;", "if (*j_narrow < 1) return -1;"),
+    "outline ends one node beyond the interface":
+        ("if (rclass[i] == OR_IFACE && ++k == p->step_layers) { *i_step = i; break; }",
+         "if (rclass[i] == OR_IFACE && ++k == p->step_layers) { *i_step = i + 1; break; }"),
     "transient sub-step tau* = tau":
         ("return 1.0 - exp(-phi / (7.0 * (p->edge_w / 100.0)));", "return 1.0 - exp(-phi / (7.0 * p->edge_w));"),
     # discrete adjoint

@@ -49,6 +49,10 @@ def test_outline_hand_derived():
     cfg = inputs.paper_case(128, 301)   # z_j = j/6 mm over 5 cm
     cfg["step"] = dict(layers=1, z=0.04)
     assert oracle.outline(cfg)[1] == 241
+    # refused: line 1 narrow, every layer kept, the half-cell placement
+    for bad in (stepped(1, 0.05e-3), stepped(4, 5e-3), stepped(2, 5e-3, placement=1)):
+        with pytest.raises(ValueError):
+            oracle.outline(bad)
 
 
 def test_step_beyond_the_end_is_the_rectangle():
