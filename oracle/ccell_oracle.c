@@ -592,7 +592,8 @@ int or_step_n(const or_problem* p, double* T, long n_steps, double t0, double ta
  * to its scheme.  Reading taken (A19): the Peaceman-Rachford splitting of
  * Eq. (scheme_eq) over two half steps of tau/2, with the operators of
  * Eqs. (Lambda_i), (Lambda_j) and the source of Eq. (source), all material
- * properties and X frozen at (T^n, t_n):
+ * properties and X frozen at (T^n, t_n) (this time level is a choice the
+ * pins do not distinguish from T*: parity unpinned for it alone):
  *   half step 1:  rho c (T* - T^n)/(tau/2)      = Lambda_i[T*]      + Lambda_j[T^n]     + X
  *   half step 2:  rho c (T^n+1 - T*)/(tau/2)    = Lambda_i[T*]      + Lambda_j[T^n+1]   + X
  * Half step 1 is the paper's step with tau/2 (radial lines, interface rows
