@@ -170,3 +170,36 @@ def test_tile_partition_covers_every_line_once(threads, rows, blocks, precision)
         share = total / blocks
         block_nodes = [int(per_tile[cta[b]:cta[b + 1]].sum()) for b in range(blocks)]
         assert max(abs(x - share) for x in block_nodes) < nr.max() + 1, (min(block_nodes), share)
+
+
+def test_entry_points_refuse_before_any_device_work():
+    """Argument errors and unsupported requests return before the library
+    touches the device (the pointer below is never dereferenced)."""
+    fake = 256
+    cfg = inputs.small_case(q0=1.0)
+    sol = ccell.Solver(cfg)
+    sol_mixed = ccell.Solver(cfg, precision=ccell.MIXED)
+    stepped = dict(cfg, step=dict(layers=2, z=6e-3))
+    sol_stepped = ccell.Solver(stepped)
+    try:
+        def status(fn):
+            with pytest.raises(ccell.CCError) as e:
+                fn()
+            return e.value.status
+        assert status(lambda: ccell.cc_step_n(sol.ctx, fake, -1, 0.0, 0.0, None, None, None)) \
+            == ccell.CC_EINVAL
+        assert status(lambda: ccell.cc_step_n(sol.ctx, None, 3, 0.0, 0.0, None, None, None)) \
+            == ccell.CC_EINVAL
+        ccell.cc_step_n(sol.ctx, fake, 0, 0.0, 0.0, None, None, None)   # nothing to do
+        assert status(lambda: ccell.cc_step_adi_n(sol_mixed.ctx, fake, 2, 0.0, 1e-6, None, None)) \
+            == ccell.CC_EUNSUPPORTED
+        assert status(lambda: ccell.cc_step_adi_n(sol_stepped.ctx, fake, 2, 0.0, 1e-6, None,
+                                                  None)) == ccell.CC_EUNSUPPORTED
+        args = (fake, 4, 0.0, 0.0, fake, 256, fake, fake, None, None)
+        assert status(lambda: ccell.cc_adjoint(sol_mixed.ctx, *args)) == ccell.CC_EUNSUPPORTED
+        assert status(lambda: ccell.cc_adjoint(sol_stepped.ctx, *args)) == ccell.CC_EUNSUPPORTED
+        assert status(lambda: ccell.cc_set_dt(sol.ctx, 0, -1.0)) == ccell.CC_EINVAL
+        assert status(lambda: ccell.cc_set_dt(sol.ctx, 3, 1e-6)) == ccell.CC_EINVAL
+    finally:
+        for s in (sol, sol_mixed, sol_stepped):
+            s.close()
