@@ -86,6 +86,10 @@ MUTATIONS = {
     "outline ends one node beyond the interface":
         ("if (rclass[i] == OR_IFACE && ++k == p->step_layers) { *i_step = i; break; }",
          "if (rclass[i] == OR_IFACE && ++k == p->step_layers) { *i_step = i + 1; break; }"),
+    "half-cell placement: Dirichlet r_max node off the boundary":
+        ("double off_hi = p->bc_rmax ? 0.0 : 0.5;", "double off_hi = 0.5;"),
+    "adjoint: loss seed without the factor 2":
+        ("lam[(size_t)j * nr + N] += 2.0 * tau * e * w[j];", "lam[(size_t)j * nr + N] += tau * e * w[j];"),
     "transient sub-step tau* = tau":
         ("return 1.0 - exp(-phi / (7.0 * (p->edge_w / 100.0)));", "return 1.0 - exp(-phi / (7.0 * p->edge_w));"),
     # discrete adjoint

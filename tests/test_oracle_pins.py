@@ -151,6 +151,22 @@ def test_axial_steady_state_dirichlet_both_ends():
     assert np.max(np.abs(T1 - T)) < 1e-12 * np.max(T)
 
 
+def test_radial_steady_state_dirichlet_rmax():
+    """Constant lambda, uniform source, Dirichlet at r = R (a node on the
+    boundary, half-cell ghost at the axis), insulated ends: the cylindrical
+    3-point operator of Eq. (Lambda_i) is exact for T = T_D + X (R^2 - r^2) /
+    (4 lambda), which one step reproduces to rounding."""
+    lam, X, R, TD = 3.0, 50.0, 1.0, 20.0
+    cfg = single_layer(9, 5, R=R, lam=lam, placement=1, bc=(1, 0, 0), t_d=TD, q0=X)
+    r = oracle.grid(cfg)["r"]
+    assert abs(r[-1] - R) < 1e-15 and abs(r[0] + r[1]) < 1e-15
+    Tr = TD + X * (R * R - r * r) / (4 * lam)
+    T = np.repeat(Tr[None, :], cfg["nz"], axis=0)
+    tau = 0.4 * oracle.tau_stab(cfg, 20.0, 40.0)
+    T1, _, _ = oracle.step_n(cfg, T, 3, 0.0, tau)
+    assert np.max(np.abs(T1 - T)) < 1e-12 * np.max(T)
+
+
 def _kirchhoff_error(M, b=1.2):
     lam0, Tr, X, L, TD = 2.0, 20.0, 400.0, 1.0, 20.0
     cfg = single_layer(3, M + 1, L=L, lam=lam0, lam_model=1, lam_b=b, t_ref=Tr,
