@@ -41,7 +41,11 @@ FLOPS_PER_NODE_FP64 = 150     # FP64 operations per node-update (2 power laws ~ 
 # profiles/step_fp64_kernel_512x4096.md (cache flushed before the launch).  Valid only for the
 # kernel as captured there: reset to None when the kernel changes.
 STEP_FP64_TRAFFIC_512x4096 = 17.251328e6 + 1.536e3
-FP64_PEAK_TFLOPS = 152 * 4 * 0.5 * 2 * 2.07e9 / 1e12   # SMs x SMSPs x DFMA lanes/clk x 2 x max clock
+FP64_PEAK_NOMINAL_TFLOPS = 152 * 4 * 0.5 * 2 * 2.07e9 / 1e12   # SMs x SMSPs x DFMA lanes/clk x 2 x max clock
+# FP64 thread-operations (DFMA + DADD + DMUL) the step kernel executes per node-update, from the
+# ncu capture of the same kernel (profiles/step_fp64_kernel_512x4096.md); None once the kernel
+# changes until it is captured again.
+EXECUTED_FP64_OPS_PER_NODE = 60.1
 L2_FLUSH_BYTES = 256 << 20
 
 
@@ -138,6 +142,13 @@ def run_ours(args, world, rank, local):
 
     stream = torch.cuda.current_stream()
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    # the FP64-pipe roofline denominator, measured on this GPU by the library
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    rate_buf = torch.empty(1024 * sms, dtype=torch.float64, device=dev)
+    fma_rate = max(ccell.cc_measure_fp64_rate(rate_buf.data_ptr(), rate_buf.numel(), 20000,
+                                              stream.cuda_stream)[0] for _ in range(3))
+    fp64_peak_tflops = 2.0 * fma_rate / 1e12
+    del rate_buf
 
     def timed_steps(sol, T, trace, energy, k_steps, warm):
         for w in range(warm):
@@ -206,6 +217,7 @@ def run_ours(args, world, rank, local):
 
     # ---- mixed-precision path on the same workload
     mixed = None
+    base = None
     if "mixed" not in args.parts:
         mixed = {"skipped": True}
     else:
@@ -221,6 +233,11 @@ def run_ours(args, world, rank, local):
         solm.close()
         if args.acc_steps > 0:
             mixed.update(mixed_accuracy(cfg, T0, args.acc_steps, dev))
+        if world == 1 and not args.no_cpu_baseline:
+            # the oracle sample of cpu_baseline (below) doubles as the parity
+            # reference of both paths at its horizon
+            base, T_or = cpu_baseline(args.cpu_sample_steps, _f32(T0))
+            mixed.update(vs_oracle(cfg, _f32(T0), args.cpu_sample_steps, T_or, dev))
       except ccell.CCError as err:
         mixed = {"unavailable": str(err)}
     batched = run_batched(args, dev) if "batched" in args.parts else {"skipped": True}
@@ -245,15 +262,30 @@ def run_ours(args, world, rank, local):
                    "parallelism": f"replicas x{world}",
                    "launch": dict(zip(("mode", "threads", "rows_per_lane"), launch_shape))},
         "roofline": {"bound": "alu", "kernel": "step_fp64_kernel",
-                     "achieved": achieved_tflops, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                     "frac": achieved_tflops / FP64_PEAK_TFLOPS,
+                     "achieved": achieved_tflops, "peak": fp64_peak_tflops, "unit": "TFLOP/s",
+                     "frac": achieved_tflops / fp64_peak_tflops,
                      "traffic": (STEP_FP64_TRAFFIC_512x4096
                                  if (cfg["nr"], cfg["nz"]) == (512, 4096)
                                  and tuple(launch_shape) == (0, 256, 16) else None),
                      "traffic_note": "ncu dram__bytes_read.sum + dram__bytes_write.sum per launch, "
                                      "cold L2 (the output rows stay in L2)",
-                     "peak_source": "FP64 unit counts x max SM clock (152 x 4 x 0.5 DFMA/clk x 2 x 2.07 GHz)",
-                     "per_unit": f"{FLOPS_PER_NODE_FP64} FP64 ops per node-update"},
+                     "peak_source": "measured on this GPU: cc_measure_fp64_rate, 8 independent "
+                                    "DFMA chains per thread, 4 x 256 threads per SM, x 2 flops "
+                                    "(profiles/fp64_rate_gb300.md)",
+                     "peak_nominal": FP64_PEAK_NOMINAL_TFLOPS,
+                     "peak_nominal_source": "FP64 unit counts x max SM clock "
+                                            "(152 x 4 x 0.5 DFMA/clk x 2 x 2.07 GHz)",
+                     "per_unit": f"{FLOPS_PER_NODE_FP64} FP64 ops per node-update "
+                                 "(algorithmic count: two power laws as log + exp, 1 divide, "
+                                 "1 reciprocal, ~30 FMA/add/mul)",
+                     "executed": (None if EXECUTED_FP64_OPS_PER_NODE is None else {
+                         "fp64_ops_per_node_update": EXECUTED_FP64_OPS_PER_NODE,
+                         "achieved": EXECUTED_FP64_OPS_PER_NODE * nodes / (per_launch_ms / 1e3) / 1e12,
+                         "frac": EXECUTED_FP64_OPS_PER_NODE * nodes / (per_launch_ms / 1e3) / 1e12
+                         / fp64_peak_tflops,
+                         "unit": "TFLOP/s",
+                         "source": "ncu DFMA + DADD + DMUL thread-operations of the same kernel "
+                                   "(profiles/step_fp64_kernel_512x4096.md)"})},
         "hbm_roofline": {"bound": "hbm", "achieved": BYTES_PER_NODE_FP64 * value / world / 1e9,
                          "peak": hbm_peak, "unit": "GB/s",
                          "frac": BYTES_PER_NODE_FP64 * value / world / 1e9 / hbm_peak,
@@ -271,7 +303,9 @@ def run_ours(args, world, rank, local):
         "clocks": clk,
     }
     if world == 1 and not args.no_cpu_baseline:
-        line["cpu_baseline"] = cpu_baseline(args.cpu_sample_steps)
+        if base is None:
+            base, _ = cpu_baseline(args.cpu_sample_steps, _f32(T0))
+        line["cpu_baseline"] = base
     return line
 
 
@@ -459,6 +493,28 @@ def run_adi(args, dev, main_ms_per_time_step: float) -> dict:
                       "paper_scheme_dt_s": cfg["dt"]}}
 
 
+def _f32(T):
+    return np.asarray(T, dtype=np.float32).astype(np.float64)
+
+
+def vs_oracle(cfg, T0, n, T_oracle, dev) -> dict:
+    """Both paths from the FP32-rounded field over the n steps of the oracle
+    sample that cpu_baseline timed: max |dT| over the field against the oracle."""
+    import torch
+
+    from paper_1408_5853_gb300 import ccell
+    out = {}
+    for prec, dt, key in ((ccell.FP64, torch.float64, "fp64"), (ccell.MIXED, torch.float32, "mixed")):
+        sol = ccell.Solver(cfg, precision=prec)
+        T = torch.tensor(T0.ravel(), dtype=dt, device=dev)
+        sol.step(T, n, 0.0, 0.0, None, None)
+        sol.sync()
+        out[key] = float(np.max(np.abs(T.double().cpu().numpy().reshape(T_oracle.shape) - T_oracle)))
+        sol.close()
+    return {"oracle_steps": n, "max_dT_vs_oracle_K": out["mixed"],
+            "fp64_max_dT_vs_oracle_K": out["fp64"]}
+
+
 def mixed_accuracy(cfg, T0, n, dev) -> dict:
     """Mixed path against the FP64 path (itself parity-checked against the
     oracle to 1e-9 K) from the same FP32-rounded field, n steps from t = 0
@@ -507,17 +563,18 @@ def _cpu_model() -> str:
     return platform.processor() or platform.machine()
 
 
-def cpu_baseline(sample_steps: int) -> dict:
-    """The FP64 oracle, as it stands, on the host cores for a bounded sample;
-    also one thread on a sample 1/16 of the size."""
+def cpu_baseline(sample_steps: int, T0) -> tuple:
+    """The FP64 oracle, as it stands, on the host cores for a bounded sample
+    (sample_steps time steps of the workload from T0 at t = 0); also one thread
+    on a sample 1/16 of the size.  Returns the line's entry and the oracle's
+    field after the sample."""
     from oracle import oracle
     from paper_1408_5853_gb300 import inputs
     cfg = inputs.production_case()
     nodes = cfg["nr"] * cfg["nz"]
-    T0 = inputs.initial_field(cfg, "smooth", seed=0)
     cores = oracle.num_threads()
     t = time.perf_counter()
-    oracle.step_n(cfg, T0, sample_steps, 0.0, cfg["dt"])
+    T_out, _, _ = oracle.step_n(cfg, T0, sample_steps, 0.0, cfg["dt"])
     s = time.perf_counter() - t
     one_steps = max(1, sample_steps // 16)
     oracle.set_threads(1)
@@ -527,11 +584,11 @@ def cpu_baseline(sample_steps: int) -> dict:
         s1 = time.perf_counter() - t
     finally:
         oracle.set_threads(cores)
-    return {"value": nodes * sample_steps / s, "unit": UNIT, "cores": cores, "kind": "oracle",
-            "sample": f"{sample_steps} time steps of the 512x4096 workload ({s:.1f} s)",
-            "single_thread": {"value": nodes * one_steps / s1, "unit": UNIT, "cores": 1,
-                              "sample": f"{one_steps} time steps ({s1:.1f} s)"},
-            "cpu_model": _cpu_model(), "nproc": os.cpu_count()}
+    return ({"value": nodes * sample_steps / s, "unit": UNIT, "cores": cores, "kind": "oracle",
+             "sample": f"{sample_steps} time steps of the 512x4096 workload ({s:.1f} s)",
+             "single_thread": {"value": nodes * one_steps / s1, "unit": UNIT, "cores": 1,
+                               "sample": f"{one_steps} time steps ({s1:.1f} s)"},
+             "cpu_model": _cpu_model(), "nproc": os.cpu_count()}, T_out)
 
 
 def run_reference(args, world, rank):
@@ -577,7 +634,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--inner", type=int, default=1000, help="time steps per bench step")
     ap.add_argument("--ref-inner", type=int, default=60, help="time steps per reference step")
-    ap.add_argument("--cpu-sample-steps", type=int, default=300)
+    ap.add_argument("--cpu-sample-steps", type=int, default=1000)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--adi-steps", type=int, default=200, help="timed ADI steps")
     ap.add_argument("--adi-check-us", type=float, default=10.0,
@@ -586,7 +643,7 @@ def main():
                     help="comma list of extra parts to run besides the FP64 headline")
     ap.add_argument("--batch-instances", type=int, default=256)
     ap.add_argument("--batch-inner", type=int, default=20, help="time steps per batched replay")
-    ap.add_argument("--adj-steps", type=int, default=4096)
+    ap.add_argument("--adj-steps", type=int, default=40000)
     ap.add_argument("--adj-batch-steps", type=int, default=512)
     ap.add_argument("--paper-ms", type=float, default=0.08,
                     help="simulated ms of the paper-cell run; with the printed graphite c_V fit "

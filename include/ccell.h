@@ -225,7 +225,7 @@ int cc_step_n(cc_ctx* ctx, void* T_dev, int64_t n_steps, double t0_s, double dt_
 int cc_step_adi_n(cc_ctx* ctx, void* T_dev, int64_t n_steps, double t0_s, double dt_s,
                   double* trace_dev, void* stream);
 
-/* Launch shape of cc_step_n (the numerics do not depend on it):/* Launch shape of cc_step_n (the numerics do not depend on it):
+/* Launch shape of cc_step_n (the numerics do not depend on it):
  *   mode 0: one kernel launch per time step; mode 1: all steps of a call in
  *   one cooperative (co-resident) launch with a grid barrier between steps
  *   (bounded wait: a barrier that does not complete within ~seconds ends the
@@ -302,13 +302,18 @@ int cc_destroy(cc_ctx* ctx);
  * allocator owns the device memory, loops that forbid allocation after
  * start-up), while cc_step_n allocates its context tables and scratch on
  * first use.  This call allocates nothing, on the device or the host: its
- * scratch (tables, work list, waveform table, error word, and the ping-pong
- * partner of T_dev) lives in a file-scope static device array of about
- * 9.4 MiB that every GPU loading the library holds until the process exits.
+ * scratch (tables, work list, waveform table, power-law tables, error word,
+ * and the ping-pong partner of T_dev) lives in a file-scope static device
+ * array of about 9.5 MiB that every GPU loading the library holds until the
+ * process exits.  The grid, checks, stability guard and device tables are
+ * those of cc_create_geometry / cc_step_n (same host code), including the
+ * tabulated power law, so the results equal cc_step_n's up to the FMA
+ * contraction of a different block size (CTA tiles of 128 threads).
  *   desc        geometry (precision must be CC_FP64, a rectangle:
  *               step_layers 0, else CC_EUNSUPPORTED); materials[n_layers];
- *               source (layer -1 for none).  Same meaning as cc_create_geometry,
- *               cc_set_materials and cc_set_source.
+ *               source (layer -1 for none; waveforms 0, 1 and 2).  Same
+ *               meaning and checks as cc_create_geometry, cc_set_materials and
+ *               cc_set_source.
  *   T_dev       caller-owned device double[nz][nr], advanced in place.
  *   trace_dev, energy_dev  as in cc_step_n (one instance), or NULL.
  *   dt_s        time step, > 0.
@@ -316,17 +321,35 @@ int cc_destroy(cc_ctx* ctx);
  * nr * nz <= CC_NOALLOC_MAX_NODES, n_steps <= CC_NOALLOC_MAX_STEPS; larger
  * requests return CC_EINVAL before any device work.
  * The first call on a device looks up the device address of the static array
- * (cudaGetSymbolAddress, with that device current); make that first call
- * before any stream capture.  All calls share the array and it keeps the
- * last call's contents: calls whose work overlaps on the GPU (different
- * streams or host threads) race and must be serialised by the caller.
- * The call waits for its own work on `stream` before returning, so that it can
- * report CC_ENONFINITE.  Errors: CC_EINVAL, CC_EUNSTABLE, CC_ECUDA,
+ * (cudaGetSymbolAddress, with that device current).  Every call copies its
+ * tables from pageable host memory and waits for its own work on `stream`
+ * before returning (so that it can report CC_ENONFINITE): it cannot be called
+ * while a stream is being captured into a CUDA graph.  All calls share the
+ * array and it keeps the last call's contents: calls whose work overlaps on
+ * the GPU (different streams or host threads) race and must be serialised by
+ * the caller.  Errors: CC_EINVAL, CC_EUNSTABLE, CC_EUNSUPPORTED, CC_ECUDA,
  * CC_ENONFINITE.
  */
 int cc_step_n_noalloc(const cc_geometry_desc* desc, const cc_material* materials,
                       const cc_source* source, double* T_dev, int64_t n_steps, double t0_s,
                       double dt_s, double* trace_dev, double* energy_dev, void* stream);
+
+/* ---- measurement -------------------------------------------------------- */
+
+/*
+ * FP64 FMA rate of the current GPU, the denominator of the FP64-pipe roofline
+ * that bounds this scheme (the paper has no counterpart: it reports wall
+ * times only).  Runs one warm-up and one timed launch of a kernel in which
+ * every thread advances 8 independent chains of `iters` dependent FP64 FMAs,
+ * four blocks of 256 threads per SM, timed with CUDA events on `stream`.
+ *   scratch_dev  device double[scratch_len], scratch_len >= 1024 x the SM
+ *                count (one result per thread; overwritten).
+ *   fma_per_s    out: thread-level FP64 FMAs per second (x2 = FLOP/s).
+ *   seconds      out (or NULL): duration of the timed launch.
+ * Synchronous.  Errors: CC_EINVAL (null output, iters < 1, scratch too short),
+ * CC_ECUDA. */
+int cc_measure_fp64_rate(double* scratch_dev, int64_t scratch_len, int32_t iters,
+                         double* fma_per_s, double* seconds, void* stream);
 
 /* ---- host-only queries (no GPU needed) ---------------------------------- */
 

@@ -9,8 +9,8 @@ Low-level functions carry the C names (``cc_create_geometry``,
 ``cc_set_materials``, ``cc_set_source``, ``cc_set_dt``, ``cc_step_n``, ``cc_step_adi_n``,
 ``cc_sync``, ``cc_adjoint``, ``cc_adjoint_vjp``, ``cc_set_launch``, ``cc_get_launch``,
 ``cc_autotune``, ``cc_destroy``, ``cc_step_n_noalloc``, ``cc_query_grid``, ``cc_query_outline``,
-``cc_query_tiles``,
-``cc_tau_stab``, ``cc_status_string``, ``cc_kernel_launches``).  ``Solver``
+``cc_query_tiles``, ``cc_tau_stab``, ``cc_status_string``, ``cc_kernel_launches``,
+``cc_measure_fp64_rate``).  ``Solver``
 builds a context from the problem dicts of ``inputs``.
 """
 from __future__ import annotations
@@ -111,6 +111,8 @@ def _load():
     lib.cc_autotune.restype = ctypes.c_int
     lib.cc_adjoint_vjp.argtypes = [vp, vp, ctypes.c_int64, _d, _d, vp, _i, vp, vp, vp]
     lib.cc_adjoint_vjp.restype = ctypes.c_int
+    lib.cc_measure_fp64_rate.argtypes = [vp, ctypes.c_int64, _i, dp, dp, vp]
+    lib.cc_measure_fp64_rate.restype = ctypes.c_int
     for name in ("cc_create_geometry", "cc_set_materials", "cc_set_source", "cc_set_dt",
                  "cc_step_n", "cc_step_adi_n", "cc_sync", "cc_adjoint", "cc_destroy",
                  "cc_query_grid", "cc_query_outline", "cc_tau_stab"):
@@ -133,6 +135,15 @@ def cc_status_string(status: int) -> str:
 
 def cc_kernel_launches() -> int:
     return int(_load().cc_kernel_launches())
+
+
+def cc_measure_fp64_rate(scratch_ptr: int, scratch_len: int, iters: int, stream_ptr) -> tuple:
+    """(FP64 FMAs per second, seconds of the timed launch) of the current GPU."""
+    rate, sec = _d(0.0), _d(0.0)
+    _check(_load().cc_measure_fp64_rate(ctypes.c_void_p(scratch_ptr), scratch_len, iters,
+                                        ctypes.byref(rate), ctypes.byref(sec),
+                                        ctypes.c_void_p(stream_ptr)), "cc_measure_fp64_rate")
+    return rate.value, sec.value
 
 
 def cc_create_geometry(descs) -> ctypes.c_void_p:

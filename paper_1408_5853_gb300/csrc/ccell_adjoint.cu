@@ -203,24 +203,10 @@ __global__ void __launch_bounds__(CC_ADJ_MAX_THREADS) adj_tile_kernel(const AdjA
 }
 
 int launch_adj_tile(const AdjArgs& a, void* stream) {
-  static int resident = 0, resident_smem = -1, resident_threads = -1;
-  static bool opted = false;
-  if (!opted) {
-    if (cudaFuncSetAttribute(adj_tile_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             kMaxTileSmem) != cudaSuccess)
-      cudaGetLastError();  // the launch then reports a tile that does not fit
-    opted = true;
-  }
-  if (resident_smem != a.smem_bytes || resident_threads != a.threads) {
-    int dev = 0, sms = 0, per_sm = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, adj_tile_kernel, a.threads,
-                                                  a.smem_bytes);
-    resident = sms * (per_sm > 0 ? per_sm : 1);
-    resident_smem = a.smem_bytes;
-    resident_threads = a.threads;
-  }
+  static KernelCache cache;
+  const int resident = cached_resident(cache, adj_tile_kernel, a.threads, a.smem_bytes,
+                                       kMaxTileSmem);
+  if (resident < 0) return -1;
   const int blocks = a.n_tiles < resident ? a.n_tiles : resident;
   adj_tile_kernel<<<blocks, a.threads, a.smem_bytes, (cudaStream_t)stream>>>(a);
   count_launch();

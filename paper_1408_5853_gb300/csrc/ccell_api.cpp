@@ -10,7 +10,7 @@
 #include <new>
 #include <vector>
 
-#include "ccell_internal.h"
+#include "ccell_host.h"
 
 using namespace ccell;
 
@@ -73,172 +73,16 @@ struct cc_ctx {
 
 namespace {
 
-int valid_desc(const cc_geometry_desc& d) {
-  if (d.n_layers < 1 || d.n_layers > CC_MAX_LAYERS) return CC_EINVAL;
-  if (d.nr < 3 || d.nz < 3) return CC_EINVAL;
-  if (d.nr > kMaxNr) return CC_EUNSUPPORTED;
-  if (!(d.length_m > 0.0) || !std::isfinite(d.length_m)) return CC_EINVAL;
-  for (int m = 0; m < d.n_layers; ++m)
-    if (!(d.thickness_m[m] > 0.0) || !std::isfinite(d.thickness_m[m])) return CC_EINVAL;
-  auto b01 = [](int v) { return v == 0 || v == 1; };
-  if (!b01(d.bc_rmax) || !b01(d.bc_z0) || !b01(d.bc_zmax) || !b01(d.placement) ||
-      !b01(d.precision) || !b01(d.face_rule) || !b01(d.interface_rule))
-    return CC_EINVAL;
-  if (d.placement == 1 && d.n_layers != 1) return CC_EINVAL;
-  if (d.placement == 0 && d.nr - 1 < 2 * d.n_layers) return CC_EINVAL;
-  if (!std::isfinite(d.t_dirichlet_K)) return CC_EINVAL;
-  if (d.step_layers < 0 || d.step_layers >= d.n_layers) return CC_EINVAL;
-  if (d.step_layers > 0 && (d.placement != 0 || !std::isfinite(d.z_step_m))) return CC_EINVAL;
-  return CC_OK;
-}
+double tau_stab(const Instance& in) { return tau_stab_of(in.d, in.mat, in.z.data()); }
 
-// Radial cells per layer: proportional to thickness with the largest
-// remainder method (ties to the lower layer), at least two per layer.
-void layer_cells(const cc_geometry_desc& d, int* n) {
-  const int L = d.n_layers, N = d.nr - 1;
-  double total = 0.0;
-  for (int m = 0; m < L; ++m) total += d.thickness_m[m];
-  double frac[CC_MAX_LAYERS];
-  int assigned = 0;
-  for (int m = 0; m < L; ++m) {
-    const double share = (double)N * d.thickness_m[m] / total;
-    const double fl = std::floor(share);
-    n[m] = (int)fl;
-    frac[m] = share - fl;
-    if (n[m] < 2) n[m] = 2;
-    assigned += n[m];
-  }
-  std::vector<int> order(L);
-  for (int m = 0; m < L; ++m) order[m] = m;
-  std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return frac[x] > frac[y]; });
-  for (int k = 0; assigned < N; k = (k + 1) % L, ++assigned) n[order[k]]++;
-  while (assigned > N) {  // minimum-count overflow: take from the largest layer
-    int big = -1;
-    for (int m = 0; m < L; ++m)
-      if (n[m] > 2 && (big < 0 || n[m] > n[big])) big = m;
-    n[big]--;
-    assigned--;
-  }
-}
-
-void build_grid(const cc_geometry_desc& d, std::vector<double>& r, std::vector<double>& z,
-                std::vector<int>& cls, std::vector<int>& seg) {
-  const int N = d.nr - 1, M = d.nz - 1;
-  r.assign(N + 1, 0.0);
-  z.assign(M + 1, 0.0);
-  cls.assign(N + 1, RC_REGULAR);
-  seg.assign(N + 1, 0);
-  if (d.placement == 0) {
-    int n[CC_MAX_LAYERS];
-    layer_cells(d, n);
-    int i = 0;
-    double r0 = 0.0;
-    for (int m = 0; m < d.n_layers; ++m) {
-      const double h = d.thickness_m[m] / (double)n[m];
-      for (int k = 0; k < n[m]; ++k, ++i) {
-        r[i] = r0 + (double)k * h;
-        seg[i] = m;
-        if (k == 0 && m > 0) cls[i] = RC_IFACE;
-      }
-      r0 += d.thickness_m[m];
-    }
-    r[N] = r0;
-    seg[N] = d.n_layers - 1;
-    const double eta = d.length_m / (double)M;
-    for (int j = 0; j <= M; ++j) z[j] = (double)j * eta;
-  } else {
-    // a Neumann face sits half a cell inside its outermost node
-    const double hi_r = d.bc_rmax == CC_DIRICHLET ? 0.0 : 0.5;
-    const double h = d.thickness_m[0] / ((double)N - 0.5 - hi_r);
-    for (int i = 0; i <= N; ++i) r[i] = ((double)i - 0.5) * h;
-    const double lo_z = d.bc_z0 == CC_DIRICHLET ? 0.0 : 0.5;
-    const double hi_z = d.bc_zmax == CC_DIRICHLET ? 0.0 : 0.5;
-    const double eta = d.length_m / ((double)M - lo_z - hi_z);
-    for (int j = 0; j <= M; ++j) z[j] = ((double)j - lo_z) * eta;
-  }
-  cls[0] = RC_AXIS;
-  cls[N] = RC_OUTER;
-}
-
-// Stepped outline r in [0, r_max(z)] (Section 2): the lines with
-// z_j > z_step (a node on the step face counts as below it) keep only the
-// step_layers innermost layers and end at the interface node that starts
-// layer step_layers.  Line 1 must keep the full width.
-int build_outline(const cc_geometry_desc& d, const std::vector<double>& z,
-                  const std::vector<int>& cls, int& i_step, int& j_narrow) {
-  const int N = d.nr - 1, M = d.nz - 1;
-  i_step = N;
-  j_narrow = d.nz;
-  if (d.step_layers == 0) return CC_OK;
-  int k = 0;
-  for (int i = 1; i < N; ++i)
-    if (cls[i] == RC_IFACE && ++k == d.step_layers) {
-      i_step = i;
-      break;
-    }
-  if (k != d.step_layers) return CC_EINVAL;
-  const double zs = d.z_step_m + 1e-9 * d.length_m;
-  for (int j = 0; j <= M; ++j)
-    if (z[j] > zs) {
-      j_narrow = j;
-      break;
-    }
-  return j_narrow < 2 ? CC_EINVAL : CC_OK;
-}
-
-// Lanes per line: the smallest power of two giving at most `rows` rows per
-// lane (rows <= kRowsPerLane), keeping at least two rows per lane.
-int choose_lanes(int nr, int rows = kRowsPerLane) {
-  int G = 1;
-  while (G < 32 && (nr + G - 1) / G > rows && nr >= 4 * G) G <<= 1;
-  while ((nr + G - 1) / G > kRowsPerLane) G <<= 1;
-  return G;
-}
-
-double lam_host(const cc_material& m, double T) {
-  double v;
-  if (m.lam_model == 0) v = m.lam0;
-  else if (m.lam_model == 1) v = m.lam0 * std::pow(T / m.t_ref, m.lam_b);
-  else {
-    v = 0.0;
-    for (int k = 4; k >= 0; --k) v = v * T + m.lam_poly[k];
-  }
-  return m.lam_scale * v;
-}
-
-double cap_host(const cc_material& m, double T) {
-  double v;
-  if (m.cap_model == 0) v = m.c0;
-  else if (m.cap_model == 1) {
-    const double x = T / m.t_ref, y = T / m.theta;
-    v = m.c0 * x * x * x / (1.0 + y * y * y);
-  } else {
-    v = 0.0;
-    for (int k = 3; k >= 0; --k) v = v * T + m.cap_poly[k];
-  }
-  return m.cap_scale * v;
-}
-
-double tau_stab(const Instance& in) {
-  double eta2 = INFINITY;
-  for (size_t j = 1; j < in.z.size(); ++j) {
-    const double e = in.z[j] - in.z[j - 1];
-    eta2 = std::min(eta2, e * e);
-  }
-  double lo = in.d.t_guard_lo_K, hi = in.d.t_guard_hi_K;
-  if (!(hi > lo)) {
-    lo = in.d.t_dirichlet_K;
-    hi = 100.0;
-  }
-  double ratio = INFINITY;
-  const int ns = 257;
-  for (int m = 0; m < in.d.n_layers; ++m)
-    for (int s = 0; s < ns; ++s) {
-      const double T = lo + (hi - lo) * (double)s / (double)(ns - 1);
-      const double q = in.mat[m].rho * cap_host(in.mat[m], T) / lam_host(in.mat[m], T);
-      if (q < ratio) ratio = q;
-    }
-  return 0.5 * eta2 * ratio;
+// The grid of a valid descriptor into vectors sized here.
+void grid_of(const cc_geometry_desc& d, std::vector<double>& r, std::vector<double>& z,
+             std::vector<int>& cls, std::vector<int>& seg) {
+  r.resize(d.nr);
+  z.resize(d.nz);
+  cls.resize(d.nr);
+  seg.resize(d.nr);
+  build_grid(d, r.data(), z.data(), cls.data(), seg.data());
 }
 
 bool force_unstable() {
@@ -394,64 +238,14 @@ int upload(cc_ctx* c, const std::vector<double>& dts, cudaStream_t st) {
     }
     if (cudaMemset(c->d_err, 0, 4 * sizeof(unsigned)) != cudaSuccess) return CC_ECUDA;
     // geometry tables (do not change after creation)
-    std::vector<RowGeo> rg;
-    std::vector<ZGeo> zg;
-    rg.reserve(nrow);
-    zg.reserve(nz);
+    std::vector<RowGeo> rg(nrow);
+    std::vector<ZGeo> zg(nz);
+    size_t ro = 0, zo = 0;
     for (auto& in : c->inst) {
-      const int N = in.d.nr - 1, M = in.d.nz - 1;
-      for (int i = 0; i <= N; ++i) {
-        RowGeo g{};
-        g.cls = in.cls[i];
-        g.seg = in.seg[i];
-        g.segw = i > 0 ? in.seg[i - 1] : in.seg[0];
-        if (i > 0 && i < N) {
-          const double hw = in.r[i] - in.r[i - 1], he = in.r[i + 1] - in.r[i];
-          const double hbar = 0.5 * (hw + he);
-          const double rw = 0.5 * (in.r[i] + in.r[i - 1]), re = 0.5 * (in.r[i] + in.r[i + 1]);
-          g.hw = hw;
-          g.he = he;
-          g.rw = rw;
-          g.re = re;
-          g.gA = rw / (in.r[i] * hbar * hw);
-          g.gC = re / (in.r[i] * hbar * he);
-          g.V2 = 2.0 * M_PI * in.r[i] * hbar;
-        }
-        g.gA_f = (float)g.gA;
-        g.gC_f = (float)g.gC;
-        g.hw_f = (float)g.hw;
-        g.he_f = (float)g.he;
-        g.rw_f = (float)g.rw;
-        g.re_f = (float)g.re;
-        g.V2_f = (float)g.V2;
-        rg.push_back(g);
-      }
-      number_ifaces(rg.data() + rg.size() - in.d.nr, in.d.nr);
-      // trapezoid weights of the r = r_max surface (the full-width lines)
-      double wsum = 0.0;
-      std::vector<double> w(M + 1, 0.0);
-      for (int j = 0; j <= M && j < in.j_narrow; ++j) {
-        if (j > 0) w[j] += 0.5 * (in.z[j] - in.z[j - 1]);
-        if (j < M && j + 1 < in.j_narrow) w[j] += 0.5 * (in.z[j + 1] - in.z[j]);
-        wsum += w[j];
-      }
-      for (int j = 0; j <= M; ++j) {
-        ZGeo q{};
-        q.wnorm = w[j] / wsum;
-        if (j > 0 && j < M) {
-          const double es = in.z[j] - in.z[j - 1], en = in.z[j + 1] - in.z[j];
-          const double eb = 0.5 * (es + en);
-          q.eta_s = es;
-          q.eta_n = en;
-          q.etabar = eb;
-          q.gzs = 1.0 / (eb * es);
-          q.gzn = 1.0 / (eb * en);
-        }
-        q.gzs_f = (float)q.gzs;
-        q.gzn_f = (float)q.gzn;
-        q.etabar_f = (float)q.etabar;
-        zg.push_back(q);
-      }
+      fill_row_geo(in.r.data(), in.cls.data(), in.seg.data(), in.d.nr, rg.data() + ro);
+      fill_z_geo(in.z.data(), in.d.nz, in.j_narrow, zg.data() + zo);
+      ro += in.d.nr;
+      zo += in.d.nz;
     }
     if (cudaMemcpy(c->d_rg, rg.data(), sizeof(RowGeo) * rg.size(), cudaMemcpyHostToDevice) !=
             cudaSuccess ||
@@ -475,6 +269,7 @@ int upload(cc_ctx* c, const std::vector<double>& dts, cudaStream_t st) {
                                       : fp64_resident_blocks(c->threads, smem))
                       : (c->mode == 1 ? mixed_persistent_resident_blocks(c->threads, smem)
                                       : mixed_resident_blocks(c->threads, smem));
+    if (B < 0) return CC_ECUDA;  // current device unreadable
     std::vector<TileTask> tiles;
     std::vector<int> cta;
     cut_tiles(c->inst, lpcs, B, tiles, cta);
@@ -520,40 +315,8 @@ int upload(cc_ctx* c, const std::vector<double>& dts, cudaStream_t st) {
   for (int k = 0; k < n; ++k) {
     const Instance& in = c->inst[k];
     DevInst& D = h[k];
-    std::memset(&D, 0, sizeof D);
-    D.nr = in.d.nr;
-    D.nz = in.d.nz;
-    D.G = in.G;
-    D.bc_rmax = in.d.bc_rmax;
-    D.bc_z0 = in.d.bc_z0;
-    D.bc_zmax = in.d.bc_zmax;
-    D.face_rule = in.d.face_rule;
-    D.interface_rule = in.d.interface_rule;
-    D.src_layer = in.src.layer;
-    D.waveform = in.src.waveform;
-    D.g_model = in.src.g_model;
-    D.j_narrow = in.j_narrow;
-    D.i_step = in.i_step;
-    D.t_off = in.t_off;
-    D.t_d = in.d.t_dirichlet_K;
-    D.tau = dts[k];
-    D.inv_tau = 1.0 / dts[k];
-    D.q0 = in.src.q0;
-    D.t_period = in.src.t_period;
-    D.t_on = in.src.t_on;
-    D.t_start = in.src.t_start;
-    D.edge_w = in.src.edge_w;
-    D.g_ref = in.src.g_ref;
-    D.tau_f = (float)D.tau;
-    D.inv_tau_f = (float)D.inv_tau;
-    D.q0_f = (float)D.q0;
-    D.g_ref_f = (float)D.g_ref;
-    D.td_hi = (float)D.t_d;
-    D.td_lo = (float)(D.t_d - (double)D.td_hi);
-    D.n_if = 0;
-    for (int i = 0; i < in.d.nr; ++i)
-      if ((in.cls[i] == RC_IFACE || in.cls[i] == RC_OUTER) && D.n_if < CC_MAX_LAYERS)
-        D.if_i[D.n_if++] = i;
+    fill_inst_scalars(in.d, in.src, dts[k], in.G, in.j_narrow, in.i_step, in.t_off,
+                      in.cls.data(), D);
     D.rg = c->d_rg + rofs;
     D.zg = c->d_zg + zofs;
     rofs += in.d.nr;
@@ -561,32 +324,7 @@ int upload(cc_ctx* c, const std::vector<double>& dts, cudaStream_t st) {
     for (int m = 0; m < in.d.n_layers; ++m) {
       const cc_material& s = in.mat[m];
       DevMaterial& t = D.mat[m];
-      t.rho = s.rho;
-      t.lam_model = s.lam_model;
-      t.cap_model = s.cap_model;
-      t.lam0s = s.lam0 * s.lam_scale;
-      t.inv_lam_scale = 1.0 / s.lam_scale;
-      t.inv_cap_scale = 1.0 / s.cap_scale;
-      t.lam_b = s.lam_b;
-      t.inv_tref = 1.0 / s.t_ref;
-      t.c0s = s.c0 * s.cap_scale;
-      t.inv_theta = 1.0 / s.theta;
-      for (int q = 0; q < 5; ++q) t.lam_poly[q] = s.lam_poly[q] * s.lam_scale;
-      for (int q = 0; q < 4; ++q) t.cap_poly[q] = s.cap_poly[q] * s.cap_scale;
-      const double rho_tau = s.rho * D.inv_tau;
-      t.rho_tau = rho_tau;  // cap_poly already carries cap_scale
-      t.inv_theta3 = 1.0 / (s.theta * s.theta * s.theta);
-      t.rct_k = s.cap_model == 1 ? rho_tau * t.c0s / (s.t_ref * s.t_ref * s.t_ref)
-                                 : rho_tau * t.c0s;
-      t.rho_f = (float)t.rho;
-      t.lam0s_f = (float)t.lam0s;
-      t.lam_b_f = (float)t.lam_b;
-      t.inv_tref_f = (float)t.inv_tref;
-      t.c0s_f = (float)t.c0s;
-      t.inv_theta_f = (float)t.inv_theta;
-      for (int q = 0; q < 5; ++q) t.lam_poly_f[q] = (float)t.lam_poly[q];
-      for (int q = 0; q < 4; ++q) t.cap_poly_f[q] = (float)t.cap_poly[q];
-      t.ptab = nullptr;
+      fold_material(s, dts[k], t);
       if (s.lam_model == 1) {
         const size_t ofs = ((size_t)k * CC_MAX_LAYERS + m) * kPowTabLen;
         const double lam0s = s.lam0 * s.lam_scale;
@@ -604,14 +342,6 @@ int upload(cc_ctx* c, const std::vector<double>& dts, cudaStream_t st) {
   c->uploaded_dt = dts;
   c->dirty = false;
   return CC_OK;
-}
-
-bool valid_material(const cc_material& m) {
-  if (!(m.rho > 0.0) || !(m.lam_scale > 0.0) || !(m.cap_scale > 0.0)) return false;
-  if (m.lam_model < 0 || m.lam_model > 2 || m.cap_model < 0 || m.cap_model > 2) return false;
-  if (m.lam_model == 1 && !(m.t_ref > 0.0)) return false;
-  if (m.cap_model == 1 && (!(m.t_ref > 0.0) || !(m.theta > 0.0))) return false;
-  return true;
 }
 
 }  // namespace
@@ -633,8 +363,8 @@ int cc_create_geometry(const cc_geometry_desc* desc, int32_t n_instances, cc_ctx
     }
     Instance in;
     in.d = desc[k];
-    build_grid(in.d, in.r, in.z, in.cls, in.seg);
-    if (build_outline(in.d, in.z, in.cls, in.i_step, in.j_narrow) != CC_OK) {
+    grid_of(in.d, in.r, in.z, in.cls, in.seg);
+    if (build_outline(in.d, in.z.data(), in.cls.data(), in.i_step, in.j_narrow) != CC_OK) {
       delete c;
       return CC_EINVAL;
     }
@@ -670,15 +400,8 @@ int cc_set_source(cc_ctx* c, int32_t instance, const cc_source* s) {
   if (instance < -1 || instance >= (int)c->inst.size()) return CC_EINVAL;
   const int k0 = instance < 0 ? 0 : instance;
   const int k1 = instance < 0 ? (int)c->inst.size() : instance + 1;
-  for (int k = k0; k < k1; ++k) {
-    if (s->layer < -1 || s->layer >= c->inst[k].d.n_layers) return CC_EINVAL;
-    if (s->layer >= 0) {
-      if (!(s->t_period > 0.0) || !(s->t_on >= 0.0) || s->waveform < 0 || s->waveform > 2 ||
-          s->g_model < 0 || s->g_model > 1 || !std::isfinite(s->q0))
-        return CC_EINVAL;
-      if (s->waveform >= 1 && !(s->edge_w > 0.0)) return CC_EINVAL;
-    }
-  }
+  for (int k = k0; k < k1; ++k)
+    if (valid_source(*s, c->inst[k].d.n_layers) != CC_OK) return CC_EINVAL;
   for (int k = k0; k < k1; ++k) c->inst[k].src = *s;
   c->dirty = true;
   return CC_OK;
@@ -1211,7 +934,7 @@ int cc_query_grid(const cc_geometry_desc* d, double* r, double* z, int32_t* rcla
   if (v != CC_OK) return v;
   std::vector<double> rr, zz;
   std::vector<int> cls, seg;
-  build_grid(*d, rr, zz, cls, seg);
+  grid_of(*d, rr, zz, cls, seg);
   if (r) std::memcpy(r, rr.data(), sizeof(double) * rr.size());
   if (z) std::memcpy(z, zz.data(), sizeof(double) * zz.size());
   if (rclass)
@@ -1259,9 +982,9 @@ int cc_query_outline(const cc_geometry_desc* d, int32_t* i_step, int32_t* j_narr
   if (v != CC_OK) return v;
   std::vector<double> rr, zz;
   std::vector<int> cls, seg;
-  build_grid(*d, rr, zz, cls, seg);
+  grid_of(*d, rr, zz, cls, seg);
   int is = 0, jn = 0;
-  const int o = build_outline(*d, zz, cls, is, jn);
+  const int o = build_outline(*d, zz.data(), cls.data(), is, jn);
   if (o != CC_OK) return o;
   *i_step = is;
   *j_narrow = jn;

@@ -2,6 +2,8 @@
 #pragma once
 #include <cuda_runtime.h>
 
+#include <mutex>
+
 #include "ccell_internal.h"
 
 namespace ccell {
@@ -285,6 +287,53 @@ __device__ __forceinline__ bool grid_barrier(unsigned* bar, unsigned extra, long
   }
   __syncthreads();
   return ok_s != 0;
+}
+
+// Per-device launch facts of one kernel.  cudaFuncSetAttribute acts on the
+// device that is current when it is called, and the resident-block count
+// depends on the device, so the dynamic shared-memory opt-in and the
+// occupancy figures (per block size: 64, 128, 256 threads) are kept per
+// device; a mutex makes the cache safe for concurrent host threads.
+struct KernelCache {
+  static constexpr int kDevices = 64;
+  std::mutex mu;
+  bool opted[kDevices] = {};
+  int resident[kDevices][3] = {};
+  int smem[kDevices][3];
+  KernelCache() {
+    for (auto& d : smem) d[0] = d[1] = d[2] = -1;
+  }
+};
+
+static inline int shape_slot(int threads) { return threads <= 64 ? 0 : (threads <= 128 ? 1 : 2); }
+
+// Resident blocks (SMs x blocks per SM) of `kernel` on the current device for
+// a block size and dynamic shared memory, opting the kernel in to the largest
+// dynamic shared memory on first use on that device.  Returns -1 if the
+// current device cannot be read or lies outside the cache.
+template <class K>
+int cached_resident(KernelCache& c, K kernel, int threads, int smem_bytes, int smem_max) {
+  int dev = -1;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= KernelCache::kDevices) {
+    cudaGetLastError();
+    return -1;
+  }
+  std::lock_guard<std::mutex> lock(c.mu);
+  if (!c.opted[dev]) {
+    if (cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_max) !=
+        cudaSuccess)
+      cudaGetLastError();  // the launch then reports a tile that does not fit
+    c.opted[dev] = true;
+  }
+  const int si = shape_slot(threads);
+  if (c.smem[dev][si] != smem_bytes) {
+    int sms = 0, per_sm = 0;
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, threads, smem_bytes);
+    c.resident[dev][si] = sms * (per_sm > 0 ? per_sm : 1);
+    c.smem[dev][si] = smem_bytes;
+  }
+  return c.resident[dev][si];
 }
 
 }  // namespace ccell

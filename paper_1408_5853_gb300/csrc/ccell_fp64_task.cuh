@@ -344,16 +344,4 @@ __device__ __forceinline__ void fp64_tiles(const StepArgs& a, double* __restrict
   }
 }
 
-// Resident blocks per SM x SMs for a kernel, block size and shared memory.
-template <class K>
-static int resident_blocks(K kernel, int threads, int smem = 0) {
-  int dev = 0, sms = 0, per_sm = 0;
-  cudaGetDevice(&dev);
-  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, threads, smem);
-  return sms * (per_sm > 0 ? per_sm : 1);
-}
-
-static inline int shape_index(int threads) { return threads <= 64 ? 0 : (threads <= 128 ? 1 : 2); }
-
 }  // namespace ccell

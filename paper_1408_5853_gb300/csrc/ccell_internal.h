@@ -145,13 +145,7 @@ CC_HOST_DEVICE inline int mixed_tile_smem_bytes(int nl, int nr) {
 // on sm_103 (227 KiB) less room for the kernels' static shared memory.
 constexpr int kMaxTileSmem = 226 * 1024;
 
-// Interface and r_max nodes of one instance, from the row classes (their
-// positions in the list are stored in RowGeo::ifo).
-inline void fill_iface_list(const RowGeo* rg, int nr, DevInst& D) {
-  D.n_if = 0;
-  for (int i = 0; i < nr && D.n_if < CC_MAX_LAYERS; ++i)
-    if (rg[i].cls == RC_IFACE || rg[i].cls == RC_OUTER) D.if_i[D.n_if++] = i;
-}
+// Positions of the interface and r_max nodes in DevInst::if_i (RowGeo::ifo).
 inline void number_ifaces(RowGeo* rg, int nr) {
   int n = 0;
   for (int i = 0; i < nr; ++i)

@@ -363,15 +363,4 @@ __device__ __forceinline__ void mixed_tiles(const StepArgs& a, float* __restrict
 #define CC_MIX_MIN_BLOCKS 1
 #endif
 
-template <class K>
-static int resident_blocks_m(K kernel, int threads, int smem) {
-  int dev = 0, sms = 0, per_sm = 0;
-  cudaGetDevice(&dev);
-  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, threads, smem);
-  return sms * (per_sm > 0 ? per_sm : 1);
-}
-
-static inline int shape_index_m(int threads) { return threads <= 64 ? 0 : (threads <= 128 ? 1 : 2); }
-
 }  // namespace ccell

@@ -93,20 +93,18 @@ __global__ void __launch_bounds__(CC_FP64_MAX_THREADS, CC_FP64_MIN_BLOCKS) step_
   eacc_flush<ENERGY, TRACE>(a, acc);
 }
 
-// Kernels are opted in to the largest dynamic shared memory once.
-constexpr int kTileSmemMax = kMaxTileSmem;
+// Per-device opt-in to the largest dynamic shared memory and occupancy cache
+// of each variant.
+template <bool ENERGY, bool TRACE>
+static KernelCache& fp64_cache() {
+  static KernelCache c;
+  return c;
+}
 
 template <bool ENERGY, bool TRACE>
 static int fp64_variant_resident(int threads, int smem) {
-  static bool opted = false;
-  if (!opted) {
-    if (cudaFuncSetAttribute(step_fp64_kernel<ENERGY, TRACE>,
-                             cudaFuncAttributeMaxDynamicSharedMemorySize, kTileSmemMax) !=
-        cudaSuccess)
-      cudaGetLastError();  // the launch then reports a tile that does not fit
-    opted = true;
-  }
-  return resident_blocks(step_fp64_kernel<ENERGY, TRACE>, threads, smem);
+  return cached_resident(fp64_cache<ENERGY, TRACE>(), step_fp64_kernel<ENERGY, TRACE>, threads,
+                         smem, kMaxTileSmem);
 }
 
 int fp64_resident_blocks(int threads, int smem) {
@@ -117,25 +115,25 @@ int fp64_resident_blocks(int threads, int smem) {
 }
 
 template <bool ENERGY, bool TRACE>
-static void launch_fp64_variant(const StepArgs& a, cudaStream_t st) {
-  static int resident[3] = {0, 0, 0}, resident_smem[3] = {-1, -1, -1};
-  const int t = a.threads > 0 ? a.threads : 128, si = shape_index(t);
-  if (resident_smem[si] != a.smem_bytes) {
-    resident[si] = fp64_variant_resident<ENERGY, TRACE>(t, a.smem_bytes);
-    resident_smem[si] = a.smem_bytes;
-  }
-  const int blocks = a.cta_start ? a.n_cta : (a.n_tiles < resident[si] ? a.n_tiles : resident[si]);
+static int launch_fp64_variant(const StepArgs& a, cudaStream_t st) {
+  const int t = a.threads > 0 ? a.threads : 128;
+  const int resident = fp64_variant_resident<ENERGY, TRACE>(t, a.smem_bytes);
+  if (resident < 0) return -1;
+  const int blocks = a.cta_start ? a.n_cta : (a.n_tiles < resident ? a.n_tiles : resident);
   step_fp64_kernel<ENERGY, TRACE><<<blocks, t, a.smem_bytes, st>>>(a);
+  return 0;
 }
 
 int launch_step_fp64(const StepArgs& a, void* stream) {
   cudaStream_t st = (cudaStream_t)stream;
   const bool E = a.energy != nullptr, T = a.trace != nullptr;
-  if (E && T) launch_fp64_variant<true, true>(a, st);
-  else if (E) launch_fp64_variant<true, false>(a, st);
-  else if (T) launch_fp64_variant<false, true>(a, st);
-  else launch_fp64_variant<false, false>(a, st);
+  int r;
+  if (E && T) r = launch_fp64_variant<true, true>(a, st);
+  else if (E) r = launch_fp64_variant<true, false>(a, st);
+  else if (T) r = launch_fp64_variant<false, true>(a, st);
+  else r = launch_fp64_variant<false, false>(a, st);
   count_launch();
+  if (r) return r;
   return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }
 

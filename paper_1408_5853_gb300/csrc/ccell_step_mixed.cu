@@ -16,16 +16,15 @@ __global__ void __launch_bounds__(CC_MIX_MAX_THREADS, CC_MIX_MIN_BLOCKS) step_mi
 }
 
 template <bool ENERGY, bool TRACE>
+static KernelCache& mixed_cache() {
+  static KernelCache c;
+  return c;
+}
+
+template <bool ENERGY, bool TRACE>
 static int mixed_variant_resident(int threads, int smem) {
-  static bool opted = false;
-  if (!opted) {
-    if (cudaFuncSetAttribute(step_mixed_kernel<ENERGY, TRACE>,
-                             cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxTileSmem) !=
-        cudaSuccess)
-      cudaGetLastError();  // the launch then reports a tile that does not fit
-    opted = true;
-  }
-  return resident_blocks_m(step_mixed_kernel<ENERGY, TRACE>, threads, smem);
+  return cached_resident(mixed_cache<ENERGY, TRACE>(), step_mixed_kernel<ENERGY, TRACE>, threads,
+                         smem, kMaxTileSmem);
 }
 
 int mixed_resident_blocks(int threads, int smem) {
@@ -36,25 +35,25 @@ int mixed_resident_blocks(int threads, int smem) {
 }
 
 template <bool ENERGY, bool TRACE>
-static void launch_mixed_variant(const StepArgs& a, cudaStream_t st) {
-  static int resident[3] = {0, 0, 0}, resident_smem[3] = {-1, -1, -1};
-  const int t = a.threads > 0 ? a.threads : 128, si = shape_index_m(t);
-  if (resident_smem[si] != a.smem_bytes) {
-    resident[si] = mixed_variant_resident<ENERGY, TRACE>(t, a.smem_bytes);
-    resident_smem[si] = a.smem_bytes;
-  }
-  const int blocks = a.cta_start ? a.n_cta : (a.n_tiles < resident[si] ? a.n_tiles : resident[si]);
+static int launch_mixed_variant(const StepArgs& a, cudaStream_t st) {
+  const int t = a.threads > 0 ? a.threads : 128;
+  const int resident = mixed_variant_resident<ENERGY, TRACE>(t, a.smem_bytes);
+  if (resident < 0) return -1;
+  const int blocks = a.cta_start ? a.n_cta : (a.n_tiles < resident ? a.n_tiles : resident);
   step_mixed_kernel<ENERGY, TRACE><<<blocks, t, a.smem_bytes, st>>>(a);
+  return 0;
 }
 
 int launch_step_mixed(const StepArgs& a, void* stream) {
   cudaStream_t st = (cudaStream_t)stream;
   const bool E = a.energy != nullptr, T = a.trace != nullptr;
-  if (E && T) launch_mixed_variant<true, true>(a, st);
-  else if (E) launch_mixed_variant<true, false>(a, st);
-  else if (T) launch_mixed_variant<false, true>(a, st);
-  else launch_mixed_variant<false, false>(a, st);
+  int r;
+  if (E && T) r = launch_mixed_variant<true, true>(a, st);
+  else if (E) r = launch_mixed_variant<true, false>(a, st);
+  else if (T) r = launch_mixed_variant<false, true>(a, st);
+  else r = launch_mixed_variant<false, false>(a, st);
   count_launch();
+  if (r) return r;
   return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }
 

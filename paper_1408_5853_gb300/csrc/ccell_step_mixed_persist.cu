@@ -25,23 +25,25 @@ __global__ void __launch_bounds__(CC_MIX_MAX_THREADS, CC_MIX_MIN_BLOCKS) steps_m
 }
 
 template <bool ENERGY, bool TRACE>
+static KernelCache& mixed_persistent_cache() {
+  static KernelCache c;
+  return c;
+}
+
+template <bool ENERGY, bool TRACE>
+static int mixed_persistent_variant_resident(int threads, int smem) {
+  return cached_resident(mixed_persistent_cache<ENERGY, TRACE>(), steps_mixed_persistent_kernel<ENERGY, TRACE>,
+                         threads, smem, kMaxTileSmem);
+}
+
+template <bool ENERGY, bool TRACE>
 static int launch_mixed_persistent_variant(const StepArgs& a, long long n, cudaStream_t st) {
-  static int resident[3] = {0, 0, 0}, resident_smem[3] = {-1, -1, -1};
-  static bool opted = false;
   auto kern = steps_mixed_persistent_kernel<ENERGY, TRACE>;
-  if (!opted) {
-    if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxTileSmem) !=
-        cudaSuccess)
-      cudaGetLastError();  // the launch then reports a tile that does not fit
-    opted = true;
-  }
-  const int t = a.threads > 0 ? a.threads : 128, si = shape_index_m(t);
-  if (resident_smem[si] != a.smem_bytes) {
-    resident[si] = resident_blocks_m(kern, t, a.smem_bytes);
-    resident_smem[si] = a.smem_bytes;
-  }
-  if (a.cta_start && resident[si] < a.n_cta) return -3;
-  const int blocks = a.cta_start ? a.n_cta : (a.n_tiles < resident[si] ? a.n_tiles : resident[si]);
+  const int t = a.threads > 0 ? a.threads : 128;
+  const int resident = mixed_persistent_variant_resident<ENERGY, TRACE>(t, a.smem_bytes);
+  if (resident < 0) return -1;
+  if (a.cta_start && resident < a.n_cta) return -3;
+  const int blocks = a.cta_start ? a.n_cta : (a.n_tiles < resident ? a.n_tiles : resident);
   StepArgs copy = a;
   void* args[] = {&copy, &n};
   const cudaError_t e =
@@ -51,15 +53,6 @@ static int launch_mixed_persistent_variant(const StepArgs& a, long long n, cudaS
     return -3;
   }
   return e == cudaSuccess ? 0 : -1;
-}
-
-template <bool ENERGY, bool TRACE>
-static int mixed_persistent_variant_resident(int threads, int smem) {
-  auto kern = steps_mixed_persistent_kernel<ENERGY, TRACE>;
-  if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxTileSmem) !=
-      cudaSuccess)
-    cudaGetLastError();
-  return resident_blocks_m(kern, threads, smem);
 }
 
 int mixed_persistent_resident_blocks(int threads, int smem) {

@@ -24,26 +24,26 @@ __global__ void __launch_bounds__(CC_FP64_MAX_THREADS, CC_FP64_MIN_BLOCKS) steps
   }
 }
 
-constexpr int kTileSmemMaxP = kMaxTileSmem;
+template <bool ENERGY, bool TRACE>
+static KernelCache& fp64_persistent_cache() {
+  static KernelCache c;
+  return c;
+}
+
+template <bool ENERGY, bool TRACE>
+static int fp64_persistent_variant_resident(int threads, int smem) {
+  return cached_resident(fp64_persistent_cache<ENERGY, TRACE>(), steps_fp64_persistent_kernel<ENERGY, TRACE>,
+                         threads, smem, kMaxTileSmem);
+}
 
 template <bool ENERGY, bool TRACE>
 static int launch_fp64_persistent_variant(const StepArgs& a, long long n, cudaStream_t st) {
-  static int resident[3] = {0, 0, 0}, resident_smem[3] = {-1, -1, -1};
-  static bool opted = false;
   auto kern = steps_fp64_persistent_kernel<ENERGY, TRACE>;
-  if (!opted) {
-    if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, kTileSmemMaxP) !=
-        cudaSuccess)
-      cudaGetLastError();  // the launch then reports a tile that does not fit
-    opted = true;
-  }
-  const int t = a.threads > 0 ? a.threads : 128, si = shape_index(t);
-  if (resident_smem[si] != a.smem_bytes) {
-    resident[si] = resident_blocks(kern, t, a.smem_bytes);
-    resident_smem[si] = a.smem_bytes;
-  }
-  if (a.cta_start && resident[si] < a.n_cta) return -3;
-  const int blocks = a.cta_start ? a.n_cta : (a.n_tiles < resident[si] ? a.n_tiles : resident[si]);
+  const int t = a.threads > 0 ? a.threads : 128;
+  const int resident = fp64_persistent_variant_resident<ENERGY, TRACE>(t, a.smem_bytes);
+  if (resident < 0) return -1;
+  if (a.cta_start && resident < a.n_cta) return -3;
+  const int blocks = a.cta_start ? a.n_cta : (a.n_tiles < resident ? a.n_tiles : resident);
   StepArgs copy = a;
   void* args[] = {&copy, &n};
   const cudaError_t e =
@@ -53,15 +53,6 @@ static int launch_fp64_persistent_variant(const StepArgs& a, long long n, cudaSt
     return -3;
   }
   return e == cudaSuccess ? 0 : -1;
-}
-
-template <bool ENERGY, bool TRACE>
-static int fp64_persistent_variant_resident(int threads, int smem) {
-  auto kern = steps_fp64_persistent_kernel<ENERGY, TRACE>;
-  if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, kTileSmemMaxP) !=
-      cudaSuccess)
-    cudaGetLastError();
-  return resident_blocks(kern, threads, smem);
 }
 
 int fp64_persistent_resident_blocks(int threads, int smem) {

@@ -10,7 +10,8 @@ import numpy as np
 def run_gpu(cfgs, T0_list, n_steps, t0=0.0, dt=0.0, precision=0, want_trace=True,
             want_energy=True, chunks=None, launch=None):
     """Run n_steps on the GPU for the instances `cfgs` from fields `T0_list`
-    (launch: (mode, threads, rows_per_lane) or the library's default).
+    (launch: (mode, threads, rows_per_lane), "autotune" for the shape the
+    library's autotuner picks on the initial field, or None for the default).
 
     Returns (list of fields, trace[n_inst, n_steps, 2], energy[n_inst, 5])."""
     import torch
@@ -18,11 +19,13 @@ def run_gpu(cfgs, T0_list, n_steps, t0=0.0, dt=0.0, precision=0, want_trace=True
     if isinstance(cfgs, dict):
         cfgs, T0_list = [cfgs], [T0_list]
     sol = ccell.Solver(cfgs, precision=precision)
-    if launch is not None:
-        sol.set_launch(*launch)
     dtype = torch.float64 if precision == ccell.FP64 else torch.float32
     flat = np.concatenate([np.asarray(T, dtype=np.float64).ravel() for T in T0_list])
     T = torch.tensor(flat, dtype=dtype, device="cuda")
+    if launch == "autotune":
+        sol.autotune(T, n_trial=2)          # restores T
+    elif launch is not None:
+        sol.set_launch(*launch)
     n_inst = len(cfgs)
     trace = torch.zeros(n_inst * n_steps * 2, dtype=torch.float64, device="cuda") if want_trace else None
     energy = torch.zeros(n_inst * 5, dtype=torch.float64, device="cuda") if want_energy else None
@@ -50,7 +53,9 @@ def run_gpu(cfgs, T0_list, n_steps, t0=0.0, dt=0.0, precision=0, want_trace=True
         ofs += n
     tr = trace.view(n_inst, n_steps, 2).cpu().numpy() if want_trace else None
     en = energy.view(n_inst, 5).cpu().numpy() if want_energy else None
+    shape = sol.get_launch()
     sol.close()
+    run_gpu.last_launch = shape
     return fields, tr, en
 
 

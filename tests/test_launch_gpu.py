@@ -137,3 +137,20 @@ def test_cuda_graph_replay_equals_direct_call(mode):
     assert torch.allclose(trb, trc, rtol=1e-13, atol=0.0)
     assert torch.allclose(enb, enc, rtol=1e-12, atol=0.0)
     sol.close()
+
+
+def test_measured_fp64_rate_is_plausible():
+    """cc_measure_fp64_rate (the FP64-pipe roofline denominator): a positive,
+    finite rate within the range of any FP64-capable GPU, repeatable within 20 %."""
+    import torch
+    from paper_1408_5853_gb300 import ccell
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    buf = torch.zeros(1024 * sms, dtype=torch.float64, device="cuda")
+    stream = torch.cuda.current_stream().cuda_stream
+    r1, s1 = ccell.cc_measure_fp64_rate(buf.data_ptr(), buf.numel(), 2000, stream)
+    r2, _ = ccell.cc_measure_fp64_rate(buf.data_ptr(), buf.numel(), 2000, stream)
+    assert 1e10 < r1 < 1e14 and s1 > 0.0
+    assert abs(r1 - r2) <= 0.2 * max(r1, r2)
+    assert bool(torch.isfinite(buf).all())
+    with pytest.raises(ccell.CCError):
+        ccell.cc_measure_fp64_rate(buf.data_ptr(), 16, 10, stream)   # scratch too short

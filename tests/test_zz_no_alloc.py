@@ -75,3 +75,51 @@ def test_noalloc_rejects_sizes_beyond_its_limit():
                                 ccell.source(cfg), T.data_ptr(), 1, 0.0, cfg["dt"], None, None,
                                 torch.cuda.current_stream().cuda_stream)
     assert e.value.status == ccell.CC_EINVAL
+
+
+def _noalloc_vs_oracle(cfg, T0, n, t0):
+    import torch
+
+    from oracle import oracle
+    from paper_1408_5853_gb300 import ccell
+
+    kw = dict(dtype=torch.float64, device="cuda")
+    T = torch.tensor(T0.ravel(), **kw)
+    tr, en = torch.zeros(2 * n, **kw), torch.zeros(5, **kw)
+    ccell.cc_step_n_noalloc(ccell.geometry_desc(cfg), ccell.materials(cfg), ccell.source(cfg),
+                            T.data_ptr(), n, t0, cfg["dt"], tr.data_ptr(), en.data_ptr(),
+                            torch.cuda.current_stream().cuda_stream)
+    torch.cuda.synchronize()
+    To, tro, eo = oracle.step_n(cfg, T0, n, t0, cfg["dt"])
+    assert np.max(np.abs(T.cpu().numpy().reshape(To.shape) - To)) <= TOL_K
+    assert np.max(np.abs(tr.view(n, 2).cpu().numpy() - tro)) <= TOL_K
+    assert np.max(np.abs(en.cpu().numpy() - eo)) <= 1e-9 * max(abs(eo[0]), abs(eo[1]))
+
+
+def test_noalloc_matches_oracle_half_cell_grid_dirichlet_face():
+    """Half-cell placement (single layer) with a Dirichlet r_max, against the
+    oracle: the grid, class and weight tables of this entry point come from
+    the host code it shares with cc_step_n."""
+    from oracle import oracle
+    from paper_1408_5853_gb300 import inputs
+
+    cfg = inputs.small_case()
+    cfg["layers"] = cfg["layers"][2:3]
+    cfg["layers"][0]["thickness"] = 0.3e-3
+    cfg.update(nr=45, nz=50, placement=1, bc_rmax=1)
+    cfg["source"]["layer"] = 0
+    cfg["dt"] = min(5e-7, 0.5 * oracle.tau_stab(cfg, 20.0, 100.0))
+    T0 = inputs.initial_field(cfg, "smooth", seed=5)
+    _noalloc_vs_oracle(cfg, T0, 40, 1e-3 - 20 * cfg["dt"])
+
+
+def test_noalloc_matches_oracle_transient_waveform():
+    """The transient turn-on waveform (2), accepted as by cc_set_source, and a
+    Dirichlet z = 0 face, against the oracle."""
+    from paper_1408_5853_gb300 import inputs
+
+    cfg = inputs.small_case()
+    cfg.update(nr=70, nz=33, bc_z0=1)
+    cfg["source"].update(waveform=2, edge_w=40 * cfg["dt"])
+    T0 = inputs.initial_field(cfg, "smooth", seed=9)
+    _noalloc_vs_oracle(cfg, T0, 60, 10e-3 - 10 * cfg["dt"])   # across a period start
