@@ -230,7 +230,13 @@ int cc_step_adi_n(cc_ctx* ctx, void* T_dev, int64_t n_steps, double t0_s, double
  *   one cooperative (co-resident) launch with a grid barrier between steps
  *   (bounded wait: a barrier that does not complete within ~seconds ends the
  *   kernel and cc_sync reports CC_ETIMEOUT; if the grid cannot be
- *   co-resident the call falls back to mode 0).
+ *   co-resident the call falls back to mode 0).  Modes 0 and 1 work on CTA
+ *   tiles: the warps of a block assemble the rows of a few lines into shared
+ *   memory, then solve them, then store, with block barriers in between.
+ *   mode 2: one launch per time step in which every warp owns a run of
+ *   consecutive lines and takes each line from its rows to its stored
+ *   values without block barriers (rectangles; a context with a stepped
+ *   outline runs mode 0).
  *   threads: 64, 128 or 256 per block.
  *   rows_per_lane: 2..16, target rows per lane of the line solve; a line of
  *   nr rows is split over the smallest power-of-two number of lanes G <= 32

@@ -49,6 +49,12 @@ struct cc_ctx {
   int* d_cta = nullptr;       // FP64 step: first tile of each block (n_cta + 1)
   int n_cta = 0;
   size_t cta_cap = 0;
+  // launch mode 2 (warp-owned lines): warp tasks and each warp's first task
+  bool lines_ok = false;      // FP64 context of rectangles
+  TileTask* d_wtasks = nullptr;
+  int* d_wcta = nullptr;
+  size_t wtasks_cap = 0, wcta_cap = 0;
+  int lines_blocks = 0, lines_smem = 0, lines_warp_doubles = 0;
   void* d_T2 = nullptr;       // ping-pong partner of the caller's field
   float* d_lo = nullptr;      // mixed precision: low-order parts (two buffers)
   double* d_s = nullptr;      // waveform table
@@ -101,6 +107,11 @@ void free_device(cc_ctx* c) {
   c->d_cta = nullptr;
   c->cta_cap = 0;
   c->n_cta = 0;
+  cudaFree(c->d_wtasks);
+  cudaFree(c->d_wcta);
+  c->d_wtasks = nullptr;
+  c->d_wcta = nullptr;
+  c->wtasks_cap = c->wcta_cap = 0;
   cudaFree(c->d_T2);
   cudaFree(c->d_lo);
   cudaFree(c->d_s);
@@ -208,6 +219,57 @@ void cut_tiles(const std::vector<Instance>& inst, const std::vector<int>& lpcs, 
   }
 }
 
+// Copy a host vector into a device buffer, growing it when needed.
+template <class V>
+int put_grown(V** dev, size_t* cap, const std::vector<V>& h) {
+  if (h.size() > *cap) {
+    cudaFree(*dev);
+    *dev = nullptr;
+    *cap = 0;
+    if (cudaMalloc(dev, sizeof(V) * h.size()) != cudaSuccess) {
+      cudaGetLastError();
+      return CC_ENOMEM;
+    }
+    *cap = h.size();
+  }
+  if (!h.empty() && cudaMemcpy(*dev, h.data(), sizeof(V) * h.size(), cudaMemcpyHostToDevice) !=
+                        cudaSuccess)
+    return CC_ECUDA;
+  return CC_OK;
+}
+
+// Warp tasks of launch mode 2: all interior lines cut into equal node shares,
+// one per warp of the resident grid.
+int cut_warp_tasks(cc_ctx* c) {
+  c->lines_ok = true;
+  int if_slots = 1;
+  for (const Instance& in : c->inst) {
+    if (in.j_narrow < in.d.nz) c->lines_ok = false;
+    int n_if = 0;
+    for (int i = 0; i < in.d.nr; ++i) n_if += (in.cls[i] == RC_IFACE || in.cls[i] == RC_OUTER);
+    if_slots = std::max(if_slots, (32 / in.G) * n_if);
+  }
+  if (!c->lines_ok) return CC_OK;
+  c->lines_warp_doubles = lines_warp_doubles(if_slots);
+  c->lines_smem = (c->threads / 32) * c->lines_warp_doubles * (int)sizeof(double);
+  if (c->lines_smem > kMaxTileSmem) {
+    c->lines_ok = false;
+    return CC_OK;
+  }
+  const int B = c->precision == CC_FP64 ? fp64_lines_resident_blocks(c->threads, c->lines_smem)
+                                        : mixed_lines_resident_blocks(c->threads, c->lines_smem);
+  if (B < 0) return CC_ECUDA;
+  std::vector<int> whole(c->inst.size());
+  for (size_t k = 0; k < c->inst.size(); ++k) whole[k] = c->inst[k].d.nz;
+  std::vector<TileTask> tasks;
+  std::vector<int> first;
+  cut_tiles(c->inst, whole, B * (c->threads / 32), tasks, first);
+  int rc = put_grown(&c->d_wtasks, &c->wtasks_cap, tasks);
+  if (rc == CC_OK) rc = put_grown(&c->d_wcta, &c->wcta_cap, first);
+  c->lines_blocks = B;
+  return rc;
+}
+
 int upload(cc_ctx* c, const std::vector<double>& dts, cudaStream_t st) {
   const int n = (int)c->inst.size();
   if (c->device < 0) {
@@ -305,6 +367,11 @@ int upload(cc_ctx* c, const std::vector<double>& dts, cudaStream_t st) {
         return CC_ECUDA;
     }
     c->smem_bytes = smem;
+    c->lines_ok = false;
+    if (c->mode == 2) {
+      const int rc = cut_warp_tasks(c);
+      if (rc != CC_OK) return rc;
+    }
     c->tasks_dirty = false;
     c->dirty = true;
   }
@@ -501,7 +568,21 @@ int cc_step_n(cc_ctx* c, void* T_dev, int64_t n_steps, double t0, double dt_s, d
     a.Tin = bufs[s & 1];
     a.Tout = bufs[(s + 1) & 1];
     int r;
-    if (c->precision == CC_FP64) {
+    if (c->mode == 2 && c->lines_ok) {
+      StepArgs w = a;
+      w.tiles = c->d_wtasks;
+      w.cta_start = c->d_wcta;
+      w.n_cta = c->lines_blocks;
+      w.smem_bytes = c->lines_smem;
+      w.warp_doubles = c->lines_warp_doubles;
+      if (c->precision == CC_FP64) {
+        r = launch_step_fp64_lines(w, stream);
+      } else {
+        w.lo_in = c->d_lo + (s & 1) * c->total_nodes;
+        w.lo_out = c->d_lo + ((s + 1) & 1) * c->total_nodes;
+        r = launch_step_mixed_lines(w, stream);
+      }
+    } else if (c->precision == CC_FP64) {
       r = launch_step_fp64(a, stream);
     } else {
       a.lo_in = c->d_lo + (s & 1) * c->total_nodes;
@@ -640,7 +721,7 @@ int cc_step_adi_n(cc_ctx* c, void* T_dev, int64_t n_steps, double t0, double dt_
 }
 
 int cc_set_launch(cc_ctx* c, int32_t mode, int32_t threads, int32_t rows_per_lane) {
-  if (!c || (mode != 0 && mode != 1) || (threads != 64 && threads != 128 && threads != 256) ||
+  if (!c || mode < 0 || mode > 2 || (threads != 64 && threads != 128 && threads != 256) ||
       rows_per_lane < 2 || rows_per_lane > kRowsPerLane)
     return CC_EINVAL;
   if (rows_per_lane != c->rows || threads != c->threads || mode != c->mode) c->tasks_dirty = true;
@@ -684,7 +765,10 @@ int cc_autotune(cc_ctx* c, void* T_dev, int32_t n_trial, float* best_ms, void* s
   float best = 1e30f;
   int bm = c->mode, bt = c->threads, br = c->rows;
   int rc = CC_OK;
-  for (int mode : {0, 1})
+  bool rect = true;
+  for (auto& in : c->inst) rect &= in.j_narrow == in.d.nz;
+  const int n_modes = rect ? 3 : 2;  // mode 2: rectangles only
+  for (int mode = 0; mode < n_modes; ++mode)
     for (int threads : {64, 128, 256})
       for (int rows : rows_opts) {
         cc_set_launch(c, mode, threads, rows);

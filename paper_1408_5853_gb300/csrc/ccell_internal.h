@@ -141,6 +141,15 @@ CC_HOST_DEVICE inline int mixed_tile_smem_bytes(int nl, int nr) {
   return 4 * nl * smem_row_stride(nr) * (int)sizeof(double) +
          ((nl + 2) * smem_row_stride(nr) + kMixIf * CC_MAX_LAYERS * nl) * (int)sizeof(float);
 }
+// Warp-owned lines (launch mode 2): one padded row of a warp's shared memory
+// holds the rows of all its lane groups' current lines (32/G lines of
+// nr <= 16 G rows: at most 512 rows).  A warp's shared memory holds c', a',
+// d' (then That) and V2 rho c / tau rows, then four values per (lane group,
+// interface node).
+constexpr int kWarpRowStride = 512 + (512 >> 4) + 1;
+CC_HOST_DEVICE inline int lines_warp_doubles(int if_slots) {
+  return 4 * kWarpRowStride + 4 * if_slots;
+}
 // Largest dynamic shared memory of an FP64 tile: the opt-in limit per block
 // on sm_103 (227 KiB) less room for the kernels' static shared memory.
 constexpr int kMaxTileSmem = 226 * 1024;
@@ -179,6 +188,7 @@ struct StepArgs {
   double* adi_lamz;
   // launch shape
   int threads;           // threads per block (64, 128 or 256)
+  int warp_doubles;      // warp-lines kernel: doubles of shared memory per warp
   // persistent launches: grid barrier state [count, generation], bounded wait
   unsigned* bar;
   unsigned bar_extra;    // extra arrivals expected (nonzero only to test the timeout)
@@ -262,6 +272,13 @@ int launch_step_mixed(const StepArgs& a, void* stream);
 int launch_steps_fp64_persistent(const StepArgs& a, long long n, void* stream);
 int launch_steps_mixed_persistent(const StepArgs& a, long long n, void* stream);
 int launch_mixed_init(float* lo, long long n_total, void* stream);
+// FP64 step with warp-owned lines (ccell_step_lines.cu): a.tiles are warp
+// tasks, a.cta_start[w] .. a.cta_start[w + 1] those of warp w, a.n_cta blocks.
+int launch_step_fp64_lines(const StepArgs& a, void* stream);
+int fp64_lines_resident_blocks(int threads, int smem);
+// The same for the mixed-precision step (ccell_step_lines_mixed.cu).
+int launch_step_mixed_lines(const StepArgs& a, void* stream);
+int mixed_lines_resident_blocks(int threads, int smem);
 int launch_boundary_trace_zero(double* trace, long long n, void* stream);
 long long kernel_launch_count();
 // Host: fill one power-law table for exponent b and scales; returns false if
