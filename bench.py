@@ -42,10 +42,15 @@ FLOPS_PER_NODE_FP64 = 150     # FP64 operations per node-update (2 power laws ~ 
 # kernel as captured there: reset to None when the kernel changes.
 STEP_FP64_TRAFFIC_512x4096 = 17.251328e6 + 1.536e3
 FP64_PEAK_NOMINAL_TFLOPS = 152 * 4 * 0.5 * 2 * 2.07e9 / 1e12   # SMs x SMSPs x DFMA lanes/clk x 2 x max clock
-# FP64 thread-operations (DFMA + DADD + DMUL) the step kernel executes per node-update, from the
-# ncu capture of the same kernel (profiles/step_fp64_kernel_512x4096.md); None once the kernel
-# changes until it is captured again.
-EXECUTED_FP64_OPS_PER_NODE = 60.1
+# Per launch mode of the FP64 headline: the dominant kernel, the FP64-pipe thread-instructions it
+# executes per node-update on the 512x4096 workload (ncu sm__thread_inst_executed_pipe_fp64_pred_on
+# of one launch / nodes) and the summary that holds the capture; None once the kernel changes until
+# it is captured again.
+EXECUTED_FP64 = {
+    0: ("step_fp64_kernel", 63.0, "profiles/step_fp64_kernel_512x4096.md"),
+    1: ("steps_fp64_persistent_kernel", None, None),
+    2: ("step_fp64_lines_kernel", None, None),
+}
 L2_FLUSH_BYTES = 256 << 20
 
 
@@ -250,6 +255,8 @@ def run_ours(args, world, rank, local):
         return None
     peaks = _peaks()
     hbm_peak = peaks["hbm_gbs"]
+    kname, executed_ops, executed_src = EXECUTED_FP64.get(
+        tuple(launch_shape)[0], ("step_fp64_kernel", None, None))
     achieved_tflops = FLOPS_PER_NODE_FP64 * nodes / (per_launch_ms / 1e3) / 1e12
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -261,7 +268,7 @@ def run_ours(args, world, rank, local):
                    "precision": "fp64", "l2": f"flushed between timed steps ({L2_FLUSH_BYTES >> 20} MB write)",
                    "parallelism": f"replicas x{world}",
                    "launch": dict(zip(("mode", "threads", "rows_per_lane"), launch_shape))},
-        "roofline": {"bound": "alu", "kernel": "step_fp64_kernel",
+        "roofline": {"bound": "alu", "kernel": kname,
                      "achieved": achieved_tflops, "peak": fp64_peak_tflops, "unit": "TFLOP/s",
                      "frac": achieved_tflops / fp64_peak_tflops,
                      "traffic": (STEP_FP64_TRAFFIC_512x4096
@@ -278,14 +285,13 @@ def run_ours(args, world, rank, local):
                      "per_unit": f"{FLOPS_PER_NODE_FP64} FP64 ops per node-update "
                                  "(algorithmic count: two power laws as log + exp, 1 divide, "
                                  "1 reciprocal, ~30 FMA/add/mul)",
-                     "executed": (None if EXECUTED_FP64_OPS_PER_NODE is None else {
-                         "fp64_ops_per_node_update": EXECUTED_FP64_OPS_PER_NODE,
-                         "achieved": EXECUTED_FP64_OPS_PER_NODE * nodes / (per_launch_ms / 1e3) / 1e12,
-                         "frac": EXECUTED_FP64_OPS_PER_NODE * nodes / (per_launch_ms / 1e3) / 1e12
-                         / fp64_peak_tflops,
-                         "unit": "TFLOP/s",
-                         "source": "ncu DFMA + DADD + DMUL thread-operations of the same kernel "
-                                   "(profiles/step_fp64_kernel_512x4096.md)"})},
+                     "executed": (None if executed_ops is None else {
+                         "fp64_pipe_ops_per_node_update": executed_ops,
+                         "achieved": executed_ops * nodes / (per_launch_ms / 1e3) / 1e12,
+                         "peak": fma_rate / 1e12,
+                         "frac": executed_ops * nodes / (per_launch_ms / 1e3) / fma_rate,
+                         "unit": "T thread-instructions/s",
+                         "source": executed_src})},
         "hbm_roofline": {"bound": "hbm", "achieved": BYTES_PER_NODE_FP64 * value / world / 1e9,
                          "peak": hbm_peak, "unit": "GB/s",
                          "frac": BYTES_PER_NODE_FP64 * value / world / 1e9 / hbm_peak,
