@@ -165,24 +165,27 @@ __device__ __forceinline__ void step_fp64_tile(const StepArgs& a, const TileTask
         const ZGeo& zg = I.zg[j];
         double ra, rb, rc, rd, m = 0.0;
         if (cls == RC_REGULAR) {
-          // Eq. (Lambda_j), explicit in T, from the face fluxes
-          const double Lj = fma(zg.gzn, fn, -zg.gzs * fs);
           double X = 0.0;  // Eq. (source)
           if (g.seg == I.src_layer && s != 0.0) {
             X = I.q0 * s;
             if (I.g_model == 1) X *= I.g_ref / sqrt(Tc);
           }
-          // Eq. (ABC)
+          // Eq. (ABC) with Eq. (Lambda_j), explicit in T, from the face fluxes
           const double A = -g.gA * lw, C = -g.gC * le;
           ra = A;
           rc = C;
           rb = rct - A - C;
-          rd = fma(rct, Tc, Lj + X);
-          if (a.adi_lj && own) {  // for the axial half step of the ADI variant
-            const long long o = I.t_off + (long long)j * nr + ic;
-            a.adi_rct[o] = rct;
-            a.adi_lj[o] = Lj;
-            a.adi_lamz[o] = ln;
+          if (a.adi_lj) {  // the axial half step of the ADI variant needs Lambda_j alone
+            const double Lj = fma(zg.gzn, fn, -zg.gzs * fs);
+            rd = fma(rct, Tc, Lj + X);
+            if (own) {
+              const long long o = I.t_off + (long long)j * nr + ic;
+              a.adi_rct[o] = rct;
+              a.adi_lj[o] = Lj;
+              a.adi_lamz[o] = ln;
+            }
+          } else {
+            rd = fma(rct, Tc, fma(zg.gzn, fn, fma(-zg.gzs, fs, X)));
           }
           if (ENERGY && own) {
             m = g.V2 * rct;  // V rho c / (etabar tau)

@@ -6,41 +6,11 @@
 // each row scaled to a unit diagonal in FP32 and widened exactly; the
 // tridiagonal elimination, separator solve, back substitution and the energy
 // sums in FP64.
-//
-// Conversions between FP32 and FP64 issue on the FP64 pipe, the pipe that
-// bounds this scheme on GB300, so the widening of the row coefficients and
-// the rounding of the increment to FP32 are done with integer operations on
-// the bit patterns (exact widening; round to nearest even; values below the
-// FP32 normal range, |x| < 2^-126, flush to zero).
+// FP32 <-> FP64 conversions use the integer forms of ccell_mixed_task.cuh.
 #pragma once
 #include "ccell_mixed_task.cuh"
 
 namespace ccell {
-
-// (double)f for normal, zero, infinite and NaN f (subnormal f become +-0).
-__device__ __forceinline__ double widen_f32(float f) {
-  const unsigned b = __float_as_uint(f);
-  const unsigned mag = b & 0x7fffffffu;
-  unsigned hi = (mag >> 3) + (896u << 20);
-  hi = (mag < 0x00800000u) ? 0u : hi;
-  hi = (mag >= 0x7f800000u) ? (0x7ff00000u | ((mag >> 3) & 0x000fffffu)) : hi;
-  const unsigned lo = (mag < 0x00800000u) ? 0u : (b << 29);
-  return __hiloint2double((int)(hi | (b & 0x80000000u)), (int)lo);
-}
-
-// x rounded to the nearest FP32 (ties to even); |x| < 2^-126 gives +-0,
-// overflow gives +-inf, NaN stays NaN.
-__device__ __forceinline__ float narrow_f64(double x) {
-  const unsigned hi = (unsigned)__double2hiint(x), lo = (unsigned)__double2loint(x);
-  const int E = (int)((hi >> 20) & 0x7ffu);
-  unsigned f = ((unsigned)(E - 896) << 23) | ((hi & 0x000fffffu) << 3) | (lo >> 29);
-  const unsigned rem = lo & 0x1fffffffu;
-  f += (rem > 0x10000000u) | ((rem == 0x10000000u) & (f & 1u));
-  f = (E < 897) ? 0u : f;
-  const bool nan = E == 2047 && ((hi & 0x000fffffu) | lo) != 0u;
-  f = (E > 1150) ? (nan ? 0x7fc00000u : 0x7f800000u) : f;
-  return __uint_as_float(f | (hi & 0x80000000u));
-}
 
 template <bool ENERGY, bool TRACE>
 __device__ __forceinline__ void mixed_warp_task(const StepArgs& a, const TileTask tk,

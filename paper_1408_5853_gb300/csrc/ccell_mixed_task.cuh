@@ -3,6 +3,12 @@
 // the row coefficients run in FP32; the tridiagonal elimination, the
 // separator solve, the update and the energy sums run in FP64.
 //
+// Conversions between FP32 and FP64 issue on the FP64 pipe, the pipe that
+// bounds this scheme on GB300, so the widening of the row coefficients and
+// the rounding of the increment to FP32 are done with integer operations on
+// the bit patterns (exact widening; round to nearest even; values below the
+// FP32 normal range, |x| < 2^-126, flush to zero).
+//
 // State.  The caller's field is FP32.  Inside one call the temperature is the
 // FP32 pair hi + lo (the low parts live in context scratch and start at zero):
 // per-step increments near the heater are ~1e-5 K against an FP32 spacing of
@@ -18,6 +24,31 @@
 #include "ccell_device.cuh"
 
 namespace ccell {
+
+// (double)f for normal, zero, infinite and NaN f (subnormal f become +-0).
+__device__ __forceinline__ double widen_f32(float f) {
+  const unsigned b = __float_as_uint(f);
+  const unsigned mag = b & 0x7fffffffu;
+  unsigned hi = (mag >> 3) + (896u << 20);
+  hi = (mag < 0x00800000u) ? 0u : hi;
+  hi = (mag >= 0x7f800000u) ? (0x7ff00000u | ((mag >> 3) & 0x000fffffu)) : hi;
+  const unsigned lo = (mag < 0x00800000u) ? 0u : (b << 29);
+  return __hiloint2double((int)(hi | (b & 0x80000000u)), (int)lo);
+}
+
+// x rounded to the nearest FP32 (ties to even); |x| < 2^-126 gives +-0,
+// overflow gives +-inf, NaN stays NaN.
+__device__ __forceinline__ float narrow_f64(double x) {
+  const unsigned hi = (unsigned)__double2hiint(x), lo = (unsigned)__double2loint(x);
+  const int E = (int)((hi >> 20) & 0x7ffu);
+  unsigned f = ((unsigned)(E - 896) << 23) | ((hi & 0x000fffffu) << 3) | (lo >> 29);
+  const unsigned rem = lo & 0x1fffffffu;
+  f += (rem > 0x10000000u) | ((rem == 0x10000000u) & (f & 1u));
+  f = (E < 897) ? 0u : f;
+  const bool nan = E == 2047 && ((hi & 0x000fffffu) | lo) != 0u;
+  f = (E > 1150) ? (nan ? 0x7fc00000u : 0x7f800000u) : f;
+  return __uint_as_float(f | (hi & 0x80000000u));
+}
 
 // ---------------------------------------------------------------------------
 // FP32 material functions
@@ -88,10 +119,9 @@ __device__ __forceinline__ void step_mixed_tile(const StepArgs& a, const TileTas
   float* Lout = a.lo_out + I.t_off;
   const float s = (float)a.s_tab[a.step * a.n_inst + tk.inst];
   const float inv_tau = I.inv_tau_f, tau = I.tau_f;
-  double eD = 0.0, eN = 0.0, eI = 0.0, tr = 0.0;
-  // stored and injected heat: FP32 partial sums over this thread's nodes of
-  // the tile (a few dozen terms), added to the FP64 accumulators once per tile
-  float eQf = 0.0f, eEf = 0.0f;
+  // energy terms: per-node products of the FP32 factors (widened exactly)
+  // with FP64 values, summed in FP64
+  double eE = 0.0, eQ = 0.0, eD = 0.0, eN = 0.0, eI = 0.0, tr = 0.0;
 
   // ---- 0a. nodal conductivities of the interface rows, Eq. (cc_first_3)
   if (I.interface_rule == 0 && n_if > 0) {
@@ -181,13 +211,13 @@ __device__ __forceinline__ void step_mixed_tile(const StepArgs& a, const TileTas
           if (ENERGY && own) {
             const float V = g.V2_f * zg.etabar_f;
             m = V * rhoc;
-            eQf = fmaf(tau * V, X, eQf);
+            if (X != 0.0f) eQ = fma(widen_f32(tau * V), widen_f32(X), eQ);
             if (j == 1) {
-              const double f = (double)(-tau * g.V2_f * fs / (float)zg.eta_s);
+              const double f = widen_f32(-tau * g.V2_f * fs / (float)zg.eta_s);
               if (I.bc_z0 == CC_DIRICHLET) eD += f; else eN += f;
             }
             if (j == M - 1) {
-              const double f = (double)(tau * g.V2_f * fn / (float)zg.eta_n);
+              const double f = widen_f32(tau * g.V2_f * fn / (float)zg.eta_n);
               if (I.bc_zmax == CC_DIRICHLET) eD += f; else eN += f;
             }
           }
@@ -229,9 +259,9 @@ __device__ __forceinline__ void step_mixed_tile(const StepArgs& a, const TileTas
           // the row divided by its diagonal in FP32 (the solve takes b = 1),
           // then widened exactly
           const float ib = __fdividef(1.0f, fb);
-          SA[w] = fa * ib;
-          SC[w] = fc * ib;
-          SD[w] = fd * ib;
+          SA[w] = widen_f32(fa * ib);
+          SC[w] = widen_f32(fc * ib);
+          SD[w] = widen_f32(fd * ib);
           if (ENERGY) FM[w] = m;
         }
         hc = hn; lc = ln;
@@ -258,8 +288,8 @@ __device__ __forceinline__ void step_mixed_tile(const StepArgs& a, const TileTas
       const int c = smem_col(i);
       const double xd = SB[(size_t)q * nrp + c];
       bad |= not_finite(xd);
-      const float x = __double2float_rn(xd);
-      if (ENERGY) eEf = fmaf(FM[(size_t)q * nrp + c], x, eEf);
+      const float x = narrow_f64(xd);
+      if (ENERGY) eE = fma(widen_f32(FM[(size_t)q * nrp + c]), xd, eE);
       const float hi = ld_state<CACHED>(Hin + rj + i), lo = ld_state<CACHED>(Lin + rj + i);
       const float v = lo + x;
       float h1 = hi + v;
@@ -285,7 +315,7 @@ __device__ __forceinline__ void step_mixed_tile(const StepArgs& a, const TileTas
         }
       }
       if (TRACE && i == N) {  // That(r_max, z_j)
-        const double surf = ((double)hi + (double)lo) + xd;
+        const double surf = (widen_f32(hi) + widen_f32(lo)) + xd;
         tr = fma(I.zg[j].wnorm, surf, tr);
         if (j == 1) {
           const double x0 = (I.bc_z0 == CC_DIRICHLET) ? I.t_d : surf;
@@ -313,16 +343,16 @@ __device__ __forceinline__ void step_mixed_tile(const StepArgs& a, const TileTas
         const double* Bq = SB + (size_t)q * nrp;
         const float* K = sI + kMixIf * it;
         const double x = Bq[smem_col(i)];
-        const double fw = (double)K[2] * ((double)K[4] + (x - Bq[smem_col(i - 1)]));
+        const double fw = widen_f32(K[2]) * (widen_f32(K[4]) + (x - Bq[smem_col(i - 1)]));
         const int cls = STP ? line_class(I, I.rg[i].cls, i, j0 + q) : I.rg[i].cls;
         if (cls == RC_OUTER) {
           if (I.bc_rmax == CC_DIRICHLET) eD += fw; else eN += fw;
         } else if (!STP || cls == RC_IFACE) {
-          eI += fw + (double)K[3] * ((double)K[5] + (x - Bq[smem_col(i + 1)]));
+          eI += fw + widen_f32(K[3]) * (widen_f32(K[5]) + (x - Bq[smem_col(i + 1)]));
         }
       }
-      acc.e[0] += (double)eEf;
-      acc.e[1] += (double)eQf;
+      acc.e[0] += eE;
+      acc.e[1] += eQ;
       acc.e[2] += eD;
       acc.e[3] += eI;
       acc.e[4] += eN;
