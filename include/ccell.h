@@ -237,6 +237,14 @@ int cc_step_adi_n(cc_ctx* ctx, void* T_dev, int64_t n_steps, double t0_s, double
  *   consecutive lines and takes each line from its rows to its stored
  *   values without block barriers (rectangles; a context with a stepped
  *   outline runs mode 0).
+ *   mode 3: all steps of a call in one cooperative launch with the field
+ *   resident in shared memory: each block (one per SM) keeps its run of
+ *   lines on chip for the whole call and exchanges only its first and last
+ *   lines with its two neighbours between steps, through global memory and
+ *   per-block step counters (bounded waits, reported as CC_ETIMEOUT).  For
+ *   FP64 contexts of one rectangular instance whose field fits in the SMs'
+ *   shared memory (e.g. 512 x 4096); other contexts, or a grid that cannot
+ *   be co-resident, run mode 0.
  *   threads: 64, 128 or 256 per block.
  *   rows_per_lane: 2..16, target rows per lane of the line solve; a line of
  *   nr rows is split over the smallest power-of-two number of lanes G <= 32

@@ -55,6 +55,17 @@ struct cc_ctx {
   int* d_wcta = nullptr;
   size_t wtasks_cap = 0, wcta_cap = 0;
   int lines_blocks = 0, lines_smem = 0, lines_warp_doubles = 0;
+  // launch mode 3 (field resident in shared memory): per-block tiles,
+  // boundary-row exchange buffer and step counters
+  bool res_ok = false;
+  TileTask* d_rtiles = nullptr;
+  int* d_rcta = nullptr;
+  size_t rtiles_cap = 0, rcta_cap = 0;
+  double* d_xb = nullptr;
+  size_t xb_cap = 0;
+  unsigned* d_rflags = nullptr;
+  size_t rflags_cap = 0;
+  int res_blocks = 0, res_smem = 0, res_offset = 0;
   void* d_T2 = nullptr;       // ping-pong partner of the caller's field
   float* d_lo = nullptr;      // mixed precision: low-order parts (two buffers)
   double* d_s = nullptr;      // waveform table
@@ -107,6 +118,15 @@ void free_device(cc_ctx* c) {
   c->d_cta = nullptr;
   c->cta_cap = 0;
   c->n_cta = 0;
+  cudaFree(c->d_rtiles);
+  cudaFree(c->d_rcta);
+  cudaFree(c->d_xb);
+  cudaFree(c->d_rflags);
+  c->d_rtiles = nullptr;
+  c->d_rcta = nullptr;
+  c->d_xb = nullptr;
+  c->d_rflags = nullptr;
+  c->rtiles_cap = c->rcta_cap = c->xb_cap = c->rflags_cap = 0;
   cudaFree(c->d_wtasks);
   cudaFree(c->d_wcta);
   c->d_wtasks = nullptr;
@@ -270,6 +290,77 @@ int cut_warp_tasks(cc_ctx* c) {
   return rc;
 }
 
+// Tiles of launch mode 3: one block per SM (at most one per interior line),
+// each holding its run of lines of the single instance resident in shared
+// memory next to the scratch of one tile; the tile size is halved until both
+// fit.  Leaves res_ok false when the context does not qualify (several
+// instances, a stepped outline, mixed precision) or the field does not fit.
+int cut_resident_tiles(cc_ctx* c) {
+  c->res_ok = false;
+  if (c->inst.size() != 1 || c->precision != CC_FP64) return CC_OK;
+  const Instance& in = c->inst[0];
+  if (in.j_narrow < in.d.nz) return CC_OK;
+  int dev = 0, sms = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+    return CC_ECUDA;
+  const int lines = in.d.nz - 2, nr = in.d.nr, nrp = smem_row_stride(nr);
+  const int B = std::min(sms, lines);
+  for (int lpc = (c->threads / 32) * (32 / in.G); lpc >= 1; lpc /= 2) {
+    std::vector<TileTask> tiles;
+    std::vector<int> cta;
+    cut_tiles(c->inst, std::vector<int>{lpc}, B, tiles, cta);
+    int max_lines = 0;
+    bool empty = false;
+    for (int b = 0; b < B; ++b) {
+      if (cta[b + 1] == cta[b]) {
+        empty = true;
+        break;
+      }
+      const TileTask& f = tiles[cta[b]];
+      const TileTask& l = tiles[cta[b + 1] - 1];
+      max_lines = std::max(max_lines, l.j0 + l.nl - f.j0);
+    }
+    if (empty) return CC_OK;
+    const int tile = fp64_tile_smem_bytes(std::min(lpc, lines), nr);
+    const int smem = tile + (max_lines + 2) * nrp * (int)sizeof(double);
+    if (smem > kMaxTileSmem) continue;
+    const int resident = fp64_resident_kernel_blocks(c->threads, smem);
+    if (resident < 0) return CC_ECUDA;
+    if (resident < B) continue;
+    int rc = put_grown(&c->d_rtiles, &c->rtiles_cap, tiles);
+    if (rc == CC_OK) rc = put_grown(&c->d_rcta, &c->rcta_cap, cta);
+    if (rc != CC_OK) return rc;
+    const size_t xb = (size_t)B * 4 * nr;
+    if (xb > c->xb_cap) {
+      cudaFree(c->d_xb);
+      c->d_xb = nullptr;
+      c->xb_cap = 0;
+      if (cudaMalloc(&c->d_xb, sizeof(double) * xb) != cudaSuccess) {
+        cudaGetLastError();
+        return CC_ENOMEM;
+      }
+      c->xb_cap = xb;
+    }
+    if ((size_t)B > c->rflags_cap) {
+      cudaFree(c->d_rflags);
+      c->d_rflags = nullptr;
+      c->rflags_cap = 0;
+      if (cudaMalloc(&c->d_rflags, sizeof(unsigned) * B) != cudaSuccess) {
+        cudaGetLastError();
+        return CC_ENOMEM;
+      }
+      c->rflags_cap = B;
+    }
+    c->res_blocks = B;
+    c->res_smem = smem;
+    c->res_offset = tile / (int)sizeof(double);
+    c->res_ok = true;
+    return CC_OK;
+  }
+  return CC_OK;
+}
+
 int upload(cc_ctx* c, const std::vector<double>& dts, cudaStream_t st) {
   const int n = (int)c->inst.size();
   if (c->device < 0) {
@@ -368,8 +459,13 @@ int upload(cc_ctx* c, const std::vector<double>& dts, cudaStream_t st) {
     }
     c->smem_bytes = smem;
     c->lines_ok = false;
+    c->res_ok = false;
     if (c->mode == 2) {
       const int rc = cut_warp_tasks(c);
+      if (rc != CC_OK) return rc;
+    }
+    if (c->mode == 3) {
+      const int rc = cut_resident_tiles(c);
       if (rc != CC_OK) return rc;
     }
     c->tasks_dirty = false;
@@ -549,8 +645,28 @@ int cc_step_n(cc_ctx* c, void* T_dev, int64_t n_steps, double t0, double dt_s, d
     if (launch_mixed_init(c->d_lo, c->total_nodes, stream))
       return CC_ECUDA;
   }
-  bool done = false;
-  if (c->mode == 1) {
+  bool done = false, in_place = false;
+  if (c->mode == 3 && c->res_ok) {
+    // all steps in one cooperative launch, field resident in shared memory;
+    // the result is written back to T_dev
+    if (cudaMemsetAsync(c->d_rflags, 0, sizeof(unsigned) * c->res_blocks, st) != cudaSuccess)
+      return CC_ECUDA;
+    StepArgs r = a;
+    r.tiles = c->d_rtiles;
+    r.cta_start = c->d_rcta;
+    r.n_cta = c->res_blocks;
+    r.smem_bytes = c->res_smem;
+    r.res_offset = c->res_offset;
+    r.xb = c->d_xb;
+    r.nbr_flags = c->d_rflags;
+    r.step = 0;
+    r.Tin = T_dev;
+    r.Tout = T_dev;
+    const int rc = launch_steps_fp64_resident(r, n_steps, stream);
+    if (rc == 0) done = in_place = true;
+    else if (rc != -3) return CC_ECUDA;  // -3: not co-resident, use per-step launches
+  }
+  if (!done && c->mode == 1) {
     // all steps in one cooperative launch with a bounded grid barrier per step
     if (cudaMemsetAsync(a.bar, 0, sizeof(unsigned), st) != cudaSuccess) return CC_ECUDA;
     a.step = 0;
@@ -591,7 +707,7 @@ int cc_step_n(cc_ctx* c, void* T_dev, int64_t n_steps, double t0, double dt_s, d
     }
     if (r) return CC_ECUDA;
   }
-  if (n_steps & 1) {
+  if ((n_steps & 1) && !in_place) {
     if (cudaMemcpyAsync(T_dev, c->d_T2, elem * c->total_nodes, cudaMemcpyDeviceToDevice, st) !=
         cudaSuccess)
       return CC_ECUDA;
@@ -721,7 +837,7 @@ int cc_step_adi_n(cc_ctx* c, void* T_dev, int64_t n_steps, double t0, double dt_
 }
 
 int cc_set_launch(cc_ctx* c, int32_t mode, int32_t threads, int32_t rows_per_lane) {
-  if (!c || mode < 0 || mode > 2 || (threads != 64 && threads != 128 && threads != 256) ||
+  if (!c || mode < 0 || mode > 3 || (threads != 64 && threads != 128 && threads != 256) ||
       rows_per_lane < 2 || rows_per_lane > kRowsPerLane)
     return CC_EINVAL;
   if (rows_per_lane != c->rows || threads != c->threads || mode != c->mode) c->tasks_dirty = true;
@@ -767,7 +883,8 @@ int cc_autotune(cc_ctx* c, void* T_dev, int32_t n_trial, float* best_ms, void* s
   int rc = CC_OK;
   bool rect = true;
   for (auto& in : c->inst) rect &= in.j_narrow == in.d.nz;
-  const int n_modes = rect ? 3 : 2;  // mode 2: rectangles only
+  // mode 2: rectangles; mode 3: one FP64 rectangle (falls back to mode 0 otherwise)
+  const int n_modes = rect ? ((c->inst.size() == 1 && c->precision == CC_FP64) ? 4 : 3) : 2;
   for (int mode = 0; mode < n_modes; ++mode)
     for (int threads : {64, 128, 256})
       for (int rows : rows_opts) {

@@ -56,15 +56,49 @@ __device__ __forceinline__ double ld_field(const double* p) {
   else return __ldcg(p);
 }
 
+// The field as the tile sees it: T^n at (line j, node i) and the store of
+// That.  In global memory (per-step and persistent launches: separate input
+// and output buffers) ...
+template <bool CACHED>
+struct GlobalField {
+  const double* in;
+  double* out;
+  int nr;
+  __device__ __forceinline__ GlobalField(const StepArgs& a, const DevInst& I)
+      : in(static_cast<const double*>(a.Tin) + I.t_off),
+        out(static_cast<double*>(a.Tout) + I.t_off), nr(I.nr) {}
+  __device__ __forceinline__ double at(int j, int i) const {
+    return ld_field<CACHED>(in + (long long)j * nr + i);
+  }
+  __device__ __forceinline__ void put(int j, int i, double v) const {
+    out[(long long)j * nr + i] = v;
+  }
+};
+
+// ... or resident in shared memory (a block's lines J0 .. J1-1 between a
+// south halo row J0-1 and a north halo row J1, padded rows of nrp doubles,
+// updated in place: a tile reads line j only before its own stores of line j,
+// and the lines above it only after they are stored by no one earlier).
+struct SmemField {
+  double* f;
+  int J0, nrp;
+  __device__ __forceinline__ double at(int j, int i) const {
+    return f[(j - J0 + 1) * nrp + smem_col(i)];
+  }
+  __device__ __forceinline__ void put(int j, int i, double v) const {
+    f[(j - J0 + 1) * nrp + smem_col(i)] = v;
+  }
+};
+
 // One tile.  sm starts with two rows of axial face fluxes: the tile takes the
 // fluxes of the face south of its first line from row par ^ 1 if carry (the
 // previous tile of this block ended on the line before j0), and leaves those
 // north of its last line in row par.  STP: the tile holds a line of a stepped
 // outline that is narrow or borders a narrow one (other tiles skip the checks).
-template <bool ENERGY, bool TRACE, bool CACHED, bool STP>
+template <bool ENERGY, bool TRACE, bool STP, class F>
 __device__ __forceinline__ void step_fp64_tile(const StepArgs& a, const TileTask tk,
                                                double* __restrict__ sm, EAcc& acc, bool carry,
-                                               int par) {
+                                               int par, const F& fld) {
   if (tk.inst != acc.inst) {  // block-uniform
     eacc_flush<ENERGY, TRACE>(a, acc);
     acc.inst = tk.inst;
@@ -85,8 +119,6 @@ __device__ __forceinline__ void step_fp64_tile(const StepArgs& a, const TileTask
   double* SD = SC + (size_t)nl * nrp;      // d, then d'
   double* SM = SD + (size_t)nl * nrp;      // V2 rho c / tau (energy)
   double* sI = SM + (size_t)nl * nrp;      // per line and interface node: lambda_w(T), lambda_e(T), kw, ke
-  const double* Tin = static_cast<const double*>(a.Tin) + I.t_off;
-  double* Tout = static_cast<double*>(a.Tout) + I.t_off;
   const double s = a.s_tab[a.step * a.n_inst + tk.inst];
   double eQ = 0.0, eD = 0.0, eN = 0.0, eI = 0.0, eE = 0.0, tr = 0.0;
 
@@ -97,7 +129,7 @@ __device__ __forceinline__ void step_fp64_tile(const StepArgs& a, const TileTask
       const int i = I.if_i[it - q * n_if];
       const RowGeo& g = I.rg[i];
       if (g.cls == RC_IFACE) {
-        const double T = ld_field<CACHED>(Tin + (long long)(j0 + q) * nr + i);
+        const double T = fld.at(j0 + q, i);
         sI[4 * it] = lam_eval(I.mat[g.segw], T);
         sI[4 * it + 1] = lam_eval(I.mat[g.seg], T);
       }
@@ -134,15 +166,14 @@ __device__ __forceinline__ void step_fp64_tile(const StepArgs& a, const TileTask
       }
       // T(i, j-1), T(i, j), T(i, j+1) and T(i+1, j) of line j = j0 + q; the
       // values of the next line are loaded one iteration ahead
-      const double* row = Tin + (long long)(j0 + q0) * nr;  // line j
-      double Tc = ld_field<CACHED>(row + ic);
-      double Tn = ld_field<CACHED>(row + nr + ic);
-      double Te = ld_field<CACHED>(row + ie);
+      double Tc = fld.at(j0 + q0, ic);
+      double Tn = fld.at(j0 + q0 + 1, ic);
+      double Te = fld.at(j0 + q0, ie);
       double fs;
       if (carry && q0 == 0) {
         fs = cin[smem_col(ic)];
       } else {
-        const double Ts = ld_field<CACHED>(row - nr + ic);
+        const double Ts = fld.at(j0 + q0 - 1, ic);
         const double ls = lam_face(Mt, frule, Ts, Tc);
         fs = ls * (Tc - Ts);
         if (a.adi_lamz && own && j0 + q0 == 1) a.adi_lamz[I.t_off + ic] = ls;  // face (0, 1)
@@ -151,10 +182,9 @@ __device__ __forceinline__ void step_fp64_tile(const StepArgs& a, const TileTask
         const int j = j0 + q;
         double Tn_next = 0.0, Te_next = 0.0;
         if (q + 1 < q1) {
-          Tn_next = ld_field<CACHED>(row + 2 * nr + ic);
-          Te_next = ld_field<CACHED>(row + nr + ie);
+          Tn_next = fld.at(j + 2, ic);
+          Te_next = fld.at(j + 1, ie);
         }
-        row += nr;
         const double ln = lam_face(Mt, frule, Tc, Tn);  // face (j, j+1)
         // no heat through a face to a node outside a stepped outline
         const double fn = (STP && j + 1 >= I.j_narrow && ic > I.i_step) ? 0.0 : ln * (Tn - Tc);
@@ -267,15 +297,14 @@ __device__ __forceinline__ void step_fp64_tile(const StepArgs& a, const TileTask
       const int c = smem_col(i);
       const double x = SB[(size_t)q * nrp + c];
       bad |= not_finite(x);
-      // nodes outside a stepped outline keep their values
-      Tout[(long long)j * nr + i] = (STP && j >= I.j_narrow && i > I.i_step)
-                                        ? ld_field<CACHED>(Tin + (long long)j * nr + i) : x;
-      if (j == 1) Tout[i] = (I.bc_z0 == CC_DIRICHLET) ? I.t_d : x;
+      const bool outside = STP && j >= I.j_narrow && i > I.i_step;
+      const double told = (ENERGY || outside) ? fld.at(j, i) : 0.0;  // before the store
+      fld.put(j, i, outside ? told : x);  // nodes outside a stepped outline keep their values
+      if (j == 1) fld.put(0, i, (I.bc_z0 == CC_DIRICHLET) ? I.t_d : x);
       if (j == M - 1)
-        Tout[(long long)M * nr + i] = (STP && M >= I.j_narrow && i > I.i_step)
-                                          ? ld_field<CACHED>(Tin + (long long)M * nr + i)
-                                          : (I.bc_zmax == CC_DIRICHLET) ? I.t_d : x;
-      if (ENERGY) eEq = fma(SM[(size_t)q * nrp + c], x - ld_field<CACHED>(Tin + (long long)j * nr + i), eEq);
+        fld.put(M, i, (STP && M >= I.j_narrow && i > I.i_step) ? fld.at(M, i)
+                      : (I.bc_zmax == CC_DIRICHLET) ? I.t_d : x);
+      if (ENERGY) eEq = fma(SM[(size_t)q * nrp + c], x - told, eEq);
       if (TRACE && i == N) {  // That(r_max, z_j)
         tr = fma(I.zg[j].wnorm, x, tr);
         if (j == 1) {
@@ -337,10 +366,12 @@ __device__ __forceinline__ void fp64_tiles(const StepArgs& a, double* __restrict
   for (int t = t0; t < t1; t += dt) {
     const TileTask tk = a.tiles[t];
     const bool carry = (tk.inst == prev_inst && tk.j0 == prev_end);
-    if (tk.j0 + tk.nl >= a.insts[tk.inst].j_narrow)
-      step_fp64_tile<ENERGY, TRACE, CACHED, true>(a, tk, sm, acc, carry, par);
+    const DevInst& I = a.insts[tk.inst];
+    const GlobalField<CACHED> fld(a, I);
+    if (tk.j0 + tk.nl >= I.j_narrow)
+      step_fp64_tile<ENERGY, TRACE, true>(a, tk, sm, acc, carry, par, fld);
     else
-      step_fp64_tile<ENERGY, TRACE, CACHED, false>(a, tk, sm, acc, carry, par);
+      step_fp64_tile<ENERGY, TRACE, false>(a, tk, sm, acc, carry, par, fld);
     prev_inst = tk.inst;
     prev_end = tk.j0 + tk.nl;
     par ^= 1;

@@ -189,6 +189,13 @@ struct StepArgs {
   // launch shape
   int threads;           // threads per block (64, 128 or 256)
   int warp_doubles;      // warp-lines kernel: doubles of shared memory per warp
+  // shared-memory-resident persistent launch: the field region starts
+  // res_offset doubles into the dynamic shared memory; boundary rows are
+  // exchanged through xb [block][2 step parities][first, last][nr] with
+  // per-block step counters nbr_flags
+  int res_offset;
+  double* xb;
+  unsigned* nbr_flags;
   // persistent launches: grid barrier state [count, generation], bounded wait
   unsigned* bar;
   unsigned bar_extra;    // extra arrivals expected (nonzero only to test the timeout)
@@ -276,6 +283,11 @@ int launch_mixed_init(float* lo, long long n_total, void* stream);
 // tasks, a.cta_start[w] .. a.cta_start[w + 1] those of warp w, a.n_cta blocks.
 int launch_step_fp64_lines(const StepArgs& a, void* stream);
 int fp64_lines_resident_blocks(int threads, int smem);
+// All n steps in one cooperative launch with the field resident in shared
+// memory (ccell_step_resident.cu): block b holds the lines of its tiles
+// [cta_start[b], cta_start[b+1]) of one instance; result in a.Tin.
+int launch_steps_fp64_resident(const StepArgs& a, long long n, void* stream);
+int fp64_resident_kernel_blocks(int threads, int smem);
 // The same for the mixed-precision step (ccell_step_lines_mixed.cu).
 int launch_step_mixed_lines(const StepArgs& a, void* stream);
 int mixed_lines_resident_blocks(int threads, int smem);

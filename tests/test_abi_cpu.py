@@ -117,10 +117,11 @@ def test_launch_shape_validation_and_round_trip():
     cfg = inputs.small_case(q0=1.0)
     sol = ccell.Solver(cfg)
     try:
-        for shape in ((1, 64, 4), (0, 256, 16), (1, 128, 8), (2, 256, 16), (2, 64, 4)):
+        for shape in ((1, 64, 4), (0, 256, 16), (1, 128, 8), (2, 256, 16), (2, 64, 4),
+                      (3, 128, 16)):
             sol.set_launch(*shape)
             assert ccell.cc_get_launch(sol.ctx) == shape
-        for bad in ((3, 128, 16), (-1, 128, 16), (0, 96, 16), (0, 128, 1), (0, 128, 32)):
+        for bad in ((4, 128, 16), (-1, 128, 16), (0, 96, 16), (0, 128, 1), (0, 128, 32)):
             with pytest.raises(ccell.CCError):
                 sol.set_launch(*bad)
     finally:

@@ -70,6 +70,23 @@ def test_persistent_small_case_matches_oracle():
     assert np.max(np.abs(en[0] - eo)) <= 1e-9 * abs(eo[1])
 
 
+@pytest.mark.parametrize("shape", [(3, 256, 16), (3, 128, 8), (3, 64, 4)])
+def test_resident_mode_matches_oracle(shape):
+    """Field resident in shared memory (one block per SM, boundary rows
+    exchanged between steps): ragged sizes across the pulse end."""
+    for nr, nz, seed in ((64, 128, 3), (100, 301, 4), (37, 700, 5)):
+        cfg = inputs.small_case()
+        cfg.update(nr=nr, nz=nz)
+        cfg["dt"] = min(5e-7, 0.5 * oracle.tau_stab(cfg, 20.0, 100.0))
+        T0 = inputs.initial_field(cfg, "smooth", seed=seed)
+        n, t0 = 41, 1e-3 - 20 * cfg["dt"]
+        out, tr, en = _run([cfg], [T0], n, 0, shape, t0=t0)
+        To, tro, eo = oracle.step_n(cfg, T0, n, t0, cfg["dt"])
+        assert np.max(np.abs(out.reshape(To.shape) - To)) <= 1e-9, (nr, nz)
+        assert np.max(np.abs(tr[0] - tro)) <= 1e-9, (nr, nz)
+        assert np.max(np.abs(en[0] - eo)) <= 1e-9 * abs(eo[1]), (nr, nz)
+
+
 def test_barrier_timeout_is_reported():
     """A barrier that can never complete (test hook: one arrival too many
     expected, short wait) must end the kernel and surface as CC_ETIMEOUT."""
@@ -78,9 +95,10 @@ def test_barrier_timeout_is_reported():
     T0 = inputs.initial_field(cfg)
     os.environ["CC_TEST_BARRIER_TIMEOUT"] = "1"
     try:
-        with pytest.raises(ccell.CCError) as e:
-            _run([cfg], [T0], 5, 0, (1, 128, 16))
-        assert e.value.status == ccell.CC_ETIMEOUT
+        for shape in ((1, 128, 16), (3, 128, 16)):   # grid barrier; neighbour step counters
+            with pytest.raises(ccell.CCError) as e:
+                _run([cfg], [T0], 5, 0, shape)
+            assert e.value.status == ccell.CC_ETIMEOUT
     finally:
         del os.environ["CC_TEST_BARRIER_TIMEOUT"]
     # the GPU context stays usable afterwards
@@ -108,7 +126,7 @@ def test_autotune_keeps_field_and_picks_a_valid_shape():
     sol.close()
 
 
-@pytest.mark.parametrize("mode", [0, 1, 2])
+@pytest.mark.parametrize("mode", [0, 1, 2, 3])
 def test_cuda_graph_replay_equals_direct_call(mode):
     import torch
     from paper_1408_5853_gb300 import ccell

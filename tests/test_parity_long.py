@@ -10,8 +10,9 @@ host and compare every node, every trace sample and the energy terms:
     1 ms pulses): FP64 in every launch mode
     (<= 1e-9 K), the mixed path (<= 1e-3 K);
   * 5-layer 512 x 4096 production cylinder, 2 000 steps across the end of a
-    pulse, all 4096 lines: FP64 with one launch per step (CTA tiles and
-    warp-owned lines) and in the persistent shape (<= 1e-9 K), the mixed path in the
+    pulse, all 4096 lines: FP64 in every launch mode (one launch per step with
+    CTA tiles or warp-owned lines, persistent, persistent with the field
+    resident in shared memory; <= 1e-9 K), the mixed path in the
     shape the autotuner picks (<= 1e-3 K), all against one oracle run from the
     FP32-rounded field;
   * the 256-instance design sweep (seed 1) in one context, mixed precision in
@@ -59,7 +60,7 @@ def small_20ms():
     return cfg, T0, n, oracle.step_n(cfg, T0, n, 0.0, cfg["dt"])
 
 
-@pytest.mark.parametrize("launch", [(0, 256, 16), (1, 256, 16), (2, 256, 16)])
+@pytest.mark.parametrize("launch", [(0, 256, 16), (1, 256, 16), (2, 256, 16), (3, 256, 16)])
 def test_small_case_full_20ms_fp64(small_20ms, launch):
     cfg, T0, n, ref = small_20ms
     (Tg,), trg, eg = run_gpu(cfg, T0, n, launch=launch)
@@ -83,7 +84,8 @@ def production_2000():
     return cfg, T0, n, t0, oracle.step_n(cfg, T0, n, t0, cfg["dt"])
 
 
-@pytest.mark.parametrize("launch", [(0, 256, 16), (1, 256, 16), (2, 256, 16)])
+@pytest.mark.parametrize("launch", [(0, 256, 16), (1, 256, 16), (2, 256, 16), (3, 256, 16),
+                                    (3, 128, 16)])
 def test_production_2000_steps_fp64_full_field(production_2000, launch):
     cfg, T0, n, t0, ref = production_2000
     (Tg,), trg, eg = run_gpu(cfg, T0, n, t0=t0, launch=launch)
