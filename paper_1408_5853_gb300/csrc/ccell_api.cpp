@@ -51,6 +51,8 @@ struct cc_ctx {
   size_t cta_cap = 0;
   // launch mode 2 (warp-owned lines): warp tasks and each warp's first task
   bool lines_ok = false;      // FP64 context of rectangles
+  LaneGeo* d_lg = nullptr;    // lane-major rows per instance (mode 2)
+  size_t lg_cap = 0;
   TileTask* d_wtasks = nullptr;
   int* d_wcta = nullptr;
   size_t wtasks_cap = 0, wcta_cap = 0;
@@ -127,6 +129,9 @@ void free_device(cc_ctx* c) {
   c->d_xb = nullptr;
   c->d_rflags = nullptr;
   c->rtiles_cap = c->rcta_cap = c->xb_cap = c->rflags_cap = 0;
+  cudaFree(c->d_lg);
+  c->d_lg = nullptr;
+  c->lg_cap = 0;
   cudaFree(c->d_wtasks);
   cudaFree(c->d_wcta);
   c->d_wtasks = nullptr;
@@ -279,6 +284,18 @@ int cut_warp_tasks(cc_ctx* c) {
   const int B = c->precision == CC_FP64 ? fp64_lines_resident_blocks(c->threads, c->lines_smem)
                                         : mixed_lines_resident_blocks(c->threads, c->lines_smem);
   if (B < 0) return CC_ECUDA;
+  // lane-major row tables for the lanes of each instance
+  std::vector<LaneGeo> lg(c->inst.size());
+  for (size_t k = 0; k < c->inst.size(); ++k) {
+    const Instance& in = c->inst[k];
+    std::vector<RowGeo> rg(in.d.nr);
+    fill_row_geo(in.r.data(), in.cls.data(), in.seg.data(), in.d.nr, rg.data());
+    fill_lane_geo(rg.data(), in.d.nr, in.G, lg[k]);
+  }
+  {
+    const int rc = put_grown(&c->d_lg, &c->lg_cap, lg);
+    if (rc != CC_OK) return rc;
+  }
   std::vector<int> whole(c->inst.size());
   for (size_t k = 0; k < c->inst.size(); ++k) whole[k] = c->inst[k].d.nz;
   std::vector<TileTask> tasks;
@@ -482,6 +499,7 @@ int upload(cc_ctx* c, const std::vector<double>& dts, cudaStream_t st) {
                       in.cls.data(), D);
     D.rg = c->d_rg + rofs;
     D.zg = c->d_zg + zofs;
+    D.lg = (c->lines_ok && c->d_lg) ? c->d_lg + k : nullptr;
     rofs += in.d.nr;
     zofs += in.d.nz;
     for (int m = 0; m < in.d.n_layers; ++m) {

@@ -37,6 +37,13 @@ __device__ __forceinline__ double lrcp(double d) {
   else return frcp46(d);
 }
 
+// lam0 (x / t_ref)^b with the exact pow, for arguments outside the table (kept
+// out of line: it is rare, and inlining it at every face evaluation would
+// multiply the code and register footprint of the step kernels).
+static __device__ __noinline__ double lam_pow_exact(const DevMaterial& M, double y, bool face) {
+  return M.lam0s * pow((face ? 0.5 * y : y) * M.inv_tref, M.lam_b);
+}
+
 // Power law lam0 (x / t_ref)^b from the material's table: y = m 2^e with
 // m in [1, 2); the scale row e holds lam0 (k t_ref)^-b 2^(e b) (k = 2 for a
 // face, where y = T_a + T_b, k = 1 for a node, where y = T), and m^b is a
@@ -57,7 +64,7 @@ __device__ __forceinline__ double lam_pow(const DevMaterial& M, double y, bool f
     for (int k = kPowDeg - 1; k >= 0; --k) r = fma(r, u, __ldg(P + k));
     return r * __ldg(M.ptab + (face ? 0 : kPowNE) + e);
   }
-  return M.lam0s * pow((face ? 0.5 * y : y) * M.inv_tref, M.lam_b);
+  return lam_pow_exact(M, y, face);
 }
 
 __device__ __forceinline__ double lam_eval(const DevMaterial& M, double T) {

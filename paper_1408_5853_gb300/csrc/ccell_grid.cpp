@@ -225,6 +225,26 @@ void fill_row_geo(const double* r, const int* cls, const int* seg, int nr, RowGe
   number_ifaces(out, nr);
 }
 
+void fill_lane_geo(const RowGeo* rg, int nr, int G, LaneGeo& out) {
+  std::memset(&out, 0, sizeof out);
+  int lg = 0;
+  while ((1 << lg) < G) ++lg;
+  for (int l = 0; l < G; ++l) {
+    const int i_lo = (l * nr) >> lg, i_hi = ((l + 1) * nr) >> lg;
+    for (int k = 0; k < i_hi - i_lo; ++k) {
+      const RowGeo& g = rg[i_lo + k];
+      const int e = k * G + l;
+      out.gA[e] = g.gA;
+      out.gC[e] = g.gC;
+      out.V2[e] = g.V2;
+      out.gA_f[e] = g.gA_f;
+      out.gC_f[e] = g.gC_f;
+      out.V2_f[e] = g.V2_f;
+      out.meta[e] = (g.cls & 15) | ((g.seg & 15) << 4) | ((g.ifo + 1) << 8);
+    }
+  }
+}
+
 void fill_z_geo(const double* z, int nz, int j_narrow, ZGeo* out) {
   const int M = nz - 1;
   // trapezoid weights of the r = r_max surface (the full-width lines)

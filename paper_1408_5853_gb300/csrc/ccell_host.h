@@ -38,6 +38,10 @@ double tau_stab_of(const cc_geometry_desc& d, const cc_material* mat, const doub
 // Per radial node tables of one instance (RowGeo::ifo numbered).
 void fill_row_geo(const double* r, const int* cls, const int* seg, int nr, RowGeo* out);
 
+// Lane-major copy of the row tables for G lanes per line (rows of lane l:
+// [(l nr) / G, ((l+1) nr) / G)).
+void fill_lane_geo(const RowGeo* rg, int nr, int G, LaneGeo& out);
+
 // Per axial node tables; the surface-trace weights cover the lines j < j_narrow.
 void fill_z_geo(const double* z, int nz, int j_narrow, ZGeo* out);
 

@@ -73,6 +73,17 @@ struct DevMaterial {
   int lam_model, cap_model;
 };
 
+// Row geometry of one instance in lane-major order for the warp-owned lines
+// (launch mode 2): entry e = k G + l is row i = (l nr) / G + k, the k-th row
+// of lane l, so the lanes of a group read consecutive entries.  meta packs
+// the class (bits 0-3), the layer seg (bits 4-7) and the interface ordinal
+// ifo + 1 (bits 8-15) of the row.
+struct LaneGeo {
+  double gA[kMaxNr], gC[kMaxNr], V2[kMaxNr];
+  float gA_f[kMaxNr], gC_f[kMaxNr], V2_f[kMaxNr];
+  int meta[kMaxNr];
+};
+
 struct DevInst {
   int nr, nz;            // nodes
   int G;                 // lanes per line
@@ -93,6 +104,7 @@ struct DevInst {
   float td_hi, td_lo;    // Dirichlet temperature as an FP32 pair
   const RowGeo* rg;      // [nr]
   const ZGeo* zg;        // [nz]
+  const LaneGeo* lg;     // lane-major rows for lanes G (launch mode 2), or null
   DevMaterial mat[CC_MAX_LAYERS];
 };
 
@@ -144,11 +156,11 @@ CC_HOST_DEVICE inline int mixed_tile_smem_bytes(int nl, int nr) {
 // Warp-owned lines (launch mode 2): one padded row of a warp's shared memory
 // holds the rows of all its lane groups' current lines (32/G lines of
 // nr <= 16 G rows: at most 512 rows).  A warp's shared memory holds c', a',
-// d' (then That) and V2 rho c / tau rows, then four values per (lane group,
-// interface node).
+// d' (then That), the energy factors and the south face fluxes carried from
+// line to line, then four values per (lane group, interface node).
 constexpr int kWarpRowStride = 512 + (512 >> 4) + 1;
 CC_HOST_DEVICE inline int lines_warp_doubles(int if_slots) {
-  return 4 * kWarpRowStride + 4 * if_slots;
+  return 5 * kWarpRowStride + 4 * if_slots;
 }
 // Largest dynamic shared memory of an FP64 tile: the opt-in limit per block
 // on sm_103 (227 KiB) less room for the kernels' static shared memory.

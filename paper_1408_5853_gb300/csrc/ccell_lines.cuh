@@ -19,7 +19,10 @@
 //   5. with the lanes over columns: coalesced stores of That, the axial
 //      boundary rows, the surface trace and the energy terms.
 // Lines of a warp's run are split over its 32/G lane groups; the south face
-// flux of a group's first line is evaluated once more at the start of the run.
+// fluxes are carried from line to line in the warp's shared memory (the first
+// line of a run evaluates them once more).  The row loop is not unrolled and
+// the row geometry is read in lane-major order (LaneGeo), so each load of it
+// is one coalesced access per warp.
 // For G = 1 the line solve is the Thomas algorithm of the paper with
 // alpha_0 = 1, beta_0 = 0 and That_N = beta_{N-1}/(1 - alpha_{N-1}).
 // Rectangles only (stepped outlines use the CTA-tile kernels).
@@ -46,7 +49,9 @@ __device__ __forceinline__ void fp64_warp_task(const StepArgs& a, const TileTask
   double* A1 = C1 + kWarpRowStride;
   double* D1 = A1 + kWarpRowStride;  // d', then That
   double* MM = D1 + kWarpRowStride;  // V2 rho c / tau
-  double* sI = MM + kWarpRowStride;  // [group][interface]: lambda_w*, lambda_e*, kw, ke
+  double* FS = MM + kWarpRowStride;  // south face fluxes, carried to the next line
+  double* sI = FS + kWarpRowStride;  // [group][interface]: lambda_w*, lambda_e*, kw, ke
+  const LaneGeo& LG = *I.lg;
   const double* Tin = static_cast<const double*>(a.Tin) + I.t_off;
   double* Tout = static_cast<double*>(a.Tout) + I.t_off;
   const double s = a.s_tab[a.step * a.n_inst + tk.inst];
@@ -54,7 +59,6 @@ __device__ __forceinline__ void fp64_warp_task(const StepArgs& a, const TileTask
   // lines [ja, jb) of this lane group; idle groups run a valid line unstored
   const int ja = tk.j0 + (grp * tk.nl) / ng, jb = tk.j0 + ((grp + 1) * tk.nl) / ng;
   const int iters = (tk.nl + ng - 1) / ng;
-  double fs[kRowsPerLane];  // south face fluxes of this lane's rows
   double eQ = 0.0, eD = 0.0, eN = 0.0, eI = 0.0, eE = 0.0, tr = 0.0;
   bool bad = false;
 
@@ -83,13 +87,12 @@ __device__ __forceinline__ void fp64_warp_task(const StepArgs& a, const TileTask
 
     // ---- the south fluxes of the first line of the run
     if (q == 0) {
-#pragma unroll
-      for (int k = 0; k < kRowsPerLane; ++k) {
-        if (k < cnt) {
-          const int i = i_lo + k;
-          const double Ts = __ldg(row - nr + i), Tc = __ldg(row + i);
-          fs[k] = lam_face(I.mat[I.rg[i].seg], frule, Ts, Tc) * (Tc - Ts);
-        }
+#pragma unroll 1
+      for (int k = 0; k < cnt; ++k) {
+        const int i = i_lo + k;
+        const double Ts = __ldg(row - nr + i), Tc = __ldg(row + i);
+        const int seg = (LG.meta[k * G + l] >> 4) & 15;
+        FS[smem_col(gb + i)] = lam_face(I.mat[seg], frule, Ts, Tc) * (Tc - Ts);
       }
     }
 
@@ -105,42 +108,47 @@ __device__ __forceinline__ void fp64_warp_task(const StepArgs& a, const TileTask
     double pc = 0.0, pa = 0.0, pd = 0.0;     // c', a', d' of the previous row
     double Dacc = 0.0, Aacc = 0.0, P = 1.0;  // first row = Dacc + P x_sep - Aacc L
     double ae = 0.0, be = 1.0, ce = 0.0, de = 0.0;
-#pragma unroll
-    for (int k = 0; k < kRowsPerLane; ++k) {
-      if (k < cnt) {
-        const int i = i_lo + k;
-        const int c = smem_col(gb + i);
-        const RowGeo& g = I.rg[i];
-        const int cls = g.cls, seg = g.seg;
-        const DevMaterial& Mt = I.mat[seg];
-        const double Te = (k < cnt - 1) ? __ldg(row + i + 1) : 0.0;
-        const double Tn = __ldg(row + nr + i);
-        const double le = (k < cnt - 1) ? lam_face(Mt, frule, Tc, Te) : le_last;
-        const double fn = lam_face(Mt, frule, Tc, Tn) * (Tn - Tc);
-        const double rct = rct_eval(Mt, Tc);
-        // Eq. (Lambda_j), explicit in T, and Eq. (source)
-        const double Lj = fma(zg.gzn, fn, -zg.gzs * fs[k]);
-        double X = (seg == I.src_layer) ? Xs : 0.0;
-        if (I.g_model == 1 && X != 0.0) X *= I.g_ref / sqrt(Tc);
-        // Eq. (ABC)
-        double ra = -g.gA * lw, rc = -g.gC * le;
-        double rb = rct - ra - rc;
-        double rd = fma(rct, Tc, Lj + X);
-        double m = 0.0;
-        if (cls == RC_REGULAR) {
-          if (ENERGY) {
-            m = g.V2 * rct;
-            if (valid && X != 0.0) eQ = fma(zg.etabar * I.tau * g.V2, X, eQ);
-            if (valid && j == 1) {
-              const double f = -I.tau * g.V2 * fs[k] / zg.eta_s;
-              if (I.bc_z0 == CC_DIRICHLET) eD += f; else eN += f;
-            }
-            if (valid && j == M - 1) {
-              const double f = I.tau * g.V2 * fn / zg.eta_n;
-              if (I.bc_zmax == CC_DIRICHLET) eD += f; else eN += f;
-            }
+    double Te = (cnt > 1) ? __ldg(row + i_lo + 1) : 0.0, Tn = __ldg(row + nr + i_lo);
+#pragma unroll 1
+    for (int k = 0; k < cnt; ++k) {
+      const int i = i_lo + k;
+      const int c = smem_col(gb + i);
+      const int e = k * G + l;
+      const int meta = LG.meta[e];
+      const int cls = meta & 15, seg = (meta >> 4) & 15;
+      const DevMaterial& Mt = I.mat[seg];
+      const bool last = k == cnt - 1;
+      // T(i+1, j) and T(i, j+1) of the next row, loaded one row ahead
+      const double Te2 = (k + 2 < cnt) ? __ldg(row + i + 2) : 0.0;
+      const double Tn2 = (k + 1 < cnt) ? __ldg(row + nr + i + 1) : 0.0;
+      const double le = last ? le_last : lam_face(Mt, frule, Tc, Te);
+      const double fn = lam_face(Mt, frule, Tc, Tn) * (Tn - Tc);
+      const double rct = rct_eval(Mt, Tc);
+      const double fs = FS[c];
+      double X = (seg == I.src_layer) ? Xs : 0.0;  // Eq. (source)
+      if (I.g_model == 1 && X != 0.0) X *= I.g_ref / sqrt(Tc);
+      // Eq. (ABC) with Eq. (Lambda_j), explicit in T
+      double ra = -LG.gA[e] * lw, rc = -LG.gC[e] * le;
+      double rb = rct - ra - rc;
+      double rd = fma(rct, Tc, fma(zg.gzn, fn, fma(-zg.gzs, fs, X)));
+      double m = 0.0;
+      if (cls == RC_REGULAR) {
+        if (ENERGY) {
+          const double V2 = LG.V2[e];
+          m = V2 * rct;
+          if (valid && X != 0.0) eQ = fma(zg.etabar * I.tau * V2, X, eQ);
+          if (valid && j == 1) {
+            const double f = -I.tau * V2 * fs / zg.eta_s;
+            if (I.bc_z0 == CC_DIRICHLET) eD += f; else eN += f;
           }
-        } else if (cls == RC_IFACE) {  // Eq. (cc_first_1)/(cc_first_3) as the row (a, b, c | 0)
+          if (valid && j == M - 1) {
+            const double f = I.tau * V2 * fn / zg.eta_n;
+            if (I.bc_zmax == CC_DIRICHLET) eD += f; else eN += f;
+          }
+        }
+      } else {
+        const RowGeo& g = I.rg[i];
+        if (cls == RC_IFACE) {  // Eq. (cc_first_1)/(cc_first_3) as the row (a, b, c | 0)
           const double* K = sI + 4 * (grp * n_if + g.ifo);
           double lmv, lpv;
           if (I.interface_rule == 0) {
@@ -161,38 +169,39 @@ __device__ __forceinline__ void fp64_warp_task(const StepArgs& a, const TileTask
         } else {
           ra = -1.0; rb = 1.0; rc = 0.0; rd = 0.0;
         }
-        if (ENERGY) {
-          MM[c] = m;
-          if (cls == RC_IFACE || cls == RC_OUTER) {  // heat-flow coefficients to the regular neighbours
-            const RowGeo& gw = I.rg[i - 1];
-            const RowGeo& ge = I.rg[i < N ? i + 1 : i];
-            double* K = sI + 4 * (grp * n_if + g.ifo);
-            K[2] = I.tau * gw.V2 * zg.etabar * gw.gC * lw;
-            K[3] = (i < N) ? I.tau * ge.V2 * zg.etabar * ge.gA * le : 0.0;
-          }
+        if (ENERGY && (cls == RC_IFACE || cls == RC_OUTER)) {
+          // heat-flow coefficients to the regular neighbours
+          const RowGeo& gw = I.rg[i - 1];
+          const RowGeo& ge = I.rg[i < N ? i + 1 : i];
+          double* K = sI + 4 * (grp * n_if + g.ifo);
+          K[2] = I.tau * gw.V2 * zg.etabar * gw.gC * lw;
+          K[3] = (i < N) ? I.tau * ge.V2 * zg.etabar * ge.gA * le : 0.0;
         }
-        if (k < cnt - 1) {
-          const double den = (k == 0) ? rb : fma(-ra, pc, rb);
-          const double r = frcp(den);
-          const double c1 = rc * r;
-          const double a1 = (k == 0) ? ra * r : -ra * pa * r;
-          const double d1 = (k == 0) ? rd * r : fma(-ra, pd, rd) * r;
-          C1[c] = c1;
-          A1[c] = a1;
-          D1[c] = d1;
-          Dacc = fma(P, d1, Dacc);
-          Aacc = fma(P, a1, Aacc);
-          P = -P * c1;
-          pc = c1;
-          pa = a1;
-          pd = d1;
-        } else {
-          ae = ra; be = rb; ce = rc; de = rd;
-        }
-        fs[k] = fn;
-        lw = le;
-        Tc = Te;
       }
+      if (ENERGY) MM[c] = m;
+      FS[c] = fn;
+      if (!last) {
+        const double den = (k == 0) ? rb : fma(-ra, pc, rb);
+        const double r = frcp(den);
+        const double c1 = rc * r;
+        const double a1 = (k == 0) ? ra * r : -ra * pa * r;
+        const double d1 = (k == 0) ? rd * r : fma(-ra, pd, rd) * r;
+        C1[c] = c1;
+        A1[c] = a1;
+        D1[c] = d1;
+        Dacc = fma(P, d1, Dacc);
+        Aacc = fma(P, a1, Aacc);
+        P = -P * c1;
+        pc = c1;
+        pa = a1;
+        pd = d1;
+      } else {
+        ae = ra; be = rb; ce = rc; de = rd;
+      }
+      lw = le;
+      Tc = Te;
+      Te = Te2;
+      Tn = Tn2;
     }
 
     // ---- 3. separators; 4. back substitution into D1
@@ -201,14 +210,12 @@ __device__ __forceinline__ void fp64_warp_task(const StepArgs& a, const TileTask
     {
       double xn = xs;
       D1[smem_col(gb + i_hi - 1)] = xs;
-#pragma unroll
-      for (int k = kRowsPerLane - 2; k >= 0; --k) {
-        if (k <= cnt - 2) {
-          const int c = smem_col(gb + i_lo + k);
-          const double x = fma(-C1[c], xn, fma(-A1[c], L, D1[c]));
-          D1[c] = x;
-          xn = x;
-        }
+#pragma unroll 4
+      for (int k = cnt - 2; k >= 0; --k) {
+        const int c = smem_col(gb + i_lo + k);
+        const double x = fma(-C1[c], xn, fma(-A1[c], L, D1[c]));
+        D1[c] = x;
+        xn = x;
       }
     }
     __syncwarp();

@@ -30,8 +30,10 @@ __device__ __forceinline__ void mixed_warp_task(const StepArgs& a, const TileTas
   double* A1 = C1 + kWarpRowStride;
   double* D1 = A1 + kWarpRowStride;  // d', then the increment dT
   double* MM = D1 + kWarpRowStride;  // V rho c
+  float* FS = reinterpret_cast<float*>(MM + kWarpRowStride);  // south face fluxes
   // [group][interface]: lambda_w*, lambda_e*, (kw, ke, dTw, dTe as FP32 in the last two doubles)
-  double* sI = MM + kWarpRowStride;
+  double* sI = MM + 2 * kWarpRowStride;
+  const LaneGeo& LG = *I.lg;
   const float* Hin = static_cast<const float*>(a.Tin) + I.t_off;
   const float* Lin = a.lo_in + I.t_off;
   float* Hout = static_cast<float*>(a.Tout) + I.t_off;
@@ -41,7 +43,6 @@ __device__ __forceinline__ void mixed_warp_task(const StepArgs& a, const TileTas
   const float Xs = (I.src_layer >= 0) ? I.q0_f * s : 0.0f;
   const int ja = tk.j0 + (grp * tk.nl) / ng, jb = tk.j0 + ((grp + 1) * tk.nl) / ng;
   const int iters = (tk.nl + ng - 1) / ng;
-  float fs[kRowsPerLane];  // lambda (T - T_S) on the south faces of this lane's rows
   double eQ = 0.0, eD = 0.0, eN = 0.0, eI = 0.0, eE = 0.0, tr = 0.0;
   bool bad = false;
 
@@ -71,14 +72,13 @@ __device__ __forceinline__ void mixed_warp_task(const StepArgs& a, const TileTas
 
     // ---- the south fluxes of the first line of the run
     if (q == 0) {
-#pragma unroll
-      for (int k = 0; k < kRowsPerLane; ++k) {
-        if (k < cnt) {
-          const int i = i_lo + k;
-          const float hs = __ldg(Hin + o - nr + i), ls = __ldg(Lin + o - nr + i);
-          const float hc = __ldg(Hin + o + i), lc = __ldg(Lin + o + i);
-          fs[k] = lam_face32(I.mat[I.rg[i].seg], frule, hs, hc) * ((hc - hs) + (lc - ls));
-        }
+#pragma unroll 1
+      for (int k = 0; k < cnt; ++k) {
+        const int i = i_lo + k;
+        const float hs = __ldg(Hin + o - nr + i), ls = __ldg(Lin + o - nr + i);
+        const float hc = __ldg(Hin + o + i), lc = __ldg(Lin + o + i);
+        const int seg = (LG.meta[k * G + l] >> 4) & 15;
+        FS[smem_col(gb + i)] = lam_face32(I.mat[seg], frule, hs, hc) * ((hc - hs) + (lc - ls));
       }
     }
 
@@ -98,117 +98,136 @@ __device__ __forceinline__ void mixed_warp_task(const StepArgs& a, const TileTas
     double pc = 0.0, pa = 0.0, pd = 0.0;
     double Dacc = 0.0, Aacc = 0.0, P = 1.0;
     double ae = 0.0, ce = 0.0, de = 0.0;
-#pragma unroll
-    for (int k = 0; k < kRowsPerLane; ++k) {
-      if (k < cnt) {
-        const int i = i_lo + k;
-        const int c = smem_col(gb + i);
-        const RowGeo& g = I.rg[i];
-        const int cls = g.cls, seg = g.seg;
-        const DevMaterial& Mt = I.mat[seg];
-        const bool last = k == cnt - 1;
-        const float he = last ? 0.0f : __ldg(Hin + o + i + 1);
-        const float lE = last ? 0.0f : __ldg(Lin + o + i + 1);
-        const float hn = __ldg(Hin + o + nr + i), ln = __ldg(Lin + o + nr + i);
-        const float dN = (hn - hc) + (ln - lc);                  // T_{j+1} - T_j
-        const float dE = last ? dE_last : (he - hc) + (lE - lc);  // T_{i+1} - T_i
-        const float le = last ? le_last : lam_face32(Mt, frule, hc, he);
-        const float fn = lam_face32(Mt, frule, hc, hn) * dN;
-        const float rhoc = Mt.rho_f * cap32(Mt, hc);
-        const float Ljv = fmaf(zg.gzn_f, fn, -zg.gzs_f * fs[k]);  // Eq. (Lambda_j)
-        float X = (seg == I.src_layer) ? Xs : 0.0f;               // Eq. (source)
-        if (I.g_model == 1 && X != 0.0f) X *= I.g_ref_f * rsqrtf(hc);
-        float fa = -g.gA_f * lw, fc = -g.gC_f * le;               // Eq. (ABC)
-        float fb = fmaf(rhoc, inv_tau, -fa - fc);
-        float fd = fmaf(-fa, dW, fmaf(-fc, dE, Ljv + X));
-        if (cls == RC_REGULAR) {
-          if (ENERGY) {
-            const float V = g.V2_f * zg.etabar_f;
-            MM[c] = widen_f32(V * rhoc);
-            if (valid && X != 0.0f) eQ = fma(widen_f32(tau * V), widen_f32(X), eQ);
-            if (valid && j == 1) {
-              const double f = widen_f32(-tau * g.V2_f * fs[k] / (float)zg.eta_s);
-              if (I.bc_z0 == CC_DIRICHLET) eD += f; else eN += f;
-            }
-            if (valid && j == M - 1) {
-              const double f = widen_f32(tau * g.V2_f * fn / (float)zg.eta_n);
-              if (I.bc_zmax == CC_DIRICHLET) eD += f; else eN += f;
-            }
-          }
-        } else {
-          if (cls == RC_IFACE) {
-            const float* K = reinterpret_cast<const float*>(sI + 4 * (grp * n_if + g.ifo));
-            float lmv, lpv;
-            if (I.interface_rule == 0) {
-              lmv = K[0];
-              lpv = K[1];
-            } else {
-              lmv = g.rw_f * lw;
-              lpv = g.re_f * le;
-            }
-            fa = -lmv * g.he_f;
-            fc = -lpv * g.hw_f;
-            fb = fmaf(lmv, g.he_f, lpv * g.hw_f);
-            fd = -fmaf(fa, dW, fc * dE);
-          } else if (cls == RC_AXIS) {  // dT_0 - dT_1 = T_1 - T_0
-            fa = 0.0f; fb = 1.0f; fc = -1.0f; fd = dE;
-          } else if (I.bc_rmax == CC_DIRICHLET) {  // r = r_max
-            fa = 0.0f; fb = 1.0f; fc = 0.0f; fd = (I.td_hi - hc) + (I.td_lo - lc);
-          } else {  // dT_N - dT_{N-1} = T_{N-1} - T_N
-            fa = -1.0f; fb = 1.0f; fc = 0.0f; fd = dW;
-          }
-          if (ENERGY) {
-            MM[c] = 0.0;
-            if (cls == RC_IFACE || cls == RC_OUTER) {
-              // heat-flow coefficients to the regular neighbours and the old
-              // temperature differences across those edges
-              const RowGeo& gw = I.rg[i - 1];
-              float* K = reinterpret_cast<float*>(sI + 4 * (grp * n_if + g.ifo));
-              K[2] = tau * gw.V2_f * gw.gC_f * zg.etabar_f * lw;
-              if (i < N) {
-                const RowGeo& ge = I.rg[i + 1];
-                K[3] = tau * ge.V2_f * ge.gA_f * zg.etabar_f * le;
-              } else {
-                K[3] = 0.0f;
-              }
-              K[4] = -dW;
-              K[5] = -dE;
-            }
-          }
-        }
-        // the row divided by its diagonal in FP32, then widened exactly
-        const float ib = __fdividef(1.0f, fb);
-        const double ra = widen_f32(fa * ib), rc = widen_f32(fc * ib), rd = widen_f32(fd * ib);
-        if (!last) {
-          double c1, a1, d1;
-          if (k == 0) {  // unit diagonal: nothing to eliminate
-            c1 = rc;
-            a1 = ra;
-            d1 = rd;
-          } else {
-            const double r = frcp46(fma(-ra, pc, 1.0));
-            c1 = rc * r;
-            a1 = -ra * pa * r;
-            d1 = fma(-ra, pd, rd) * r;
-          }
-          C1[c] = c1;
-          A1[c] = a1;
-          D1[c] = d1;
-          Dacc = fma(P, d1, Dacc);
-          Aacc = fma(P, a1, Aacc);
-          P = -P * c1;
-          pc = c1;
-          pa = a1;
-          pd = d1;
-        } else {
-          ae = ra; ce = rc; de = rd;
-        }
-        fs[k] = fn;
-        lw = le;
-        dW = -dE;
-        hc = he;
-        lc = lE;
+    float he = 0.0f, lE = 0.0f;
+    if (cnt > 1) {
+      he = __ldg(Hin + o + i_lo + 1);
+      lE = __ldg(Lin + o + i_lo + 1);
+    }
+    float hn = __ldg(Hin + o + nr + i_lo), ln = __ldg(Lin + o + nr + i_lo);
+#pragma unroll 1
+    for (int k = 0; k < cnt; ++k) {
+      const int i = i_lo + k;
+      const int c = smem_col(gb + i);
+      const int e = k * G + l;
+      const int meta = LG.meta[e];
+      const int cls = meta & 15, seg = (meta >> 4) & 15;
+      const DevMaterial& Mt = I.mat[seg];
+      const bool last = k == cnt - 1;
+      // the next row's T(i+1, j) and T(i, j+1), loaded one row ahead
+      float he2 = 0.0f, lE2 = 0.0f, hn2 = 0.0f, ln2 = 0.0f;
+      if (k + 2 < cnt) {
+        he2 = __ldg(Hin + o + i + 2);
+        lE2 = __ldg(Lin + o + i + 2);
       }
+      if (k + 1 < cnt) {
+        hn2 = __ldg(Hin + o + nr + i + 1);
+        ln2 = __ldg(Lin + o + nr + i + 1);
+      }
+      const float dN = (hn - hc) + (ln - lc);                  // T_{j+1} - T_j
+      const float dE = last ? dE_last : (he - hc) + (lE - lc);  // T_{i+1} - T_i
+      const float le = last ? le_last : lam_face32(Mt, frule, hc, he);
+      const float fn = lam_face32(Mt, frule, hc, hn) * dN;
+      const float rhoc = Mt.rho_f * cap32(Mt, hc);
+      const float fs = FS[c];
+      const float Ljv = fmaf(zg.gzn_f, fn, -zg.gzs_f * fs);  // Eq. (Lambda_j)
+      float X = (seg == I.src_layer) ? Xs : 0.0f;            // Eq. (source)
+      if (I.g_model == 1 && X != 0.0f) X *= I.g_ref_f * rsqrtf(hc);
+      float fa = -LG.gA_f[e] * lw, fc = -LG.gC_f[e] * le;    // Eq. (ABC)
+      float fb = fmaf(rhoc, inv_tau, -fa - fc);
+      float fd = fmaf(-fa, dW, fmaf(-fc, dE, Ljv + X));
+      if (cls == RC_REGULAR) {
+        if (ENERGY) {
+          const float V2f = LG.V2_f[e];
+          const float V = V2f * zg.etabar_f;
+          MM[c] = widen_f32(V * rhoc);
+          if (valid && X != 0.0f) eQ = fma(widen_f32(tau * V), widen_f32(X), eQ);
+          if (valid && j == 1) {
+            const double f = widen_f32(-tau * V2f * fs / (float)zg.eta_s);
+            if (I.bc_z0 == CC_DIRICHLET) eD += f; else eN += f;
+          }
+          if (valid && j == M - 1) {
+            const double f = widen_f32(tau * V2f * fn / (float)zg.eta_n);
+            if (I.bc_zmax == CC_DIRICHLET) eD += f; else eN += f;
+          }
+        }
+      } else {
+        const RowGeo& g = I.rg[i];
+        if (cls == RC_IFACE) {
+          const float* K = reinterpret_cast<const float*>(sI + 4 * (grp * n_if + g.ifo));
+          float lmv, lpv;
+          if (I.interface_rule == 0) {
+            lmv = K[0];
+            lpv = K[1];
+          } else {
+            lmv = g.rw_f * lw;
+            lpv = g.re_f * le;
+          }
+          fa = -lmv * g.he_f;
+          fc = -lpv * g.hw_f;
+          fb = fmaf(lmv, g.he_f, lpv * g.hw_f);
+          fd = -fmaf(fa, dW, fc * dE);
+        } else if (cls == RC_AXIS) {  // dT_0 - dT_1 = T_1 - T_0
+          fa = 0.0f; fb = 1.0f; fc = -1.0f; fd = dE;
+        } else if (I.bc_rmax == CC_DIRICHLET) {  // r = r_max
+          fa = 0.0f; fb = 1.0f; fc = 0.0f; fd = (I.td_hi - hc) + (I.td_lo - lc);
+        } else {  // dT_N - dT_{N-1} = T_{N-1} - T_N
+          fa = -1.0f; fb = 1.0f; fc = 0.0f; fd = dW;
+        }
+        if (ENERGY) {
+          MM[c] = 0.0;
+          if (cls == RC_IFACE || cls == RC_OUTER) {
+            // heat-flow coefficients to the regular neighbours and the old
+            // temperature differences across those edges
+            const RowGeo& gw = I.rg[i - 1];
+            float* K = reinterpret_cast<float*>(sI + 4 * (grp * n_if + g.ifo));
+            K[2] = tau * gw.V2_f * gw.gC_f * zg.etabar_f * lw;
+            if (i < N) {
+              const RowGeo& ge = I.rg[i + 1];
+              K[3] = tau * ge.V2_f * ge.gA_f * zg.etabar_f * le;
+            } else {
+              K[3] = 0.0f;
+            }
+            K[4] = -dW;
+            K[5] = -dE;
+          }
+        }
+      }
+      FS[c] = fn;
+      // the row divided by its diagonal in FP32, then widened exactly
+      const float ib = __fdividef(1.0f, fb);
+      const double ra = widen_f32(fa * ib), rc = widen_f32(fc * ib), rd = widen_f32(fd * ib);
+      if (!last) {
+        double c1, a1, d1;
+        if (k == 0) {  // unit diagonal: nothing to eliminate
+          c1 = rc;
+          a1 = ra;
+          d1 = rd;
+        } else {
+          const double r = frcp46(fma(-ra, pc, 1.0));
+          c1 = rc * r;
+          a1 = -ra * pa * r;
+          d1 = fma(-ra, pd, rd) * r;
+        }
+        C1[c] = c1;
+        A1[c] = a1;
+        D1[c] = d1;
+        Dacc = fma(P, d1, Dacc);
+        Aacc = fma(P, a1, Aacc);
+        P = -P * c1;
+        pc = c1;
+        pa = a1;
+        pd = d1;
+      } else {
+        ae = ra; ce = rc; de = rd;
+      }
+      lw = le;
+      dW = -dE;
+      hc = he;
+      lc = lE;
+      he = he2;
+      lE = lE2;
+      hn = hn2;
+      ln = ln2;
     }
 
     // ---- 3. separators; 4. back substitution into D1 (unit diagonal)
@@ -217,14 +236,12 @@ __device__ __forceinline__ void mixed_warp_task(const StepArgs& a, const TileTas
     {
       double xn = xs;
       D1[smem_col(gb + i_hi - 1)] = xs;
-#pragma unroll
-      for (int k = kRowsPerLane - 2; k >= 0; --k) {
-        if (k <= cnt - 2) {
-          const int c = smem_col(gb + i_lo + k);
-          const double x = fma(-C1[c], xn, fma(-A1[c], L, D1[c]));
-          D1[c] = x;
-          xn = x;
-        }
+#pragma unroll 4
+      for (int k = cnt - 2; k >= 0; --k) {
+        const int c = smem_col(gb + i_lo + k);
+        const double x = fma(-C1[c], xn, fma(-A1[c], L, D1[c]));
+        D1[c] = x;
+        xn = x;
       }
     }
     __syncwarp();
