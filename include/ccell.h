@@ -245,6 +245,10 @@ int cc_step_adi_n(cc_ctx* ctx, void* T_dev, int64_t n_steps, double t0_s, double
  *   FP64 contexts of one rectangular instance whose field fits in the SMs'
  *   shared memory (e.g. 512 x 4096); other contexts, or a grid that cannot
  *   be co-resident, run mode 0.
+ *   mode 4: one launch per time step with pipelined CTA tiles: half of the
+ *   block's warps assemble the rows of the next tile while the other half
+ *   solve and store the current one, two row buffers changing hands through
+ *   named barriers (every context).
  *   threads: 64, 128 or 256 per block.
  *   rows_per_lane: 2..16, target rows per lane of the line solve; a line of
  *   nr rows is split over the smallest power-of-two number of lanes G <= 32

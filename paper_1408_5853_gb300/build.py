@@ -14,7 +14,8 @@ SOURCES = ["ccell_step.cu", "ccell_step_persist.cu", "ccell_step_mixed.cu",
            "ccell_step_mixed_persist.cu", "ccell_adjoint.cu", "ccell_api.cpp", "ccell_noalloc.cu",
            "ccell_powtab.cpp", "ccell_adi.cu", "ccell_grid.cpp",
            "ccell_fp64_rate.cu", "ccell_step_lines.cu",
-           "ccell_step_lines_mixed.cu", "ccell_step_resident.cu"]
+           "ccell_step_lines_mixed.cu", "ccell_step_resident.cu",
+           "ccell_step_pipe.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 HEADERS = ["ccell_internal.h", "ccell_host.h", "ccell_device.cuh", "ccell_fp64_task.cuh", "ccell_mixed_task.cuh",
            "ccell_lines.cuh", "ccell_lines_mixed.cuh",

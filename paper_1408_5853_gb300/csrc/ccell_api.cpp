@@ -68,6 +68,12 @@ struct cc_ctx {
   unsigned* d_rflags = nullptr;
   size_t rflags_cap = 0;
   int res_blocks = 0, res_smem = 0, res_offset = 0;
+  // launch mode 4 (pipelined tiles): tiles and blocks of the launch
+  bool pipe_ok = false;
+  TileTask* d_ptiles = nullptr;
+  int* d_pcta = nullptr;
+  size_t ptiles_cap = 0, pcta_cap = 0;
+  int pipe_blocks = 0, pipe_smem = 0, pipe_buf = 0;
   void* d_T2 = nullptr;       // ping-pong partner of the caller's field
   float* d_lo = nullptr;      // mixed precision: low-order parts (two buffers)
   double* d_s = nullptr;      // waveform table
@@ -120,6 +126,11 @@ void free_device(cc_ctx* c) {
   c->d_cta = nullptr;
   c->cta_cap = 0;
   c->n_cta = 0;
+  cudaFree(c->d_ptiles);
+  cudaFree(c->d_pcta);
+  c->d_ptiles = nullptr;
+  c->d_pcta = nullptr;
+  c->ptiles_cap = c->pcta_cap = 0;
   cudaFree(c->d_rtiles);
   cudaFree(c->d_rcta);
   cudaFree(c->d_xb);
@@ -307,6 +318,51 @@ int cut_warp_tasks(cc_ctx* c) {
   return rc;
 }
 
+// Tiles of launch mode 4: as many lines per tile as the consumer half of the
+// block's warps solve at once (halved until two row buffers fit), one launch
+// grid of resident blocks taking equal node shares.
+int cut_pipe_tiles(cc_ctx* c) {
+  c->pipe_ok = false;
+  const int warps = c->threads / 32, cons = warps - warps / 2;
+  const bool mixed = c->precision == CC_MIXED;
+  const int elem = mixed ? (int)sizeof(float) : (int)sizeof(double);
+  std::vector<int> lpcs(c->inst.size());
+  for (size_t k = 0; k < c->inst.size(); ++k) lpcs[k] = cons * (32 / c->inst[k].G);
+  for (;;) {
+    int buf = 0;
+    for (size_t k = 0; k < c->inst.size(); ++k) {
+      const Instance& in = c->inst[k];
+      const int nl = std::min(lpcs[k], in.d.nz - 2);
+      buf = std::max(buf, mixed ? mixed_buf_floats(nl, in.d.nr) : fp64_buf_doubles(nl, in.d.nr));
+    }
+    const int smem = (2 * kCarryStride + 2 * buf) * elem;
+    if (smem > kMaxTileSmem) {
+      bool halved = false;
+      for (int& l : lpcs)
+        if (l > 1) {
+          l /= 2;
+          halved = true;
+        }
+      if (!halved) return CC_OK;  // does not fit: mode 0 runs instead
+      continue;
+    }
+    const int B = mixed ? mixed_pipe_resident_blocks(c->threads, smem)
+                        : fp64_pipe_resident_blocks(c->threads, smem);
+    if (B < 0) return CC_ECUDA;
+    std::vector<TileTask> tiles;
+    std::vector<int> cta;
+    cut_tiles(c->inst, lpcs, B, tiles, cta);
+    int rc = put_grown(&c->d_ptiles, &c->ptiles_cap, tiles);
+    if (rc == CC_OK) rc = put_grown(&c->d_pcta, &c->pcta_cap, cta);
+    if (rc != CC_OK) return rc;
+    c->pipe_blocks = B;
+    c->pipe_smem = smem;
+    c->pipe_buf = buf;
+    c->pipe_ok = true;
+    return CC_OK;
+  }
+}
+
 // Tiles of launch mode 3: one block per SM (at most one per interior line),
 // each holding its run of lines of the single instance resident in shared
 // memory next to the scratch of one tile; the tile size is halved until both
@@ -483,6 +539,11 @@ int upload(cc_ctx* c, const std::vector<double>& dts, cudaStream_t st) {
     }
     if (c->mode == 3) {
       const int rc = cut_resident_tiles(c);
+      if (rc != CC_OK) return rc;
+    }
+    c->pipe_ok = false;
+    if (c->mode == 4) {
+      const int rc = cut_pipe_tiles(c);
       if (rc != CC_OK) return rc;
     }
     c->tasks_dirty = false;
@@ -702,7 +763,21 @@ int cc_step_n(cc_ctx* c, void* T_dev, int64_t n_steps, double t0, double dt_s, d
     a.Tin = bufs[s & 1];
     a.Tout = bufs[(s + 1) & 1];
     int r;
-    if (c->mode == 2 && c->lines_ok) {
+    if (c->mode == 4 && c->pipe_ok) {
+      StepArgs p = a;
+      p.tiles = c->d_ptiles;
+      p.cta_start = c->d_pcta;
+      p.n_cta = c->pipe_blocks;
+      p.smem_bytes = c->pipe_smem;
+      p.pipe_buf = c->pipe_buf;
+      if (c->precision == CC_FP64) {
+        r = launch_step_fp64_pipe(p, stream);
+      } else {
+        p.lo_in = c->d_lo + (s & 1) * c->total_nodes;
+        p.lo_out = c->d_lo + ((s + 1) & 1) * c->total_nodes;
+        r = launch_step_mixed_pipe(p, stream);
+      }
+    } else if (c->mode == 2 && c->lines_ok) {
       StepArgs w = a;
       w.tiles = c->d_wtasks;
       w.cta_start = c->d_wcta;
@@ -855,7 +930,7 @@ int cc_step_adi_n(cc_ctx* c, void* T_dev, int64_t n_steps, double t0, double dt_
 }
 
 int cc_set_launch(cc_ctx* c, int32_t mode, int32_t threads, int32_t rows_per_lane) {
-  if (!c || mode < 0 || mode > 3 || (threads != 64 && threads != 128 && threads != 256) ||
+  if (!c || mode < 0 || mode > 4 || (threads != 64 && threads != 128 && threads != 256) ||
       rows_per_lane < 2 || rows_per_lane > kRowsPerLane)
     return CC_EINVAL;
   if (rows_per_lane != c->rows || threads != c->threads || mode != c->mode) c->tasks_dirty = true;
@@ -901,9 +976,11 @@ int cc_autotune(cc_ctx* c, void* T_dev, int32_t n_trial, float* best_ms, void* s
   int rc = CC_OK;
   bool rect = true;
   for (auto& in : c->inst) rect &= in.j_narrow == in.d.nz;
-  // mode 2: rectangles; mode 3: one FP64 rectangle (falls back to mode 0 otherwise)
-  const int n_modes = rect ? ((c->inst.size() == 1 && c->precision == CC_FP64) ? 4 : 3) : 2;
-  for (int mode = 0; mode < n_modes; ++mode)
+  // mode 2: rectangles; mode 3: one FP64 rectangle (others fall back to mode 0)
+  std::vector<int> modes = {0, 1, 4};
+  if (rect) modes.push_back(2);
+  if (rect && c->inst.size() == 1 && c->precision == CC_FP64) modes.push_back(3);
+  for (int mode : modes)
     for (int threads : {64, 128, 256})
       for (int rows : rows_opts) {
         cc_set_launch(c, mode, threads, rows);

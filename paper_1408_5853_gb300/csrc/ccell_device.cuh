@@ -181,6 +181,34 @@ __device__ __forceinline__ void eacc_flush(const StepArgs& a, EAcc& c) {
   c.tr = 0.0;
 }
 
+// A group of consecutive warps of the block that runs one phase of a tile:
+// the whole block (barrier 0, __syncthreads) or, in the pipelined launch, the
+// producer or the consumer warps (a named barrier of the group's threads).
+struct WarpGroup {
+  int warp0, nwarps, bar;
+  __device__ __forceinline__ int warp() const { return (int)(threadIdx.x >> 5) - warp0; }
+  __device__ __forceinline__ int tid() const { return (int)threadIdx.x - 32 * warp0; }
+  __device__ __forceinline__ int size() const { return 32 * nwarps; }
+  __device__ __forceinline__ void sync() const {
+    if (bar == 0) __syncthreads();
+    else asm volatile("bar.sync %0, %1;" ::"r"(bar), "r"(32 * nwarps) : "memory");
+  }
+};
+
+__device__ __forceinline__ WarpGroup whole_block() {
+  return WarpGroup{0, (int)(blockDim.x >> 5), 0};
+}
+
+// Named barrier `id` over n threads: wait for it, or arrive without waiting
+// (the arriving thread's earlier shared-memory writes are fenced first).
+__device__ __forceinline__ void named_sync(int id, int n) {
+  asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(n) : "memory");
+}
+__device__ __forceinline__ void named_arrive(int id, int n) {
+  __threadfence_block();
+  asm volatile("bar.arrive %0, %1;" ::"r"(id), "r"(n) : "memory");
+}
+
 // Phases 1-3 of a CTA tile: the tridiagonal systems of its nl lines, rows
 // (a, b, c | d) in SA .. SD (line q in the padded row q of nrp doubles), solved
 // in place.  Each line is split over G lanes (lane l holds rows
@@ -193,13 +221,15 @@ __device__ __forceinline__ void eacc_flush(const StepArgs& a, EAcc& c) {
 // accuracy that are scaled to a unit diagonal (b is not read).
 // For G = 1 this is the Thomas algorithm of the paper with alpha_0 = 1,
 // beta_0 = 0 and x_N = beta_{N-1} / (1 - alpha_{N-1}).
+// warp: index of this warp among the warps that solve (default: in the block).
 template <bool FULL>
 __device__ __forceinline__ void solve_tile_lines(double* __restrict__ SA, double* __restrict__ SB,
                                                  double* __restrict__ SC, double* __restrict__ SD,
-                                                 int nl, int nr, int G) {
+                                                 int nl, int nr, int G, int warp = -1) {
   const int nrp = smem_row_stride(nr);
   const int lg = __ffs(G) - 1;
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int lane = threadIdx.x & 31;
+  if (warp < 0) warp = threadIdx.x >> 5;
   const int grp = lane >> lg, l = lane & (G - 1);
   const int q_req = warp * (32 >> lg) + grp;
   const bool active = q_req < nl;

@@ -90,41 +90,55 @@ struct SmemField {
   }
 };
 
-// One tile.  sm starts with two rows of axial face fluxes: the tile takes the
-// fluxes of the face south of its first line from row par ^ 1 if carry (the
-// previous tile of this block ended on the line before j0), and leaves those
-// north of its last line in row par.  STP: the tile holds a line of a stepped
-// outline that is narrow or borders a narrow one (other tiles skip the checks).
-template <bool ENERGY, bool TRACE, bool STP, class F>
-__device__ __forceinline__ void step_fp64_tile(const StepArgs& a, const TileTask tk,
-                                               double* __restrict__ sm, EAcc& acc, bool carry,
-                                               int par, const F& fld) {
-  if (tk.inst != acc.inst) {  // block-uniform
-    eacc_flush<ENERGY, TRACE>(a, acc);
-    acc.inst = tk.inst;
-  }
+// Row buffers of one FP64 tile of nl lines (padded rows of nrp doubles): the
+// four rows of every line's system, the heat capacities, and four values per
+// line and interface node.
+struct Fp64Tile {
+  double *SA, *SB, *SC, *SD;  // a then a', b then That, c then c', d then d'
+  double *SM, *sI;            // V2 rho c / tau (energy); lambda_w(T), lambda_e(T), kw, ke
+};
+
+__device__ __forceinline__ Fp64Tile fp64_tile_at(double* base, int nl, int nrp) {
+  Fp64Tile B;
+  B.SA = base;
+  B.SB = B.SA + (size_t)nl * nrp;
+  B.SC = B.SB + (size_t)nl * nrp;
+  B.SD = B.SC + (size_t)nl * nrp;
+  B.SM = B.SD + (size_t)nl * nrp;
+  B.sI = B.SM + (size_t)nl * nrp;
+  return B;
+}
+
+// Phases 0a-0b of a tile, run by the warps of g: nodal conductivities of the
+// interface rows, then properties and rows with the lanes over columns into
+// the tile's row buffers.  The axial fluxes south of the first line come from
+// cin if carry; those north of the last line go to cout.  STP: the tile holds
+// a line of a stepped outline that is narrow or borders a narrow one (other
+// tiles skip the checks).
+template <bool ENERGY, bool STP, class F>
+__device__ __forceinline__ void fp64_produce(const StepArgs& a, const TileTask tk, const Fp64Tile& B,
+                                             const double* __restrict__ cin, double* __restrict__ cout,
+                                             bool carry, const WarpGroup& grp, EAcc& acc,
+                                             const F& fld) {
   const DevInst& I = a.insts[tk.inst];
   const int nr = I.nr, N = nr - 1, M = I.nz - 1;
-  const int G = I.G;
   const int j0 = tk.j0, nl = tk.nl;
   const int nrp = smem_row_stride(nr);
   const int frule = I.face_rule;
   const int n_if = I.n_if;
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarps = blockDim.x >> 5;
-  const double* cin = sm + (size_t)(par ^ 1) * nrp;  // fluxes south of line j0
-  double* cout = sm + (size_t)par * nrp;             // fluxes north of line j0+nl-1
-  double* SA = sm + 2 * (size_t)nrp;       // a, then a' (coupling to the previous separator)
-  double* SB = SA + (size_t)nl * nrp;      // b, then That
-  double* SC = SB + (size_t)nl * nrp;      // c, then c'
-  double* SD = SC + (size_t)nl * nrp;      // d, then d'
-  double* SM = SD + (size_t)nl * nrp;      // V2 rho c / tau (energy)
-  double* sI = SM + (size_t)nl * nrp;      // per line and interface node: lambda_w(T), lambda_e(T), kw, ke
+  const int warp = grp.warp(), lane = threadIdx.x & 31, nwarps = grp.nwarps;
+  double* SA = B.SA;
+  double* SB = B.SB;
+  double* SC = B.SC;
+  double* SD = B.SD;
+  double* SM = B.SM;
+  double* sI = B.sI;
   const double s = a.s_tab[a.step * a.n_inst + tk.inst];
-  double eQ = 0.0, eD = 0.0, eN = 0.0, eI = 0.0, eE = 0.0, tr = 0.0;
+  double eQ = 0.0, eD = 0.0, eN = 0.0;
 
   // ---- 0a. nodal conductivities of the interface rows, Eq. (cc_first_3)
   if (I.interface_rule == 0 && n_if > 0) {  // block-uniform
-    for (int it = threadIdx.x; it < nl * n_if; it += blockDim.x) {
+    for (int it = grp.tid(); it < nl * n_if; it += grp.size()) {
       const int q = it / n_if;
       const int i = I.if_i[it - q * n_if];
       const RowGeo& g = I.rg[i];
@@ -134,8 +148,8 @@ __device__ __forceinline__ void step_fp64_tile(const StepArgs& a, const TileTask
         sI[4 * it + 1] = lam_eval(I.mat[g.seg], T);
       }
     }
-    __syncthreads();
   }
+  grp.sync();  // the interface values, and the previous tile's carried fluxes
 
   // ---- 0b. properties and rows, lanes over columns.  Block b of a warp
   // covers columns 31b .. 31b+31; lane 0 (column 31b) only supplies the face
@@ -274,18 +288,34 @@ __device__ __forceinline__ void step_fp64_tile(const StepArgs& a, const TileTask
       }
     }
   }
-  __syncthreads();
+  if (ENERGY) {
+    acc.e[1] += eQ;
+    acc.e[2] += eD;
+    acc.e[4] += eN;
+  }
+}
 
-  // ---- 1.-3. line solves, lanes over the rows of a line
-  solve_tile_lines<true>(SA, SB, SC, SD, nl, nr, G);
-  __syncthreads();
-
+// Phase 4 of a tile, run by the threads of g after the line solves: stores,
+// axial boundary rows, surface trace and energy terms, with the threads over
+// the nodes of the tile.
+template <bool ENERGY, bool TRACE, bool STP, class F>
+__device__ __forceinline__ void fp64_finish(const StepArgs& a, const TileTask tk, const Fp64Tile& B,
+                                            const WarpGroup& grp, EAcc& acc, const F& fld) {
+  const DevInst& I = a.insts[tk.inst];
+  const int nr = I.nr, N = nr - 1, M = I.nz - 1;
+  const int j0 = tk.j0, nl = tk.nl;
+  const int nrp = smem_row_stride(nr);
+  const int n_if = I.n_if;
+  const double* SB = B.SB;
+  const double* SM = B.SM;
+  const double* sI = B.sI;
+  double eE = 0.0, eD = 0.0, eN = 0.0, eI = 0.0, tr = 0.0;
   // ---- 4. stores, boundary rows, trace and energy, lanes over columns
   {
     bool bad = false;
     // threads over the nl x nr nodes of the tile, line by line (all threads
     // stay busy when nr is below the block size)
-    int q = threadIdx.x / nr, i = threadIdx.x - q * nr, qe = -1;
+    int q = grp.tid() / nr, i = grp.tid() - q * nr, qe = -1;
     double eEq = 0.0;
     for (; q < nl;) {
       const int j = j0 + q;
@@ -317,7 +347,7 @@ __device__ __forceinline__ void step_fp64_tile(const StepArgs& a, const TileTask
           tr = fma(I.zg[M].wnorm, xM, tr);
         }
       }
-      i += blockDim.x;
+      i += grp.size();
       while (i >= nr) {
         i -= nr;
         ++q;
@@ -328,7 +358,7 @@ __device__ __forceinline__ void step_fp64_tile(const StepArgs& a, const TileTask
     if (ENERGY) {
       // heat through the radial edges between each interface (or r_max) node
       // and its regular neighbours, at That
-      for (int it = threadIdx.x; it < nl * n_if; it += blockDim.x) {
+      for (int it = grp.tid(); it < nl * n_if; it += grp.size()) {
         const int q = it / n_if;
         const int i = I.if_i[it - q * n_if];
         const double* Bq = SB + (size_t)q * nrp;
@@ -343,13 +373,37 @@ __device__ __forceinline__ void step_fp64_tile(const StepArgs& a, const TileTask
         }
       }
       acc.e[0] += eE;
-      acc.e[1] += eQ;
       acc.e[2] += eD;
       acc.e[3] += eI;
       acc.e[4] += eN;
     }
     if (TRACE) acc.tr += tr;
   }
+}
+
+// One tile with the whole block: rows, solves, stores, separated by block
+// barriers.  sm starts with two rows of axial face fluxes (row par ^ 1 holds
+// those south of the tile's first line if carry; those north of its last
+// line go to row par), then the tile's row buffers.
+template <bool ENERGY, bool TRACE, bool STP, class F>
+__device__ __forceinline__ void step_fp64_tile(const StepArgs& a, const TileTask tk,
+                                               double* __restrict__ sm, EAcc& acc, bool carry,
+                                               int par, const F& fld) {
+  if (tk.inst != acc.inst) {  // block-uniform
+    eacc_flush<ENERGY, TRACE>(a, acc);
+    acc.inst = tk.inst;
+  }
+  const DevInst& I = a.insts[tk.inst];
+  const int nrp = smem_row_stride(I.nr);
+  const Fp64Tile B = fp64_tile_at(sm + 2 * (size_t)nrp, tk.nl, nrp);
+  const WarpGroup all = whole_block();
+  fp64_produce<ENERGY, STP>(a, tk, B, sm + (size_t)(par ^ 1) * nrp, sm + (size_t)par * nrp, carry,
+                            all, acc, fld);
+  __syncthreads();
+  // ---- 1.-3. line solves, lanes over the rows of a line
+  solve_tile_lines<true>(B.SA, B.SB, B.SC, B.SD, tk.nl, I.nr, I.G);
+  __syncthreads();
+  fp64_finish<ENERGY, TRACE, STP>(a, tk, B, all, acc, fld);
   __syncthreads();  // the next tile reuses the shared memory
 }
 

@@ -162,6 +162,16 @@ constexpr int kWarpRowStride = 512 + (512 >> 4) + 1;
 CC_HOST_DEVICE inline int lines_warp_doubles(int if_slots) {
   return 5 * kWarpRowStride + 4 * if_slots;
 }
+// Row buffers of one tile of nl lines (the tile shared memory above without
+// the two carry rows): doubles of an FP64 tile; floats of a mixed tile,
+// rounded up to keep a following buffer's doubles aligned.
+CC_HOST_DEVICE inline int fp64_buf_doubles(int nl, int nr) {
+  return 5 * nl * smem_row_stride(nr) + 4 * CC_MAX_LAYERS * nl;
+}
+CC_HOST_DEVICE inline int mixed_buf_floats(int nl, int nr) {
+  const int nrp = smem_row_stride(nr);
+  return (8 * nl * nrp + nl * nrp + kMixIf * CC_MAX_LAYERS * nl + 1) & ~1;
+}
 // Largest dynamic shared memory of an FP64 tile: the opt-in limit per block
 // on sm_103 (227 KiB) less room for the kernels' static shared memory.
 constexpr int kMaxTileSmem = 226 * 1024;
@@ -208,6 +218,9 @@ struct StepArgs {
   int res_offset;
   double* xb;
   unsigned* nbr_flags;
+  // pipelined tiles (launch mode 4): elements (FP64: doubles, mixed: floats)
+  // of one of the two row buffers after the two carry rows
+  int pipe_buf;
   // persistent launches: grid barrier state [count, generation], bounded wait
   unsigned* bar;
   unsigned bar_extra;    // extra arrivals expected (nonzero only to test the timeout)
@@ -300,6 +313,15 @@ int fp64_lines_resident_blocks(int threads, int smem);
 // [cta_start[b], cta_start[b+1]) of one instance; result in a.Tin.
 int launch_steps_fp64_resident(const StepArgs& a, long long n, void* stream);
 int fp64_resident_kernel_blocks(int threads, int smem);
+// Pipelined CTA tiles, one launch per step (ccell_step_pipe.cu): half of the
+// block's warps assemble the rows of tile k+1 while the other half solve and
+// store tile k; a.tiles / a.cta_start / a.n_cta are the launch's tiles.
+int launch_step_fp64_pipe(const StepArgs& a, void* stream);
+int launch_step_mixed_pipe(const StepArgs& a, void* stream);
+int fp64_pipe_resident_blocks(int threads, int smem);
+int mixed_pipe_resident_blocks(int threads, int smem);
+// Shared memory of the pipelined tiles: two carry rows and two row buffers.
+constexpr int kCarryStride = kMaxNr + (kMaxNr >> 4) + 1;
 // The same for the mixed-precision step (ccell_step_lines_mixed.cu).
 int launch_step_mixed_lines(const StepArgs& a, void* stream);
 int mixed_lines_resident_blocks(int threads, int smem);

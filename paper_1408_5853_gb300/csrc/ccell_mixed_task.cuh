@@ -87,45 +87,56 @@ __device__ __forceinline__ float ld_state(const float* p) {
   else return __ldcg(p);
 }
 
-// STP: the tile holds a line of a stepped outline that is narrow or borders a
-// narrow one (other tiles skip the checks).
-template <bool ENERGY, bool TRACE, bool CACHED, bool STP>
-__device__ __forceinline__ void step_mixed_tile(const StepArgs& a, const TileTask tk,
-                                                float* __restrict__ sm, EAcc& acc, bool carry,
-                                                int par) {
-  if (tk.inst != acc.inst) {  // block-uniform
-    eacc_flush<ENERGY, TRACE>(a, acc);
-    acc.inst = tk.inst;
-  }
+// Row buffers of one mixed-precision tile of nl lines (padded rows of nrp):
+// the four rows of every line's system (FP64), then in FP32 the capacities
+// and kMixIf floats per line and interface node.
+struct MixTile {
+  double *SA, *SB, *SC, *SD;  // a, b (then the increment dT), c, d
+  float *FM, *sI;             // V rho c (energy); lam_w, lam_e, kw, ke, dTw, dTe per interface
+};
+
+__device__ __forceinline__ MixTile mix_tile_at(float* base, int nl, int nrp) {
+  MixTile B;
+  B.SA = reinterpret_cast<double*>(base);
+  B.SB = B.SA + (size_t)nl * nrp;
+  B.SC = B.SB + (size_t)nl * nrp;
+  B.SD = B.SC + (size_t)nl * nrp;
+  B.FM = reinterpret_cast<float*>(B.SD + (size_t)nl * nrp);
+  B.sI = B.FM + (size_t)nl * nrp;
+  return B;
+}
+
+// Phases 0a-0b of a tile, run by the warps of g: nodal conductivities of the
+// interface rows, then FP32 properties and rows in delta form with the lanes
+// over columns, widened into the tile's FP64 rows.  The axial fluxes south of
+// the first line come from cin if carry, those north of the last line go to
+// cout.  STP: the tile holds a line of a stepped outline that is narrow or
+// borders a narrow one (other tiles skip the checks).
+template <bool ENERGY, bool CACHED, bool STP>
+__device__ __forceinline__ void mixed_produce(const StepArgs& a, const TileTask tk, const MixTile& B,
+                                              const float* __restrict__ cin, float* __restrict__ cout,
+                                              bool carry, const WarpGroup& grp, EAcc& acc) {
   const DevInst& I = a.insts[tk.inst];
   const int nr = I.nr, N = nr - 1, M = I.nz - 1;
-  const int G = I.G;
   const int j0 = tk.j0, nl = tk.nl;
   const int nrp = smem_row_stride(nr);
   const int frule = I.face_rule;
   const int n_if = I.n_if;
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarps = blockDim.x >> 5;
-  const float* cin = sm + (size_t)(par ^ 1) * nrp;  // axial fluxes south of line j0
-  float* cout = sm + (size_t)par * nrp;             // axial fluxes north of line j0+nl-1
-  double* SA = reinterpret_cast<double*>(sm + 2 * (size_t)nrp);  // rows (delta form, FP32 values widened)
-  double* SB = SA + (size_t)nl * nrp;          // b, then the increment dT
-  double* SC = SB + (size_t)nl * nrp;
-  double* SD = SC + (size_t)nl * nrp;
-  float* FM = reinterpret_cast<float*>(SD + (size_t)nl * nrp);  // V rho c (energy)
-  float* sI = FM + (size_t)nl * nrp;  // per line and interface node: lam_w, lam_e, kw, ke, dTw, dTe
+  const int warp = grp.warp(), lane = threadIdx.x & 31, nwarps = grp.nwarps;
+  double* SA = B.SA;
+  double* SC = B.SC;
+  double* SD = B.SD;
+  float* FM = B.FM;
+  float* sI = B.sI;
   const float* Hin = static_cast<const float*>(a.Tin) + I.t_off;
   const float* Lin = a.lo_in + I.t_off;
-  float* Hout = static_cast<float*>(a.Tout) + I.t_off;
-  float* Lout = a.lo_out + I.t_off;
   const float s = (float)a.s_tab[a.step * a.n_inst + tk.inst];
   const float inv_tau = I.inv_tau_f, tau = I.tau_f;
-  // energy terms: per-node products of the FP32 factors (widened exactly)
-  // with FP64 values, summed in FP64
-  double eE = 0.0, eQ = 0.0, eD = 0.0, eN = 0.0, eI = 0.0, tr = 0.0;
+  double eQ = 0.0, eD = 0.0, eN = 0.0;
 
   // ---- 0a. nodal conductivities of the interface rows, Eq. (cc_first_3)
   if (I.interface_rule == 0 && n_if > 0) {
-    for (int it = threadIdx.x; it < nl * n_if; it += blockDim.x) {
+    for (int it = grp.tid(); it < nl * n_if; it += grp.size()) {
       const int q = it / n_if;
       const int i = I.if_i[it - q * n_if];
       const RowGeo& g = I.rg[i];
@@ -135,8 +146,8 @@ __device__ __forceinline__ void step_mixed_tile(const StepArgs& a, const TileTas
         sI[kMixIf * it + 1] = lam32(I.mat[g.seg], h);
       }
     }
-    __syncthreads();
   }
+  grp.sync();  // the interface values, and the previous tile's carried fluxes
 
   // ---- 0b. FP32 properties and rows in delta form, lanes over columns
   // (block b covers columns 31b .. 31b+31; see the FP64 tile)
@@ -271,17 +282,37 @@ __device__ __forceinline__ void step_mixed_tile(const StepArgs& a, const TileTas
       }
     }
   }
-  __syncthreads();
+  if (ENERGY) {
+    acc.e[1] += eQ;
+    acc.e[2] += eD;
+    acc.e[4] += eN;
+  }
+}
 
-  // ---- 1.-3. FP64 line solves, lanes over the rows of a line
-  solve_tile_lines<false>(SA, SB, SC, SD, nl, nr, G);  // unit diagonal
-  __syncthreads();
-
+// Phase 4 of a tile, run by the threads of g after the line solves: pair
+// update, axial boundary rows, surface trace and the energy terms, with the
+// threads over the nodes of the tile.
+template <bool ENERGY, bool TRACE, bool CACHED, bool STP>
+__device__ __forceinline__ void mixed_finish(const StepArgs& a, const TileTask tk, const MixTile& B,
+                                             const WarpGroup& grp, EAcc& acc) {
+  const DevInst& I = a.insts[tk.inst];
+  const int nr = I.nr, N = nr - 1, M = I.nz - 1;
+  const int j0 = tk.j0, nl = tk.nl;
+  const int nrp = smem_row_stride(nr);
+  const int n_if = I.n_if;
+  const double* SB = B.SB;
+  const float* FM = B.FM;
+  const float* sI = B.sI;
+  const float* Hin = static_cast<const float*>(a.Tin) + I.t_off;
+  const float* Lin = a.lo_in + I.t_off;
+  float* Hout = static_cast<float*>(a.Tout) + I.t_off;
+  float* Lout = a.lo_out + I.t_off;
+  double eE = 0.0, eD = 0.0, eN = 0.0, eI = 0.0, tr = 0.0;
   // ---- 4. pair update, boundary rows, trace, interface energy; lanes over columns
   {
     bool bad = false;
     // threads over the nl x nr nodes of the tile, line by line
-    int q = threadIdx.x / nr, i = threadIdx.x - q * nr;
+    int q = grp.tid() / nr, i = grp.tid() - q * nr;
     for (; q < nl;) {
       const int j = j0 + q;
       const long long rj = (long long)j * nr;
@@ -327,7 +358,7 @@ __device__ __forceinline__ void step_mixed_tile(const StepArgs& a, const TileTas
           tr = fma(I.zg[M].wnorm, xM, tr);
         }
       }
-      i += blockDim.x;
+      i += grp.size();
       while (i >= nr) {
         i -= nr;
         ++q;
@@ -337,7 +368,7 @@ __device__ __forceinline__ void step_mixed_tile(const StepArgs& a, const TileTas
     if (ENERGY) {
       // heat through the edges between each interface (or r_max) node and its
       // regular neighbours, at the new temperatures: k (dT_old + d(dT))
-      for (int it = threadIdx.x; it < nl * n_if; it += blockDim.x) {
+      for (int it = grp.tid(); it < nl * n_if; it += grp.size()) {
         const int q = it / n_if;
         const int i = I.if_i[it - q * n_if];
         const double* Bq = SB + (size_t)q * nrp;
@@ -352,13 +383,37 @@ __device__ __forceinline__ void step_mixed_tile(const StepArgs& a, const TileTas
         }
       }
       acc.e[0] += eE;
-      acc.e[1] += eQ;
       acc.e[2] += eD;
       acc.e[3] += eI;
       acc.e[4] += eN;
     }
     if (TRACE) acc.tr += tr;
   }
+}
+
+// One tile with the whole block: rows, solves, stores, separated by block
+// barriers.  sm starts with two rows of axial face fluxes (row par ^ 1 holds
+// those south of the tile's first line if carry; those north of its last
+// line go to row par), then the tile's row buffers.
+template <bool ENERGY, bool TRACE, bool CACHED, bool STP>
+__device__ __forceinline__ void step_mixed_tile(const StepArgs& a, const TileTask tk,
+                                                float* __restrict__ sm, EAcc& acc, bool carry,
+                                                int par) {
+  if (tk.inst != acc.inst) {  // block-uniform
+    eacc_flush<ENERGY, TRACE>(a, acc);
+    acc.inst = tk.inst;
+  }
+  const DevInst& I = a.insts[tk.inst];
+  const int nrp = smem_row_stride(I.nr);
+  const MixTile B = mix_tile_at(sm + 2 * (size_t)nrp, tk.nl, nrp);
+  const WarpGroup all = whole_block();
+  mixed_produce<ENERGY, CACHED, STP>(a, tk, B, sm + (size_t)(par ^ 1) * nrp,
+                                     sm + (size_t)par * nrp, carry, all, acc);
+  __syncthreads();
+  // ---- 1.-3. FP64 line solves, lanes over the rows of a line (unit diagonal)
+  solve_tile_lines<false>(B.SA, B.SB, B.SC, B.SD, tk.nl, I.nr, I.G);
+  __syncthreads();
+  mixed_finish<ENERGY, TRACE, CACHED, STP>(a, tk, B, all, acc);
   __syncthreads();  // the next tile reuses the shared memory
 }
 

@@ -1,0 +1,194 @@
+// Pipelined CTA tiles (launch mode 4), one launch per time step.
+//
+// The tile kernels of modes 0 and 1 run the three phases of a tile -- rows
+// (properties, Eq. (ABC), interface and closure rows), line solves, stores --
+// one after the other with block barriers between them, so while the block
+// assembles rows the FP64 line solves wait and vice versa (in the mixed
+// precision step the rows are FP32 work and the solves FP64 work).  Here the
+// block's warps split into producers and consumers with two row buffers:
+// producers assemble tile k+1 into one buffer while consumers solve and store
+// tile k from the other.  Buffers change hands through named barriers: a
+// "full" barrier per buffer (producers arrive, consumers wait) and an "empty"
+// barrier per buffer (consumers arrive, producers wait).  The axial fluxes
+// handed from tile to tile stay with the producers.  A tile holds as many
+// lines as the consumer warps solve at once.
+#include <cuda_runtime.h>
+
+#include "ccell_fp64_task.cuh"
+#include "ccell_mixed_task.cuh"
+
+namespace ccell {
+
+constexpr int kBarProd = 1, kBarCons = 2, kBarFull = 3, kBarEmpty = 5;
+
+// Producer / consumer loops over the block's tiles; Buf(k) gives the row
+// buffers of the k-th tile of the block, Produce / Consume run its phases.
+template <bool ENERGY, bool TRACE, class Produce, class Consume>
+__device__ __forceinline__ void pipe_tiles(const StepArgs& a, EAcc& acc, Produce produce,
+                                           Consume consume) {
+  const int nw = blockDim.x >> 5, P = nw / 2, C = nw - P, NT = blockDim.x;
+  const bool producer = (int)(threadIdx.x >> 5) < P;
+  const WarpGroup grp = producer ? WarpGroup{0, P, kBarProd} : WarpGroup{P, C, kBarCons};
+  const int t0 = a.cta_start[blockIdx.x], t1 = a.cta_start[blockIdx.x + 1];
+  const int n = t1 - t0;
+  if (producer) {
+    int prev_inst = -1, prev_end = -1, par = 0;
+    for (int k = 0; k < n; ++k) {
+      const TileTask tk = a.tiles[t0 + k];
+      if (k >= 2) named_sync(kBarEmpty + (k & 1), NT);  // consumers are done with tile k-2
+      if (tk.inst != acc.inst) {
+        eacc_flush<ENERGY, TRACE>(a, acc);
+        acc.inst = tk.inst;
+      }
+      produce(tk, k & 1, tk.inst == prev_inst && tk.j0 == prev_end, par, grp, acc);
+      named_arrive(kBarFull + (k & 1), NT);
+      prev_inst = tk.inst;
+      prev_end = tk.j0 + tk.nl;
+      par ^= 1;
+    }
+    for (int k = n > 2 ? n - 2 : 0; k < n; ++k) named_sync(kBarEmpty + (k & 1), NT);
+  } else {
+    for (int k = 0; k < n; ++k) {
+      const TileTask tk = a.tiles[t0 + k];
+      if (tk.inst != acc.inst) {
+        eacc_flush<ENERGY, TRACE>(a, acc);
+        acc.inst = tk.inst;
+      }
+      named_sync(kBarFull + (k & 1), NT);
+      consume(tk, k & 1, grp, acc);
+      named_arrive(kBarEmpty + (k & 1), NT);
+    }
+  }
+}
+
+template <bool ENERGY, bool TRACE>
+__global__ void __launch_bounds__(256, 1) step_fp64_pipe_kernel(const StepArgs a) {
+  extern __shared__ double sm[];
+  double* buf0 = sm + 2 * kCarryStride;
+  EAcc acc;
+  eacc_init(acc);
+  auto tile = [&](const TileTask& tk, int b) {
+    const int nrp = smem_row_stride(a.insts[tk.inst].nr);
+    return fp64_tile_at(buf0 + (size_t)b * a.pipe_buf, tk.nl, nrp);
+  };
+  pipe_tiles<ENERGY, TRACE>(
+      a, acc,
+      [&](const TileTask& tk, int b, bool carry, int par, const WarpGroup& grp, EAcc& ac) {
+        const DevInst& I = a.insts[tk.inst];
+        const int nrp = smem_row_stride(I.nr);
+        const GlobalField<true> fld(a, I);
+        if (tk.j0 + tk.nl >= I.j_narrow)
+          fp64_produce<ENERGY, true>(a, tk, tile(tk, b), sm + (size_t)(par ^ 1) * nrp,
+                                     sm + (size_t)par * nrp, carry, grp, ac, fld);
+        else
+          fp64_produce<ENERGY, false>(a, tk, tile(tk, b), sm + (size_t)(par ^ 1) * nrp,
+                                      sm + (size_t)par * nrp, carry, grp, ac, fld);
+      },
+      [&](const TileTask& tk, int b, const WarpGroup& grp, EAcc& ac) {
+        const DevInst& I = a.insts[tk.inst];
+        const Fp64Tile B = tile(tk, b);
+        const GlobalField<true> fld(a, I);
+        solve_tile_lines<true>(B.SA, B.SB, B.SC, B.SD, tk.nl, I.nr, I.G, grp.warp());
+        grp.sync();  // the stores read every consumer warp's solutions
+        if (tk.j0 + tk.nl >= I.j_narrow)
+          fp64_finish<ENERGY, TRACE, true>(a, tk, B, grp, ac, fld);
+        else
+          fp64_finish<ENERGY, TRACE, false>(a, tk, B, grp, ac, fld);
+      });
+  eacc_flush<ENERGY, TRACE>(a, acc);
+}
+
+template <bool ENERGY, bool TRACE>
+__global__ void __launch_bounds__(256, 1) step_mixed_pipe_kernel(const StepArgs a) {
+  extern __shared__ float smf[];
+  float* buf0 = smf + 2 * kCarryStride;
+  EAcc acc;
+  eacc_init(acc);
+  auto tile = [&](const TileTask& tk, int b) {
+    const int nrp = smem_row_stride(a.insts[tk.inst].nr);
+    return mix_tile_at(buf0 + (size_t)b * a.pipe_buf, tk.nl, nrp);
+  };
+  pipe_tiles<ENERGY, TRACE>(
+      a, acc,
+      [&](const TileTask& tk, int b, bool carry, int par, const WarpGroup& grp, EAcc& ac) {
+        const DevInst& I = a.insts[tk.inst];
+        const int nrp = smem_row_stride(I.nr);
+        if (tk.j0 + tk.nl >= I.j_narrow)
+          mixed_produce<ENERGY, true, true>(a, tk, tile(tk, b), smf + (size_t)(par ^ 1) * nrp,
+                                            smf + (size_t)par * nrp, carry, grp, ac);
+        else
+          mixed_produce<ENERGY, true, false>(a, tk, tile(tk, b), smf + (size_t)(par ^ 1) * nrp,
+                                             smf + (size_t)par * nrp, carry, grp, ac);
+      },
+      [&](const TileTask& tk, int b, const WarpGroup& grp, EAcc& ac) {
+        const DevInst& I = a.insts[tk.inst];
+        const MixTile B = tile(tk, b);
+        solve_tile_lines<false>(B.SA, B.SB, B.SC, B.SD, tk.nl, I.nr, I.G, grp.warp());
+        grp.sync();  // the stores read every consumer warp's solutions
+        if (tk.j0 + tk.nl >= I.j_narrow)
+          mixed_finish<ENERGY, TRACE, true, true>(a, tk, B, grp, ac);
+        else
+          mixed_finish<ENERGY, TRACE, true, false>(a, tk, B, grp, ac);
+      });
+  eacc_flush<ENERGY, TRACE>(a, acc);
+}
+
+template <bool ENERGY, bool TRACE>
+static KernelCache& fp64_pipe_cache() {
+  static KernelCache c;
+  return c;
+}
+template <bool ENERGY, bool TRACE>
+static KernelCache& mixed_pipe_cache() {
+  static KernelCache c;
+  return c;
+}
+
+template <bool MIXED, bool ENERGY, bool TRACE>
+static int pipe_variant_resident(int threads, int smem) {
+  if constexpr (MIXED)
+    return cached_resident(mixed_pipe_cache<ENERGY, TRACE>(), step_mixed_pipe_kernel<ENERGY, TRACE>,
+                           threads, smem, kMaxTileSmem);
+  else
+    return cached_resident(fp64_pipe_cache<ENERGY, TRACE>(), step_fp64_pipe_kernel<ENERGY, TRACE>,
+                           threads, smem, kMaxTileSmem);
+}
+
+template <bool MIXED>
+static int pipe_resident(int threads, int smem) {
+  int r = pipe_variant_resident<MIXED, true, true>(threads, smem);
+  r = min(r, pipe_variant_resident<MIXED, true, false>(threads, smem));
+  r = min(r, pipe_variant_resident<MIXED, false, true>(threads, smem));
+  return min(r, pipe_variant_resident<MIXED, false, false>(threads, smem));
+}
+int fp64_pipe_resident_blocks(int threads, int smem) { return pipe_resident<false>(threads, smem); }
+int mixed_pipe_resident_blocks(int threads, int smem) { return pipe_resident<true>(threads, smem); }
+
+template <bool MIXED, bool ENERGY, bool TRACE>
+static int launch_pipe_variant(const StepArgs& a, cudaStream_t st) {
+  if (pipe_variant_resident<MIXED, ENERGY, TRACE>(a.threads, a.smem_bytes) < 0) return -1;
+  if constexpr (MIXED)
+    step_mixed_pipe_kernel<ENERGY, TRACE><<<a.n_cta, a.threads, a.smem_bytes, st>>>(a);
+  else
+    step_fp64_pipe_kernel<ENERGY, TRACE><<<a.n_cta, a.threads, a.smem_bytes, st>>>(a);
+  return 0;
+}
+
+template <bool MIXED>
+static int launch_pipe(const StepArgs& a, void* stream) {
+  cudaStream_t st = (cudaStream_t)stream;
+  const bool E = a.energy != nullptr, T = a.trace != nullptr;
+  int r;
+  if (E && T) r = launch_pipe_variant<MIXED, true, true>(a, st);
+  else if (E) r = launch_pipe_variant<MIXED, true, false>(a, st);
+  else if (T) r = launch_pipe_variant<MIXED, false, true>(a, st);
+  else r = launch_pipe_variant<MIXED, false, false>(a, st);
+  count_launch();
+  if (r) return r;
+  return cudaGetLastError() == cudaSuccess ? 0 : -1;
+}
+
+int launch_step_fp64_pipe(const StepArgs& a, void* stream) { return launch_pipe<false>(a, stream); }
+int launch_step_mixed_pipe(const StepArgs& a, void* stream) { return launch_pipe<true>(a, stream); }
+
+}  // namespace ccell

@@ -118,10 +118,10 @@ def test_launch_shape_validation_and_round_trip():
     sol = ccell.Solver(cfg)
     try:
         for shape in ((1, 64, 4), (0, 256, 16), (1, 128, 8), (2, 256, 16), (2, 64, 4),
-                      (3, 128, 16)):
+                      (3, 128, 16), (4, 256, 16), (4, 64, 2)):
             sol.set_launch(*shape)
             assert ccell.cc_get_launch(sol.ctx) == shape
-        for bad in ((4, 128, 16), (-1, 128, 16), (0, 96, 16), (0, 128, 1), (0, 128, 32)):
+        for bad in ((5, 128, 16), (-1, 128, 16), (0, 96, 16), (0, 128, 1), (0, 128, 32)):
             with pytest.raises(ccell.CCError):
                 sol.set_launch(*bad)
     finally:

@@ -60,7 +60,8 @@ def small_20ms():
     return cfg, T0, n, oracle.step_n(cfg, T0, n, 0.0, cfg["dt"])
 
 
-@pytest.mark.parametrize("launch", [(0, 256, 16), (1, 256, 16), (2, 256, 16), (3, 256, 16)])
+@pytest.mark.parametrize("launch", [(0, 256, 16), (1, 256, 16), (2, 256, 16), (3, 256, 16),
+                                    (4, 256, 16)])
 def test_small_case_full_20ms_fp64(small_20ms, launch):
     cfg, T0, n, ref = small_20ms
     (Tg,), trg, eg = run_gpu(cfg, T0, n, launch=launch)
@@ -85,16 +86,17 @@ def production_2000():
 
 
 @pytest.mark.parametrize("launch", [(0, 256, 16), (1, 256, 16), (2, 256, 16), (3, 256, 16),
-                                    (3, 128, 16)])
+                                    (3, 128, 16), (4, 256, 16)])
 def test_production_2000_steps_fp64_full_field(production_2000, launch):
     cfg, T0, n, t0, ref = production_2000
     (Tg,), trg, eg = run_gpu(cfg, T0, n, t0=t0, launch=launch)
     _check(Tg, trg[0], eg[0], ref, TOL_FP64_K, 1e-9)
 
 
-def test_production_2000_steps_mixed_full_field(production_2000):
+@pytest.mark.parametrize("launch", ["autotune", (4, 256, 16)])
+def test_production_2000_steps_mixed_full_field(production_2000, launch):
     cfg, T0, n, t0, ref = production_2000
-    (Tg,), trg, eg = run_gpu(cfg, T0, n, t0=t0, precision=MIXED, launch="autotune")
+    (Tg,), trg, eg = run_gpu(cfg, T0, n, t0=t0, precision=MIXED, launch=launch)
     err, _ = _check(Tg, trg[0], eg[0], ref, TOL_MIXED_K, 1e-4)
     assert err < 1e-5, err                       # far inside the bar at this horizon
 
