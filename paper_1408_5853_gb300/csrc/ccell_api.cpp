@@ -333,9 +333,10 @@ int cut_pipe_tiles(cc_ctx* c) {
     for (size_t k = 0; k < c->inst.size(); ++k) {
       const Instance& in = c->inst[k];
       const int nl = std::min(lpcs[k], in.d.nz - 2);
-      buf = std::max(buf, mixed ? mixed_buf_floats(nl, in.d.nr) : fp64_buf_doubles(nl, in.d.nr));
+      buf = std::max(buf, mixed ? mixed_packed_buf_floats(nl, in.d.nr)
+                                : fp64_buf_doubles(nl, in.d.nr));
     }
-    const int smem = (2 * kCarryStride + 2 * buf) * elem;
+    const int smem = ((mixed ? kCarryFloats : 2 * kCarryStride) + 2 * buf) * elem;
     if (smem > kMaxTileSmem) {
       bool halved = false;
       for (int& l : lpcs)
@@ -930,7 +931,8 @@ int cc_step_adi_n(cc_ctx* c, void* T_dev, int64_t n_steps, double t0, double dt_
 }
 
 int cc_set_launch(cc_ctx* c, int32_t mode, int32_t threads, int32_t rows_per_lane) {
-  if (!c || mode < 0 || mode > 4 || (threads != 64 && threads != 128 && threads != 256) ||
+  if (!c || mode < 0 || mode > 4 ||
+      (threads != 64 && threads != 128 && threads != 256 && !(threads == 384 && mode == 4)) ||
       rows_per_lane < 2 || rows_per_lane > kRowsPerLane)
     return CC_EINVAL;
   if (rows_per_lane != c->rows || threads != c->threads || mode != c->mode) c->tasks_dirty = true;
@@ -981,8 +983,9 @@ int cc_autotune(cc_ctx* c, void* T_dev, int32_t n_trial, float* best_ms, void* s
   if (rect) modes.push_back(2);
   if (rect && c->inst.size() == 1 && c->precision == CC_FP64) modes.push_back(3);
   for (int mode : modes)
-    for (int threads : {64, 128, 256})
+    for (int threads : {64, 128, 256, 384})
       for (int rows : rows_opts) {
+        if (threads == 384 && mode != 4) continue;
         cc_set_launch(c, mode, threads, rows);
         rc = cc_step_n(c, T_dev, 1, 0.0, 0.0, nullptr, nullptr, stream);  // warm and upload
         if (rc != CC_OK) break;

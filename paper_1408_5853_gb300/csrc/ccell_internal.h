@@ -172,6 +172,12 @@ CC_HOST_DEVICE inline int mixed_buf_floats(int nl, int nr) {
   const int nrp = smem_row_stride(nr);
   return (8 * nl * nrp + nl * nrp + kMixIf * CC_MAX_LAYERS * nl + 1) & ~1;
 }
+// Floats of one packed mixed tile (float4 per node, then the interface
+// values), a multiple of 4 so that a following buffer stays 16-byte aligned;
+// and the carry rows ahead of the pipelined buffers, rounded the same way.
+CC_HOST_DEVICE inline int mixed_packed_buf_floats(int nl, int nr) {
+  return (4 * nl * smem_row_stride(nr) + kMixIf * CC_MAX_LAYERS * nl + 3) & ~3;
+}
 // Largest dynamic shared memory of an FP64 tile: the opt-in limit per block
 // on sm_103 (227 KiB) less room for the kernels' static shared memory.
 constexpr int kMaxTileSmem = 226 * 1024;
@@ -320,8 +326,10 @@ int launch_step_fp64_pipe(const StepArgs& a, void* stream);
 int launch_step_mixed_pipe(const StepArgs& a, void* stream);
 int fp64_pipe_resident_blocks(int threads, int smem);
 int mixed_pipe_resident_blocks(int threads, int smem);
-// Shared memory of the pipelined tiles: two carry rows and two row buffers.
+// Shared memory of the pipelined tiles: two carry rows and two row buffers
+// (kCarryFloats: the mixed kernels' carry rows padded to 16 bytes).
 constexpr int kCarryStride = kMaxNr + (kMaxNr >> 4) + 1;
+constexpr int kCarryFloats = (2 * kCarryStride + 3) & ~3;
 // The same for the mixed-precision step (ccell_step_lines_mixed.cu).
 int launch_step_mixed_lines(const StepArgs& a, void* stream);
 int mixed_lines_resident_blocks(int threads, int smem);

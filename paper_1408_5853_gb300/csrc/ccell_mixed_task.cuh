@@ -93,7 +93,25 @@ __device__ __forceinline__ float ld_state(const float* p) {
 struct MixTile {
   double *SA, *SB, *SC, *SD;  // a, b (then the increment dT), c, d
   float *FM, *sI;             // V rho c (energy); lam_w, lam_e, kw, ke, dTw, dTe per interface
+  // packed layout (pipelined launch): per node the FP32 row (a, c, d) and
+  // V rho c; the FP64 increment later replaces (a, c) of its node
+  float4* Q;
 };
+
+// Packed rows: the FP64 increment stored over (a, c) of a node, and read back.
+__device__ __forceinline__ void put_packed_x(float4* Q, int c, double x) {
+  *reinterpret_cast<double*>(Q + c) = x;
+}
+__device__ __forceinline__ double packed_x(const float4* Q, int c) {
+  return *reinterpret_cast<const double*>(Q + c);
+}
+
+__device__ __forceinline__ MixTile mix_tile_packed_at(float* base, int nl, int nrp) {
+  MixTile B{};
+  B.Q = reinterpret_cast<float4*>(base);
+  B.sI = base + 4 * (size_t)nl * nrp;
+  return B;
+}
 
 __device__ __forceinline__ MixTile mix_tile_at(float* base, int nl, int nrp) {
   MixTile B;
@@ -112,7 +130,7 @@ __device__ __forceinline__ MixTile mix_tile_at(float* base, int nl, int nrp) {
 // the first line come from cin if carry, those north of the last line go to
 // cout.  STP: the tile holds a line of a stepped outline that is narrow or
 // borders a narrow one (other tiles skip the checks).
-template <bool ENERGY, bool CACHED, bool STP>
+template <bool ENERGY, bool CACHED, bool STP, bool PACKED = false>
 __device__ __forceinline__ void mixed_produce(const StepArgs& a, const TileTask tk, const MixTile& B,
                                               const float* __restrict__ cin, float* __restrict__ cout,
                                               bool carry, const WarpGroup& grp, EAcc& acc) {
@@ -268,12 +286,16 @@ __device__ __forceinline__ void mixed_produce(const StepArgs& a, const TileTask 
         if (own) {
           const size_t w = (size_t)q * nrp + smem_col(ic);
           // the row divided by its diagonal in FP32 (the solve takes b = 1),
-          // then widened exactly
+          // then widened exactly (packed: widened by the solve)
           const float ib = __fdividef(1.0f, fb);
-          SA[w] = widen_f32(fa * ib);
-          SC[w] = widen_f32(fc * ib);
-          SD[w] = widen_f32(fd * ib);
-          if (ENERGY) FM[w] = m;
+          if constexpr (PACKED) {
+            B.Q[w] = make_float4(fa * ib, fc * ib, fd * ib, m);
+          } else {
+            SA[w] = widen_f32(fa * ib);
+            SC[w] = widen_f32(fc * ib);
+            SD[w] = widen_f32(fd * ib);
+            if (ENERGY) FM[w] = m;
+          }
         }
         hc = hn; lc = ln;
         hn = hn2; ln = ln2;
@@ -292,7 +314,7 @@ __device__ __forceinline__ void mixed_produce(const StepArgs& a, const TileTask 
 // Phase 4 of a tile, run by the threads of g after the line solves: pair
 // update, axial boundary rows, surface trace and the energy terms, with the
 // threads over the nodes of the tile.
-template <bool ENERGY, bool TRACE, bool CACHED, bool STP>
+template <bool ENERGY, bool TRACE, bool CACHED, bool STP, bool PACKED = false>
 __device__ __forceinline__ void mixed_finish(const StepArgs& a, const TileTask tk, const MixTile& B,
                                              const WarpGroup& grp, EAcc& acc) {
   const DevInst& I = a.insts[tk.inst];
@@ -317,10 +339,10 @@ __device__ __forceinline__ void mixed_finish(const StepArgs& a, const TileTask t
       const int j = j0 + q;
       const long long rj = (long long)j * nr;
       const int c = smem_col(i);
-      const double xd = SB[(size_t)q * nrp + c];
+      const double xd = PACKED ? packed_x(B.Q, q * nrp + c) : SB[(size_t)q * nrp + c];
       bad |= not_finite(xd);
       const float x = narrow_f64(xd);
-      if (ENERGY) eE = fma(widen_f32(FM[(size_t)q * nrp + c]), xd, eE);
+      if (ENERGY) eE = fma(widen_f32(PACKED ? B.Q[q * nrp + c].w : FM[(size_t)q * nrp + c]), xd, eE);
       const float hi = ld_state<CACHED>(Hin + rj + i), lo = ld_state<CACHED>(Lin + rj + i);
       const float v = lo + x;
       float h1 = hi + v;
@@ -371,15 +393,17 @@ __device__ __forceinline__ void mixed_finish(const StepArgs& a, const TileTask t
       for (int it = grp.tid(); it < nl * n_if; it += grp.size()) {
         const int q = it / n_if;
         const int i = I.if_i[it - q * n_if];
-        const double* Bq = SB + (size_t)q * nrp;
+        auto xat = [&](int ii) {
+          return PACKED ? packed_x(B.Q, q * nrp + smem_col(ii)) : SB[(size_t)q * nrp + smem_col(ii)];
+        };
         const float* K = sI + kMixIf * it;
-        const double x = Bq[smem_col(i)];
-        const double fw = widen_f32(K[2]) * (widen_f32(K[4]) + (x - Bq[smem_col(i - 1)]));
+        const double x = xat(i);
+        const double fw = widen_f32(K[2]) * (widen_f32(K[4]) + (x - xat(i - 1)));
         const int cls = STP ? line_class(I, I.rg[i].cls, i, j0 + q) : I.rg[i].cls;
         if (cls == RC_OUTER) {
           if (I.bc_rmax == CC_DIRICHLET) eD += fw; else eN += fw;
         } else if (!STP || cls == RC_IFACE) {
-          eI += fw + widen_f32(K[3]) * (widen_f32(K[5]) + (x - Bq[smem_col(i + 1)]));
+          eI += fw + widen_f32(K[3]) * (widen_f32(K[5]) + (x - xat(i + 1)));
         }
       }
       acc.e[0] += eE;
@@ -388,6 +412,76 @@ __device__ __forceinline__ void mixed_finish(const StepArgs& a, const TileTask t
       acc.e[4] += eN;
     }
     if (TRACE) acc.tr += tr;
+  }
+}
+
+// Line solves of a mixed tile with packed rows (unit diagonal), run by one
+// group of warps (warp: index in the group): the FP32 rows are widened on
+// read, the eliminated FP64 coefficients of a lane's segment stay in its
+// registers, and each solution replaces (a, c) of its node.  Same segment
+// elimination, separator cyclic reduction and back substitution as
+// solve_tile_lines.
+__device__ __forceinline__ void solve_mixed_packed(float4* __restrict__ Q, int nl, int nr, int G,
+                                                   int warp) {
+  const int nrp = smem_row_stride(nr);
+  const int lg = __ffs(G) - 1;
+  const int lane = threadIdx.x & 31;
+  const int grp = lane >> lg, l = lane & (G - 1);
+  const int q_req = warp * (32 >> lg) + grp;
+  const bool active = q_req < nl;
+  const int q = active ? q_req : nl - 1;  // idle lane groups solve a valid line, store nothing
+  const int i_lo = (l * nr) >> lg;
+  const int i_hi = ((l + 1) * nr) >> lg;
+  const int cnt = i_hi - i_lo;  // 2 .. kRowsPerLane
+  float4* R = Q + (size_t)q * nrp;
+  double cc[kRowsPerLane], aa[kRowsPerLane], dd[kRowsPerLane];
+  double pc = 0.0, pa = 0.0, pd = 0.0;
+  double Dacc = 0.0, Aacc = 0.0, P = 1.0;
+  double ae = 0.0, ce = 0.0, de = 0.0;
+#pragma unroll
+  for (int k = 0; k < kRowsPerLane; ++k) {
+    if (k < cnt) {
+      const float4 v = R[smem_col(i_lo + k)];
+      const double ra = widen_f32(v.x), rc = widen_f32(v.y), rd = widen_f32(v.z);
+      if (k < cnt - 1) {
+        double c1, a1, d1;
+        if (k == 0) {  // unit diagonal: nothing to eliminate
+          c1 = rc;
+          a1 = ra;
+          d1 = rd;
+        } else {
+          const double r = frcp46(fma(-ra, pc, 1.0));
+          c1 = rc * r;
+          a1 = -ra * pa * r;
+          d1 = fma(-ra, pd, rd) * r;
+        }
+        cc[k] = c1;
+        aa[k] = a1;
+        dd[k] = d1;
+        Dacc = fma(P, d1, Dacc);
+        Aacc = fma(P, a1, Aacc);
+        P = -P * c1;
+        pc = c1;
+        pa = a1;
+        pd = d1;
+      } else {
+        ae = ra; ce = rc; de = rd;
+      }
+    }
+  }
+  const double xs = solve_separators<false>(ae, 1.0, ce, de, pa, pc, pd, Dacc, Aacc, P, G, l);
+  const double L = __shfl_up_sync(kFull, xs, 1, G);
+  if (active) {
+    double xn = xs;
+    put_packed_x(R, smem_col(i_hi - 1), xs);
+#pragma unroll
+    for (int k = kRowsPerLane - 2; k >= 0; --k) {
+      if (k <= cnt - 2) {
+        const double x = fma(-cc[k], xn, fma(-aa[k], L, dd[k]));
+        put_packed_x(R, smem_col(i_lo + k), x);
+        xn = x;
+      }
+    }
   }
 }
 

@@ -11,7 +11,11 @@
 // "full" barrier per buffer (producers arrive, consumers wait) and an "empty"
 // barrier per buffer (consumers arrive, producers wait).  The axial fluxes
 // handed from tile to tile stay with the producers.  A tile holds as many
-// lines as the consumer warps solve at once.
+// lines as the consumer warps solve at once.  The mixed-precision rows are
+// kept as packed FP32 (a, c, d) per node -- the values the FP32 assembly
+// produces, widened exactly by the consumers -- and the consumers hold the
+// eliminated FP64 coefficients in registers, which leaves room in shared
+// memory for more warps.
 #include <cuda_runtime.h>
 
 #include "ccell_fp64_task.cuh"
@@ -62,7 +66,7 @@ __device__ __forceinline__ void pipe_tiles(const StepArgs& a, EAcc& acc, Produce
 }
 
 template <bool ENERGY, bool TRACE>
-__global__ void __launch_bounds__(256, 1) step_fp64_pipe_kernel(const StepArgs a) {
+__global__ void __launch_bounds__(384, 1) step_fp64_pipe_kernel(const StepArgs a) {
   extern __shared__ double sm[];
   double* buf0 = sm + 2 * kCarryStride;
   EAcc acc;
@@ -99,14 +103,15 @@ __global__ void __launch_bounds__(256, 1) step_fp64_pipe_kernel(const StepArgs a
 }
 
 template <bool ENERGY, bool TRACE>
-__global__ void __launch_bounds__(256, 1) step_mixed_pipe_kernel(const StepArgs a) {
-  extern __shared__ float smf[];
-  float* buf0 = smf + 2 * kCarryStride;
+__global__ void __launch_bounds__(384, 1) step_mixed_pipe_kernel(const StepArgs a) {
+  extern __shared__ float4 smq[];
+  float* smf = reinterpret_cast<float*>(smq);
+  float* buf0 = smf + kCarryFloats;
   EAcc acc;
   eacc_init(acc);
-  auto tile = [&](const TileTask& tk, int b) {
+  auto tile = [&](const TileTask& tk, int b) {  // packed rows
     const int nrp = smem_row_stride(a.insts[tk.inst].nr);
-    return mix_tile_at(buf0 + (size_t)b * a.pipe_buf, tk.nl, nrp);
+    return mix_tile_packed_at(buf0 + (size_t)b * a.pipe_buf, tk.nl, nrp);
   };
   pipe_tiles<ENERGY, TRACE>(
       a, acc,
@@ -114,21 +119,21 @@ __global__ void __launch_bounds__(256, 1) step_mixed_pipe_kernel(const StepArgs 
         const DevInst& I = a.insts[tk.inst];
         const int nrp = smem_row_stride(I.nr);
         if (tk.j0 + tk.nl >= I.j_narrow)
-          mixed_produce<ENERGY, true, true>(a, tk, tile(tk, b), smf + (size_t)(par ^ 1) * nrp,
-                                            smf + (size_t)par * nrp, carry, grp, ac);
+          mixed_produce<ENERGY, true, true, true>(a, tk, tile(tk, b), smf + (size_t)(par ^ 1) * nrp,
+                                                  smf + (size_t)par * nrp, carry, grp, ac);
         else
-          mixed_produce<ENERGY, true, false>(a, tk, tile(tk, b), smf + (size_t)(par ^ 1) * nrp,
-                                             smf + (size_t)par * nrp, carry, grp, ac);
+          mixed_produce<ENERGY, true, false, true>(a, tk, tile(tk, b), smf + (size_t)(par ^ 1) * nrp,
+                                                   smf + (size_t)par * nrp, carry, grp, ac);
       },
       [&](const TileTask& tk, int b, const WarpGroup& grp, EAcc& ac) {
         const DevInst& I = a.insts[tk.inst];
         const MixTile B = tile(tk, b);
-        solve_tile_lines<false>(B.SA, B.SB, B.SC, B.SD, tk.nl, I.nr, I.G, grp.warp());
+        solve_mixed_packed(B.Q, tk.nl, I.nr, I.G, grp.warp());
         grp.sync();  // the stores read every consumer warp's solutions
         if (tk.j0 + tk.nl >= I.j_narrow)
-          mixed_finish<ENERGY, TRACE, true, true>(a, tk, B, grp, ac);
+          mixed_finish<ENERGY, TRACE, true, true, true>(a, tk, B, grp, ac);
         else
-          mixed_finish<ENERGY, TRACE, true, false>(a, tk, B, grp, ac);
+          mixed_finish<ENERGY, TRACE, true, false, true>(a, tk, B, grp, ac);
       });
   eacc_flush<ENERGY, TRACE>(a, acc);
 }

@@ -118,10 +118,11 @@ def test_launch_shape_validation_and_round_trip():
     sol = ccell.Solver(cfg)
     try:
         for shape in ((1, 64, 4), (0, 256, 16), (1, 128, 8), (2, 256, 16), (2, 64, 4),
-                      (3, 128, 16), (4, 256, 16), (4, 64, 2)):
+                      (3, 128, 16), (4, 256, 16), (4, 64, 2), (4, 384, 16)):
             sol.set_launch(*shape)
             assert ccell.cc_get_launch(sol.ctx) == shape
-        for bad in ((5, 128, 16), (-1, 128, 16), (0, 96, 16), (0, 128, 1), (0, 128, 32)):
+        for bad in ((5, 128, 16), (-1, 128, 16), (0, 96, 16), (0, 128, 1), (0, 128, 32),
+                    (0, 384, 16), (2, 384, 16)):
             with pytest.raises(ccell.CCError):
                 sol.set_launch(*bad)
     finally:

@@ -183,3 +183,36 @@ def test_gpu_adjoint_checkpoint_invariance(ckpt):
     assert abs(lg[0] - lo) <= 1e-10 * lo
     assert np.max(np.abs(gg - go)) <= 1e-8 * np.max(np.abs(go)), (gg, go)
     assert np.max(np.abs(dg.reshape(T0.shape) - do)) <= 1e-8 * np.max(np.abs(do))
+
+
+def test_gpu_adjoint_central_differences_256x1024():
+    """Central differences of the GPU loss (h = 1e-6 relative) on the gradient
+    workload's own grid (5 layers, 256 x 1024, tanh pulse edges), 400 steps
+    across the pulse's switch-off, for the heater amplitude, the pulse length and
+    the heater layer's conductivity and capacity scales."""
+    cfg = inputs.adjoint_case()
+    n = 400
+    t0 = cfg["source"]["t_on"] - 200 * cfg["dt"]   # the smoothed falling edge mid-run
+    T0 = inputs.initial_field(cfg, "smooth", seed=3)
+    target = inputs.target_waveform(cfg, t0 + cfg["dt"] * np.arange(1, n + 1))
+    _, gg, _ = _gpu_adjoint([cfg], [T0], n, t0, [target], ckpt=128, want_dT0=False)
+    L = len(cfg["layers"])
+    heater = cfg["source"]["layer"]
+    for k in (0, 1, 2 + heater, 2 + L + heater):
+        h = 1e-6
+        vals = []
+        for sgn in (+1, -1):
+            c = copy.deepcopy(cfg)
+            if k == 0:
+                base = c["source"]["q0"]
+                c["source"]["q0"] = base * (1 + sgn * h)
+            elif k == 1:
+                base = c["source"]["t_on"]
+                c["source"]["t_on"] = base * (1 + sgn * h)
+            else:
+                key = "lam_scale" if k < 2 + L else "cap_scale"
+                base = c["layers"][heater].get(key, 1.0)
+                c["layers"][heater][key] = base * (1 + sgn * h)
+            vals.append(_gpu_loss(c, T0, n, t0, target))
+        fd = (vals[0] - vals[1]) / (2 * h * base)
+        assert abs(fd - gg[k]) <= 1e-5 * abs(fd) + 1e-9 * np.max(np.abs(gg)), (k, fd, gg[k])

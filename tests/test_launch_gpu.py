@@ -32,7 +32,8 @@ def _run(cfgs, T0s, n, precision, shape, t0=0.0):
 
 
 SHAPES = [(1, 128, 16), (1, 256, 8), (1, 64, 4), (0, 64, 4), (0, 256, 8), (2, 256, 16),
-          (2, 128, 8), (2, 64, 4), (4, 256, 16), (4, 128, 8), (4, 64, 4)]
+          (2, 128, 8), (2, 64, 4), (4, 256, 16), (4, 128, 8), (4, 64, 4), (4, 384, 16),
+          (4, 384, 4)]
 
 
 @pytest.mark.parametrize("shape", SHAPES)
