@@ -73,7 +73,7 @@ struct cc_ctx {
   TileTask* d_ptiles = nullptr;
   int* d_pcta = nullptr;
   size_t ptiles_cap = 0, pcta_cap = 0;
-  int pipe_blocks = 0, pipe_smem = 0, pipe_buf = 0;
+  int pipe_blocks = 0, pipe_smem = 0, pipe_buf = 0, pipe_producers = 0;
   void* d_T2 = nullptr;       // ping-pong partner of the caller's field
   float* d_lo = nullptr;      // mixed precision: low-order parts (two buffers)
   double* d_s = nullptr;      // waveform table
@@ -323,8 +323,12 @@ int cut_warp_tasks(cc_ctx* c) {
 // grid of resident blocks taking equal node shares.
 int cut_pipe_tiles(cc_ctx* c) {
   c->pipe_ok = false;
-  const int warps = c->threads / 32, cons = warps - warps / 2;
   const bool mixed = c->precision == CC_MIXED;
+  // producer / consumer warps: half and half for the mixed step, three
+  // quarters producers for the FP64 step (at least one of each)
+  const int warps = c->threads / 32;
+  const int prod = std::max(1, std::min(warps - 1, mixed ? warps / 2 : (3 * warps) / 4));
+  const int cons = warps - prod;
   const int elem = mixed ? (int)sizeof(float) : (int)sizeof(double);
   std::vector<int> lpcs(c->inst.size());
   for (size_t k = 0; k < c->inst.size(); ++k) lpcs[k] = cons * (32 / c->inst[k].G);
@@ -359,6 +363,7 @@ int cut_pipe_tiles(cc_ctx* c) {
     c->pipe_blocks = B;
     c->pipe_smem = smem;
     c->pipe_buf = buf;
+    c->pipe_producers = prod;
     c->pipe_ok = true;
     return CC_OK;
   }
@@ -771,6 +776,7 @@ int cc_step_n(cc_ctx* c, void* T_dev, int64_t n_steps, double t0, double dt_s, d
       p.n_cta = c->pipe_blocks;
       p.smem_bytes = c->pipe_smem;
       p.pipe_buf = c->pipe_buf;
+      p.pipe_producers = c->pipe_producers;
       if (c->precision == CC_FP64) {
         r = launch_step_fp64_pipe(p, stream);
       } else {

@@ -225,8 +225,10 @@ struct StepArgs {
   double* xb;
   unsigned* nbr_flags;
   // pipelined tiles (launch mode 4): elements (FP64: doubles, mixed: floats)
-  // of one of the two row buffers after the two carry rows
+  // of one of the two row buffers after the two carry rows, and the number
+  // of producer warps (the rest of the block's warps consume)
   int pipe_buf;
+  int pipe_producers;
   // persistent launches: grid barrier state [count, generation], bounded wait
   unsigned* bar;
   unsigned bar_extra;    // extra arrivals expected (nonzero only to test the timeout)

@@ -5,7 +5,10 @@
 // one after the other with block barriers between them, so while the block
 // assembles rows the FP64 line solves wait and vice versa (in the mixed
 // precision step the rows are FP32 work and the solves FP64 work).  Here the
-// block's warps split into producers and consumers with two row buffers:
+// block's warps split into producers and consumers (a split chosen by the
+// host from the phases' work: the FP64 rows cost about twice the FP64
+// solves, the FP32 rows of the mixed step about as much as its FP64 solves)
+// with two row buffers:
 // producers assemble tile k+1 into one buffer while consumers solve and store
 // tile k from the other.  Buffers change hands through named barriers: a
 // "full" barrier per buffer (producers arrive, consumers wait) and an "empty"
@@ -30,7 +33,7 @@ constexpr int kBarProd = 1, kBarCons = 2, kBarFull = 3, kBarEmpty = 5;
 template <bool ENERGY, bool TRACE, class Produce, class Consume>
 __device__ __forceinline__ void pipe_tiles(const StepArgs& a, EAcc& acc, Produce produce,
                                            Consume consume) {
-  const int nw = blockDim.x >> 5, P = nw / 2, C = nw - P, NT = blockDim.x;
+  const int nw = blockDim.x >> 5, P = a.pipe_producers, C = nw - P, NT = blockDim.x;
   const bool producer = (int)(threadIdx.x >> 5) < P;
   const WarpGroup grp = producer ? WarpGroup{0, P, kBarProd} : WarpGroup{P, C, kBarCons};
   const int t0 = a.cta_start[blockIdx.x], t1 = a.cta_start[blockIdx.x + 1];
