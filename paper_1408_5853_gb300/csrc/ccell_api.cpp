@@ -594,6 +594,38 @@ int upload(cc_ctx* c, const std::vector<double>& dts, cudaStream_t st) {
 
 }  // namespace
 
+namespace {
+
+// One time step with the per-step kernel of the context's launch mode: the
+// pipelined tiles (mode 4), the warp-owned lines (mode 2) or the CTA tiles
+// (modes 0, 1 and 3, and any mode whose tiles the context could not use).
+int launch_one_step(const cc_ctx* c, const StepArgs& a, void* stream) {
+  if (c->mode == 4 && c->pipe_ok) {
+    StepArgs p = a;
+    p.tiles = c->d_ptiles;
+    p.cta_start = c->d_pcta;
+    p.n_cta = c->pipe_blocks;
+    p.smem_bytes = c->pipe_smem;
+    p.pipe_buf = c->pipe_buf;
+    p.pipe_producers = c->pipe_producers;
+    return c->precision == CC_FP64 ? launch_step_fp64_pipe(p, stream)
+                                   : launch_step_mixed_pipe(p, stream);
+  }
+  if (c->mode == 2 && c->lines_ok) {
+    StepArgs w = a;
+    w.tiles = c->d_wtasks;
+    w.cta_start = c->d_wcta;
+    w.n_cta = c->lines_blocks;
+    w.smem_bytes = c->lines_smem;
+    w.warp_doubles = c->lines_warp_doubles;
+    return c->precision == CC_FP64 ? launch_step_fp64_lines(w, stream)
+                                   : launch_step_mixed_lines(w, stream);
+  }
+  return c->precision == CC_FP64 ? launch_step_fp64(a, stream) : launch_step_mixed(a, stream);
+}
+
+}  // namespace
+
 extern "C" {
 
 int cc_create_geometry(const cc_geometry_desc* desc, int32_t n_instances, cc_ctx** out) {
@@ -768,43 +800,11 @@ int cc_step_n(cc_ctx* c, void* T_dev, int64_t n_steps, double t0, double dt_s, d
     a.step = s;
     a.Tin = bufs[s & 1];
     a.Tout = bufs[(s + 1) & 1];
-    int r;
-    if (c->mode == 4 && c->pipe_ok) {
-      StepArgs p = a;
-      p.tiles = c->d_ptiles;
-      p.cta_start = c->d_pcta;
-      p.n_cta = c->pipe_blocks;
-      p.smem_bytes = c->pipe_smem;
-      p.pipe_buf = c->pipe_buf;
-      p.pipe_producers = c->pipe_producers;
-      if (c->precision == CC_FP64) {
-        r = launch_step_fp64_pipe(p, stream);
-      } else {
-        p.lo_in = c->d_lo + (s & 1) * c->total_nodes;
-        p.lo_out = c->d_lo + ((s + 1) & 1) * c->total_nodes;
-        r = launch_step_mixed_pipe(p, stream);
-      }
-    } else if (c->mode == 2 && c->lines_ok) {
-      StepArgs w = a;
-      w.tiles = c->d_wtasks;
-      w.cta_start = c->d_wcta;
-      w.n_cta = c->lines_blocks;
-      w.smem_bytes = c->lines_smem;
-      w.warp_doubles = c->lines_warp_doubles;
-      if (c->precision == CC_FP64) {
-        r = launch_step_fp64_lines(w, stream);
-      } else {
-        w.lo_in = c->d_lo + (s & 1) * c->total_nodes;
-        w.lo_out = c->d_lo + ((s + 1) & 1) * c->total_nodes;
-        r = launch_step_mixed_lines(w, stream);
-      }
-    } else if (c->precision == CC_FP64) {
-      r = launch_step_fp64(a, stream);
-    } else {
+    if (c->precision == CC_MIXED) {
       a.lo_in = c->d_lo + (s & 1) * c->total_nodes;
       a.lo_out = c->d_lo + ((s + 1) & 1) * c->total_nodes;
-      r = launch_step_mixed(a, stream);
     }
+    const int r = launch_one_step(c, a, stream);
     if (r) return CC_ECUDA;
   }
   if ((n_steps & 1) && !in_place) {
@@ -1147,7 +1147,7 @@ int adjoint_impl(cc_ctx* c, const void* T0_dev, int64_t n_steps, double t0, doub
     a.Tin = cur;
     a.Tout = segs + nodes * slot(s + 1);
     a.trace = trace;
-    if (launch_step_fp64(a, stream)) return CC_ECUDA;
+    if (launch_one_step(c, a, stream)) return CC_ECUDA;
   }
   if (target) {
     if (launch_adj_seed(c->d_inst, n, trace, target, n_steps, seed, loss_dev, stream))
@@ -1182,7 +1182,7 @@ int adjoint_impl(cc_ctx* c, const void* T0_dev, int64_t n_steps, double t0, doub
       a.step = s;
       a.Tin = segs + nodes * (s - lo);
       a.Tout = segs + nodes * (s - lo + 1);
-      if (launch_step_fp64(a, stream)) return CC_ECUDA;
+      if (launch_one_step(c, a, stream)) return CC_ECUDA;
     }
     for (long long s = hi - 1; s >= lo; --s) {
       b.step = s;

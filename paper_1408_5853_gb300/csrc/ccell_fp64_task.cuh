@@ -36,11 +36,15 @@
 
 namespace ccell {
 
-// rho c(T) / tau from the folded material constants
+// rho c(T) / tau from the folded material constants.  The Debye-saturated
+// form takes its reciprocal to 2^-46 (one Newton step): rho c / tau multiplies
+// only the increment That - T of its row (Eq. (ABC): (rho c / tau)(That - T) =
+// the fluxes + X), so the relative error it leaves in a step's increment,
+// <= 2^-46, is below the FP64 rounding of the temperature itself.
 __device__ __forceinline__ double rct_eval(const DevMaterial& M, double T) {
   if (M.cap_model == 1) {
     const double T3 = T * T * T;
-    return M.rct_k * T3 * frcp(fma(M.inv_theta3, T3, 1.0));
+    return M.rct_k * T3 * frcp46(fma(M.inv_theta3, T3, 1.0));
   }
   if (M.cap_model == 0) return M.rct_k;
   const double* a = M.cap_poly;
