@@ -138,8 +138,8 @@ def run_ours(args, world, rank, local):
             sol.set_launch(*[int(v) for v in args.launch.split(",")])
         elif precision == ccell.MIXED:
             # the library's autotuner picks the mixed path's launch shape (field
-            # restored); the FP64 headline keeps the default shape (one launch
-            # per step, 256 threads), which the autotuner matches within noise
+            # restored); the FP64 headline keeps the library's default shape
+            # (pipelined tiles, 128 threads)
             sol.autotune(T, n_trial=args.tune_steps)
         trace = torch.zeros(2 * n_in, dtype=torch.float64, device=dev)
         energy = torch.zeros(5, dtype=torch.float64, device=dev)
@@ -373,7 +373,13 @@ def run_adjoint(args, dev) -> dict:
 
     from paper_1408_5853_gb300 import ccell, inputs
     out = {}
-    for label, n_inst, n in (("single", 1, args.adj_steps), ("batch64", 64, args.adj_batch_steps)):
+    # checkpoints every 256 steps (the workload's setting); then every state of
+    # the single run kept in HBM (about 84 GB at 40 000 steps), which removes
+    # the recompute
+    runs = [("single", 1, args.adj_steps, 256), ("batch64", 64, args.adj_batch_steps, 256)]
+    if args.adj_keep_all:
+        runs.append(("single_all_states", 1, args.adj_steps, args.adj_steps))
+    for label, n_inst, n, ckpt in runs:
         cfg = inputs.adjoint_case()
         cfgs = [cfg] * n_inst
         sol = ccell.Solver(cfgs)
@@ -388,13 +394,25 @@ def run_adjoint(args, dev) -> dict:
         torch.cuda.synchronize()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record()
-        loss, grad, _ = sol.adjoint(T0, n, 0.0, 0.0, tgt, ckpt_every=256)
+        loss, grad, _ = sol.adjoint(T0, n, 0.0, 0.0, tgt, ckpt_every=ckpt)
         e1.record()
         torch.cuda.synchronize()
         sol.sync()
         ms = e0.elapsed_time(e1)
         nodes = cfg["nr"] * cfg["nz"] * n_inst
+        # one forward step of the same context, for the reverse step's cost in forward steps
+        T1 = T0.clone()
+        sol.step(T1, 64, 0.0, 0.0, None, None)
+        torch.cuda.synchronize()
+        f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        f0.record()
+        sol.step(T1, 256, 0.0, 0.0, None, None)
+        f1.record()
+        torch.cuda.synchronize()
+        fwd_ms = f0.elapsed_time(f1) / 256
         out[label] = {"instances": n_inst, "grid": f"{cfg['nr']}x{cfg['nz']}", "steps": n,
+                      "ckpt_every": ckpt, "ms_per_reverse_step": ms / n,
+                      "forward_steps_per_reverse_step": (ms / n) / fwd_ms,
                       "ms_per_gradient": ms / n_inst, "ms_total": ms,
                       "forward_equivalent_node_updates_per_s": nodes * n / (ms / 1e3),
                       "loss": float(loss[0].item()), "grad_norm": float(grad.norm().item())}
@@ -651,6 +669,8 @@ def main():
     ap.add_argument("--batch-inner", type=int, default=20, help="time steps per batched replay")
     ap.add_argument("--adj-steps", type=int, default=40000)
     ap.add_argument("--adj-batch-steps", type=int, default=512)
+    ap.add_argument("--no-adj-keep-all", dest="adj_keep_all", action="store_false",
+                    help="skip the adjoint run that keeps every state (no recompute)")
     ap.add_argument("--paper-ms", type=float, default=0.08,
                     help="simulated ms of the paper-cell run; with the printed graphite c_V fit "
                          "(negative above ~22 K) the heater stays below 20 K up to ~0.1 ms")

@@ -249,7 +249,10 @@ int cc_step_adi_n(cc_ctx* ctx, void* T_dev, int64_t n_steps, double t0_s, double
  *   block's warps assemble the rows of the next tile while the other half
  *   solve and store the current one, two row buffers changing hands through
  *   named barriers (every context).
- *   threads: 64, 128 or 256 per block; 384 with mode 4 only.
+ *   threads: 64, 128 or 256 per block; 384 with mode 4 only; 512 with mode
+ *   4 in CC_MIXED contexts only.
+ *   Default (a new context): mode 4 with 128 threads per block for CC_FP64,
+ *   384 for CC_MIXED, rows_per_lane 16.
  *   rows_per_lane: 2..16, target rows per lane of the line solve; a line of
  *   nr rows is split over the smallest power-of-two number of lanes G <= 32
  *   that meets it (at least 2 rows per lane, at most 16).

@@ -84,9 +84,10 @@ struct cc_ctx {
   // adjoint scratch, grown on demand
   double* d_adj = nullptr;
   size_t adj_cap = 0;
-  // launch shape: 0 one launch per step, 1 one persistent cooperative launch;
-  // threads per block; target rows per lane (sets the lanes per line G)
-  int mode = 0, threads = 256, rows = kRowsPerLane;
+  // launch shape (modes as in cc_set_launch), threads per block, target rows
+  // per lane (sets the lanes per line G); the default is set per precision
+  // at creation
+  int mode = 4, threads = 128, rows = kRowsPerLane;
   bool tasks_dirty = true;
   void* d_tune = nullptr;  // autotuner copy of the caller's field
   // ADI variant: column tasks and scratch, built on first use
@@ -634,6 +635,11 @@ int cc_create_geometry(const cc_geometry_desc* desc, int32_t n_instances, cc_ctx
   cc_ctx* c = new (std::nothrow) cc_ctx();
   if (!c) return CC_ENOMEM;
   c->precision = desc[0].precision;
+  // default launch: pipelined tiles, the block size measured fastest for the
+  // precision on GB300 (FP64: 3 producer + 1 consumer warps, three blocks per
+  // SM; mixed: 6 + 6 warps)
+  c->mode = 4;
+  c->threads = c->precision == CC_FP64 ? 128 : 384;
   long long off = 0;
   for (int k = 0; k < n_instances; ++k) {
     const int v = valid_desc(desc[k]);
@@ -938,7 +944,8 @@ int cc_step_adi_n(cc_ctx* c, void* T_dev, int64_t n_steps, double t0, double dt_
 
 int cc_set_launch(cc_ctx* c, int32_t mode, int32_t threads, int32_t rows_per_lane) {
   if (!c || mode < 0 || mode > 4 ||
-      (threads != 64 && threads != 128 && threads != 256 && !(threads == 384 && mode == 4)) ||
+      (threads != 64 && threads != 128 && threads != 256 && !(threads == 384 && mode == 4) &&
+       !(threads == 512 && mode == 4 && c->precision == CC_MIXED)) ||
       rows_per_lane < 2 || rows_per_lane > kRowsPerLane)
     return CC_EINVAL;
   if (rows_per_lane != c->rows || threads != c->threads || mode != c->mode) c->tasks_dirty = true;
@@ -989,9 +996,10 @@ int cc_autotune(cc_ctx* c, void* T_dev, int32_t n_trial, float* best_ms, void* s
   if (rect) modes.push_back(2);
   if (rect && c->inst.size() == 1 && c->precision == CC_FP64) modes.push_back(3);
   for (int mode : modes)
-    for (int threads : {64, 128, 256, 384})
+    for (int threads : {64, 128, 256, 384, 512})
       for (int rows : rows_opts) {
-        if (threads == 384 && mode != 4) continue;
+        if (threads >= 384 && mode != 4) continue;
+        if (threads == 512 && c->precision != CC_MIXED) continue;
         cc_set_launch(c, mode, threads, rows);
         rc = cc_step_n(c, T_dev, 1, 0.0, 0.0, nullptr, nullptr, stream);  // warm and upload
         if (rc != CC_OK) break;

@@ -105,8 +105,10 @@ __global__ void __launch_bounds__(384, 1) step_fp64_pipe_kernel(const StepArgs a
   eacc_flush<ENERGY, TRACE>(a, acc);
 }
 
-template <bool ENERGY, bool TRACE>
-__global__ void __launch_bounds__(384, 1) step_mixed_pipe_kernel(const StepArgs a) {
+// MAXT: the largest block the variant is compiled for (its register budget:
+// 384 threads leave about 170 registers a thread, 512 threads 128).
+template <bool ENERGY, bool TRACE, int MAXT>
+__global__ void __launch_bounds__(MAXT, 1) step_mixed_pipe_kernel(const StepArgs a) {
   extern __shared__ float4 smq[];
   float* smf = reinterpret_cast<float*>(smq);
   float* buf0 = smf + kCarryFloats;
@@ -146,7 +148,7 @@ static KernelCache& fp64_pipe_cache() {
   static KernelCache c;
   return c;
 }
-template <bool ENERGY, bool TRACE>
+template <bool ENERGY, bool TRACE, int MAXT>
 static KernelCache& mixed_pipe_cache() {
   static KernelCache c;
   return c;
@@ -154,12 +156,16 @@ static KernelCache& mixed_pipe_cache() {
 
 template <bool MIXED, bool ENERGY, bool TRACE>
 static int pipe_variant_resident(int threads, int smem) {
-  if constexpr (MIXED)
-    return cached_resident(mixed_pipe_cache<ENERGY, TRACE>(), step_mixed_pipe_kernel<ENERGY, TRACE>,
-                           threads, smem, kMaxTileSmem);
-  else
+  if constexpr (MIXED) {
+    if (threads > 384)
+      return cached_resident(mixed_pipe_cache<ENERGY, TRACE, 512>(),
+                             step_mixed_pipe_kernel<ENERGY, TRACE, 512>, threads, smem, kMaxTileSmem);
+    return cached_resident(mixed_pipe_cache<ENERGY, TRACE, 384>(),
+                           step_mixed_pipe_kernel<ENERGY, TRACE, 384>, threads, smem, kMaxTileSmem);
+  } else {
     return cached_resident(fp64_pipe_cache<ENERGY, TRACE>(), step_fp64_pipe_kernel<ENERGY, TRACE>,
                            threads, smem, kMaxTileSmem);
+  }
 }
 
 template <bool MIXED>
@@ -175,9 +181,12 @@ int mixed_pipe_resident_blocks(int threads, int smem) { return pipe_resident<tru
 template <bool MIXED, bool ENERGY, bool TRACE>
 static int launch_pipe_variant(const StepArgs& a, cudaStream_t st) {
   if (pipe_variant_resident<MIXED, ENERGY, TRACE>(a.threads, a.smem_bytes) < 0) return -1;
-  if constexpr (MIXED)
-    step_mixed_pipe_kernel<ENERGY, TRACE><<<a.n_cta, a.threads, a.smem_bytes, st>>>(a);
-  else
+  if constexpr (MIXED) {
+    if (a.threads > 384)
+      step_mixed_pipe_kernel<ENERGY, TRACE, 512><<<a.n_cta, a.threads, a.smem_bytes, st>>>(a);
+    else
+      step_mixed_pipe_kernel<ENERGY, TRACE, 384><<<a.n_cta, a.threads, a.smem_bytes, st>>>(a);
+  } else
     step_fp64_pipe_kernel<ENERGY, TRACE><<<a.n_cta, a.threads, a.smem_bytes, st>>>(a);
   return 0;
 }

@@ -113,6 +113,31 @@ def test_descriptor_and_material_validation():
         ccell.cc_destroy(ctx)
 
 
+def test_default_launch_shape_per_precision():
+    for precision, threads in ((ccell.FP64, 128), (ccell.MIXED, 384)):
+        sol = ccell.Solver(inputs.small_case(q0=1.0), precision=precision)
+        try:
+            assert ccell.cc_get_launch(sol.ctx) == (4, threads, 16)
+        finally:
+            sol.close()
+
+
+def test_mixed_only_512_thread_blocks():
+    for precision, ok in ((ccell.FP64, False), (ccell.MIXED, True)):
+        sol = ccell.Solver(inputs.small_case(q0=1.0), precision=precision)
+        try:
+            if ok:
+                sol.set_launch(4, 512, 16)
+                assert ccell.cc_get_launch(sol.ctx) == (4, 512, 16)
+            else:
+                with pytest.raises(ccell.CCError):
+                    sol.set_launch(4, 512, 16)
+            with pytest.raises(ccell.CCError):
+                sol.set_launch(0, 512, 16)
+        finally:
+            sol.close()
+
+
 def test_launch_shape_validation_and_round_trip():
     cfg = inputs.small_case(q0=1.0)
     sol = ccell.Solver(cfg)

@@ -36,8 +36,8 @@ SHAPES = [(1, 128, 16), (1, 256, 8), (1, 64, 4), (0, 64, 4), (0, 256, 8), (2, 25
           (4, 384, 4)]
 
 
-@pytest.mark.parametrize("shape", SHAPES)
-@pytest.mark.parametrize("precision", [0, 1])
+@pytest.mark.parametrize("shape,precision", [(s, p) for s in SHAPES for p in (0, 1)] +
+                         [((4, 512, 16), 1), ((4, 512, 4), 1)])
 def test_launch_shapes_parity(shape, precision):
     cfgs = inputs.batched_cases(seed=1, n=5)
     T0s = []
