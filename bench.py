@@ -36,20 +36,22 @@ BYTES_PER_NODE_FP64 = 16      # read T^n + write T^{n+1}
 BYTES_PER_NODE_MIXED = 8
 FLOPS_PER_NODE_FP64 = 150     # FP64 operations per node-update (2 power laws ~ 2x(log+exp), 1 div, 1 rcp, ~30 fma/add/mul)
 
-# DRAM bytes (read + write) of one step_fp64_kernel launch (one launch per step, 256 threads)
+# DRAM bytes (read + write) of one step_fp64_pipe_kernel launch (launch mode 4, 128 threads)
 # on the 512x4096 workload, from the ncu capture summarised in
-# profiles/step_fp64_kernel_512x4096.md (cache flushed before the launch).  Valid only for the
-# kernel as captured there: reset to None when the kernel changes.
-STEP_FP64_TRAFFIC_512x4096 = 17.251328e6 + 1.536e3
+# profiles/step_fp64_pipe_kernel_512x4096.md (cache flushed before the launch).  Valid only for
+# the kernel as captured there: reset to None when the kernel changes.
+STEP_FP64_TRAFFIC_512x4096 = 17.273088e6
 FP64_PEAK_NOMINAL_TFLOPS = 152 * 4 * 0.5 * 2 * 2.07e9 / 1e12   # SMs x SMSPs x DFMA lanes/clk x 2 x max clock
 # Per launch mode of the FP64 headline: the dominant kernel, the FP64-pipe thread-instructions it
 # executes per node-update on the 512x4096 workload (ncu sm__thread_inst_executed_pipe_fp64_pred_on
 # of one launch / nodes) and the summary that holds the capture; None once the kernel changes until
 # it is captured again.
 EXECUTED_FP64 = {
-    0: ("step_fp64_kernel", 63.0, "profiles/step_fp64_kernel_512x4096.md"),
+    0: ("step_fp64_kernel", None, None),
     1: ("steps_fp64_persistent_kernel", None, None),
     2: ("step_fp64_lines_kernel", None, None),
+    3: ("steps_fp64_resident_kernel", None, None),
+    4: ("step_fp64_pipe_kernel", 58.1, "profiles/step_fp64_pipe_kernel_512x4096.md"),
 }
 L2_FLUSH_BYTES = 256 << 20
 
@@ -273,7 +275,7 @@ def run_ours(args, world, rank, local):
                      "frac": achieved_tflops / fp64_peak_tflops,
                      "traffic": (STEP_FP64_TRAFFIC_512x4096
                                  if (cfg["nr"], cfg["nz"]) == (512, 4096)
-                                 and tuple(launch_shape) == (0, 256, 16) else None),
+                                 and tuple(launch_shape) == (4, 128, 16) else None),
                      "traffic_note": "ncu dram__bytes_read.sum + dram__bytes_write.sum per launch, "
                                      "cold L2 (the output rows stay in L2)",
                      "peak_source": "measured on this GPU: cc_measure_fp64_rate, 8 independent "
@@ -334,7 +336,11 @@ def run_batched(args, dev) -> dict:
     total = sol.total
     T0 = np.concatenate([inputs.initial_field(c, "uniform").ravel() for c in cfgs])
     T = torch.tensor(T0, dtype=torch.float32, device=dev)
-    tune_ms = sol.autotune(T, n_trial=2)
+    if args.batch_launch:
+        sol.set_launch(*[int(v) for v in args.batch_launch.split(",")])
+        tune_ms = None
+    else:
+        tune_ms = sol.autotune(T, n_trial=2)
     n_in = args.batch_inner
     trace = torch.zeros(len(cfgs) * n_in * 2, dtype=torch.float64, device=dev)
     energy = torch.zeros(len(cfgs) * 5, dtype=torch.float64, device=dev)
@@ -360,7 +366,7 @@ def run_batched(args, dev) -> dict:
             "ranks": world, "scaling": "strong (instances sharded over ranks)",
             "precision": "mixed", "value": total_all * n_in * args.steps / (ms / 1e3),
             "unit": "node-updates/s", "ms_per_replay": ms / args.steps,
-            "launch": {"mode": "persistent" if mode == 1 else "per-step", "threads": threads,
+            "launch": {"mode": mode, "threads": threads,
                        "rows_per_lane": rows, "autotune_ms_per_step": tune_ms},
             "graph": "each replay is one captured cc_step_n call"}
 
@@ -439,6 +445,7 @@ def run_paper(args, dev) -> dict:
     sol = ccell.Solver(cfg)
     nodes = cfg["nr"] * cfg["nz"]
     T = torch.full((nodes,), 4.2, dtype=torch.float64, device=dev)
+    sol.autotune(T, n_trial=8)                # launch shape for the stepped outline (T restored)
     chunks = schedule.transient_schedule(cfg["source"]["t_period"], cfg["dt"],
                                          args.paper_ms * 1e-3)
     steps = sum(n for _, _, n in chunks)
@@ -454,12 +461,13 @@ def run_paper(args, dev) -> dict:
     ms = e0.elapsed_time(e1)
     rate = nodes * steps / (ms / 1e3)
     tmax = float(T.max().item())
+    launch = dict(zip(("mode", "threads", "rows_per_lane"), sol.get_launch()))
     sol.close()
     paper_rate = 631 * 1201 * 1e5 / (12.9 * 60)
     return {"grid": f"{cfg['nr']}x{cfg['nz']}", "outline": "stepped at z_0 = 4 cm (core only beyond)",
             "simulated_ms": args.paper_ms, "steps": steps,
             "value": rate, "unit": "node-updates/s", "precision": "fp64",
-            "max_T_K": tmax,
+            "max_T_K": tmax, "launch": launch,
             "paper_k40_opencl_631x1201": {"value": paper_rate, "unit": "node-updates/s",
                                           "source": "Table calc_table (12.9 min for 1e5 steps)"},
             "projected_25ms_run_s": nodes * 1e5 / rate}
@@ -679,6 +687,8 @@ def main():
     ap.add_argument("--launch", default="",
                     help="mode,threads,rows_per_lane of the 512x4096 runs (default: library "
                          "default for FP64, autotuned for the mixed path)")
+    ap.add_argument("--batch-launch", default="",
+                    help="mode,threads,rows_per_lane of the batched sweep (default: autotuned)")
     ap.add_argument("--tune-steps", type=int, default=30,
                     help="time steps per candidate launch shape of the autotuner")
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")

@@ -186,10 +186,15 @@ def test_gpu_adjoint_checkpoint_invariance(ckpt):
 
 
 def test_gpu_adjoint_central_differences_256x1024():
-    """Central differences of the GPU loss (h = 1e-6 relative) on the gradient
-    workload's own grid (5 layers, 256 x 1024, tanh pulse edges), 400 steps
-    across the pulse's switch-off, for the heater amplitude, the pulse length and
-    the heater layer's conductivity and capacity scales."""
+    """Central differences of the GPU loss on the gradient workload's own grid
+    (5 layers, 256 x 1024, tanh pulse edges), 400 steps across the pulse's
+    switch-off, for the three parameters the loss depends on most over that
+    horizon (in 2.5 us the heater's effect has not reached the surface, so the
+    heater amplitude and pulse length move the loss by less than its FP64
+    summation error; they are checked on the smaller grid above and against
+    the oracle adjoint at this size).  h = 1e-4 relative keeps both the
+    cancellation in the differences and their O(h^2) truncation well below the
+    1e-5 bar."""
     cfg = inputs.adjoint_case()
     n = 400
     t0 = cfg["source"]["t_on"] - 200 * cfg["dt"]   # the smoothed falling edge mid-run
@@ -197,22 +202,18 @@ def test_gpu_adjoint_central_differences_256x1024():
     target = inputs.target_waveform(cfg, t0 + cfg["dt"] * np.arange(1, n + 1))
     _, gg, _ = _gpu_adjoint([cfg], [T0], n, t0, [target], ckpt=128, want_dT0=False)
     L = len(cfg["layers"])
-    heater = cfg["source"]["layer"]
-    for k in (0, 1, 2 + heater, 2 + L + heater):
-        h = 1e-6
+    loss0 = _gpu_loss(cfg, T0, n, t0, target)
+    for k in np.argsort(-np.abs(gg[2:]))[:3] + 2:   # layer scales by |dJ/dtheta|
+        k = int(k)
+        assert abs(gg[k]) > 1e-8 * loss0, (k, gg)      # sensitive enough for differences
+        h = 1e-4
+        key = "lam_scale" if k < 2 + L else "cap_scale"
+        m = (k - 2) % L
         vals = []
         for sgn in (+1, -1):
             c = copy.deepcopy(cfg)
-            if k == 0:
-                base = c["source"]["q0"]
-                c["source"]["q0"] = base * (1 + sgn * h)
-            elif k == 1:
-                base = c["source"]["t_on"]
-                c["source"]["t_on"] = base * (1 + sgn * h)
-            else:
-                key = "lam_scale" if k < 2 + L else "cap_scale"
-                base = c["layers"][heater].get(key, 1.0)
-                c["layers"][heater][key] = base * (1 + sgn * h)
+            base = c["layers"][m].get(key, 1.0)
+            c["layers"][m][key] = base * (1 + sgn * h)
             vals.append(_gpu_loss(c, T0, n, t0, target))
         fd = (vals[0] - vals[1]) / (2 * h * base)
-        assert abs(fd - gg[k]) <= 1e-5 * abs(fd) + 1e-9 * np.max(np.abs(gg)), (k, fd, gg[k])
+        assert abs(fd - gg[k]) <= 1e-5 * abs(fd), (k, fd, gg[k])
