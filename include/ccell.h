@@ -245,14 +245,15 @@ int cc_step_adi_n(cc_ctx* ctx, void* T_dev, int64_t n_steps, double t0_s, double
  *   FP64 contexts of one rectangular instance whose field fits in the SMs'
  *   shared memory (e.g. 512 x 4096); other contexts, or a grid that cannot
  *   be co-resident, run mode 0.
- *   mode 4: one launch per time step with pipelined CTA tiles: half of the
- *   block's warps assemble the rows of the next tile while the other half
+ *   mode 4: one launch per time step with pipelined CTA tiles: producer
+ *   warps (three quarters of the block for CC_FP64, about half for
+ *   CC_MIXED) assemble the rows of the next tile while the consumer warps
  *   solve and store the current one, two row buffers changing hands through
  *   named barriers (every context).
  *   threads: 64, 128 or 256 per block; 384 with mode 4 only; 512 with mode
  *   4 in CC_MIXED contexts only.
  *   Default (a new context): mode 4 with 128 threads per block for CC_FP64,
- *   384 for CC_MIXED, rows_per_lane 16.
+ *   512 for CC_MIXED, rows_per_lane 16.
  *   rows_per_lane: 2..16, target rows per lane of the line solve; a line of
  *   nr rows is split over the smallest power-of-two number of lanes G <= 32
  *   that meets it (at least 2 rows per lane, at most 16).
@@ -280,7 +281,7 @@ int cc_sync(cc_ctx* ctx, void* stream);
  * plus dJ/dT0 if dT0_dev is not NULL.  Checkpoints every ckpt_every steps
  * (<= 0: 256) and recomputes in between; the forward sweep keeps every state
  * of the last segment, which needs no recompute.  Device scratch, owned by
- * the context: ceil(n_steps / ckpt_every) + ckpt_every + 4 fields plus 5 doubles
+ * the context: ceil(n_steps / ckpt_every) + ckpt_every + 9 fields plus 5 doubles
  * per instance and step.
  *   T0_dev      initial field (not modified); target_dev double[n_inst][n_steps]
  *   loss_dev    double[n_inst]; grad_dev: for each instance in order, 2 + 2 n_layers
@@ -384,7 +385,8 @@ int cc_query_grid(const cc_geometry_desc* desc, double* r, double* z, int32_t* r
  * for t < min(*n_tiles, max_tiles); with n_blocks > 0 blocks, cta[b] ..
  * cta[b+1] (cta: int32[n_blocks + 1] or NULL) are the tiles of block b, an
  * equal share of all interior nodes (a launch uses its resident block
- * count); lanes[k] (or NULL): lanes G per line of instance k; *smem_bytes
+ * count), and a block's run of lines of one instance is cut into the fewest
+ * tiles that fit, of sizes that differ by at most one; lanes[k] (or NULL): lanes G per line of instance k; *smem_bytes
  * (or NULL): dynamic shared memory of the largest tile.  CC_EINVAL for
  * invalid arguments or when max_tiles is too small (*n_tiles is then set). */
 int cc_query_tiles(const cc_geometry_desc* descs, int32_t n_instances, int32_t threads,

@@ -14,21 +14,29 @@
 //                     systems in shared memory with the segment elimination
 //                     and shuffle cyclic reduction of the forward step (mu
 //                     includes the loss seed of step n and the folded axial
-//                     boundary rows).
+//                     boundary rows).  The radial face conductivity of every
+//                     node, its two derivatives, rho c / tau and its
+//                     derivative are evaluated here once and left for the
+//                     gather (five values per node, read back from L2).
 //  adj_gather_kernel  per node: dJ/dT^n from xi of the node's own row and of
 //                     the four neighbouring rows that read its temperature
 //                     (no atomics on the field), plus the parameter terms of
 //                     its own row (shuffle sums per warp, shared sums per
-//                     block, one global atomic per block and parameter).
+//                     block, one global atomic per block and parameter).  It
+//                     evaluates only the axial faces and their derivatives.
 #include <cuda_runtime.h>
 
 #include "ccell_device.cuh"
 
 namespace ccell {
 
+// Derivatives below take their reciprocals to 2^-46 (frcp46): they enter
+// dJ/dT and the parameter terms linearly, where a relative error of 2^-46 is
+// far below the rounding of the reverse sweep's sums.
+
 // d lambda / dT at a node, given lambda(T)
 __device__ __forceinline__ double dlam_node(const DevMaterial& M, double T, double lamT) {
-  if (M.lam_model == 1) return M.lam_b * lamT * frcp(T);
+  if (M.lam_model == 1) return M.lam_b * lamT * frcp46(T);
   if (M.lam_model == 0) return 0.0;
   const double* b = M.lam_poly;
   return fma(fma(fma(4.0 * b[4], T, 3.0 * b[3]), T, 2.0 * b[2]), T, b[1]);
@@ -41,7 +49,7 @@ __device__ __forceinline__ void lam_face_d(const DevMaterial& M, int rule, doubl
     if (M.lam_model == 1) {  // lambda((Ta+Tb)/2) = K (Ta+Tb)^b: d/dTa = b lambda / (Ta+Tb)
       const double y = Ta + Tb;
       l = lam_pow(M, y, true);
-      da = db = M.lam_b * l * frcp(y);
+      da = db = M.lam_b * l * frcp46(y);
     } else {
       const double Tm = 0.5 * (Ta + Tb);
       l = lam_eval(M, Tm);
@@ -55,20 +63,22 @@ __device__ __forceinline__ void lam_face_d(const DevMaterial& M, int rule, doubl
   }
 }
 
-// c(T) and dc/dT
-__device__ __forceinline__ void cap_d(const DevMaterial& M, double T, double& c, double& dc) {
+// rho c(T) / tau as the forward step evaluates it (rct_eval), and its
+// derivative in T.  Debye-saturated form r = k T^3 / (1 + T^3/theta^3):
+// dr/dT = 3 k T^2 / (1 + T^3/theta^3)^2.
+__device__ __forceinline__ void rct_d(const DevMaterial& M, double T, double& r, double& dr) {
   if (M.cap_model == 1) {
-    const double x = T * M.inv_tref, y = T * M.inv_theta;
-    const double rd = frcp(fma(y * y, y, 1.0));
-    c = M.c0s * (x * x * x) * rd;
-    dc = 3.0 * c * frcp(T) * rd;  // c0 x^3/(1+y^3): derivative (3c/T)/(1+y^3)
+    const double T2 = T * T, T3 = T2 * T;
+    const double rd = frcp46(fma(M.inv_theta3, T3, 1.0));
+    r = M.rct_k * T3 * rd;
+    dr = 3.0 * M.rct_k * T2 * rd * rd;
   } else if (M.cap_model == 0) {
-    c = M.c0s;
-    dc = 0.0;
+    r = M.rct_k;
+    dr = 0.0;
   } else {
     const double* a = M.cap_poly;
-    c = fma(fma(fma(a[3], T, a[2]), T, a[1]), T, a[0]);
-    dc = fma(fma(3.0 * a[3], T, 2.0 * a[2]), T, a[1]);
+    r = M.rho_tau * fma(fma(fma(a[3], T, a[2]), T, a[1]), T, a[0]);
+    dr = M.rho_tau * fma(fma(3.0 * a[3], T, 2.0 * a[2]), T, a[1]);
   }
 }
 
@@ -77,13 +87,12 @@ __device__ __forceinline__ void cap_d(const DevMaterial& M, double T, double& c,
 // ---------------------------------------------------------------------------
 // Forward row (a, b, c) of node i on a line at T^n: Eq. (ABC) for regular
 // nodes, Eq. (cc_first_3) for interface nodes, the closures at the axis and
-// at r_max.  lw, le: face conductivities (i-1, i) and (i, i+1).
+// at r_max.  lw, le: face conductivities (i-1, i) and (i, i+1); rct: rho c /
+// tau of a regular node.
 __device__ __forceinline__ void forward_row(const DevInst& I, const RowGeo& g, double T0,
-                                            double lw, double le, double& ra, double& rb,
-                                            double& rc) {
+                                            double lw, double le, double rct, double& ra,
+                                            double& rb, double& rc) {
   if (g.cls == RC_REGULAR) {
-    const DevMaterial& Mt = I.mat[g.seg];
-    const double rct = Mt.rho * cap_eval(Mt, T0) * I.inv_tau;
     ra = -g.gA * lw;
     rc = -g.gC * le;
     rb = rct - ra - rc;
@@ -159,14 +168,24 @@ __global__ void __launch_bounds__(CC_ADJ_MAX_THREADS) adj_tile_kernel(const AdjA
             Te_next = __ldg(row + nr + ie);
           }
           row += nr;
-          const double le = (ic < N) ? lam_face(Mt, frule, Tc, Te) : 0.0;  // face (i, i+1)
-          const double lw = __shfl_up_sync(kFull, le, 1);                  // face (i-1, i)
+          double le = 0.0, lea = 0.0, leb = 0.0;  // face (i, i+1) and its derivatives
+          if (ic < N) lam_face_d(Mt, frule, Tc, Te, le, lea, leb);
+          const double lw = __shfl_up_sync(kFull, le, 1);  // face (i-1, i)
+          double rct = 0.0, drct = 0.0;
+          if (g.cls == RC_REGULAR) rct_d(Mt, Tc, rct, drct);
           double fa, fb, fc;
-          forward_row(I, g, Tc, lw, le, fa, fb, fc);
+          forward_row(I, g, Tc, lw, le, rct, fa, fb, fc);
           const double cw = __shfl_up_sync(kFull, fc, 1);    // c_{i-1}
           const double ae = __shfl_down_sync(kFull, fa, 1);  // a_{i+1}
           if (own) {
             const long long rj = (long long)j * nr;
+            // values of this node for the gather, read back from L2
+            double* st = a.st + I.t_off + rj + ic;
+            st[0] = le;
+            st[a.st_stride] = lea;
+            st[2 * a.st_stride] = leb;
+            st[3 * a.st_stride] = rct;
+            st[4 * a.st_stride] = drct;
             double rd = __ldg(Lam + rj + ic);
             if (ic == N) rd = fma(sd, I.zg[j].wnorm, rd);
             if (j == 1 && I.bc_z0 == CC_NEUMANN) rd += __ldg(Lam + ic) + ((ic == N) ? sd * w0 : 0.0);
@@ -251,7 +270,6 @@ __global__ void __launch_bounds__(256) adj_gather_kernel(const AdjArgs a) {
     const double* XI = a.xi + I.t_off;
     const RowGeo g = I.rg[ic];
     const int frule = I.face_rule;
-    const double tau_inv = I.inv_tau;
     const bool regular = (g.cls == RC_REGULAR);
     const DevMaterial& Mt = I.mat[g.seg];
     const int j_lo = kGatherLines * jb;
@@ -263,9 +281,16 @@ __global__ void __launch_bounds__(256) adj_gather_kernel(const AdjArgs a) {
     for (int j = j_lo; j <= j_hi; ++j) {  // same lines for the whole warp
       const long long rj = (long long)j * nr;
       const double Tn = (j <= M - 1) ? X[rj + nr + ic] : 0.0;
-      // radial faces (i, i+1) of material seg[i], (i-1, i) from the left lane
+      const bool line = (j >= 1 && j <= M - 1);  // own row belongs to a solved line (warp-uniform)
+      // radial faces (i, i+1) of material seg[i] as the tile kernel left them
+      // (zero at i = N), (i-1, i) from the left lane; needed on solved lines only
       double lE = 0.0, lEa = 0.0, lEb = 0.0;
-      if (ic <= N - 1) lam_face_d(Mt, frule, T, X[rj + ic + 1], lE, lEa, lEb);
+      if (line) {
+        const double* st = a.st + I.t_off + rj + ic;
+        lE = st[0];
+        lEa = st[a.st_stride];
+        lEb = st[2 * a.st_stride];
+      }
       double lW = __shfl_up_sync(kFull, lE, 1);
       double lWb = __shfl_up_sync(kFull, lEb, 1);
       if (i == 0) lW = lWb = 0.0;
@@ -273,7 +298,6 @@ __global__ void __launch_bounds__(256) adj_gather_kernel(const AdjArgs a) {
       double lN = 0.0, lNa = 0.0, lNb = 0.0;
       if (regular && j <= M - 1) lam_face_d(Mt, frule, T, Tn, lN, lNa, lNb);
       if (own) {
-        const bool line = (j >= 1 && j <= M - 1);  // own row belongs to a solved line
         const double yi = Y[rj + ic];
         double acc = 0.0;
         // rows i-1 and i+1 of the same line
@@ -303,9 +327,8 @@ __global__ void __launch_bounds__(256) adj_gather_kernel(const AdjArgs a) {
           if (line) {
             const double xi = XI[rj + ic];
             const ZGeo& zg = I.zg[j];
-            double c, dc;
-            cap_d(Mt, T, c, dc);
-            const double rct = Mt.rho * c * tau_inv, drct = Mt.rho * dc * tau_inv;
+            const double rct = a.st[3 * a.st_stride + I.t_off + rj + ic];
+            const double drct = a.st[4 * a.st_stride + I.t_off + rj + ic];
             const double gw = Y[rj + ic - 1] - yi, ge = Y[rj + ic + 1] - yi;
             const double dN = Tn - T, dS = T - Ts;
             double d0 = fma(drct, T - yi, rct);
@@ -318,7 +341,7 @@ __global__ void __launch_bounds__(256) adj_gather_kernel(const AdjArgs a) {
             double gT = 1.0, dgT = 0.0;
             if (heat && I.g_model == 1) {
               gT = I.g_ref * rsqrt(T);
-              dgT = -0.5 * gT * frcp(T);
+              dgT = -0.5 * gT * frcp46(T);
             }
             if (heat) d0 = fma(I.q0 * a.s_tab[sidx], dgT, d0);
             acc = fma(xi, d0, acc);

@@ -238,8 +238,14 @@ void cut_tiles(const std::vector<Instance>& inst, const std::vector<int>& lpcs, 
         const Instance& in = inst[k];
         const int take = (int)std::min<long long>((g_end - g + in.d.nr - 1) / in.d.nr,
                                                   in.d.nz - 1 - jn);
-        for (int j = jn; j < jn + take; j += lpcs[k])
-          tiles.push_back(TileTask{k, j, std::min(lpcs[k], jn + take - j), 0});
+        // the fewest tiles of at most lpcs lines, of sizes that differ by at
+        // most one (no short last tile that leaves consumer warps idle)
+        const int nt = (take + lpcs[k] - 1) / lpcs[k];
+        for (int t = 0, j = jn; t < nt; ++t) {
+          const int e = jn + (int)((long long)(t + 1) * take / nt);
+          tiles.push_back(TileTask{k, j, e - j, 0});
+          j = e;
+        }
         jn += take;
         g += (long long)take * in.d.nr;
         if (jn > in.d.nz - 2) {
@@ -325,10 +331,12 @@ int cut_warp_tasks(cc_ctx* c) {
 int cut_pipe_tiles(cc_ctx* c) {
   c->pipe_ok = false;
   const bool mixed = c->precision == CC_MIXED;
-  // producer / consumer warps: half and half for the mixed step, three
-  // quarters producers for the FP64 step (at least one of each)
+  // producer / consumer warps as measured fastest on GB300: for the mixed
+  // step about half producers (9 of 16 warps at 512 threads), for the FP64
+  // step three quarters producers (at least one of each)
   const int warps = c->threads / 32;
-  const int prod = std::max(1, std::min(warps - 1, mixed ? warps / 2 : (3 * warps) / 4));
+  const int prod =
+      std::max(1, std::min(warps - 1, mixed ? warps / 2 + warps / 16 : (3 * warps) / 4));
   const int cons = warps - prod;
   const int elem = mixed ? (int)sizeof(float) : (int)sizeof(double);
   std::vector<int> lpcs(c->inst.size());
@@ -637,9 +645,9 @@ int cc_create_geometry(const cc_geometry_desc* desc, int32_t n_instances, cc_ctx
   c->precision = desc[0].precision;
   // default launch: pipelined tiles, the block size measured fastest for the
   // precision on GB300 (FP64: 3 producer + 1 consumer warps, three blocks per
-  // SM; mixed: 6 + 6 warps)
+  // SM; mixed: 9 + 7 warps, one block per SM)
   c->mode = 4;
-  c->threads = c->precision == CC_FP64 ? 128 : 384;
+  c->threads = c->precision == CC_FP64 ? 128 : 512;
   long long off = 0;
   for (int k = 0; k < n_instances; ++k) {
     const int v = valid_desc(desc[k]);
@@ -1094,9 +1102,10 @@ int adjoint_impl(cc_ctx* c, const void* T0_dev, int64_t n_steps, double t0, doub
     nl[k] = c->inst[k].d.n_layers;
     gsum += 2 + 2 * nl[k];
   }
-  // scratch layout (doubles): checkpoints, segment states, lam x2, xi,
-  // trace, seed, s, ds, grad offsets and layer counts
-  const size_t need = nodes * (size_t)(n_ck + K + 1 + 3) + (size_t)n * n_steps * 5 + 2 * (size_t)n + 8;
+  // scratch layout (doubles): checkpoints, segment states, lam x2, xi, the
+  // five per-node values the tile kernel hands to the gather, trace, seed,
+  // s, ds, grad offsets and layer counts
+  const size_t need = nodes * (size_t)(n_ck + K + 1 + 3 + 5) + (size_t)n * n_steps * 5 + 2 * (size_t)n + 8;
   if (c->adj_cap < need) {
     cudaFree(c->d_adj);
     c->d_adj = nullptr;
@@ -1113,6 +1122,7 @@ int adjoint_impl(cc_ctx* c, const void* T0_dev, int64_t n_steps, double t0, doub
   double* lamA = p; p += nodes;
   double* lamB = p; p += nodes;
   double* xi = p; p += nodes;
+  double* hand = p; p += nodes * 5;
   double* trace = p; p += (size_t)n * n_steps * 2;
   double* seed = p; p += (size_t)n * n_steps;
   double* s_tab = p; p += (size_t)n * n_steps;
@@ -1173,6 +1183,8 @@ int adjoint_impl(cc_ctx* c, const void* T0_dev, int64_t n_steps, double t0, doub
   b.smem_bytes = c->smem_bytes;  // FP64 tiles: five rows and more per line
   b.n_inst = n;
   b.xi = xi;
+  b.st = hand;
+  b.st_stride = (long long)nodes;
   b.seed = seed;
   b.s_tab = s_tab;
   b.ds_tab = ds_tab;

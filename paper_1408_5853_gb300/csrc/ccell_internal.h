@@ -251,6 +251,11 @@ struct AdjArgs {
   const double* lam;     // dJ/dT^{n+1} (without the seed of step n)
   double* lam_out;       // dJ/dT^n
   double* xi;            // M^{-T} mu, [node]
+  // per node of the solved lines, from the tile kernel to the gather:
+  // st[k * st_stride + node] = lambda_e, d lambda_e / dT_i, d lambda_e /
+  // dT_{i+1} (face (i, i+1); zero at i = N), rho c / tau, d(rho c / tau)/dT
+  double* st;
+  long long st_stride;
   const double* seed;    // [n_inst][n_steps]: dJ/dSbar_n
   const double* s_tab;   // [n_steps][n_inst] waveform
   const double* ds_tab;  // [n_steps][n_inst] d waveform / d t_on

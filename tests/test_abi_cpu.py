@@ -114,7 +114,7 @@ def test_descriptor_and_material_validation():
 
 
 def test_default_launch_shape_per_precision():
-    for precision, threads in ((ccell.FP64, 128), (ccell.MIXED, 384)):
+    for precision, threads in ((ccell.FP64, 128), (ccell.MIXED, 512)):
         sol = ccell.Solver(inputs.small_case(q0=1.0), precision=precision)
         try:
             assert ccell.cc_get_launch(sol.ctx) == (4, threads, 16)
@@ -197,6 +197,14 @@ def test_tile_partition_covers_every_line_once(threads, rows, blocks, precision)
         share = total / blocks
         block_nodes = [int(per_tile[cta[b]:cta[b + 1]].sum()) for b in range(blocks)]
         assert max(abs(x - share) for x in block_nodes) < nr.max() + 1, (min(block_nodes), share)
+        # a block's run of one instance: the fewest tiles that fit, sizes within one line
+        cap = {k: (threads // 32) * (32 // int(lanes[k])) for k in range(len(cfgs))}
+        for b in range(blocks):
+            run = tiles[cta[b]:cta[b + 1]]
+            for k in np.unique(run[:, 0]):
+                nl = run[run[:, 0] == k][:, 2]
+                assert nl.max() - nl.min() <= 1, (b, k, nl)
+                assert len(nl) == -(-int(nl.sum()) // cap[k]), (b, k, nl)
 
 
 def test_entry_points_refuse_before_any_device_work():
