@@ -264,12 +264,7 @@ def run_ours(args, world, rank, local):
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": f"5-layer r-z cylinder {cfg['nr']}x{cfg['nz']}, jittered seed 0, "
-                               f"tau {cfg['dt']:.2e} s, {n_in} time steps per bench step",
-                   "nr": cfg["nr"], "nz": cfg["nz"], "time_steps_per_step": n_in,
-                   "precision": "fp64", "l2": f"flushed between timed steps ({L2_FLUSH_BYTES >> 20} MB write)",
-                   "parallelism": f"replicas x{world}",
-                   "launch": dict(zip(("mode", "threads", "rows_per_lane"), launch_shape))},
+        "config": headline_config(cfg, n_in, world, launch_shape),
         "roofline": {"bound": "alu", "kernel": kname,
                      "achieved": achieved_tflops, "peak": fp64_peak_tflops, "unit": "TFLOP/s",
                      "frac": achieved_tflops / fp64_peak_tflops,
@@ -623,6 +618,25 @@ def cpu_baseline(sample_steps: int, T0) -> tuple:
              "cpu_model": _cpu_model(), "nproc": os.cpu_count()}, T_out)
 
 
+# The library's default launch shape of an FP64 context (cc_set_launch).
+DEFAULT_FP64_LAUNCH = (4, 128, 16)
+
+
+def _launch_arg(text):
+    return tuple(int(v) for v in text.split(",")) if text else None
+
+
+def headline_config(cfg, n_in, world, launch_shape) -> dict:
+    """The headline workload, as both arms name it."""
+    return {"workload": f"5-layer r-z cylinder {cfg['nr']}x{cfg['nz']}, jittered seed 0, "
+                        f"tau {cfg['dt']:.2e} s, {n_in} time steps per bench step",
+            "nr": cfg["nr"], "nz": cfg["nz"], "time_steps_per_step": n_in,
+            "precision": "fp64",
+            "l2": f"flushed between timed steps ({L2_FLUSH_BYTES >> 20} MB write)",
+            "parallelism": f"replicas x{world}",
+            "launch": dict(zip(("mode", "threads", "rows_per_lane"), launch_shape))}
+
+
 def run_reference(args, world, rank):
     """Reference arm: the FP64 CPU oracle on the host cores (rank 0 only)."""
     if rank != 0:
@@ -647,13 +661,12 @@ def run_reference(args, world, rank):
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * s / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic",
-        "config": {"workload": f"5-layer r-z cylinder {cfg['nr']}x{cfg['nz']}, jittered seed 0, "
-                               f"tau {cfg['dt']:.2e} s, {n_in} time steps per bench step (CPU sample)",
-                   "nr": cfg["nr"], "nz": cfg["nz"], "time_steps_per_step": n_in,
-                   "precision": "fp64"},
+        "config": headline_config(cfg, args.inner, world, _launch_arg(args.launch)
+                                  or DEFAULT_FP64_LAUNCH),
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": oracle.num_threads(),
                          "kind": "oracle",
-                         "sample": f"{n_in} time steps of the 512x4096 workload per bench step",
+                         "sample": f"{n_in} time steps of the 512x4096 workload per bench step "
+                                   f"(the GPU arm's bench step is {args.inner})",
                          "cpu_model": _cpu_model(), "nproc": os.cpu_count()},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }

@@ -236,14 +236,14 @@ int launch_adj_tile(const AdjArgs& a, void* stream) {
 // per-node gather of dJ/dT^n and of the parameter terms
 // ---------------------------------------------------------------------------
 constexpr int kGradMax = 2 + 2 * CC_MAX_LAYERS;
-constexpr int kGatherLines = 8;  // lines per thread: the axial face is carried down
 
 // Warp task (column block cb, line block jb): lane l holds column 31 cb + l
 // (lane 0 of cb > 0 only supplies its east face to lane 1) on the lines
-// 8 jb .. 8 jb + 7.  Every face conductivity and its derivatives are
-// evaluated once per face: the east face per lane (the west face comes from
-// the left lane), the north face per line (the south face is the previous
-// line's north face).
+// gl jb .. gl jb + gl - 1 (gl = a.gather_lines).  The radial faces come from
+// the tile kernel (the west face from the left lane); each axial face and its
+// derivatives are evaluated once per line block: the north face per line, the
+// south face carried from the previous line (one extra evaluation at the top
+// of the block).
 __global__ void __launch_bounds__(256) adj_gather_kernel(const AdjArgs a) {
   __shared__ double sg[kGradMax];
   const int inst = blockIdx.y;
@@ -258,7 +258,8 @@ __global__ void __launch_bounds__(256) adj_gather_kernel(const AdjArgs a) {
   // summed over the warp per parameter below
   double pq = 0.0, pt = 0.0, pl = 0.0, pl2 = 0.0, pc = 0.0;
   int mL = -1, mL2 = -1, mC = -1;
-  const int ncb = (N + 30) / 31, njb = (M + kGatherLines) / kGatherLines;
+  const int gl = a.gather_lines;
+  const int ncb = (N + 30) / 31, njb = (M + gl) / gl;
   const int w = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
   if (w < ncb * njb) {  // warp-uniform
     const int cb = w % ncb, jb = w / ncb;
@@ -272,8 +273,8 @@ __global__ void __launch_bounds__(256) adj_gather_kernel(const AdjArgs a) {
     const int frule = I.face_rule;
     const bool regular = (g.cls == RC_REGULAR);
     const DevMaterial& Mt = I.mat[g.seg];
-    const int j_lo = kGatherLines * jb;
-    const int j_hi = min(j_lo + kGatherLines - 1, M);
+    const int j_lo = gl * jb;
+    const int j_hi = min(j_lo + gl - 1, M);
     double Ts = (j_lo >= 1) ? X[(long long)(j_lo - 1) * nr + ic] : 0.0;
     double T = X[(long long)j_lo * nr + ic];
     double lS = 0.0, lSa = 0.0, lSb = 0.0;  // face (j-1, j) of a regular column
@@ -408,7 +409,8 @@ __global__ void __launch_bounds__(256) adj_gather_kernel(const AdjArgs a) {
 
 int launch_adj_gather(const AdjArgs& a, int max_nr, int max_nz, void* stream) {
   const int threads = 256;
-  const long long warps = (long long)((max_nr - 1 + 30) / 31) * ((max_nz + kGatherLines - 1) / kGatherLines);
+  const int gl = a.gather_lines;
+  const long long warps = (long long)((max_nr - 1 + 30) / 31) * ((max_nz + gl - 1) / gl);
   const dim3 grid((unsigned)((warps * 32 + threads - 1) / threads), (unsigned)a.n_inst);
   adj_gather_kernel<<<grid, threads, 0, (cudaStream_t)stream>>>(a);
   count_launch();

@@ -256,6 +256,7 @@ struct AdjArgs {
   // dT_{i+1} (face (i, i+1); zero at i = N), rho c / tau, d(rho c / tau)/dT
   double* st;
   long long st_stride;
+  int gather_lines;      // lines per warp task of the gather (1..8)
   const double* seed;    // [n_inst][n_steps]: dJ/dSbar_n
   const double* s_tab;   // [n_steps][n_inst] waveform
   const double* ds_tab;  // [n_steps][n_inst] d waveform / d t_on

@@ -217,3 +217,21 @@ def test_gpu_adjoint_central_differences_256x1024():
             vals.append(_gpu_loss(c, T0, n, t0, target))
         fd = (vals[0] - vals[1]) / (2 * h * base)
         assert abs(fd - gg[k]) <= 1e-5 * abs(fd), (k, fd, gg[k])
+
+
+def test_gpu_adjoint_64x128_full_20ms():
+    """The gradient workload's source and materials on the 64 x 128 grid over
+    the full 20 ms (40 000 steps of 0.5 us, two smoothed pulses) from the
+    configured 20 K start, checkpoints every 256 steps, against the oracle
+    adjoint: loss, every parameter and dJ/dT0."""
+    cfg = inputs.adjoint_case(nr=64, nz=128)
+    cfg["dt"] = 5.0e-7                               # 0.92 x the stability bound
+    assert cfg["dt"] <= oracle.tau_stab(cfg, 20.0, 100.0)
+    n = int(round(20e-3 / cfg["dt"]))
+    T0 = inputs.initial_field(cfg, "uniform")
+    target = inputs.target_waveform(cfg, cfg["dt"] * np.arange(1, n + 1))
+    lo, go, do = oracle.adjoint(cfg, T0, n, 0.0, cfg["dt"], target, ckpt=256)
+    lg, gg, dg = _gpu_adjoint([cfg], [T0], n, 0.0, [target], ckpt=256)
+    assert abs(lg[0] - lo) <= 1e-10 * lo
+    assert np.max(np.abs(gg - go)) <= 1e-8 * np.max(np.abs(go)), (gg, go)
+    assert np.max(np.abs(dg.reshape(T0.shape) - do)) <= 1e-8 * np.max(np.abs(do))

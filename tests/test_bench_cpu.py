@@ -26,3 +26,14 @@ def test_reference_arm_json_line():
     assert cb["kind"] == "oracle" and cb["value"] == d["value"] and cb["cores"] >= 1
     assert d["e2e"]["value"] == d["value"]
     assert d["e2e"]["h2d_bytes_per_step"] == 0 and d["e2e"]["d2h_bytes_per_step"] == 0
+    # the reference arm names the GPU arm's workload and default launch shape
+    sys.path.insert(0, ROOT)
+    import bench
+    from paper_1408_5853_gb300 import ccell, inputs
+    cfg = inputs.production_case()
+    assert d["config"] == bench.headline_config(cfg, 1000, 1, bench.DEFAULT_FP64_LAUNCH)
+    sol = ccell.Solver(inputs.small_case(q0=1.0))
+    try:
+        assert ccell.cc_get_launch(sol.ctx) == bench.DEFAULT_FP64_LAUNCH
+    finally:
+        sol.close()
