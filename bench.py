@@ -377,15 +377,21 @@ def run_adjoint(args, dev) -> dict:
     # checkpoints every 256 steps (the workload's setting); then every state of
     # the single run kept in HBM (about 84 GB at 40 000 steps), which removes
     # the recompute
-    runs = [("single", 1, args.adj_steps, 256), ("batch64", 64, args.adj_batch_steps, 256)]
+    # the library's default launch, then (every state kept) the launch the
+    # autotuner picks for this grid's forward step
+    runs = [("single", 1, args.adj_steps, 256, False),
+            ("batch64", 64, args.adj_batch_steps, 256, False)]
     if args.adj_keep_all:
-        runs.append(("single_all_states", 1, args.adj_steps, args.adj_steps))
-    for label, n_inst, n, ckpt in runs:
+        runs += [("single_all_states", 1, args.adj_steps, args.adj_steps, False),
+                 ("single_all_states_autotuned", 1, args.adj_steps, args.adj_steps, True)]
+    for label, n_inst, n, ckpt, tune in runs:
         cfg = inputs.adjoint_case()
         cfgs = [cfg] * n_inst
         sol = ccell.Solver(cfgs)
         T0 = torch.tensor(np.tile(inputs.initial_field(cfg, "uniform").ravel(), n_inst),
                           dtype=torch.float64, device=dev)
+        if tune:
+            sol.autotune(T0.clone(), n_trial=args.tune_steps)
         t = cfg["dt"] * np.arange(1, n + 1)
         tgt = torch.tensor(np.tile(inputs.target_waveform(cfg, t), n_inst), dtype=torch.float64,
                            device=dev)
@@ -416,6 +422,8 @@ def run_adjoint(args, dev) -> dict:
                       "forward_steps_per_reverse_step": (ms / n) / fwd_ms,
                       "ms_per_gradient": ms / n_inst, "ms_total": ms,
                       "forward_equivalent_node_updates_per_s": nodes * n / (ms / 1e3),
+                      "launch": dict(zip(("mode", "threads", "rows_per_lane"), sol.get_launch())),
+                      "ms_per_forward_step": fwd_ms,
                       "loss": float(loss[0].item()), "grad_norm": float(grad.norm().item())}
         sol.close()
     return out
