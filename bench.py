@@ -40,7 +40,7 @@ FLOPS_PER_NODE_FP64 = 150     # FP64 operations per node-update (2 power laws ~ 
 # on the 512x4096 workload, from the ncu capture summarised in
 # profiles/step_fp64_pipe_kernel_512x4096.md (cache flushed before the launch).  Valid only for
 # the kernel as captured there: reset to None when the kernel changes.
-STEP_FP64_TRAFFIC_512x4096 = 17.273088e6
+STEP_FP64_TRAFFIC_512x4096 = None
 FP64_PEAK_NOMINAL_TFLOPS = 152 * 4 * 0.5 * 2 * 2.07e9 / 1e12   # SMs x SMSPs x DFMA lanes/clk x 2 x max clock
 # Per launch mode of the FP64 headline: the dominant kernel, the FP64-pipe thread-instructions it
 # executes per node-update on the 512x4096 workload (ncu sm__thread_inst_executed_pipe_fp64_pred_on
@@ -51,7 +51,7 @@ EXECUTED_FP64 = {
     1: ("steps_fp64_persistent_kernel", None, None),
     2: ("step_fp64_lines_kernel", None, None),
     3: ("steps_fp64_resident_kernel", None, None),
-    4: ("step_fp64_pipe_kernel", 58.1, "profiles/step_fp64_pipe_kernel_512x4096.md"),
+    4: ("step_fp64_pipe_kernel", None, None),
 }
 L2_FLUSH_BYTES = 256 << 20
 
@@ -136,8 +136,10 @@ def run_ours(args, world, rank, local):
         sol = ccell.Solver(cfg, precision=precision)
         dt = torch.float64 if precision == ccell.FP64 else torch.float32
         T = torch.tensor(T0.ravel(), dtype=dt, device=dev)
-        if args.launch:
-            sol.set_launch(*[int(v) for v in args.launch.split(",")])
+        if precision == ccell.MIXED and args.mixed_launch:
+            sol.set_launch(*_launch_arg(args.mixed_launch))
+        elif args.launch:
+            sol.set_launch(*_launch_arg(args.launch))
         elif precision == ccell.MIXED:
             # the library's autotuner picks the mixed path's launch shape (field
             # restored); the FP64 headline keeps the library's default shape
@@ -708,6 +710,8 @@ def main():
     ap.add_argument("--launch", default="",
                     help="mode,threads,rows_per_lane of the 512x4096 runs (default: library "
                          "default for FP64, autotuned for the mixed path)")
+    ap.add_argument("--mixed-launch", default="",
+                    help="mode,threads,rows_per_lane of the mixed 512x4096 runs (overrides --launch)")
     ap.add_argument("--batch-launch", default="",
                     help="mode,threads,rows_per_lane of the batched sweep (default: autotuned)")
     ap.add_argument("--tune-steps", type=int, default=30,

@@ -138,7 +138,6 @@ __device__ __forceinline__ void fp64_produce(const StepArgs& a, const TileTask t
   double* SM = B.SM;
   double* sI = B.sI;
   const double s = a.s_tab[a.step * a.n_inst + tk.inst];
-  double eQ = 0.0, eD = 0.0, eN = 0.0;
 
   // ---- 0a. nodal conductivities of the interface rows, Eq. (cc_first_3)
   if (I.interface_rule == 0 && n_if > 0) {  // block-uniform
@@ -237,14 +236,14 @@ __device__ __forceinline__ void fp64_produce(const StepArgs& a, const TileTask t
           }
           if (ENERGY && own) {
             m = g.V2 * rct;  // V rho c / (etabar tau)
-            if (X != 0.0) eQ = fma(zg.etabar * I.tau * g.V2, X, eQ);
+            if (X != 0.0) acc.e[1] = fma(zg.etabar * I.tau * g.V2, X, acc.e[1]);
             if (j == 1) {
               const double f = -I.tau * g.V2 * fs / zg.eta_s;
-              if (I.bc_z0 == CC_DIRICHLET) eD += f; else eN += f;
+              if (I.bc_z0 == CC_DIRICHLET) acc.e[2] += f; else acc.e[4] += f;
             }
             if (j == M - 1) {
               const double f = I.tau * g.V2 * fn / zg.eta_n;
-              if (I.bc_zmax == CC_DIRICHLET) eD += f; else eN += f;
+              if (I.bc_zmax == CC_DIRICHLET) acc.e[2] += f; else acc.e[4] += f;
             }
           }
         } else if (cls == RC_IFACE) {
@@ -291,11 +290,6 @@ __device__ __forceinline__ void fp64_produce(const StepArgs& a, const TileTask t
         fs = fn;
       }
     }
-  }
-  if (ENERGY) {
-    acc.e[1] += eQ;
-    acc.e[2] += eD;
-    acc.e[4] += eN;
   }
 }
 
