@@ -301,21 +301,28 @@ __global__ void __launch_bounds__(256) adj_gather_kernel(const AdjArgs a) {
       if (own) {
         const double yi = Y[rj + ic];
         double acc = 0.0;
+        // That differences to the radial neighbours on this line (zero off the line and at the
+        // ends); the neighbours' rows read them with the opposite sign
+        double gw = 0.0, ge = 0.0;
+        if (line) {
+          if (ic >= 1) gw = Y[rj + ic - 1] - yi;
+          if (ic <= N - 1) ge = Y[rj + ic + 1] - yi;
+        }
         // rows i-1 and i+1 of the same line
         if (line) {
           if (ic >= 1) {
-            const RowGeo& gw = I.rg[ic - 1];
-            const double xw = XI[rj + ic - 1], dy = yi - Y[rj + ic - 1];
-            if (gw.cls == RC_REGULAR) acc = fma(xw * gw.gC * lWb, dy, acc);
-            else if (gw.cls == RC_IFACE && I.interface_rule == 1)
-              acc = fma(xw * gw.re * lWb * gw.hw, dy, acc);
+            const RowGeo& gm = I.rg[ic - 1];
+            const double xw = XI[rj + ic - 1];
+            if (gm.cls == RC_REGULAR) acc = fma(xw * gm.gC * lWb, -gw, acc);
+            else if (gm.cls == RC_IFACE && I.interface_rule == 1)
+              acc = fma(xw * gm.re * lWb * gm.hw, -gw, acc);
           }
           if (ic <= N - 1) {
-            const RowGeo& ge = I.rg[ic + 1];
-            const double xe = XI[rj + ic + 1], dy = yi - Y[rj + ic + 1];
-            if (ge.cls == RC_REGULAR) acc = fma(xe * ge.gA * lEa, dy, acc);
-            else if (ge.cls == RC_IFACE && I.interface_rule == 1)
-              acc = fma(xe * ge.rw * lEa * ge.he, dy, acc);
+            const RowGeo& gp = I.rg[ic + 1];
+            const double xe = XI[rj + ic + 1];
+            if (gp.cls == RC_REGULAR) acc = fma(xe * gp.gA * lEa, -ge, acc);
+            else if (gp.cls == RC_IFACE && I.interface_rule == 1)
+              acc = fma(xe * gp.rw * lEa * gp.he, -ge, acc);
           }
         }
         if (regular) {
@@ -330,7 +337,6 @@ __global__ void __launch_bounds__(256) adj_gather_kernel(const AdjArgs a) {
             const ZGeo& zg = I.zg[j];
             const double rct = a.st[3 * a.st_stride + I.t_off + rj + ic];
             const double drct = a.st[4 * a.st_stride + I.t_off + rj + ic];
-            const double gw = Y[rj + ic - 1] - yi, ge = Y[rj + ic + 1] - yi;
             const double dN = Tn - T, dS = T - Ts;
             double d0 = fma(drct, T - yi, rct);
             d0 = fma(fma(lNa, dN, -lN), zg.gzn, d0);
@@ -361,7 +367,6 @@ __global__ void __launch_bounds__(256) adj_gather_kernel(const AdjArgs a) {
         } else if (g.cls == RC_IFACE && line) {
           const double xi = XI[rj + ic];
           const int mi = g.segw, mo = g.seg;
-          const double gw = Y[rj + ic - 1] - yi, ge = Y[rj + ic + 1] - yi;
           double lm, lp, dlm, dlp;
           if (I.interface_rule == 0) {
             lm = lam_eval(I.mat[mi], T);
