@@ -222,6 +222,25 @@ def run_ours(args, world, rank, local):
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         e2e_s = float(t.item())
     e2e_val = nodes * n_in * len(e2e_times) * world / e2e_s
+
+    # ---- time steps per cc_step_n call: the rate with every call's launch and host
+    # overhead included (device time from the first call's start to the last one's end)
+    nsweep = None
+    if "nsweep" in args.parts:
+        nsweep = {"unit": UNIT}
+        for n_call in (1, 10, 100, 1000):
+            calls = max(3, 4000 // n_call)
+            tr_n = torch.zeros(2 * n_call, dtype=torch.float64, device=dev)
+            sol.step(T, n_call, 0.0, 0.0, tr_n, energy)
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for c in range(calls):
+                sol.step(T, n_call, c * n_call * cfg["dt"], 0.0, tr_n, energy)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            nsweep[str(n_call)] = nodes * n_call * calls / (e0.elapsed_time(e1) / 1e3)
+        sol.sync()
     sol.close()
 
     # ---- mixed-precision path on the same workload
@@ -298,6 +317,7 @@ def run_ours(args, world, rank, local):
                          "note": "effective: the field stays L2-resident during a call"},
         "energy_identity_rel": ident,
         "mixed": mixed,
+        "steps_per_call_sweep": nsweep if nsweep is not None else {"skipped": True},
         "batched": batched,
         "adjoint": adjoint,
         "paper_cell": paper,
@@ -317,8 +337,9 @@ def run_ours(args, world, rank, local):
 def run_batched(args, dev) -> dict:
     """Design sweep: 256 ragged 5-layer instances (seed 1) in one context,
     mixed precision, per-instance dt = 0.9 x the axial stability bound, the
-    launch shape chosen by the autotuner, each call captured in a CUDA graph
-    and replayed."""
+    launch shape chosen by the autotuner; one cc_step_n call of --batch-inner
+    time steps (2000 by default) captured in a CUDA graph, one warm-up replay,
+    then --batch-replays timed replays."""
     import torch
 
     from paper_1408_5853_gb300 import ccell, inputs, shard
@@ -346,12 +367,11 @@ def run_batched(args, dev) -> dict:
     graph = torch.cuda.CUDAGraph()
     with torch.cuda.graph(graph):
         sol.step(T, n_in, 0.0, 0.0, trace, energy)
-    for _ in range(args.warmup):
-        graph.replay()
+    graph.replay()                                  # warm-up replay
     torch.cuda.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record()
-    for _ in range(args.steps):
+    for _ in range(args.batch_replays):
         graph.replay()
     e1.record()
     torch.cuda.synchronize()
@@ -361,8 +381,9 @@ def run_batched(args, dev) -> dict:
     sol.close()
     return {"instances": len(all_cfgs), "nodes": int(total_all), "time_steps_per_replay": n_in,
             "ranks": world, "scaling": "strong (instances sharded over ranks)",
-            "precision": "mixed", "value": total_all * n_in * args.steps / (ms / 1e3),
-            "unit": "node-updates/s", "ms_per_replay": ms / args.steps,
+            "precision": "mixed", "value": total_all * n_in * args.batch_replays / (ms / 1e3),
+            "unit": "node-updates/s", "replays": args.batch_replays,
+            "ms_per_replay": ms / args.batch_replays,
             "launch": {"mode": mode, "threads": threads,
                        "rows_per_lane": rows, "autotune_ms_per_step": tune_ms},
             "graph": "each replay is one captured cc_step_n call"}
@@ -426,6 +447,10 @@ def run_adjoint(args, dev) -> dict:
                       "forward_equivalent_node_updates_per_s": nodes * n / (ms / 1e3),
                       "launch": dict(zip(("mode", "threads", "rows_per_lane"), sol.get_launch())),
                       "ms_per_forward_step": fwd_ms,
+                      # the configured horizon, 20 ms = 3.2e6 steps of 6.25 ns, at this run's
+                      # cost per reverse step (with checkpoints: every state would need 6.7 TB)
+                      "projected_full_20ms_s": ((20e-3 / cfg["dt"]) * (ms / n) / 1e3
+                                                if ckpt < n and n_inst == 1 else None),
                       "loss": float(loss[0].item()), "grad_norm": float(grad.norm().item())}
         sol.close()
     return out
@@ -694,10 +719,12 @@ def main():
     ap.add_argument("--adi-steps", type=int, default=200, help="timed ADI steps")
     ap.add_argument("--adi-check-us", type=float, default=10.0,
                     help="simulated microseconds of the ADI accuracy check")
-    ap.add_argument("--parts", default="fp64,mixed,batched,adjoint,paper,adi",
+    ap.add_argument("--parts", default="fp64,nsweep,mixed,batched,adjoint,paper,adi",
                     help="comma list of extra parts to run besides the FP64 headline")
     ap.add_argument("--batch-instances", type=int, default=256)
-    ap.add_argument("--batch-inner", type=int, default=20, help="time steps per batched replay")
+    ap.add_argument("--batch-inner", type=int, default=2000,
+                    help="time steps per batched replay (one captured cc_step_n call)")
+    ap.add_argument("--batch-replays", type=int, default=2, help="timed replays of the sweep")
     ap.add_argument("--adj-steps", type=int, default=40000)
     ap.add_argument("--adj-batch-steps", type=int, default=512)
     ap.add_argument("--no-adj-keep-all", dest="adj_keep_all", action="store_false",
