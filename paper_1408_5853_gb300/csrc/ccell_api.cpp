@@ -325,9 +325,9 @@ int cut_warp_tasks(cc_ctx* c) {
   return rc;
 }
 
-// Tiles of launch mode 4: as many lines per tile as the consumer half of the
-// block's warps solve at once (halved until two row buffers fit), one launch
-// grid of resident blocks taking equal node shares.
+// Tiles of launch mode 4: as many lines per tile as the block's consumer warps
+// solve at once (halved until two row buffers fit), one launch grid of
+// resident blocks taking equal node shares.
 int cut_pipe_tiles(cc_ctx* c) {
   c->pipe_ok = false;
   const bool mixed = c->precision == CC_MIXED;

@@ -327,9 +327,10 @@ int fp64_lines_resident_blocks(int threads, int smem);
 // [cta_start[b], cta_start[b+1]) of one instance; result in a.Tin.
 int launch_steps_fp64_resident(const StepArgs& a, long long n, void* stream);
 int fp64_resident_kernel_blocks(int threads, int smem);
-// Pipelined CTA tiles, one launch per step (ccell_step_pipe.cu): half of the
-// block's warps assemble the rows of tile k+1 while the other half solve and
-// store tile k; a.tiles / a.cta_start / a.n_cta are the launch's tiles.
+// Pipelined CTA tiles, one launch per step (ccell_step_pipe.cu): the block's
+// first a.pipe_producers warps assemble the rows of tile k+1 while the others
+// solve and store tile k; a.tiles / a.cta_start / a.n_cta are the launch's
+// tiles.
 int launch_step_fp64_pipe(const StepArgs& a, void* stream);
 int launch_step_mixed_pipe(const StepArgs& a, void* stream);
 int fp64_pipe_resident_blocks(int threads, int smem);

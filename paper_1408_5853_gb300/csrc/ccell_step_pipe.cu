@@ -6,9 +6,9 @@
 // assembles rows the FP64 line solves wait and vice versa (in the mixed
 // precision step the rows are FP32 work and the solves FP64 work).  Here the
 // block's warps split into producers and consumers (a split chosen by the
-// host from the phases' work: the FP64 rows cost about twice the FP64
-// solves, the FP32 rows of the mixed step about as much as its FP64 solves)
-// with two row buffers:
+// host and measured: three producers per consumer for the FP64 rows, which
+// cost about twice the FP64 solves; 9 of 16 warps for the mixed step, whose
+// FP32 rows cost about as much as its FP64 solves) with two row buffers:
 // producers assemble tile k+1 into one buffer while consumers solve and store
 // tile k from the other.  Buffers change hands through named barriers: a
 // "full" barrier per buffer (producers arrive, consumers wait) and an "empty"
