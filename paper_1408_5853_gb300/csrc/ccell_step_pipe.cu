@@ -14,7 +14,11 @@
 // "full" barrier per buffer (producers arrive, consumers wait) and an "empty"
 // barrier per buffer (consumers arrive, producers wait).  The axial fluxes
 // handed from tile to tile stay with the producers.  A tile holds as many
-// lines as the consumer warps solve at once.  The mixed-precision rows are
+// lines as the consumer warps solve at once.  The block's first tile, which
+// the consumers would otherwise wait for with nothing to do, is assembled by
+// all warps of the block together (one block barrier), so the pipeline fills
+// in a fraction of the time of one tile; likewise the stores of its last
+// tile, for which the producers would otherwise wait idle.  The mixed-precision rows are
 // kept as packed FP32 (a, c, d) per node -- the values the FP32 assembly
 // produces, widened exactly by the consumers -- and the consumers hold the
 // eliminated FP64 coefficients in registers, which leaves room in shared
@@ -30,9 +34,9 @@ constexpr int kBarProd = 1, kBarCons = 2, kBarFull = 3, kBarEmpty = 5;
 
 // Producer / consumer loops over the block's tiles; Buf(k) gives the row
 // buffers of the k-th tile of the block, Produce / Consume run its phases.
-template <bool ENERGY, bool TRACE, class Produce, class Consume>
+template <bool ENERGY, bool TRACE, class Produce, class Solve, class Finish>
 __device__ __forceinline__ void pipe_tiles(const StepArgs& a, EAcc& acc, Produce produce,
-                                           Consume consume) {
+                                           Solve solve, Finish finish) {
   const int nw = blockDim.x >> 5, P = a.pipe_producers, C = nw - P, NT = blockDim.x;
   const bool producer = (int)(threadIdx.x >> 5) < P;
   const WarpGroup grp = producer ? WarpGroup{0, P, kBarProd} : WarpGroup{P, C, kBarCons};
@@ -47,13 +51,22 @@ __device__ __forceinline__ void pipe_tiles(const StepArgs& a, EAcc& acc, Produce
         eacc_flush<ENERGY, TRACE>(a, acc);
         acc.inst = tk.inst;
       }
-      produce(tk, k & 1, tk.inst == prev_inst && tk.j0 == prev_end, par, grp, acc);
-      named_arrive(kBarFull + (k & 1), NT);
+      if (k == 0) {  // the block's first tile with the consumer warps, which have nothing to solve yet
+        produce(tk, 0, false, par, whole_block(), acc);
+        __syncthreads();
+      } else {
+        produce(tk, k & 1, tk.inst == prev_inst && tk.j0 == prev_end, par, grp, acc);
+        named_arrive(kBarFull + (k & 1), NT);
+      }
       prev_inst = tk.inst;
       prev_end = tk.j0 + tk.nl;
       par ^= 1;
     }
-    for (int k = n > 2 ? n - 2 : 0; k < n; ++k) named_sync(kBarEmpty + (k & 1), NT);
+    if (n >= 2) named_sync(kBarEmpty + (n & 1), NT);  // consumers are done with tile n-2
+    if (n >= 1) {  // the last tile's stores with the consumer warps, once they have solved it
+      __syncthreads();
+      finish(a.tiles[t1 - 1], (n - 1) & 1, whole_block(), acc);
+    }
   } else {
     for (int k = 0; k < n; ++k) {
       const TileTask tk = a.tiles[t0 + k];
@@ -61,9 +74,21 @@ __device__ __forceinline__ void pipe_tiles(const StepArgs& a, EAcc& acc, Produce
         eacc_flush<ENERGY, TRACE>(a, acc);
         acc.inst = tk.inst;
       }
-      named_sync(kBarFull + (k & 1), NT);
-      consume(tk, k & 1, grp, acc);
-      named_arrive(kBarEmpty + (k & 1), NT);
+      if (k == 0) {
+        produce(tk, 0, false, 0, whole_block(), acc);
+        __syncthreads();
+      } else {
+        named_sync(kBarFull + (k & 1), NT);
+      }
+      solve(tk, k & 1, grp);
+      if (k == n - 1) {  // the last tile's stores with the producer warps, which are done
+        __syncthreads();
+        finish(tk, k & 1, whole_block(), acc);
+      } else {
+        grp.sync();  // the stores read every consumer warp's solutions
+        finish(tk, k & 1, grp, acc);
+        named_arrive(kBarEmpty + (k & 1), NT);
+      }
     }
   }
 }
@@ -91,12 +116,15 @@ __global__ void __launch_bounds__(384, 1) step_fp64_pipe_kernel(const StepArgs a
           fp64_produce<ENERGY, false>(a, tk, tile(tk, b), sm + (size_t)(par ^ 1) * nrp,
                                       sm + (size_t)par * nrp, carry, grp, ac, fld);
       },
+      [&](const TileTask& tk, int b, const WarpGroup& grp) {
+        const DevInst& I = a.insts[tk.inst];
+        const Fp64Tile B = tile(tk, b);
+        solve_tile_lines<true>(B.SA, B.SB, B.SC, B.SD, tk.nl, I.nr, I.G, grp.warp());
+      },
       [&](const TileTask& tk, int b, const WarpGroup& grp, EAcc& ac) {
         const DevInst& I = a.insts[tk.inst];
         const Fp64Tile B = tile(tk, b);
         const GlobalField<true> fld(a, I);
-        solve_tile_lines<true>(B.SA, B.SB, B.SC, B.SD, tk.nl, I.nr, I.G, grp.warp());
-        grp.sync();  // the stores read every consumer warp's solutions
         if (tk.j0 + tk.nl >= I.j_narrow)
           fp64_finish<ENERGY, TRACE, true>(a, tk, B, grp, ac, fld);
         else
@@ -130,11 +158,13 @@ __global__ void __launch_bounds__(MAXT, 1) step_mixed_pipe_kernel(const StepArgs
           mixed_produce<ENERGY, true, false, true>(a, tk, tile(tk, b), smf + (size_t)(par ^ 1) * nrp,
                                                    smf + (size_t)par * nrp, carry, grp, ac);
       },
+      [&](const TileTask& tk, int b, const WarpGroup& grp) {
+        const DevInst& I = a.insts[tk.inst];
+        solve_mixed_packed(tile(tk, b).Q, tk.nl, I.nr, I.G, grp.warp());
+      },
       [&](const TileTask& tk, int b, const WarpGroup& grp, EAcc& ac) {
         const DevInst& I = a.insts[tk.inst];
         const MixTile B = tile(tk, b);
-        solve_mixed_packed(B.Q, tk.nl, I.nr, I.G, grp.warp());
-        grp.sync();  // the stores read every consumer warp's solutions
         if (tk.j0 + tk.nl >= I.j_narrow)
           mixed_finish<ENERGY, TRACE, true, true, true>(a, tk, B, grp, ac);
         else
