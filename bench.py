@@ -40,7 +40,7 @@ FLOPS_PER_NODE_FP64 = 150     # FP64 operations per node-update (2 power laws ~ 
 # on the 512x4096 workload, from the ncu capture summarised in
 # profiles/step_fp64_pipe_kernel_512x4096.md (cache flushed before the launch).  Valid only for
 # the kernel as captured there: reset to None when the kernel changes.
-STEP_FP64_TRAFFIC_512x4096 = None
+STEP_FP64_TRAFFIC_512x4096 = 17.355e6
 FP64_PEAK_NOMINAL_TFLOPS = 152 * 4 * 0.5 * 2 * 2.07e9 / 1e12   # SMs x SMSPs x DFMA lanes/clk x 2 x max clock
 # Per launch mode of the FP64 headline: the dominant kernel, the FP64-pipe thread-instructions it
 # executes per node-update on the 512x4096 workload (ncu sm__thread_inst_executed_pipe_fp64_pred_on
@@ -51,7 +51,7 @@ EXECUTED_FP64 = {
     1: ("steps_fp64_persistent_kernel", None, None),
     2: ("step_fp64_lines_kernel", None, None),
     3: ("steps_fp64_resident_kernel", None, None),
-    4: ("step_fp64_pipe_kernel", None, None),
+    4: ("step_fp64_pipe_kernel", 57.6, "profiles/step_fp64_pipe_kernel_512x4096.md"),
 }
 L2_FLUSH_BYTES = 256 << 20
 
