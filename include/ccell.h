@@ -250,8 +250,12 @@ int cc_step_adi_n(cc_ctx* ctx, void* T_dev, int64_t n_steps, double t0_s, double
  *   CC_MIXED) assemble the rows of the next tile while the consumer warps
  *   solve and store the current one, two row buffers changing hands through
  *   named barriers (every context).
- *   threads: 64, 128 or 256 per block; 384 with mode 4 only; 512 with mode
- *   4 in CC_MIXED contexts only.
+ *   mode 5 (CC_MIXED contexts only): mode 4 with the stores, trace and
+ *   energy sums of every tile done by the producer warps, so the consumers
+ *   only solve; faster when the line solves dominate (long lines, e.g.
+ *   512 x 4096), slower when the rows do (short lines of a ragged batch).
+ *   threads: 64, 128 or 256 per block; 384 with modes 4 and 5 only; 512
+ *   with modes 4 and 5 in CC_MIXED contexts only.
  *   Default (a new context): mode 4 with 128 threads per block for CC_FP64,
  *   512 for CC_MIXED, rows_per_lane 16.
  *   rows_per_lane: 2..16, target rows per lane of the line solve; a line of

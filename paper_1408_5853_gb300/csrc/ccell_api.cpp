@@ -325,18 +325,20 @@ int cut_warp_tasks(cc_ctx* c) {
   return rc;
 }
 
-// Tiles of launch mode 4: as many lines per tile as the block's consumer warps
-// solve at once (halved until two row buffers fit), one launch grid of
-// resident blocks taking equal node shares.
+// Tiles of launch modes 4 and 5: as many lines per tile as the block's
+// consumer warps solve at once (halved until two row buffers fit), one launch
+// grid of resident blocks taking equal node shares.
 int cut_pipe_tiles(cc_ctx* c) {
   c->pipe_ok = false;
   const bool mixed = c->precision == CC_MIXED;
   // producer / consumer warps as measured fastest on GB300: for the mixed
-  // step about half producers (9 of 16 warps at 512 threads), for the FP64
+  // step about half producers (9 of 16 warps at 512 threads; with the stores
+  // also on the producers, mode 5, 7/16 of the warps consume), for the FP64
   // step three quarters producers (at least one of each)
   const int warps = c->threads / 32;
-  const int prod =
-      std::max(1, std::min(warps - 1, mixed ? warps / 2 + warps / 16 : (3 * warps) / 4));
+  const int prod = std::max(
+      1, std::min(warps - 1, !mixed ? (3 * warps) / 4
+                             : c->mode == 5 ? warps - (7 * warps) / 16 : warps / 2 + warps / 16));
   const int cons = warps - prod;
   const int elem = mixed ? (int)sizeof(float) : (int)sizeof(double);
   std::vector<int> lpcs(c->inst.size());
@@ -557,7 +559,7 @@ int upload(cc_ctx* c, const std::vector<double>& dts, cudaStream_t st) {
       if (rc != CC_OK) return rc;
     }
     c->pipe_ok = false;
-    if (c->mode == 4) {
+    if (c->mode == 4 || c->mode == 5) {
       const int rc = cut_pipe_tiles(c);
       if (rc != CC_OK) return rc;
     }
@@ -606,11 +608,12 @@ int upload(cc_ctx* c, const std::vector<double>& dts, cudaStream_t st) {
 namespace {
 
 // One time step with the per-step kernel of the context's launch mode: the
-// pipelined tiles (mode 4), the warp-owned lines (mode 2) or the CTA tiles
+// pipelined tiles (modes 4 and 5), the warp-owned lines (mode 2) or the CTA tiles
 // (modes 0, 1 and 3, and any mode whose tiles the context could not use).
 int launch_one_step(const cc_ctx* c, const StepArgs& a, void* stream) {
-  if (c->mode == 4 && c->pipe_ok) {
+  if ((c->mode == 4 || c->mode == 5) && c->pipe_ok) {
     StepArgs p = a;
+    p.pipe_stores = c->mode == 5;
     p.tiles = c->d_ptiles;
     p.cta_start = c->d_pcta;
     p.n_cta = c->pipe_blocks;
@@ -951,9 +954,9 @@ int cc_step_adi_n(cc_ctx* c, void* T_dev, int64_t n_steps, double t0, double dt_
 }
 
 int cc_set_launch(cc_ctx* c, int32_t mode, int32_t threads, int32_t rows_per_lane) {
-  if (!c || mode < 0 || mode > 4 ||
-      (threads != 64 && threads != 128 && threads != 256 && !(threads == 384 && mode == 4) &&
-       !(threads == 512 && mode == 4 && c->precision == CC_MIXED)) ||
+  if (!c || mode < 0 || mode > 5 || (mode == 5 && c->precision != CC_MIXED) ||
+      (threads != 64 && threads != 128 && threads != 256 && !(threads == 384 && mode >= 4) &&
+       !(threads == 512 && mode >= 4 && c->precision == CC_MIXED)) ||
       rows_per_lane < 2 || rows_per_lane > kRowsPerLane)
     return CC_EINVAL;
   if (rows_per_lane != c->rows || threads != c->threads || mode != c->mode) c->tasks_dirty = true;
@@ -1001,12 +1004,13 @@ int cc_autotune(cc_ctx* c, void* T_dev, int32_t n_trial, float* best_ms, void* s
   for (auto& in : c->inst) rect &= in.j_narrow == in.d.nz;
   // mode 2: rectangles; mode 3: one FP64 rectangle (others fall back to mode 0)
   std::vector<int> modes = {0, 1, 4};
+  if (c->precision == CC_MIXED) modes.push_back(5);
   if (rect) modes.push_back(2);
   if (rect && c->inst.size() == 1 && c->precision == CC_FP64) modes.push_back(3);
   for (int mode : modes)
     for (int threads : {64, 128, 256, 384, 512})
       for (int rows : rows_opts) {
-        if (threads >= 384 && mode != 4) continue;
+        if (threads >= 384 && mode < 4) continue;
         if (threads == 512 && c->precision != CC_MIXED) continue;
         cc_set_launch(c, mode, threads, rows);
         rc = cc_step_n(c, T_dev, 1, 0.0, 0.0, nullptr, nullptr, stream);  // warm and upload

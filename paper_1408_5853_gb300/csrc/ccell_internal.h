@@ -229,6 +229,7 @@ struct StepArgs {
   // of producer warps (the rest of the block's warps consume)
   int pipe_buf;
   int pipe_producers;
+  int pipe_stores;       // mixed launch mode 5: the producers also store every tile
   // persistent launches: grid barrier state [count, generation], bounded wait
   unsigned* bar;
   unsigned bar_extra;    // extra arrivals expected (nonzero only to test the timeout)

@@ -18,7 +18,8 @@
 // the consumers would otherwise wait for with nothing to do, is assembled by
 // all warps of the block together (one block barrier), so the pipeline fills
 // in a fraction of the time of one tile; likewise the stores of its last
-// tile, for which the producers would otherwise wait idle.  The mixed-precision rows are
+// tile, for which the producers would otherwise wait idle.  The mixed step
+// moves every tile's stores to the producers (pipe_tiles_finish_by_producers).  The mixed-precision rows are
 // kept as packed FP32 (a, c, d) per node -- the values the FP32 assembly
 // produces, widened exactly by the consumers -- and the consumers hold the
 // eliminated FP64 coefficients in registers, which leaves room in shared
@@ -30,7 +31,7 @@
 
 namespace ccell {
 
-constexpr int kBarProd = 1, kBarCons = 2, kBarFull = 3, kBarEmpty = 5;
+constexpr int kBarProd = 1, kBarCons = 2, kBarFull = 3, kBarEmpty = 5, kBarSolved = 5;
 
 // Producer / consumer loops over the block's tiles; Buf(k) gives the row
 // buffers of the k-th tile of the block, Produce / Consume run its phases.
@@ -93,6 +94,70 @@ __device__ __forceinline__ void pipe_tiles(const StepArgs& a, EAcc& acc, Produce
   }
 }
 
+// The same pipeline with the stores moved to the producers: consumers only
+// solve (tile t after "full" t, then "solved" t), producers finish tile t
+// (stores, trace, energy) before assembling tile t+2 into the same buffer.
+// For the mixed step, whose FP32 rows and pair update are cheap next to its
+// FP64 solves, this keeps the solving warps on the FP64 work alone.
+template <bool ENERGY, bool TRACE, class Produce, class Solve, class Finish>
+__device__ __forceinline__ void pipe_tiles_finish_by_producers(const StepArgs& a, EAcc& acc,
+                                                                Produce produce, Solve solve,
+                                                                Finish finish) {
+  const int nw = blockDim.x >> 5, P = a.pipe_producers, C = nw - P, NT = blockDim.x;
+  const bool producer = (int)(threadIdx.x >> 5) < P;
+  const WarpGroup grp = producer ? WarpGroup{0, P, kBarProd} : WarpGroup{P, C, kBarCons};
+  const int t0 = a.cta_start[blockIdx.x], t1 = a.cta_start[blockIdx.x + 1];
+  const int n = t1 - t0;
+  if (n == 0) return;
+  auto use_inst = [&](int inst) {  // the energy and trace sums belong to one instance
+    if (inst != acc.inst) {
+      eacc_flush<ENERGY, TRACE>(a, acc);
+      acc.inst = inst;
+    }
+  };
+  // tile 0 with all warps (the consumers have nothing to solve yet)
+  {
+    const TileTask tk = a.tiles[t0];
+    use_inst(tk.inst);
+    produce(tk, 0, false, 0, whole_block(), acc);
+    __syncthreads();
+  }
+  if (producer) {
+    int prev_inst = a.tiles[t0].inst, prev_end = a.tiles[t0].j0 + a.tiles[t0].nl, par = 1;
+    auto next = [&](int k) {  // assemble tile k into buffer k & 1, hand it to the consumers
+      const TileTask tk = a.tiles[t0 + k];
+      use_inst(tk.inst);
+      produce(tk, k & 1, tk.inst == prev_inst && tk.j0 == prev_end, par, grp, acc);
+      named_arrive(kBarFull + (k & 1), NT);
+      prev_inst = tk.inst;
+      prev_end = tk.j0 + tk.nl;
+      par ^= 1;
+    };
+    if (n >= 2) next(1);
+    for (int t = 0; t < n - 1; ++t) {
+      named_sync(kBarSolved + (t & 1), NT);  // the consumers have solved tile t
+      const TileTask tk = a.tiles[t0 + t];
+      use_inst(tk.inst);
+      finish(tk, t & 1, grp, acc);
+      if (t + 2 < n) {
+        grp.sync();  // every producer is done reading buffer t & 1
+        next(t + 2);
+      }
+    }
+  } else {
+    for (int t = 0; t < n; ++t) {
+      if (t >= 1) named_sync(kBarFull + (t & 1), NT);
+      solve(a.tiles[t0 + t], t & 1, grp);
+      if (t < n - 1) named_arrive(kBarSolved + (t & 1), NT);
+    }
+  }
+  // the last tile's stores with all warps, once it is solved
+  __syncthreads();
+  const TileTask tk = a.tiles[t1 - 1];
+  use_inst(tk.inst);
+  finish(tk, (n - 1) & 1, whole_block(), acc);
+}
+
 template <bool ENERGY, bool TRACE>
 __global__ void __launch_bounds__(384, 1) step_fp64_pipe_kernel(const StepArgs a) {
   extern __shared__ double sm[];
@@ -134,8 +199,10 @@ __global__ void __launch_bounds__(384, 1) step_fp64_pipe_kernel(const StepArgs a
 }
 
 // MAXT: the largest block the variant is compiled for (its register budget:
-// 384 threads leave about 170 registers a thread, 512 threads 128).
-template <bool ENERGY, bool TRACE, int MAXT>
+// 384 threads leave about 170 registers a thread, 512 threads 128).  STORES:
+// the producers store every tile (launch mode 5) instead of the consumers
+// (launch mode 4).
+template <bool ENERGY, bool TRACE, int MAXT, bool STORES>
 __global__ void __launch_bounds__(MAXT, 1) step_mixed_pipe_kernel(const StepArgs a) {
   extern __shared__ float4 smq[];
   float* smf = reinterpret_cast<float*>(smq);
@@ -146,9 +213,8 @@ __global__ void __launch_bounds__(MAXT, 1) step_mixed_pipe_kernel(const StepArgs
     const int nrp = smem_row_stride(a.insts[tk.inst].nr);
     return mix_tile_packed_at(buf0 + (size_t)b * a.pipe_buf, tk.nl, nrp);
   };
-  pipe_tiles<ENERGY, TRACE>(
-      a, acc,
-      [&](const TileTask& tk, int b, bool carry, int par, const WarpGroup& grp, EAcc& ac) {
+  auto produce = [&](const TileTask& tk, int b, bool carry, int par, const WarpGroup& grp,
+                     EAcc& ac) {
         const DevInst& I = a.insts[tk.inst];
         const int nrp = smem_row_stride(I.nr);
         if (tk.j0 + tk.nl >= I.j_narrow)
@@ -157,19 +223,23 @@ __global__ void __launch_bounds__(MAXT, 1) step_mixed_pipe_kernel(const StepArgs
         else
           mixed_produce<ENERGY, true, false, true>(a, tk, tile(tk, b), smf + (size_t)(par ^ 1) * nrp,
                                                    smf + (size_t)par * nrp, carry, grp, ac);
-      },
-      [&](const TileTask& tk, int b, const WarpGroup& grp) {
+      };
+  auto solve = [&](const TileTask& tk, int b, const WarpGroup& grp) {
         const DevInst& I = a.insts[tk.inst];
         solve_mixed_packed(tile(tk, b).Q, tk.nl, I.nr, I.G, grp.warp());
-      },
-      [&](const TileTask& tk, int b, const WarpGroup& grp, EAcc& ac) {
+      };
+  auto finish = [&](const TileTask& tk, int b, const WarpGroup& grp, EAcc& ac) {
         const DevInst& I = a.insts[tk.inst];
         const MixTile B = tile(tk, b);
         if (tk.j0 + tk.nl >= I.j_narrow)
           mixed_finish<ENERGY, TRACE, true, true, true>(a, tk, B, grp, ac);
         else
           mixed_finish<ENERGY, TRACE, true, false, true>(a, tk, B, grp, ac);
-      });
+      };
+  if constexpr (STORES)
+    pipe_tiles_finish_by_producers<ENERGY, TRACE>(a, acc, produce, solve, finish);
+  else
+    pipe_tiles<ENERGY, TRACE>(a, acc, produce, solve, finish);
   eacc_flush<ENERGY, TRACE>(a, acc);
 }
 
@@ -178,20 +248,28 @@ static KernelCache& fp64_pipe_cache() {
   static KernelCache c;
   return c;
 }
-template <bool ENERGY, bool TRACE, int MAXT>
+template <bool ENERGY, bool TRACE, int MAXT, bool STORES>
 static KernelCache& mixed_pipe_cache() {
   static KernelCache c;
   return c;
 }
 
+template <bool ENERGY, bool TRACE, bool STORES>
+static int mixed_variant_resident(int threads, int smem) {
+  if (threads > 384)
+    return cached_resident(mixed_pipe_cache<ENERGY, TRACE, 512, STORES>(),
+                           step_mixed_pipe_kernel<ENERGY, TRACE, 512, STORES>, threads, smem,
+                           kMaxTileSmem);
+  return cached_resident(mixed_pipe_cache<ENERGY, TRACE, 384, STORES>(),
+                         step_mixed_pipe_kernel<ENERGY, TRACE, 384, STORES>, threads, smem,
+                         kMaxTileSmem);
+}
+
 template <bool MIXED, bool ENERGY, bool TRACE>
 static int pipe_variant_resident(int threads, int smem) {
   if constexpr (MIXED) {
-    if (threads > 384)
-      return cached_resident(mixed_pipe_cache<ENERGY, TRACE, 512>(),
-                             step_mixed_pipe_kernel<ENERGY, TRACE, 512>, threads, smem, kMaxTileSmem);
-    return cached_resident(mixed_pipe_cache<ENERGY, TRACE, 384>(),
-                           step_mixed_pipe_kernel<ENERGY, TRACE, 384>, threads, smem, kMaxTileSmem);
+    return min(mixed_variant_resident<ENERGY, TRACE, false>(threads, smem),
+               mixed_variant_resident<ENERGY, TRACE, true>(threads, smem));
   } else {
     return cached_resident(fp64_pipe_cache<ENERGY, TRACE>(), step_fp64_pipe_kernel<ENERGY, TRACE>,
                            threads, smem, kMaxTileSmem);
@@ -212,10 +290,17 @@ template <bool MIXED, bool ENERGY, bool TRACE>
 static int launch_pipe_variant(const StepArgs& a, cudaStream_t st) {
   if (pipe_variant_resident<MIXED, ENERGY, TRACE>(a.threads, a.smem_bytes) < 0) return -1;
   if constexpr (MIXED) {
-    if (a.threads > 384)
-      step_mixed_pipe_kernel<ENERGY, TRACE, 512><<<a.n_cta, a.threads, a.smem_bytes, st>>>(a);
-    else
-      step_mixed_pipe_kernel<ENERGY, TRACE, 384><<<a.n_cta, a.threads, a.smem_bytes, st>>>(a);
+    if (a.threads > 384) {
+      if (a.pipe_stores)
+        step_mixed_pipe_kernel<ENERGY, TRACE, 512, true><<<a.n_cta, a.threads, a.smem_bytes, st>>>(a);
+      else
+        step_mixed_pipe_kernel<ENERGY, TRACE, 512, false><<<a.n_cta, a.threads, a.smem_bytes, st>>>(a);
+    } else {
+      if (a.pipe_stores)
+        step_mixed_pipe_kernel<ENERGY, TRACE, 384, true><<<a.n_cta, a.threads, a.smem_bytes, st>>>(a);
+      else
+        step_mixed_pipe_kernel<ENERGY, TRACE, 384, false><<<a.n_cta, a.threads, a.smem_bytes, st>>>(a);
+    }
   } else
     step_fp64_pipe_kernel<ENERGY, TRACE><<<a.n_cta, a.threads, a.smem_bytes, st>>>(a);
   return 0;

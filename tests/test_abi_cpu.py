@@ -122,18 +122,20 @@ def test_default_launch_shape_per_precision():
             sol.close()
 
 
-def test_mixed_only_512_thread_blocks():
+def test_mixed_only_launch_shapes():
     for precision, ok in ((ccell.FP64, False), (ccell.MIXED, True)):
         sol = ccell.Solver(inputs.small_case(q0=1.0), precision=precision)
         try:
-            if ok:
-                sol.set_launch(4, 512, 16)
-                assert ccell.cc_get_launch(sol.ctx) == (4, 512, 16)
-            else:
+            for shape in ((4, 512, 16), (5, 512, 16), (5, 384, 16), (5, 128, 8)):
+                if ok:
+                    sol.set_launch(*shape)
+                    assert ccell.cc_get_launch(sol.ctx) == shape
+                else:  # launch mode 5 and 512-thread blocks: mixed precision only
+                    with pytest.raises(ccell.CCError):
+                        sol.set_launch(*shape)
+            for bad in ((0, 512, 16), (6, 128, 16), (3, 384, 16)):
                 with pytest.raises(ccell.CCError):
-                    sol.set_launch(4, 512, 16)
-            with pytest.raises(ccell.CCError):
-                sol.set_launch(0, 512, 16)
+                    sol.set_launch(*bad)
         finally:
             sol.close()
 

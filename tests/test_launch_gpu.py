@@ -36,8 +36,13 @@ SHAPES = [(1, 128, 16), (1, 256, 8), (1, 64, 4), (0, 64, 4), (0, 256, 8), (2, 25
           (4, 384, 4)]
 
 
+# launch mode 5 (stores by the producers) is for mixed-precision contexts only
+MIXED_ONLY = [(4, 512, 16), (4, 512, 4), (5, 512, 16), (5, 384, 16), (5, 256, 8), (5, 128, 16),
+              (5, 64, 4)]
+
+
 @pytest.mark.parametrize("shape,precision", [(s, p) for s in SHAPES for p in (0, 1)] +
-                         [((4, 512, 16), 1), ((4, 512, 4), 1)])
+                         [(s, 1) for s in MIXED_ONLY])
 def test_launch_shapes_parity(shape, precision):
     cfgs = inputs.batched_cases(seed=1, n=5)
     T0s = []
@@ -122,21 +127,22 @@ def test_autotune_keeps_field_and_picks_a_valid_shape():
     ms = sol.autotune(T, n_trial=2)
     assert ms > 0.0
     mode, threads, rows = sol.get_launch()
-    assert mode in (0, 1, 2, 4) and threads in (64, 128, 256, 384, 512) and 2 <= rows <= 16
+    assert mode in (0, 1, 2, 4, 5) and threads in (64, 128, 256, 384, 512) and 2 <= rows <= 16
     assert torch.equal(T, keep)
     sol.close()
 
 
-@pytest.mark.parametrize("mode", [0, 1, 2, 3, 4])
-def test_cuda_graph_replay_equals_direct_call(mode):
+@pytest.mark.parametrize("mode,precision", [(0, 0), (1, 0), (2, 0), (3, 0), (4, 0), (4, 1), (5, 1)])
+def test_cuda_graph_replay_equals_direct_call(mode, precision):
     import torch
     from paper_1408_5853_gb300 import ccell
     cfg = inputs.small_case()
     T0 = inputs.initial_field(cfg, "smooth", seed=8)
     n = 25
-    sol = ccell.Solver(cfg)
+    sol = ccell.Solver(cfg, precision=precision)
     sol.set_launch(mode, 128, 16)
-    Ta = torch.tensor(T0.ravel(), dtype=torch.float64, device="cuda")
+    Ta = torch.tensor(T0.ravel(), dtype=torch.float64 if precision == 0 else torch.float32,
+                      device="cuda")
     tra = torch.zeros(2 * n, dtype=torch.float64, device="cuda")
     ena = torch.zeros(5, dtype=torch.float64, device="cuda")
     sol.step(Ta.clone(), n, 0.0, 0.0, tra, ena)   # warm-up: sizes the context's buffers

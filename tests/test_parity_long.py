@@ -93,7 +93,7 @@ def test_production_2000_steps_fp64_full_field(production_2000, launch):
     _check(Tg, trg[0], eg[0], ref, TOL_FP64_K, 1e-9)
 
 
-@pytest.mark.parametrize("launch", ["autotune", (4, 384, 16), (4, 512, 16)])
+@pytest.mark.parametrize("launch", ["autotune", (4, 384, 16), (4, 512, 16), (5, 512, 16)])
 def test_production_2000_steps_mixed_full_field(production_2000, launch):
     cfg, T0, n, t0, ref = production_2000
     (Tg,), trg, eg = run_gpu(cfg, T0, n, t0=t0, precision=MIXED, launch=launch)
