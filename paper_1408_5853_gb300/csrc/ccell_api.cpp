@@ -68,7 +68,7 @@ struct cc_ctx {
   unsigned* d_rflags = nullptr;
   size_t rflags_cap = 0;
   int res_blocks = 0, res_smem = 0, res_offset = 0;
-  // launch mode 4 (pipelined tiles): tiles and blocks of the launch
+  // launch modes 4 and 5 (pipelined tiles): tiles and blocks of the launch
   bool pipe_ok = false;
   TileTask* d_ptiles = nullptr;
   int* d_pcta = nullptr;

@@ -224,7 +224,7 @@ struct StepArgs {
   int res_offset;
   double* xb;
   unsigned* nbr_flags;
-  // pipelined tiles (launch mode 4): elements (FP64: doubles, mixed: floats)
+  // pipelined tiles (launch modes 4 and 5): elements (FP64: doubles, mixed: floats)
   // of one of the two row buffers after the two carry rows, and the number
   // of producer warps (the rest of the block's warps consume)
   int pipe_buf;

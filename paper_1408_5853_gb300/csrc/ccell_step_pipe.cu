@@ -1,4 +1,4 @@
-// Pipelined CTA tiles (launch mode 4), one launch per time step.
+// Pipelined CTA tiles (launch modes 4 and 5), one launch per time step.
 //
 // The tile kernels of modes 0 and 1 run the three phases of a tile -- rows
 // (properties, Eq. (ABC), interface and closure rows), line solves, stores --
